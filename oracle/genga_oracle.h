@@ -1,0 +1,97 @@
+/*
+ * genga_oracle.h -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Plain, slow, FP64 CPU restatement of the hybrid symplectic N-body step of Grimm & Stadel,
+ * "The GENGA Code" (Sect. 2.1-2.3, Sect. 3.2). It exists to check the CUDA path: only the
+ * tests, __graft_entry__.smoke() and the CPU-baseline leg of bench.py may load it. It shares
+ * no code, header, table or helper with the CUDA library.
+ *
+ * Conventions (all arrays are caller-owned):
+ *   n      number of orbiting bodies; the central mass m0 sits at the origin and is not stored.
+ *   x[3n]  heliocentric positions, v[3n] barycentric ("democratic") velocities (Sect. 2.1).
+ *   alive  1 for a live body, 0 for a ghost left by a merger (Sect. 3.2, Collisions).
+ *   pairs  int pairs (i, j) with i < j, stored as pairs[2k], pairs[2k+1], ascending in (i, j).
+ */
+#ifndef GENGA_ORACLE_H
+#define GENGA_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct orc_params {
+  double G;          /* gravitational constant */
+  double m0;         /* central mass */
+  double dt;         /* full time step tau */
+  int order;         /* 2, 4 or 6: Eq. z1 and its Yoshida compositions (Sect. 2.3) */
+  int kmode;         /* 0: K multiplies the Newtonian pair force; 1: exact gradient of H_B */
+  double n1, n2;     /* critical-radius parameters of Eq. rcrit */
+  double pc;         /* precheck factor: candidate if r < pc * rcrit (Sect. 2.2) */
+  double bs_eps;     /* Bulirsch-Stoer relative tolerance */
+  int bs_kmax;       /* deepest extrapolation level (sequence n_k = 2k) */
+  int bs_max_halvings; /* consecutive step halvings before a group is declared failed */
+  int kepler_maxit;  /* Newton iteration cap of the universal Kepler solve */
+  int collisions;    /* 1: perfect merging on contact (Sect. 3.2, Collisions) */
+} orc_params;
+
+/* Status bits returned by orc_step and the phase routines. */
+#define ORC_ST_KEPLER_FALLBACK 1   /* a Kepler solve failed and the body went to BS (not an error) */
+#define ORC_ST_BS_FAILED       2   /* a BS group exceeded its halving cap */
+#define ORC_ST_REUSE_VIOLATION 4   /* a non-candidate pair had K(r; new rcrit) != 1 */
+#define ORC_ST_CAPACITY        8   /* a pair list exceeded its capacity */
+
+void orc_default_params(orc_params *p);
+
+/* ---- Sect. 2.1: changeover function and critical radius ---- */
+double orc_changeover(double r, double rc);          /* K(r) */
+double orc_changeover_dr(double r, double rc);       /* dK/dr */
+double orc_weight_B(double r2, double rc, int kmode); /* factor on G m_j (x_j-x_i)/r^3 in the kick */
+void orc_rcrit(int n, const orc_params *p, double tau_abs, const double *m, const int *alive,
+               const double *x, const double *v, double *rc);
+
+/* ---- Sect. 2.2: operators ---- */
+void orc_accel_B(int n, const orc_params *p, const double *m, const int *alive, const double *x,
+                 const double *rc, double *a);
+int orc_precheck(int n, const orc_params *p, const int *alive, const double *x, const double *rc,
+                 int *pairs, int cap);
+void orc_momentum(int n, const double *m, const int *alive, const double *v, double P[3]);
+void orc_sun_drift(int n, const orc_params *p, const int *alive, double *x, const double P[3],
+                   double h);
+void orc_stumpff(double z, double c[4]);
+int orc_kepler_drift(double mu, double x[3], double v[3], double dt, int maxit, int *iters);
+double orc_hermite_min(const double dx0[3], const double dv0[3], const double dx1[3],
+                       const double dv1[3], double tau);
+int orc_encounters(int n, const int *alive, const double *x0, const double *v0, const double *x1,
+                   const double *v1, const double *rc, const int *cand, int ncand, double tau,
+                   int *pairs, int cap);
+int orc_groups(int n, const int *pairs, int npairs, const int *single, int *group_start,
+               int *members);
+double orc_energy(int n, const orc_params *p, const double *m, const int *alive, const double *x,
+                  const double *v);
+
+/* BS integration of one group over tau from (x, v) in place (Sect. 3.2, Bulirsch-Stoer). The
+ * group's members are idx[0..g-1] (ascending); x, v, m, R, alive, rc are full-system arrays.
+ * With collisions on, merges update m, R, alive, x, v and add to *U. Returns 0 or ORC_ST_BS_FAILED. */
+int orc_bs_group(int n, const orc_params *p, int g, const int *idx, double tau, double *m,
+                 double *R, int *alive, double *x, double *v, const double *rc, double *U,
+                 int *ncoll, int *coll_pairs, int coll_cap, int *bs_steps);
+
+/* ---- whole simulation (main mode) ---- */
+typedef struct orc_sim orc_sim;
+orc_sim *orc_create(int n, const orc_params *p, const double *m, const double *R, const double *xh,
+                    const double *vh);
+void orc_free(orc_sim *s);
+int orc_step(orc_sim *s, int nsteps);
+void orc_get_state(const orc_sim *s, double *xh, double *vh, double *m, double *R, int *alive);
+void orc_get_internal(const orc_sim *s, double *x, double *v, double *a, double *rc);
+double orc_get_energy(const orc_sim *s, double *U);
+int orc_get_candidates(const orc_sim *s, int *pairs, int cap);
+int orc_get_encounters(const orc_sim *s, int substep, int *pairs, int cap);
+int orc_get_groups(const orc_sim *s, int substep, int *group_start, int *members, int cap);
+void orc_get_stats(const orc_sim *s, long long *stats, int nstats);
+int orc_get_collisions(const orc_sim *s, int *pairs, int cap);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
