@@ -1,0 +1,178 @@
+/*
+ * genga.h -- C ABI of the GB300 (sm_103a) FP64 implementation of the hybrid symplectic N-body
+ * step of Grimm & Stadel, "The GENGA Code" (arXiv:1404.2324).
+ *
+ * The library integrates N bodies around a central mass m0 with the splitting H = H_A + H_B + H_C
+ * in democratic coordinates (Sect. 2.1, Eqs. Ha, Hb, Hc): a kick weighted by the changeover
+ * function K(r_ij) (Eq. Hb) with the prechecker, the Sun drift (Eq. Hc), the Kepler drift with
+ * Gauss' f and g functions (Eq. fg) in universal variables, the close-encounter search with the
+ * cubic Hermite interpolant (Eqs. teqn, polydelta), encounter grouping (Appendix), and
+ * Bulirsch-Stoer integration of the groups with perfect merging (Sect. 3.2), composed to 2nd order
+ * (Eq. z1) or Yoshida's 4th/6th order (Sect. 2.3).
+ *
+ * Conventions
+ *   - All floating point is IEEE binary64 (double).
+ *   - Bodies: index 0 of every host array passed to genga_init / genga_get_state is the central
+ *     mass (its position and velocity are ignored on input and returned as zero); bodies 1..n-1
+ *     orbit it. Positions are heliocentric, velocities heliocentric on input and output (the
+ *     library converts to barycentric "democratic" velocities internally, Sect. 2.1).
+ *   - Host arrays are AoS row-major: x[3*i + c]. The caller owns every host buffer it passes; the
+ *     context owns all device memory it allocates and frees it in genga_free.
+ *   - "Phase" entry points (genga_phase_*) take DEVICE pointers in SoA layout (component-major:
+ *     x[c*n + i]) and a cudaStream_t passed as void*; they exist so that each step of the method can
+ *     be checked on its own. They allocate their own temporary device memory.
+ *   - Return codes: 0 success; negative = invalid argument or CUDA failure, detected on the host
+ *     before anything is launched (or reported by the CUDA runtime); positive = numerical status
+ *     raised by the kernels (see GENGA_ST_*), read back by genga_status / genga_sync. Kernels
+ *     never trap: every device loop is bounded and reports through the status word.
+ */
+#ifndef GENGA_H
+#define GENGA_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error and status codes ---- */
+#define GENGA_OK 0
+#define GENGA_EINVAL (-1)      /* bad argument (NULL, n out of range, dt = 0, order not 2/4/6, NaN) */
+#define GENGA_ECUDA (-2)       /* a CUDA runtime call failed */
+#define GENGA_ENOMEM (-3)      /* device allocation failed */
+#define GENGA_ECAP (-4)        /* output capacity too small */
+
+/* status bits accumulated on the device (genga_status); none of them stops the integration */
+#define GENGA_ST_KEPLER_FALLBACK 1   /* a Kepler solve did not converge; that body went to BS */
+#define GENGA_ST_BS_FAILED 2         /* a BS group exceeded its step-halving cap (state kept) */
+#define GENGA_ST_REUSE_FULLKICK 4    /* rcrit grew past pc*rcrit_old: the opening kick was recomputed */
+#define GENGA_ST_GROUP_TOO_LARGE 8   /* an encounter group exceeded the in-kernel size cap */
+#define GENGA_ST_UNION_ROUNDS 16     /* grouping did not reach its fixpoint within its round cap */
+
+/* modes of genga_init (Sect. 3): main mode with up to 2048 massive bodies */
+#define GENGA_MODE_MASSIVE 0
+
+typedef struct genga_ctx genga_ctx;
+
+/* Method parameters (Sect. 2.1 Eq. rcrit, Sect. 2.2 prechecker, Sect. 3.2 BS). */
+typedef struct genga_params {
+  double n1;            /* Hill-radius factor of Eq. rcrit (paper default 3) */
+  double n2;            /* velocity factor of Eq. rcrit (paper default 0.4) */
+  double pc;            /* precheck factor: candidate if r < pc * rcrit (paper: 3) */
+  double bs_eps;        /* BS relative tolerance (1e-12) */
+  int bs_kmax;          /* deepest BS extrapolation level, sequence n_k = 2k (8, at most 8) */
+  int bs_max_halvings;  /* consecutive BS step halvings before a group is declared failed (30) */
+  int kepler_maxit;     /* iteration cap of the universal Kepler solve (30) */
+  int kmode;            /* 0: K multiplies the Newtonian pair force; 1: exact gradient of H_B */
+  int collisions;       /* 1: perfect merging on contact (Sect. 3.2, Collisions) */
+  int precise_div;      /* 1: kick uses IEEE sqrt and division; 0: refined reciprocal square root */
+} genga_params;
+
+/* Fills *p with the paper's defaults (n1 = 3, n2 = 0.4, pc = 3) and the library's BS/Kepler caps. */
+int genga_default_params(genga_params *p);
+
+/* Creates a context on the current CUDA device and uploads the initial state (Sect. 3, main mode).
+ *   n        bodies including the central mass at index 0; 2 <= n <= 2049 (2048 orbiting bodies)
+ *   masses   [n] masses (masses[0] = m0 > 0; orbiting masses >= 0)
+ *   radii    [n] physical radii used for collisions (radii[0] ignored)
+ *   x, v     [3n] heliocentric positions and velocities (row 0 ignored)
+ *   G        gravitational constant; dt the step tau (sign gives the direction of time)
+ *   order    2 (Eq. z1), 4 or 6 (Yoshida compositions, Sect. 2.3); mode GENGA_MODE_MASSIVE
+ * The first kick's accelerations and precheck candidates are computed here (Sect. 2.2). The host
+ * buffers are not retained. Returns 0 or a negative code; *ctx is NULL on failure. */
+int genga_init(genga_ctx **ctx, int n, const double *masses, const double *radii, const double *x,
+               const double *v, double G, double dt, int order, int mode);
+
+/* Replaces the method parameters; the next genga_step recomputes the first kick. */
+int genga_set_params(genga_ctx *ctx, const genga_params *p);
+
+/* Makes the context launch on the given cudaStream_t (NULL: the context's own stream). */
+int genga_set_stream(genga_ctx *ctx, void *stream);
+
+/* Enqueues n_steps full steps on the context's stream and returns without waiting. All branching
+ * (kick reuse, encounters, groups, BS, mergers) is decided on the device. */
+int genga_step(genga_ctx *ctx, int n_steps);
+
+/* Waits for the context's stream; returns 0, a negative CUDA code, or the status bits. */
+int genga_sync(genga_ctx *ctx);
+
+/* Replaces positions and velocities (heliocentric, host, [3n] with row 0 ignored) of all bodies;
+ * masses and radii stay. The next step recomputes the first kick, as after genga_init. */
+int genga_set_state(genga_ctx *ctx, const double *x, const double *v);
+
+/* Copies the state back (waits for the stream). Any pointer may be NULL. x, v [3n] heliocentric;
+ * m, R [n]; alive [n] (1 live, 0 ghost left by a merger; the central mass counts as live). */
+int genga_get_state(genga_ctx *ctx, double *x, double *v, double *m, double *R, int *alive);
+
+/* Total energy E of the live bodies in democratic coordinates (Sect. 4.1) and the internal
+ * energy U booked by mergers (Sect. 3.2); E + U is the conserved quantity. Waits for the stream. */
+int genga_energy(genga_ctx *ctx, double *E, double *U);
+
+/* Confirmed close-encounter pairs (i < j, body indices with the central mass at 0, ascending) found
+ * in a substep of the last step (substep -1: the last substep). *n_pairs receives the count;
+ * returns GENGA_ECAP if cap < count (the first cap pairs are written). */
+int genga_encounters(genga_ctx *ctx, int substep, int *pairs, int cap, int *n_pairs);
+
+/* Device status word: bits GENGA_ST_*; *detail receives counters (may be NULL): detail[0] steps,
+ * [1] candidates, [2] encounters, [3] groups, [4] BS steps, [5] Kepler fallbacks, [6] mergers,
+ * [7] full-kick recomputes (8 entries). Waits for the stream. */
+int genga_status(genga_ctx *ctx, int *code, long long *detail);
+
+/* Frees the context and every device buffer it owns. */
+void genga_free(genga_ctx *ctx);
+
+/* ------------------------------------------------------------------------------------------ */
+/* Phase entry points: one step of the method on caller-provided device arrays (SoA layout).     */
+/* n counts orbiting bodies only (no central mass); 1 <= n <= 2048. alive: int [n] (0 = ghost).  */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Eq. rcrit: rc[i] = max(n1 a_i (m_i/(3 m0))^(1/3), n2 |tau| |v_i|), a_i from the democratic
+ * state (1/a = 2/|x| - |v|^2/(G m0); |x| if unbound). x, v [3n]; m, rc [n]. */
+int genga_phase_rcrit(int n, double G, double m0, double n1, double n2, double tau_abs,
+                      const double *m, const int *alive, const double *x, const double *v,
+                      double *rc, void *stream);
+
+/* Eq. Hb kick accelerations a[3n] = sum_j G m_j W(r_ij) (x_j - x_i)/r_ij^3 over live j != i with
+ * W = K (kmode 0) or K - rK' (kmode 1) and pair radius max(rc_i, rc_j), plus the prechecker
+ * (Sect. 2.2): pairs (i < j) with r_ij^2 < max((pc rc_i)^2, (pc rc_j)^2), written ascending to
+ * cand[2*cap] (device) with the count in *ncand (host). Returns GENGA_ECAP if cap is too small. */
+int genga_phase_kick(int n, double G, double pc, int kmode, int precise_div, const double *m,
+                     const int *alive, const double *x, const double *rc, double *a, int *cand,
+                     int cap, int *ncand, void *stream);
+
+/* Eq. fg Kepler drift of every live body about mu for dt, in place on x, v [3n]; fail[n] (device)
+ * receives 1 where the solve did not converge within maxit (state untouched there). */
+int genga_phase_kepler(int n, double mu, double dt, int maxit, const int *alive, double *x,
+                       double *v, int *fail, void *stream);
+
+/* Eqs. teqn/polydelta: candidates cand[2*ncand] (device, i < j) whose Hermite minimum separation
+ * over the drift from (x0, v0) to (x1, v1) of length tau is below max(rc_i, rc_j); out[2*cap]
+ * (device) receives them ascending, *nout (host) the count. Bit-exact with the CPU oracle. */
+int genga_phase_encounters(int n, const int *alive, const double *x0, const double *v0,
+                           const double *x1, const double *v1, const double *rc, const int *cand,
+                           int ncand, double tau, int *out, int cap, int *nout, void *stream);
+
+/* Appendix: connected components of the pair graph pairs[2*npairs] (device) plus the bodies with
+ * single[i] != 0 as groups of their own. group_start[n+1] and members[n] (device) receive the
+ * groups ordered by smallest member, members ascending; *ngroups (host) the count. */
+int genga_phase_groups(int n, const int *pairs, int npairs, const int *single, int *group_start,
+                       int *members, int *ngroups, void *stream);
+
+/* Sect. 3.2: Bulirsch-Stoer integration of H_A for each group (group_start/members as produced by
+ * genga_phase_groups, device) over tau, in place on x, v [3n]; with collisions on, mergers update
+ * m, R, alive and add their internal energy to *U (host). Returns 0 or positive status bits. */
+int genga_phase_bs(int n, double G, double m0, double tau, double bs_eps, int bs_kmax,
+                   int bs_max_halvings, int kmode, int collisions, int ngroups,
+                   const int *group_start, const int *members, const double *rc, double *m,
+                   double *R, int *alive, double *x, double *v, double *U, void *stream);
+
+/* Energy of the live bodies in democratic coordinates (x heliocentric, v barycentric), (Sect. 4.1). */
+int genga_phase_energy(int n, double G, double m0, const double *m, const int *alive,
+                       const double *x, const double *v, double *E, void *stream);
+
+/* Self-test of the device arithmetic helpers: out[i] = f(in[i]) for which = 0: x^(-1/2),
+ * 1: x^(-3/2), 2: 1/x (the refined estimates used by the kernels). Device arrays. */
+int genga_phase_mathcheck(int n, int which, const double *in, double *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,585 @@
+// api.cu -- the C ABI (include/genga.h): context, device memory, the host step driver (one full
+// step captured once into a CUDA graph and replayed; every branch is decided on the device),
+// state I/O and the phase entry points.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/genga.h"
+#include "genga_launch.h"
+
+using namespace genga;
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return GENGA_ECUDA;     \
+  } while (0)
+
+namespace {
+
+struct DevMem {
+  std::vector<void *> ptrs;
+  cudaError_t err = cudaSuccess;
+  template <class T>
+  T *get(size_t count) {
+    void *p = nullptr;
+    if (err == cudaSuccess) err = cudaMalloc(&p, (count ? count : 1) * sizeof(T));
+    if (err == cudaSuccess) { ptrs.push_back(p); cudaMemset(p, 0, (count ? count : 1) * sizeof(T)); }
+    return (T *)p;
+  }
+  void release() {
+    for (void *p : ptrs) cudaFree(p);
+    ptrs.clear();
+  }
+};
+
+int num_sms() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
+// Allocates a Sim for n orbiting bodies with room for nsub encounter bitmaps.
+bool alloc_sim(Sim &S, DevMem &mem, int n, int nsub) {
+  memset(&S, 0, sizeof(S));
+  S.n = n;
+  S.npad = ((n + 31) / 32) * 32;
+  if (S.npad < 32) S.npad = 32;
+  S.nt = S.npad / 32;
+  S.W = S.npad / 32;
+  const size_t np = S.npad, nt = S.nt, W = S.W;
+  S.x = mem.get<double>(3 * np); S.v = mem.get<double>(3 * np);
+  S.x0 = mem.get<double>(3 * np); S.v0 = mem.get<double>(3 * np);
+  S.m = mem.get<double>(np); S.gm = mem.get<double>(np); S.R = mem.get<double>(np); S.hill = mem.get<double>(np);
+  S.alive = mem.get<int>(np);
+  S.rc = mem.get<double>(np); S.A = mem.get<double>(np);
+  S.T = mem.get<u64>(np); S.rcsq = mem.get<u64>(np);
+  S.afar = mem.get<double>(3 * np);
+  S.part = mem.get<double>(nt * nt * 2 * 96);
+  S.pkick = mem.get<double>(nt * 3); S.pfin = mem.get<double>(nt * 3);
+  S.cbm = mem.get<unsigned>(np * W); S.rowany = mem.get<unsigned>(W);
+  S.ebm = mem.get<unsigned>((size_t)nsub * np * W);
+  const size_t ecap = np * (np - 1) / 2 + 1;
+  S.edges = mem.get<int>(2 * ecap); S.nedges = mem.get<int>(1);
+  S.fail = mem.get<int>(np); S.nfail = mem.get<int>(1);
+  S.gstart = mem.get<int>(np + 1); S.gmem = mem.get<int>(np); S.ngroups = mem.get<int>(1);
+  // kick work list: for each tile I, the diagonal tile, then both halves of every J > I
+  std::vector<int> items;
+  for (int I = 0; I < S.nt; ++I) {
+    items.push_back(I | (I << 10));
+    for (int J = I + 1; J < S.nt; ++J) {
+      items.push_back(I | (J << 10));
+      items.push_back(I | (J << 10) | (1 << 20));
+    }
+  }
+  S.nitems = (int)items.size();
+  S.items = mem.get<int>(items.size());
+  const int target = 4 * num_sms();  // one warp per sub-partition
+  S.nwarps = S.nitems < target ? S.nitems : target;
+  S.flags = mem.get<int>(4); S.status = mem.get<int>(1);
+  S.counters = mem.get<long long>(NCOUNTERS); S.U = mem.get<double>(1);
+  if (mem.err != cudaSuccess) return false;
+  cudaMemcpy(S.items, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice);
+  return cudaGetLastError() == cudaSuccess;
+}
+
+DevParams make_params(double G, double m0, const genga_params &p) {
+  DevParams P;
+  memset(&P, 0, sizeof(P));
+  P.G = G; P.m0 = m0; P.Gm0 = G * m0; P.inv_m0 = 1.0 / m0;
+  P.mu2 = 2.0 * G * m0; P.inv_mu = 1.0 / (G * m0);
+  P.n1 = p.n1; P.n2 = p.n2; P.pc = p.pc; P.bs_eps = p.bs_eps;
+  P.bs_kmax = p.bs_kmax; P.bs_max_halvings = p.bs_max_halvings; P.kepler_maxit = p.kepler_maxit;
+  P.kmode = p.kmode; P.collisions = p.collisions;
+  return P;
+}
+
+int substep_weights(int order, double *w) {
+  if (order == 4) {  // Yoshida (1990): w1 = 1/(2 - 2^(1/3)), w0 = -2^(1/3)/(2 - 2^(1/3))
+    const double c = cbrt(2.0);
+    w[0] = w[2] = 1.0 / (2.0 - c);
+    w[1] = -c / (2.0 - c);
+    return 3;
+  }
+  if (order == 6) {  // Yoshida (1990) Table 1, solution A
+    const double w1 = -1.17767998417887, w2 = 0.235573213359357, w3 = 0.784513610477560;
+    const double w0 = 1.0 - 2.0 * (w1 + w2 + w3);
+    const double s[7] = {w3, w2, w1, w0, w1, w2, w3};
+    for (int k = 0; k < 7; ++k) w[k] = s[k];
+    return 7;
+  }
+  w[0] = 1.0;
+  return 1;
+}
+
+bool finite_all(const double *a, size_t n) {
+  for (size_t k = 0; k < n; ++k)
+    if (!std::isfinite(a[k])) return false;
+  return true;
+}
+
+}  // namespace
+
+struct genga_ctx {
+  int n;  // orbiting bodies
+  double G, m0, dt;
+  int order, nsub;
+  double w[7];
+  genga_params prm;
+  DevParams P;
+  Sim S;
+  DevMem mem;
+  cudaStream_t own = nullptr, stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int bs_grid = 1;
+  // staging
+  double *sx = nullptr, *sv = nullptr, *sm = nullptr, *sR = nullptr, *scratch = nullptr, *sE = nullptr;
+  int *salive = nullptr, *spairs = nullptr, *scount = nullptr;
+  size_t pair_cap = 0;
+};
+
+namespace {
+
+void drop_graph(genga_ctx *c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  c->gexec = nullptr;
+  c->graph = nullptr;
+}
+
+// The first kick (Sect. 2.2): critical radii, far-field accelerations and candidates of the
+// current state, with no velocity change. Also run after set_state / set_params.
+int first_kick(genga_ctx *c) {
+  Sim &S = c->S;
+  cudaStream_t st = c->stream;
+  CK(cudaMemsetAsync(S.cbm, 0, (size_t)S.npad * S.W * sizeof(unsigned), st));
+  CK(cudaMemsetAsync(S.rowany, 0, (size_t)S.W * sizeof(unsigned), st));
+  CK(cudaMemsetAsync(S.flags, 0, 4 * sizeof(int), st));
+  CK(cudaMemsetAsync(S.nedges, 0, sizeof(int), st));
+  CK(cudaMemsetAsync(S.nfail, 0, sizeof(int), st));
+  launch_rcrit(S, c->P, std::fabs(c->dt), 0, st);
+  launch_kick(S, c->P, false, c->prm.precise_div != 0, st);
+  launch_fin(S, c->P, FIN_INIT, 0.0, 0.0, nullptr, st);
+  CK(cudaGetLastError());
+  return GENGA_OK;
+}
+
+// One full step (Sect. 2.2 second list, composed per Sect. 2.3).
+void enqueue_step(genga_ctx *c, cudaStream_t st) {
+  const Sim &S = c->S;
+  const DevParams &P = c->P;
+  const bool precise = c->prm.precise_div != 0;
+  const double dt = c->dt, inv_m0 = 1.0 / c->m0;
+  launch_rcrit(S, P, std::fabs(dt), 1, st);
+  launch_kick(S, P, true, precise, st);  // runs only if the critical radii grew too much
+  launch_fin(S, P, FIN_OPEN, 0.5 * c->w[0] * dt, 0.0, nullptr, st);
+  for (int j = 0; j < c->nsub; ++j) {
+    const double tau = c->w[j] * dt;
+    const double hcm2 = j > 0 ? 0.5 * c->w[j - 1] * dt * inv_m0 : 0.0;
+    launch_drift(S, P, tau, 0.5 * tau * inv_m0, hcm2, j == 0, st);
+    launch_encounter(S, tau, S.ebm + (size_t)j * S.npad * S.W, st);
+    launch_group(S, st);
+    launch_bs(S, P, tau, c->bs_grid, st);
+    launch_kick(S, P, false, precise, st);
+    const double h2 = (j + 1 < c->nsub) ? 0.5 * c->w[j + 1] * dt : 0.0;
+    launch_fin(S, P, FIN_CLOSE, 0.5 * tau, h2, nullptr, st);
+  }
+  launch_hc(S, 0.5 * c->w[c->nsub - 1] * dt * inv_m0, st);
+}
+
+int build_graph(genga_ctx *c) {
+  drop_graph(c);
+  CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  enqueue_step(c, c->stream);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+  if (e != cudaSuccess || !g) return GENGA_ECUDA;
+  c->graph = g;
+  CK(cudaGraphInstantiate(&c->gexec, c->graph, 0));
+  return GENGA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int genga_default_params(genga_params *p) {
+  if (!p) return GENGA_EINVAL;
+  p->n1 = 3.0;
+  p->n2 = 0.4;
+  p->pc = 3.0;
+  p->bs_eps = 1e-12;
+  p->bs_kmax = 8;
+  p->bs_max_halvings = 30;
+  p->kepler_maxit = 30;
+  p->kmode = 0;
+  p->collisions = 1;
+  p->precise_div = 0;
+  return GENGA_OK;
+}
+
+int genga_init(genga_ctx **out, int n, const double *masses, const double *radii, const double *x,
+               const double *v, double G, double dt, int order, int mode) {
+  if (!out) return GENGA_EINVAL;
+  *out = nullptr;
+  if (n < 2 || n > NMAX + 1 || !masses || !radii || !x || !v) return GENGA_EINVAL;
+  if (!(G > 0.0) || !std::isfinite(G) || !std::isfinite(dt) || dt == 0.0) return GENGA_EINVAL;
+  if (order != 2 && order != 4 && order != 6) return GENGA_EINVAL;
+  if (mode != GENGA_MODE_MASSIVE) return GENGA_EINVAL;
+  if (!(masses[0] > 0.0) || !finite_all(masses, n) || !finite_all(radii, n) ||
+      !finite_all(x, 3 * (size_t)n) || !finite_all(v, 3 * (size_t)n))
+    return GENGA_EINVAL;
+  for (int i = 1; i < n; ++i)
+    if (masses[i] < 0.0 || radii[i] < 0.0) return GENGA_EINVAL;
+  genga_ctx *c = new genga_ctx();
+  c->n = n - 1;
+  c->G = G; c->m0 = masses[0]; c->dt = dt; c->order = order;
+  c->nsub = substep_weights(order, c->w);
+  genga_default_params(&c->prm);
+  c->P = make_params(G, c->m0, c->prm);
+  if (cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking) != cudaSuccess) { delete c; return GENGA_ECUDA; }
+  c->stream = c->own;
+  if (!alloc_sim(c->S, c->mem, c->n, c->nsub)) { c->mem.release(); cudaStreamDestroy(c->own); delete c; return GENGA_ENOMEM; }
+  const size_t nn = (size_t)n;
+  c->sx = c->mem.get<double>(3 * nn); c->sv = c->mem.get<double>(3 * nn);
+  c->sm = c->mem.get<double>(nn); c->sR = c->mem.get<double>(nn);
+  c->salive = c->mem.get<int>(nn);
+  c->scratch = c->mem.get<double>((size_t)c->S.nt * c->S.nt); c->sE = c->mem.get<double>(1);
+  c->pair_cap = (size_t)c->S.npad * (c->S.npad - 1) / 2 + 1;
+  c->spairs = c->mem.get<int>(2 * c->pair_cap); c->scount = c->mem.get<int>(1);
+  if (c->mem.err != cudaSuccess) { genga_free(c); return GENGA_ENOMEM; }
+  c->bs_grid = 2 * num_sms();
+  if (c->bs_grid > c->S.npad) c->bs_grid = c->S.npad;
+  bs_init_constants();
+  cudaStream_t st = c->stream;
+  if (cudaMemcpyAsync(c->sx, x, 3 * nn * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(c->sv, v, 3 * nn * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(c->sm, masses, nn * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(c->sR, radii, nn * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess) {
+    genga_free(c);
+    return GENGA_ECUDA;
+  }
+  launch_from_helio(c->S, c->P, c->sx, c->sv, c->sm, c->sR, st);
+  int rc = first_kick(c);
+  if (rc == GENGA_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = GENGA_ECUDA;
+  if (rc != GENGA_OK) { genga_free(c); return rc; }
+  *out = c;
+  return GENGA_OK;
+}
+
+int genga_set_params(genga_ctx *c, const genga_params *p) {
+  if (!c || !p) return GENGA_EINVAL;
+  if (!(p->n1 >= 0.0) || !(p->n2 >= 0.0) || !(p->pc >= 1.0) || !(p->bs_eps > 0.0) || p->bs_kmax < 2 ||
+      p->bs_kmax > BS_LEVELS || p->bs_max_halvings < 0 || p->kepler_maxit < 1 || (p->kmode != 0 && p->kmode != 1))
+    return GENGA_EINVAL;
+  c->prm = *p;
+  c->P = make_params(c->G, c->m0, c->prm);
+  drop_graph(c);
+  return first_kick(c);
+}
+
+int genga_set_stream(genga_ctx *c, void *stream) {
+  if (!c) return GENGA_EINVAL;
+  c->stream = stream ? (cudaStream_t)stream : c->own;
+  drop_graph(c);
+  return GENGA_OK;
+}
+
+int genga_step(genga_ctx *c, int n_steps) {
+  if (!c || n_steps < 0) return GENGA_EINVAL;
+  if (n_steps == 0) return GENGA_OK;
+  if (!c->gexec) {
+    int rc = build_graph(c);
+    if (rc != GENGA_OK) return rc;
+  }
+  for (int k = 0; k < n_steps; ++k) CK(cudaGraphLaunch(c->gexec, c->stream));
+  return GENGA_OK;
+}
+
+int genga_sync(genga_ctx *c) {
+  if (!c) return GENGA_EINVAL;
+  CK(cudaStreamSynchronize(c->stream));
+  int st = 0;
+  CK(cudaMemcpy(&st, c->S.status, sizeof(int), cudaMemcpyDeviceToHost));
+  return st;
+}
+
+int genga_set_state(genga_ctx *c, const double *x, const double *v) {
+  if (!c || !x || !v) return GENGA_EINVAL;
+  const size_t nn = (size_t)c->n + 1;
+  cudaStream_t st = c->stream;
+  CK(cudaMemcpyAsync(c->sx, x, 3 * nn * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(c->sv, v, 3 * nn * sizeof(double), cudaMemcpyHostToDevice, st));
+  // masses, radii and live flags stay as they are on the device
+  launch_from_helio(c->S, c->P, c->sx, c->sv, nullptr, nullptr, st);
+  CK(cudaGetLastError());
+  return first_kick(c);
+}
+
+int genga_get_state(genga_ctx *c, double *x, double *v, double *m, double *R, int *alive) {
+  if (!c) return GENGA_EINVAL;
+  const size_t nn = (size_t)c->n + 1;
+  cudaStream_t st = c->stream;
+  launch_to_helio(c->S, c->P, x ? c->sx : nullptr, v ? c->sv : nullptr, m ? c->sm : nullptr,
+                  R ? c->sR : nullptr, alive ? c->salive : nullptr, st);
+  CK(cudaGetLastError());
+  if (x) CK(cudaMemcpyAsync(x, c->sx, 3 * nn * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (v) CK(cudaMemcpyAsync(v, c->sv, 3 * nn * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (m) CK(cudaMemcpyAsync(m, c->sm, nn * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (R) CK(cudaMemcpyAsync(R, c->sR, nn * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (alive) CK(cudaMemcpyAsync(alive, c->salive, nn * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return GENGA_OK;
+}
+
+int genga_energy(genga_ctx *c, double *E, double *U) {
+  if (!c) return GENGA_EINVAL;
+  cudaStream_t st = c->stream;
+  launch_energy(c->S, c->P, c->scratch, c->sE, st);
+  CK(cudaGetLastError());
+  double e = 0.0, u = 0.0;
+  CK(cudaMemcpyAsync(&e, c->sE, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&u, c->S.U, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (E) *E = e;
+  if (U) *U = u;
+  return GENGA_OK;
+}
+
+int genga_encounters(genga_ctx *c, int substep, int *pairs, int cap, int *n_pairs) {
+  if (!c || cap < 0) return GENGA_EINVAL;
+  if (substep < 0) substep = c->nsub - 1;
+  if (substep >= c->nsub) return GENGA_EINVAL;
+  cudaStream_t st = c->stream;
+  launch_bitmap_pairs(c->S.ebm + (size_t)substep * c->S.npad * c->S.W, c->S.npad, c->S.W, c->spairs,
+                      (int)c->pair_cap, c->scount, st);
+  CK(cudaGetLastError());
+  int cnt = 0;
+  CK(cudaMemcpyAsync(&cnt, c->scount, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (n_pairs) *n_pairs = cnt;
+  const int ncopy = cnt < cap ? cnt : cap;
+  if (pairs && ncopy > 0) {
+    CK(cudaMemcpy(pairs, c->spairs, 2 * (size_t)ncopy * sizeof(int), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < 2 * ncopy; ++k) pairs[k] += 1;  // the central mass is body 0
+  }
+  return cnt > cap ? GENGA_ECAP : GENGA_OK;
+}
+
+int genga_status(genga_ctx *c, int *code, long long *detail) {
+  if (!c) return GENGA_EINVAL;
+  CK(cudaStreamSynchronize(c->stream));
+  int st = 0;
+  CK(cudaMemcpy(&st, c->S.status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (code) *code = st;
+  if (detail) CK(cudaMemcpy(detail, c->S.counters, NCOUNTERS * sizeof(long long), cudaMemcpyDeviceToHost));
+  return GENGA_OK;
+}
+
+void genga_free(genga_ctx *c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  drop_graph(c);
+  c->mem.release();
+  if (c->own) cudaStreamDestroy(c->own);
+  delete c;
+}
+
+// ------------------------------------------------------------------------------------------
+// Phase entry points
+// ------------------------------------------------------------------------------------------
+static int phase_sim(Sim &S, DevMem &mem, int n) {
+  if (n < 1 || n > NMAX) return GENGA_EINVAL;
+  if (!alloc_sim(S, mem, n, 1)) { mem.release(); return GENGA_ENOMEM; }
+  return GENGA_OK;
+}
+
+static int phase_finish(DevMem &mem, cudaStream_t st, int rc) {
+  if (cudaStreamSynchronize(st) != cudaSuccess && rc == GENGA_OK) rc = GENGA_ECUDA;
+  if (cudaGetLastError() != cudaSuccess && rc == GENGA_OK) rc = GENGA_ECUDA;
+  mem.release();
+  return rc;
+}
+
+// copy a [3 n] SoA array into a [3 npad] SoA array (or back)
+static cudaError_t soa_copy(double *dst, size_t dpitch, const double *src, size_t spitch, int n, cudaStream_t st) {
+  return cudaMemcpy2DAsync(dst, dpitch * sizeof(double), src, spitch * sizeof(double), n * sizeof(double), 3,
+                           cudaMemcpyDeviceToDevice, st);
+}
+
+int genga_phase_rcrit(int n, double G, double m0, double n1, double n2, double tau_abs, const double *m,
+                      const int *alive, const double *x, const double *v, double *rc, void *stream) {
+  if (!m || !alive || !x || !v || !rc || !(G > 0.0) || !(m0 > 0.0)) return GENGA_EINVAL;
+  Sim S; DevMem mem;
+  int r = phase_sim(S, mem, n);
+  if (r) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  genga_params prm; genga_default_params(&prm); prm.n1 = n1; prm.n2 = n2;
+  DevParams P = make_params(G, m0, prm);
+  launch_soa_setup(S, P, m, alive, x, v, nullptr, n, st);
+  launch_rcrit(S, P, tau_abs, 0, st);
+  cudaMemcpyAsync(rc, S.rc, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  return phase_finish(mem, st, GENGA_OK);
+}
+
+int genga_phase_kick(int n, double G, double pc, int kmode, int precise_div, const double *m, const int *alive,
+                     const double *x, const double *rc, double *a, int *cand, int cap, int *ncand, void *stream) {
+  if (!m || !alive || !x || !rc || !a || !ncand || cap < 0 || !(G > 0.0) || !(pc >= 1.0)) return GENGA_EINVAL;
+  Sim S; DevMem mem;
+  int r = phase_sim(S, mem, n);
+  if (r) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  genga_params prm; genga_default_params(&prm); prm.pc = pc; prm.kmode = kmode;
+  DevParams P = make_params(G, 1.0, prm);
+  double *aout = mem.get<double>(3 * (size_t)S.npad);
+  int *dcnt = mem.get<int>(1);
+  int *tmp = mem.get<int>(2 * ((size_t)S.npad * (S.npad - 1) / 2 + 1));
+  if (mem.err != cudaSuccess) { mem.release(); return GENGA_ENOMEM; }
+  launch_soa_setup(S, P, m, alive, x, nullptr, rc, n, st);
+  launch_kick(S, P, false, precise_div != 0, st);
+  launch_fin(S, P, FIN_INIT, 0.0, 0.0, aout, st);
+  soa_copy(a, n, aout, S.npad, n, st);
+  launch_bitmap_pairs(S.cbm, S.npad, S.W, tmp, S.npad * (S.npad - 1) / 2 + 1, dcnt, st);
+  int cnt = 0;
+  cudaMemcpyAsync(&cnt, dcnt, sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  *ncand = cnt;
+  const int ncopy = cnt < cap ? cnt : cap;
+  if (cand && ncopy > 0) cudaMemcpyAsync(cand, tmp, 2 * (size_t)ncopy * sizeof(int), cudaMemcpyDeviceToDevice, st);
+  return phase_finish(mem, st, cnt > cap ? GENGA_ECAP : GENGA_OK);
+}
+
+int genga_phase_kepler(int n, double mu, double dt, int maxit, const int *alive, double *x, double *v, int *fail,
+                       void *stream) {
+  if (n < 1 || !alive || !x || !v || !fail || !(mu > 0.0) || maxit < 1) return GENGA_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  launch_kepler_phase(n, mu, dt, maxit, alive, x, v, fail, st);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  return GENGA_OK;
+}
+
+int genga_phase_encounters(int n, const int *alive, const double *x0, const double *v0, const double *x1,
+                           const double *v1, const double *rc, const int *cand, int ncand, double tau, int *out,
+                           int cap, int *nout, void *stream) {
+  if (!alive || !x0 || !v0 || !x1 || !v1 || !rc || (ncand > 0 && !cand) || ncand < 0 || !nout || cap < 0)
+    return GENGA_EINVAL;
+  Sim S; DevMem mem;
+  int r = phase_sim(S, mem, n);
+  if (r) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  genga_params prm; genga_default_params(&prm);
+  DevParams P = make_params(1.0, 1.0, prm);
+  int *dcnt = mem.get<int>(1);
+  int *tmp = mem.get<int>(2 * ((size_t)S.npad * (S.npad - 1) / 2 + 1));
+  if (mem.err != cudaSuccess) { mem.release(); return GENGA_ENOMEM; }
+  launch_soa_setup(S, P, nullptr, alive, x1, v1, rc, n, st);
+  soa_copy(S.x0, S.npad, x0, n, n, st);
+  soa_copy(S.v0, S.npad, v0, n, n, st);
+  launch_pairs_to_bitmap(S, cand, ncand, st);
+  launch_encounter(S, tau, S.ebm, st);
+  launch_bitmap_pairs(S.ebm, S.npad, S.W, tmp, S.npad * (S.npad - 1) / 2 + 1, dcnt, st);
+  int cnt = 0;
+  cudaMemcpyAsync(&cnt, dcnt, sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  *nout = cnt;
+  const int ncopy = cnt < cap ? cnt : cap;
+  if (out && ncopy > 0) cudaMemcpyAsync(out, tmp, 2 * (size_t)ncopy * sizeof(int), cudaMemcpyDeviceToDevice, st);
+  return phase_finish(mem, st, cnt > cap ? GENGA_ECAP : GENGA_OK);
+}
+
+int genga_phase_groups(int n, const int *pairs, int npairs, const int *single, int *group_start, int *members,
+                       int *ngroups, void *stream) {
+  if (npairs < 0 || (npairs > 0 && !pairs) || !group_start || !members || !ngroups) return GENGA_EINVAL;
+  Sim S; DevMem mem;
+  int r = phase_sim(S, mem, n);
+  if (r) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((size_t)npairs > (size_t)S.npad * (S.npad - 1) / 2 + 1) { mem.release(); return GENGA_EINVAL; }
+  launch_copy_edges(S, pairs, npairs, st);
+  if (single) launch_single_to_fail(S, single, st);
+  launch_group(S, st);
+  int ng = 0;
+  cudaMemcpyAsync(&ng, S.ngroups, sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  *ngroups = ng;
+  int nm = 0;
+  cudaMemcpyAsync(&nm, S.gstart + ng, sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  cudaMemcpyAsync(group_start, S.gstart, (ng + 1) * sizeof(int), cudaMemcpyDeviceToDevice, st);
+  if (nm > 0) cudaMemcpyAsync(members, S.gmem, nm * sizeof(int), cudaMemcpyDeviceToDevice, st);
+  return phase_finish(mem, st, GENGA_OK);
+}
+
+int genga_phase_bs(int n, double G, double m0, double tau, double bs_eps, int bs_kmax, int bs_max_halvings,
+                   int kmode, int collisions, int ngroups, const int *group_start, const int *members,
+                   const double *rc, double *m, double *R, int *alive, double *x, double *v, double *U, void *stream) {
+  if (ngroups < 0 || (ngroups > 0 && (!group_start || !members)) || !rc || !m || !R || !alive || !x || !v || !U ||
+      !(G > 0.0) || !(m0 > 0.0) || bs_kmax < 2 || bs_kmax > BS_LEVELS)
+    return GENGA_EINVAL;
+  Sim S; DevMem mem;
+  int r = phase_sim(S, mem, n);
+  if (r) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  genga_params prm; genga_default_params(&prm);
+  prm.bs_eps = bs_eps; prm.bs_kmax = bs_kmax; prm.bs_max_halvings = bs_max_halvings; prm.kmode = kmode;
+  prm.collisions = collisions;
+  DevParams P = make_params(G, m0, prm);
+  bs_init_constants();
+  launch_soa_setup(S, P, m, alive, x, v, rc, n, st);
+  cudaMemcpyAsync(S.R, R, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  soa_copy(S.x0, S.npad, x, n, n, st);
+  soa_copy(S.v0, S.npad, v, n, n, st);
+  cudaMemcpyAsync(S.ngroups, &ngroups, sizeof(int), cudaMemcpyHostToDevice, st);
+  if (ngroups > 0) {
+    int nm = 0;
+    cudaMemcpyAsync(&nm, group_start + ngroups, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    cudaMemcpyAsync(S.gstart, group_start, (ngroups + 1) * sizeof(int), cudaMemcpyDeviceToDevice, st);
+    if (nm > 0) cudaMemcpyAsync(S.gmem, members, nm * sizeof(int), cudaMemcpyDeviceToDevice, st);
+  }
+  launch_bs(S, P, tau, 2 * num_sms(), st);
+  soa_copy(x, n, S.x, S.npad, n, st);
+  soa_copy(v, n, S.v, S.npad, n, st);
+  cudaMemcpyAsync(m, S.m, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(R, S.R, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(alive, S.alive, n * sizeof(int), cudaMemcpyDeviceToDevice, st);
+  int status = 0;
+  cudaMemcpyAsync(U, S.U, sizeof(double), cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(&status, S.status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  int rc2 = phase_finish(mem, st, GENGA_OK);
+  return rc2 != GENGA_OK ? rc2 : status;
+}
+
+int genga_phase_energy(int n, double G, double m0, const double *m, const int *alive, const double *x,
+                       const double *v, double *E, void *stream) {
+  if (!m || !alive || !x || !v || !E || !(G > 0.0) || !(m0 > 0.0)) return GENGA_EINVAL;
+  Sim S; DevMem mem;
+  int r = phase_sim(S, mem, n);
+  if (r) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  genga_params prm; genga_default_params(&prm);
+  DevParams P = make_params(G, m0, prm);
+  double *scratch = mem.get<double>((size_t)S.nt * S.nt), *dE = mem.get<double>(1);
+  if (mem.err != cudaSuccess) { mem.release(); return GENGA_ENOMEM; }
+  launch_soa_setup(S, P, m, alive, x, v, nullptr, n, st);
+  launch_energy(S, P, scratch, dE, st);
+  cudaMemcpyAsync(E, dE, sizeof(double), cudaMemcpyDeviceToHost, st);
+  return phase_finish(mem, st, GENGA_OK);
+}
+
+int genga_phase_mathcheck(int n, int which, const double *in, double *out, void *stream) {
+  if (n < 0 || !in || !out || which < 0 || which > 2) return GENGA_EINVAL;
+  if (n == 0) return GENGA_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  launch_mathcheck(n, which, in, out, st);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  return GENGA_OK;
+}
+
+}  // extern "C"

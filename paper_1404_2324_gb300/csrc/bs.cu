@@ -1,0 +1,275 @@
+// bs.cu -- Bulirsch-Stoer integration of the encounter groups (Sect. 3.2) with perfect merging
+// on contact (Sect. 3.2, Collisions).
+//
+// One CTA per group. The modified-midpoint integrations of all extrapolation levels
+// (n_k = 2k, k = 1..8) run at once: thread (level, member, term) evaluates one term of the
+// member's acceleration (the central mass or one partner), so a step costs the critical path of
+// the deepest level (16 evaluations) instead of the 72 evaluations of the serial scheme. The
+// tableau is then built as a wavefront across levels and the first converged level is accepted,
+// which is exactly the decision of the serial algorithm.
+#include "genga_launch.h"
+
+namespace genga {
+
+// 1/((L/(L-j))^2 - 1) for the Neville extrapolation in h^2 with n_k = 2k
+__constant__ double c_facinv[BS_LEVELS + 1][BS_LEVELS];
+
+struct BsShared {
+  int idx[BS_GMAX], alive[BS_GMAX];
+  double gm[BS_GMAX], m[BS_GMAX], R[BS_GMAX], A[BS_GMAX];
+  u64 rcsq[BS_GMAX];
+  double y[BS_GMAX][6], yn[BS_GMAX][6];
+  double pos[2][BS_LEVELS][BS_GMAX][3];
+  double tab[BS_LEVELS][BS_GMAX][6];
+  u64 err[BS_LEVELS];
+  unsigned char cont[BS_GMAX * (BS_GMAX - 1) / 2];
+  double H, rem, U;
+  int accept;
+};
+
+// Acceleration terms of member q assigned to this thread: term p == q is the central mass, any
+// other p the (1 - K)-weighted pull of partner p (H_A, Eq. Ha). Summed over the slot's threads.
+__device__ __forceinline__ void bs_terms(const BsShared &sh, const DevParams &P, int g, int q, int sub, int tps,
+                                         const double (*pos)[3], bool q_alive, double &ax, double &ay, double &az) {
+  ax = ay = az = 0.0;
+  const double xq = pos[q][0], yq = pos[q][1], zq = pos[q][2];
+  if (q_alive) {
+    for (int p = sub; p < g; p += tps) {
+      if (p == q) {
+        const double r2 = fma(zq, zq, fma(yq, yq, xq * xq));
+        const double f = -P.Gm0 * rcube_refined(r2);
+        ax = fma(f, xq, ax); ay = fma(f, yq, ay); az = fma(f, zq, az);
+      } else if (sh.alive[p]) {
+        const double dx = pos[p][0] - xq, dy = pos[p][1] - yq, dz = pos[p][2] - zq;
+        const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+        if (dbits(r2) < umax64(sh.rcsq[q], sh.rcsq[p])) {
+          const double yr = rsqrt_refined(r2);
+          double wB, wA;
+          changeover_w(r2 * yr, pmin(sh.A[q], sh.A[p]), P.kmode, wB, wA);
+          const double f = sh.gm[p] * wA * (yr * yr * yr);
+          ax = fma(f, dx, ax); ay = fma(f, dy, ay); az = fma(f, dz, az);
+        }
+      }
+    }
+  }
+  for (int o = tps >> 1; o > 0; o >>= 1) {
+    ax += __shfl_xor_sync(0xffffffffu, ax, o);
+    ay += __shfl_xor_sync(0xffffffffu, ay, o);
+    az += __shfl_xor_sync(0xffffffffu, az, o);
+  }
+}
+
+__global__ void __launch_bounds__(BS_THREADS) k_bs(Sim S, DevParams P, double tau) {
+  __shared__ BsShared sh;
+  const int tid = threadIdx.x;
+  const int np = S.npad;
+  const int ngroups = *S.ngroups;
+  for (int gidx = blockIdx.x; gidx < ngroups; gidx += gridDim.x) {
+    const int g0 = S.gstart[gidx], g = S.gstart[gidx + 1] - g0;
+    if (g > BS_GMAX) {
+      if (tid == 0) atomicOr(S.status, ST_GROUP_TOO_LARGE);
+      continue;  // uniform across the CTA
+    }
+    const int tps = g <= 8 ? 4 : (g <= 16 ? 2 : 1);  // threads per (level, member) slot
+    const int slot = tid / tps, sub = tid % tps;
+    const bool act = slot < BS_LEVELS * g;
+    const int lev = act ? slot / g : 0;  // level k = lev + 1, n_k = 2k substeps
+    const int q = act ? slot % g : 0;
+    const int L = lev + 1, nk = 2 * L;
+    if (tid < g) {
+      const int i = S.gmem[g0 + tid];
+      sh.idx[tid] = i;
+      sh.alive[tid] = S.alive[i];
+      sh.gm[tid] = S.gm[i]; sh.m[tid] = S.m[i]; sh.R[tid] = S.R[i]; sh.A[tid] = S.A[i];
+      sh.rcsq[tid] = S.rcsq[i];
+      for (int c = 0; c < 3; ++c) { sh.y[tid][c] = S.x0[c * np + i]; sh.y[tid][3 + c] = S.v0[c * np + i]; }
+    }
+    if (tid == 0) { sh.H = tau; sh.rem = tau; sh.U = 0.0; }
+    __syncthreads();
+    int halvings = 0, attempts = 0, steps = 0;
+    while (true) {
+      const double rem = sh.rem;
+      double H = sh.H;
+      if (absbits(rem) == 0ULL) break;
+      if (absbits(H) > absbits(rem)) H = rem;
+      if (++attempts > 200000) { if (tid == 0) atomicOr(S.status, ST_BS_FAILED); break; }
+      // ---- one attempt of length H: all levels' modified-midpoint integrations at once ----
+      const double h = __ddiv_rn(H, (double)nk), h2 = 2.0 * h;
+      const bool qa = act && sh.alive[q];
+      double zA[6], zB[6], out[6];
+      for (int c = 0; c < 6; ++c) zA[c] = sh.y[q][c];
+      if (act && sub == 0) for (int c = 0; c < 3; ++c) sh.pos[0][lev][q][c] = zA[c];
+      // error scales 1/|x|, 1/|v| at the start of the attempt
+      double isx, isv;
+      {
+        const double sx2 = fma(zA[2], zA[2], fma(zA[1], zA[1], zA[0] * zA[0]));
+        const double sv2 = fma(zA[5], zA[5], fma(zA[4], zA[4], zA[3] * zA[3]));
+        isx = dbits(sx2) == 0ULL ? 4.49423283715579e307 : rsqrt_refined(sx2);
+        isv = dbits(sv2) == 0ULL ? 4.49423283715579e307 : rsqrt_refined(sv2);
+      }
+      __syncthreads();
+      double ax = 0.0, ay = 0.0, az = 0.0;
+      // every lane of a warp that holds any active slot takes part (the term sums shuffle across
+      // lanes); warps without active slots stay off the FP64 pipe
+      if (__any_sync(0xffffffffu, act)) bs_terms(sh, P, g, q, sub, tps, sh.pos[0][lev], qa, ax, ay, az);
+      if (qa) {
+        zB[0] = fma(h, zA[3], zA[0]); zB[1] = fma(h, zA[4], zA[1]); zB[2] = fma(h, zA[5], zA[2]);
+        zB[3] = fma(h, ax, zA[3]); zB[4] = fma(h, ay, zA[4]); zB[5] = fma(h, az, zA[5]);
+      } else {
+        for (int c = 0; c < 6; ++c) zB[c] = zA[c];
+      }
+      int b = 1;
+      for (int e = 1; e <= 2 * BS_LEVELS; ++e) {
+        const bool lv = act && e <= nk;
+        if (lv && sub == 0) for (int c = 0; c < 3; ++c) sh.pos[b][lev][q][c] = zB[c];
+        __syncthreads();
+        if (__any_sync(0xffffffffu, lv)) bs_terms(sh, P, g, q, sub, tps, sh.pos[b][lev], qa, ax, ay, az);
+        if (lv) {
+          if (qa) {
+            if (e < nk) {
+              double zn[6];
+              zn[0] = fma(h2, zB[3], zA[0]); zn[1] = fma(h2, zB[4], zA[1]); zn[2] = fma(h2, zB[5], zA[2]);
+              zn[3] = fma(h2, ax, zA[3]); zn[4] = fma(h2, ay, zA[4]); zn[5] = fma(h2, az, zA[5]);
+              for (int c = 0; c < 6; ++c) { zA[c] = zB[c]; zB[c] = zn[c]; }
+            } else {
+              out[0] = 0.5 * fma(h, zB[3], zB[0] + zA[0]);
+              out[1] = 0.5 * fma(h, zB[4], zB[1] + zA[1]);
+              out[2] = 0.5 * fma(h, zB[5], zB[2] + zA[2]);
+              out[3] = 0.5 * fma(h, ax, zB[3] + zA[3]);
+              out[4] = 0.5 * fma(h, ay, zB[4] + zA[4]);
+              out[5] = 0.5 * fma(h, az, zB[5] + zA[5]);
+            }
+          } else if (e == nk) {
+            for (int c = 0; c < 6; ++c) out[c] = zA[c];
+          }
+        }
+        b ^= 1;
+      }
+      // ---- polynomial extrapolation in h^2 (Neville), as a wavefront across levels ----
+      double T[6], Tm1[6];
+      for (int c = 0; c < 6; ++c) { T[c] = out[c]; Tm1[c] = out[c]; }
+      if (tid < BS_LEVELS) sh.err[tid] = 0ULL;
+      for (int j = 1; j < BS_LEVELS; ++j) {
+        __syncthreads();
+        if (act && sub == 0) for (int c = 0; c < 6; ++c) sh.tab[lev][q][c] = T[c];
+        __syncthreads();
+        if (act && L > j) {
+          const double fi = c_facinv[L][j];
+          if (j == L - 1) for (int c = 0; c < 6; ++c) Tm1[c] = T[c];
+          for (int c = 0; c < 6; ++c) T[c] = fma(T[c] - sh.tab[lev - 1][q][c], fi, T[c]);
+        }
+      }
+      // level error: max over live members and components of |T[L][L] - T[L][L-1]| / scale
+      if (act && sub == 0 && L >= 2 && L <= P.bs_kmax && qa) {
+        u64 em = 0ULL;
+        for (int c = 0; c < 6; ++c) em = umax64(em, absbits((T[c] - Tm1[c]) * (c < 3 ? isx : isv)));
+        atomicMax(&sh.err[lev], em);
+      }
+      __syncthreads();
+      if (tid == 0) {
+        int acc = 0;
+        const u64 eps = dbits(P.bs_eps);
+        for (int l = 1; l < P.bs_kmax && l < BS_LEVELS; ++l)
+          if (sh.err[l] <= eps) { acc = l + 1; break; }
+        sh.accept = acc;
+      }
+      __syncthreads();
+      const int acc = sh.accept;
+      if (acc) {
+        if (act && sub == 0 && L == acc) for (int c = 0; c < 6; ++c) sh.yn[q][c] = T[c];
+        __syncthreads();
+        if (P.collisions) {  // contact test over the accepted substep (Hermite, threshold (R_a + R_b)^2)
+          const int npair = g * (g - 1) / 2;
+          for (int pi = tid; pi < npair; pi += BS_THREADS) {
+            int a = 0, rest = pi;
+            while (rest >= g - 1 - a) { rest -= g - 1 - a; a++; }
+            const int bq = a + 1 + rest;
+            unsigned char hit = 0;
+            if (sh.alive[a] && sh.alive[bq]) {
+              const double dmin = hermite_min_exact(
+                  __dsub_rn(sh.y[bq][0], sh.y[a][0]), __dsub_rn(sh.y[bq][1], sh.y[a][1]), __dsub_rn(sh.y[bq][2], sh.y[a][2]),
+                  __dsub_rn(sh.y[bq][3], sh.y[a][3]), __dsub_rn(sh.y[bq][4], sh.y[a][4]), __dsub_rn(sh.y[bq][5], sh.y[a][5]),
+                  __dsub_rn(sh.yn[bq][0], sh.yn[a][0]), __dsub_rn(sh.yn[bq][1], sh.yn[a][1]), __dsub_rn(sh.yn[bq][2], sh.yn[a][2]),
+                  __dsub_rn(sh.yn[bq][3], sh.yn[a][3]), __dsub_rn(sh.yn[bq][4], sh.yn[a][4]), __dsub_rn(sh.yn[bq][5], sh.yn[a][5]), H);
+              const double rr = sh.R[a] + sh.R[bq];
+              hit = dmin < rr * rr;
+            }
+            sh.cont[pi] = hit;
+          }
+          __syncthreads();
+          if (tid == 0) {  // mergers in ascending pair order on the post-substep states
+            int pi = 0;
+            for (int a = 0; a < g; ++a)
+              for (int bq = a + 1; bq < g; ++bq, ++pi) {
+                if (!sh.cont[pi] || !sh.alive[a] || !sh.alive[bq]) continue;
+                const int ia = sh.idx[a], ib = sh.idx[bq];
+                const double ma = sh.m[a], mb = sh.m[bq], M = ma + mb;
+                const double dx = sh.yn[bq][0] - sh.yn[a][0], dy = sh.yn[bq][1] - sh.yn[a][1], dz = sh.yn[bq][2] - sh.yn[a][2];
+                const double dvx = sh.yn[bq][3] - sh.yn[a][3], dvy = sh.yn[bq][4] - sh.yn[a][4], dvz = sh.yn[bq][5] - sh.yn[a][5];
+                const double r = sqrt(dx * dx + dy * dy + dz * dz);
+                const double v2 = dvx * dvx + dvy * dvy + dvz * dvz;
+                sh.U += 0.5 * ma * mb / M * v2 - P.G * ma * mb / r;
+                const bool keep_a = ma > mb || (ma == mb && ia < ib);
+                const int s = keep_a ? a : bq, d = keep_a ? bq : a;
+                for (int c = 0; c < 6; ++c) sh.yn[s][c] = (ma * sh.yn[a][c] + mb * sh.yn[bq][c]) / M;
+                const double Ra = sh.R[a], Rb = sh.R[bq];
+                sh.R[s] = cbrt(Ra * Ra * Ra + Rb * Rb * Rb);
+                sh.m[s] = M; sh.gm[s] = P.G * M;
+                sh.m[d] = 0.0; sh.gm[d] = 0.0; sh.R[d] = 0.0; sh.alive[d] = 0;
+                const int is = sh.idx[s], idd = sh.idx[d];
+                S.m[is] = M; S.gm[is] = P.G * M; S.R[is] = sh.R[s]; S.hill[is] = cbrt(M / (3.0 * P.m0));
+                S.m[idd] = 0.0; S.gm[idd] = 0.0; S.R[idd] = 0.0; S.hill[idd] = 0.0; S.alive[idd] = 0;
+                S.T[idd] = 0ULL; S.rcsq[idd] = 0ULL;
+                atomicAdd((unsigned long long *)&S.counters[C_MERGE], 1ULL);
+              }
+          }
+          __syncthreads();
+        }
+        if (tid < g) for (int c = 0; c < 6; ++c) sh.y[tid][c] = sh.yn[tid][c];
+        if (tid == 0) { sh.rem = rem - H; sh.H = 2.0 * H; }
+        halvings = 0;
+        steps++;
+      } else {
+        if (tid == 0) sh.H = 0.5 * H;
+        if (++halvings > P.bs_max_halvings) {
+          if (tid == 0) atomicOr(S.status, ST_BS_FAILED);
+          __syncthreads();
+          break;
+        }
+      }
+      __syncthreads();
+    }
+    // write back: live members take the integrated state, ghosts are parked far out
+    if (tid < g) {
+      const int i = sh.idx[tid];
+      if (sh.alive[tid]) {
+        for (int c = 0; c < 3; ++c) { S.x[c * np + i] = sh.y[tid][c]; S.v[c * np + i] = sh.y[tid][3 + c]; }
+      } else {
+        S.x[i] = PARK + 1.0e4 * i; S.x[np + i] = 0.0; S.x[2 * np + i] = 0.0;
+        for (int c = 0; c < 3; ++c) S.v[c * np + i] = 0.0;
+      }
+    }
+    if (tid == 0) {
+      atomicAdd((unsigned long long *)&S.counters[C_BSSTEPS], (unsigned long long)steps);
+      if (dbits(sh.U) != 0ULL) atomicAdd(S.U, sh.U);
+    }
+    __syncthreads();
+  }
+}
+
+void bs_init_constants() {
+  double h[BS_LEVELS + 1][BS_LEVELS] = {};
+  for (int L = 2; L <= BS_LEVELS; ++L)
+    for (int j = 1; j < L; ++j) {
+      const double ratio = (double)L / (double)(L - j);
+      h[L][j] = 1.0 / (ratio * ratio - 1.0);
+    }
+  cudaMemcpyToSymbol(c_facinv, h, sizeof(h));
+}
+
+void launch_bs(const Sim &S, const DevParams &P, double tau, int max_groups, cudaStream_t st) {
+  const int grid = max_groups < 1 ? 1 : max_groups;
+  k_bs<<<grid, BS_THREADS, 0, st>>>(S, P, tau);
+}
+
+}  // namespace genga

@@ -1,0 +1,46 @@
+// genga_launch.h -- host-side launchers of the sm_103a kernels (one per kernel family).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "genga_dev.cuh"
+
+namespace genga {
+
+enum FinMode { FIN_CLOSE = 0, FIN_OPEN = 1, FIN_INIT = 2 };
+
+// kick.cu
+void launch_rcrit(const Sim &S, const DevParams &P, double tau_abs, int check_reuse, cudaStream_t st);
+void launch_kick(const Sim &S, const DevParams &P, bool full, bool precise, cudaStream_t st);
+void launch_fin(const Sim &S, const DevParams &P, FinMode mode, double h1, double h2, double *aout,
+                cudaStream_t st);
+void launch_hc(const Sim &S, double hcm, cudaStream_t st);
+int kick_grid(const Sim &S);
+
+// step.cu
+void launch_drift(const Sim &S, const DevParams &P, double tau, double hcm1, double hcm2,
+                  int first_substep, cudaStream_t st);
+void launch_encounter(const Sim &S, double tau, unsigned *ebm, cudaStream_t st);
+void launch_group(const Sim &S, cudaStream_t st);
+void launch_kepler_phase(int n, double mu, double dt, int maxit, const int *alive, double *x, double *v,
+                         int *fail, cudaStream_t st);
+void launch_pairs_to_bitmap(const Sim &S, const int *pairs, int npairs, cudaStream_t st);
+void launch_bitmap_pairs(const unsigned *bm, int npad, int W, int *out, int cap, int *count, cudaStream_t st);
+void launch_single_to_fail(const Sim &S, const int *single, cudaStream_t st);
+void launch_copy_edges(const Sim &S, const int *pairs, int npairs, cudaStream_t st);
+
+// bs.cu
+void bs_init_constants();  // once per device, before any capture
+void launch_bs(const Sim &S, const DevParams &P, double tau, int max_groups, cudaStream_t st);
+
+// io.cu
+void launch_from_helio(const Sim &S, const DevParams &P, const double *xh, const double *vh,
+                       const double *m_in, const double *R_in, cudaStream_t st);
+void launch_to_helio(const Sim &S, const DevParams &P, double *xh, double *vh, double *m_out,
+                     double *R_out, int *alive_out, cudaStream_t st);
+void launch_energy(const Sim &S, const DevParams &P, double *scratch, double *E, cudaStream_t st);
+void launch_mathcheck(int n, int which, const double *in, double *out, cudaStream_t st);
+void launch_soa_setup(const Sim &S, const DevParams &P, const double *m, const int *alive,
+                      const double *x, const double *v, const double *rc, int n, cudaStream_t st);
+void launch_soa_out(const Sim &S, double *x, double *v, int n, cudaStream_t st);
+
+}  // namespace genga

@@ -1,0 +1,340 @@
+// step.cu -- the per-substep kernels between two kicks: Sun drift + Kepler drift (Eqs. Hc, fg),
+// the close-encounter search (Eqs. teqn, polydelta) and the grouping of encounter pairs
+// (Sect. 3.2 and Appendix), plus the list/bitmap conversions used by the phase entry points.
+#include "genga_launch.h"
+
+namespace genga {
+
+// ---------------------------------------------------------------------------------------------
+// Drift: x += hcm2 P_pre + hcm1 P_post (the previous substep's second Sun drift, if any, and this
+// substep's first), keep (x0, v0), then the Kepler drift for tau. One warp per 32 bodies; every
+// warp sums the per-tile momentum partials itself (no extra launch).
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(32) k_drift(Sim S, DevParams P, double tau, double hcm1, double hcm2, int first) {
+  const int lane = threadIdx.x;
+  const int i = blockIdx.x * 32 + lane;
+  const int np = S.npad, nt = S.nt;
+  if (first && i == 0) S.flags[0] = 0;  // the opening kick of this step has consumed the flag
+  double shift[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    double a = 0.0, b = 0.0;
+    for (int t = lane; t < nt; t += 32) {
+      a += S.pfin[t * 3 + c];
+      if (hcm2 != 0.0) b += S.pkick[t * 3 + c];
+    }
+    a = warp_sum(a);
+    shift[c] = hcm1 * a;
+    if (hcm2 != 0.0) shift[c] = fma(hcm2, warp_sum(b), shift[c]);
+  }
+  if (!S.alive[i]) return;
+  double x = S.x[i] + shift[0], y = S.x[np + i] + shift[1], z = S.x[2 * np + i] + shift[2];
+  double vx = S.v[i], vy = S.v[np + i], vz = S.v[2 * np + i];
+  S.x0[i] = x; S.x0[np + i] = y; S.x0[2 * np + i] = z;
+  S.v0[i] = vx; S.v0[np + i] = vy; S.v0[2 * np + i] = vz;
+  int it = 0;
+  if (kepler_drift_dev(P.G * P.m0, P.mu2, x, y, z, vx, vy, vz, tau, P.kepler_maxit, &it)) {
+    atomicOr(S.status, ST_KEPLER_FALLBACK);
+    atomicAdd((unsigned long long *)&S.counters[C_KFALL], 1ULL);
+    S.fail[atomicAdd(S.nfail, 1)] = i;  // integrated by BS as a group of its own
+  }
+  S.x[i] = x; S.x[np + i] = y; S.x[2 * np + i] = z;
+  S.v[i] = vx; S.v[np + i] = vy; S.v[2 * np + i] = vz;
+}
+
+__global__ void k_kepler_phase(int n, double mu, double dt, int maxit, const int *alive, double *X,
+                               double *V, int *fail) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  fail[i] = 0;
+  if (!alive[i]) return;
+  double x = X[i], y = X[n + i], z = X[2 * n + i], vx = V[i], vy = V[n + i], vz = V[2 * n + i];
+  int it = 0;
+  if (kepler_drift_dev(mu, 2.0 * mu, x, y, z, vx, vy, vz, dt, maxit, &it)) { fail[i] = 1; return; }
+  X[i] = x; X[n + i] = y; X[2 * n + i] = z;
+  V[i] = vx; V[n + i] = vy; V[2 * n + i] = vz;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Encounter search: one warp per body i scans its row of the candidate bitmap (clearing it for
+// the next kick), tests the pairs j > i with the Hermite minimum over the drift and writes the
+// confirmed pairs into the row of this substep's encounter bitmap and into the edge list.
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_encounter(Sim S, double tau, unsigned *ebm) {
+  const int lane = threadIdx.x & 31;
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (i >= S.npad) return;
+  const int np = S.npad, W = S.W;
+  unsigned *erow = ebm + (size_t)i * W;
+  unsigned *crow = S.cbm + (size_t)i * W;
+  if (!((S.rowany[i >> 5] >> (i & 31)) & 1u)) {
+    for (int w = lane; w < W; w += 32) erow[w] = 0u;
+    return;
+  }
+  const double x0i = S.x0[i], y0i = S.x0[np + i], z0i = S.x0[2 * np + i];
+  const double u0i = S.v0[i], v0i = S.v0[np + i], w0i = S.v0[2 * np + i];
+  const double x1i = S.x[i], y1i = S.x[np + i], z1i = S.x[2 * np + i];
+  const double u1i = S.v[i], v1i = S.v[np + i], w1i = S.v[2 * np + i];
+  const double rci = S.rc[i];
+  const bool ai = S.alive[i] != 0;
+  int found = 0;
+  for (int w = lane; w < W; w += 32) {
+    unsigned bits = crow[w];
+    crow[w] = 0u;
+    // keep j > i only
+    const int lo = w * 32;
+    if (lo + 31 <= i) bits = 0u;
+    else if (lo <= i) bits &= (i - lo + 1 >= 32) ? 0u : (0xffffffffu << (i - lo + 1));
+    unsigned eb = 0u;
+    while (bits) {
+      const int b = __ffs(bits) - 1;
+      bits &= bits - 1;
+      const int j = lo + b;
+      if (!ai || !S.alive[j]) continue;
+      const double dmin = hermite_min_exact(
+          __dsub_rn(S.x0[j], x0i), __dsub_rn(S.x0[np + j], y0i), __dsub_rn(S.x0[2 * np + j], z0i),
+          __dsub_rn(S.v0[j], u0i), __dsub_rn(S.v0[np + j], v0i), __dsub_rn(S.v0[2 * np + j], w0i),
+          __dsub_rn(S.x[j], x1i), __dsub_rn(S.x[np + j], y1i), __dsub_rn(S.x[2 * np + j], z1i),
+          __dsub_rn(S.v[j], u1i), __dsub_rn(S.v[np + j], v1i), __dsub_rn(S.v[2 * np + j], w1i), tau);
+      const double rcij = pmax(rci, S.rc[j]);
+      if (dmin < __dmul_rn(rcij, rcij)) {
+        eb |= 1u << b;
+        const int e = atomicAdd(S.nedges, 1);
+        S.edges[2 * e] = i;
+        S.edges[2 * e + 1] = j;
+        found++;
+      }
+    }
+    erow[w] = eb;
+  }
+  if (found) atomicAdd((unsigned long long *)&S.counters[C_ENC], (unsigned long long)found);
+  if (lane == 0) atomicAnd(&S.rowany[i >> 5], ~(1u << (i & 31)));
+}
+
+// ---------------------------------------------------------------------------------------------
+// Grouping (Appendix): one CTA. LINK[i] = i; every edge hooks the larger root onto the smaller
+// with atomicMin; pointer jumping compresses the links; repeat until no edge joins two roots.
+// Then the members (bodies in an edge or in the Kepler-fallback list) are sorted by
+// (root, index) with a bitonic sort, which yields groups ordered by smallest member and members
+// ascending -- the same lists as a breadth-first search.
+// ---------------------------------------------------------------------------------------------
+constexpr int GROUP_THREADS = 1024;
+constexpr int GROUP_MAX_ROUNDS = 64;
+
+// Ordered compaction over [0, n) by one CTA of GROUP_THREADS threads: emit(i, k) is called for the
+// k-th index (in ascending order) with pred(i) true. Returns the count (uniform across the CTA).
+template <class Pred, class Emit>
+__device__ int block_compact(int n, Pred pred, Emit emit, int *wtot, int *s_base) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) *s_base = 0;
+  __syncthreads();
+  for (int c0 = 0; c0 < n; c0 += GROUP_THREADS) {
+    const int i = c0 + tid;
+    const bool f = i < n && pred(i);
+    const unsigned bal = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) wtot[wid] = __popc(bal);
+    __syncthreads();
+    if (wid == 0) {
+      const int v = wtot[lane];
+      int incl = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      wtot[lane] = incl - v;  // exclusive offsets of the warps
+    }
+    __syncthreads();
+    if (f) emit(i, *s_base + wtot[wid] + __popc(bal & ((1u << lane) - 1u)));
+    __syncthreads();
+    if (tid == GROUP_THREADS - 1) *s_base += wtot[wid] + __popc(bal);
+    __syncthreads();
+  }
+  return *s_base;
+}
+
+__device__ __forceinline__ int find_root(const int *link, int r) {
+  for (int k = 0; k < NMAX + 2; ++k) {
+    const int l = link[r];
+    if (l == r) break;
+    r = l;
+  }
+  return r;
+}
+
+__global__ void __launch_bounds__(GROUP_THREADS) k_group(Sim S) {
+  __shared__ int link[NMAX];
+  __shared__ int key[NMAX];
+  __shared__ unsigned char part[NMAX];
+  __shared__ int wtot[GROUP_THREADS / 32];
+  __shared__ int s_changed, s_base, s_ng;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int np = S.npad;
+  const int ne = *S.nedges, nf = *S.nfail;
+  for (int i = tid; i < np; i += GROUP_THREADS) { link[i] = i; part[i] = 0; }
+  __syncthreads();
+  for (int e = tid; e < ne; e += GROUP_THREADS) { part[S.edges[2 * e]] = 1; part[S.edges[2 * e + 1]] = 1; }
+  for (int f = tid; f < nf; f += GROUP_THREADS) part[S.fail[f]] = 1;
+  int round = 0;
+  for (; round < GROUP_MAX_ROUNDS; ++round) {
+    if (tid == 0) s_changed = 0;
+    __syncthreads();
+    for (int e = tid; e < ne; e += GROUP_THREADS) {
+      const int ru = find_root(link, S.edges[2 * e]), rv = find_root(link, S.edges[2 * e + 1]);
+      if (ru != rv) {
+        atomicMin(&link[ru > rv ? ru : rv], ru < rv ? ru : rv);
+        s_changed = 1;
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < np; i += GROUP_THREADS) link[i] = find_root(link, link[i]);
+    __syncthreads();
+    if (!s_changed) break;
+  }
+  if (round >= GROUP_MAX_ROUNDS && tid == 0) atomicOr(S.status, ST_UNION_ROUNDS);
+  // compact the participants as keys root * npad + i (block-wide ordered scan)
+  const int cnt = block_compact(np, [&](int i) { return part[i] != 0; },
+                                [&](int i, int pos) { key[pos] = link[i] * np + i; }, wtot, &s_base);
+  int M = 1;
+  while (M < cnt) M <<= 1;
+  for (int t = cnt + tid; t < M; t += GROUP_THREADS) key[t] = 0x7fffffff;
+  __syncthreads();
+  for (int k = 2; k <= M; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = tid; t < M; t += GROUP_THREADS) {
+        const int u = t ^ j;
+        if (u > t) {
+          const int a = key[t], b = key[u];
+          const bool up = (t & k) == 0;
+          if ((a > b) == up) { key[t] = b; key[u] = a; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int t = tid; t < cnt; t += GROUP_THREADS) S.gmem[t] = key[t] % np;
+  // a new group starts where the root changes; ordered scan of the start flags numbers them
+  s_ng = block_compact(cnt, [&](int t) { return t == 0 || key[t] / np != key[t - 1] / np; },
+                       [&](int t, int g) { S.gstart[g] = t; }, wtot, &s_base);
+  if (tid == 0) {
+    S.gstart[s_ng] = cnt;
+    *S.ngroups = s_ng;
+    if (s_ng) atomicAdd((unsigned long long *)&S.counters[C_GROUPS], (unsigned long long)s_ng);
+    *S.nedges = 0;
+    *S.nfail = 0;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// List <-> bitmap helpers for the phase entry points and genga_encounters
+// ---------------------------------------------------------------------------------------------
+__global__ void k_pairs_to_bitmap(Sim S, const int *pairs, int npairs) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= npairs) return;
+  const int i = pairs[2 * k], j = pairs[2 * k + 1];
+  atomicOr(&S.cbm[(size_t)i * S.W + (j >> 5)], 1u << (j & 31));
+  atomicOr(&S.cbm[(size_t)j * S.W + (i >> 5)], 1u << (i & 31));
+  atomicOr(&S.rowany[i >> 5], 1u << (i & 31));
+  atomicOr(&S.rowany[j >> 5], 1u << (j & 31));
+}
+
+// Pairs (i < j) of a bitmap, ascending, into out[2*cap]; *count receives the total.
+__global__ void __launch_bounds__(1024) k_bitmap_pairs(const unsigned *bm, int npad, int W, int *out, int cap, int *count) {
+  __shared__ int wtot[32];
+  __shared__ int s_base;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) s_base = 0;
+  __syncthreads();
+  for (int r0 = 0; r0 < npad; r0 += 1024) {
+    const int i = r0 + tid;
+    int c = 0;
+    if (i < npad) {
+      for (int w = 0; w < W; ++w) {
+        unsigned bits = bm[(size_t)i * W + w];
+        const int lo = w * 32;
+        if (lo + 31 <= i) bits = 0u;
+        else if (lo <= i) bits &= (i - lo + 1 >= 32) ? 0u : (0xffffffffu << (i - lo + 1));
+        c += __popc(bits);
+      }
+    }
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) wtot[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      int v = wtot[lane], in2 = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, in2, o);
+        if (lane >= o) in2 += t;
+      }
+      wtot[lane] = in2 - v;
+    }
+    __syncthreads();
+    int pos = s_base + wtot[wid] + incl - c;
+    if (i < npad && c) {
+      for (int w = 0; w < W; ++w) {
+        unsigned bits = bm[(size_t)i * W + w];
+        const int lo = w * 32;
+        if (lo + 31 <= i) bits = 0u;
+        else if (lo <= i) bits &= (i - lo + 1 >= 32) ? 0u : (0xffffffffu << (i - lo + 1));
+        while (bits) {
+          const int b = __ffs(bits) - 1;
+          bits &= bits - 1;
+          if (pos < cap) { out[2 * pos] = i; out[2 * pos + 1] = lo + b; }
+          pos++;
+        }
+      }
+    }
+    __syncthreads();
+    if (tid == 1023) s_base = pos;  // end of the last thread's run = total so far
+    __syncthreads();
+  }
+  if (tid == 0) *count = s_base;
+}
+
+__global__ void k_single_to_fail(Sim S, const int *single) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= S.n) return;
+  if (single[i]) S.fail[atomicAdd(S.nfail, 1)] = i;
+}
+
+__global__ void k_copy_edges(Sim S, const int *pairs, int npairs) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k == 0) *S.nedges = npairs;
+  if (k >= npairs) return;
+  S.edges[2 * k] = pairs[2 * k];
+  S.edges[2 * k + 1] = pairs[2 * k + 1];
+}
+
+// ---------------------------------------------------------------------------------------------
+void launch_drift(const Sim &S, const DevParams &P, double tau, double hcm1, double hcm2,
+                  int first_substep, cudaStream_t st) {
+  k_drift<<<S.npad / 32, 32, 0, st>>>(S, P, tau, hcm1, hcm2, first_substep);
+}
+void launch_encounter(const Sim &S, double tau, unsigned *ebm, cudaStream_t st) {
+  k_encounter<<<(S.npad * 32 + 127) / 128, 128, 0, st>>>(S, tau, ebm);
+}
+void launch_group(const Sim &S, cudaStream_t st) { k_group<<<1, GROUP_THREADS, 0, st>>>(S); }
+void launch_kepler_phase(int n, double mu, double dt, int maxit, const int *alive, double *x, double *v,
+                         int *fail, cudaStream_t st) {
+  k_kepler_phase<<<(n + 31) / 32, 32, 0, st>>>(n, mu, dt, maxit, alive, x, v, fail);
+}
+void launch_pairs_to_bitmap(const Sim &S, const int *pairs, int npairs, cudaStream_t st) {
+  if (npairs > 0) k_pairs_to_bitmap<<<(npairs + 127) / 128, 128, 0, st>>>(S, pairs, npairs);
+}
+void launch_bitmap_pairs(const unsigned *bm, int npad, int W, int *out, int cap, int *count, cudaStream_t st) {
+  k_bitmap_pairs<<<1, 1024, 0, st>>>(bm, npad, W, out, cap, count);
+}
+void launch_single_to_fail(const Sim &S, const int *single, cudaStream_t st) {
+  k_single_to_fail<<<(S.n + 127) / 128, 128, 0, st>>>(S, single);
+}
+void launch_copy_edges(const Sim &S, const int *pairs, int npairs, cudaStream_t st) {
+  k_copy_edges<<<(npairs + 128) / 128, 128, 0, st>>>(S, pairs, npairs);
+}
+
+}  // namespace genga

@@ -1,0 +1,129 @@
+"""GPU whole-step parity with the CPU oracle through the C ABI (genga_init / genga_step / ...).
+
+Acceptance: relative state error <= 1e-12 after one step and <= 1e-9 after 100 steps on the same
+seeded input; encounter pair lists identical; live flags identical. The N = 2048 4th-order case
+is the benchmark's workload and launch configuration (one captured CUDA graph per step).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1404_2324_gb300 import genga, ics
+from tests.gpu_util import pair_sims, rel_state_error, with_central
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("order", [2, 4, 6])
+def test_disk32_one_step_and_hundred_steps(order):
+    d = ics.disk32(1)
+    g, o = pair_sims(d, order, steps=1)
+    err, same = rel_state_error(g, o)
+    assert same and err <= 1e-12, err
+    for s in range(-1, 0):
+        np.testing.assert_array_equal(g.encounters(s), o.encounters(s) + 1)
+    g.step(99)
+    o.step(99)
+    err, same = rel_state_error(g, o)
+    assert same and err <= 1e-9, err
+    E, U = g.energy()
+    Eo, Uo = o.energy()
+    assert E == pytest.approx(Eo, rel=1e-12) and U == pytest.approx(Uo, rel=1e-9, abs=1e-30)
+    code, cnt = g.status()
+    st = o.stats()
+    assert cnt["steps"] == 100
+    assert cnt["encounters"] == st["encounters"] and cnt["groups"] == st["groups"]
+
+
+def test_disk2048_fourth_order_parity():
+    d = ics.disk2048(2)
+    g, o = pair_sims(d, 4, steps=1)
+    err, same = rel_state_error(g, o)
+    assert same and err <= 1e-12, err
+    for s in range(3):
+        ge, oe = g.encounters(s), o.encounters(s) + 1
+        np.testing.assert_array_equal(ge, oe)
+    assert len(g.encounters(0)) > 20  # encounters, groups and BS took part
+    g.step(4)
+    o.step(4)
+    err, same = rel_state_error(g, o)
+    assert same and err <= 1e-11, err
+    code, cnt = g.status()
+    assert code & (genga.ST_BS_FAILED | genga.ST_GROUP_TOO_LARGE | genga.ST_UNION_ROUNDS) == 0
+    assert cnt["candidates"] > 0 and cnt["encounters"] > 0 and cnt["bs_steps"] > 0
+
+
+def test_gradient_mode_and_precise_division_parity():
+    d = ics.disk32(3)
+    for params in ({"kmode": 1}, {"precise_div": 1}):
+        g, o = pair_sims(d, 2, steps=20, **params)
+        err, same = rel_state_error(g, o)
+        assert same and err <= 1e-10, (params, err)
+
+
+def test_runs_are_bitwise_reproducible():
+    d = ics.disk2048(5, n=512)
+    m, R, x, v = with_central(d)
+    out = []
+    for _ in range(2):
+        s = genga.Genga(m, R, x, v, d["G"], d["dt"], 4)
+        s.step(5)
+        st = s.state()
+        out.append((st["x"].copy(), st["v"].copy()))
+        s.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("n", [1, 2, 33, 2047])
+def test_ragged_and_tiny_systems(n):
+    d = ics.disk2048(6, n=n, order=2)
+    g, o = pair_sims(d, 2, steps=3)
+    err, same = rel_state_error(g, o)
+    assert same and err <= 1e-11, err
+
+
+def test_single_massless_body_is_kepler_orbit():
+    from tests import twobody_ref
+    xh, vh = ics.elements_to_cartesian(ics.G_GAUSS, 1.0, 0.3, 0.1, 1.0, 2.0, 3.0)
+    m = np.array([1.0, 0.0]); R = np.zeros(2)
+    s = genga.Genga(m, R, np.vstack([np.zeros(3), xh]), np.vstack([np.zeros(3), vh]), ics.G_GAUSS, 6.0, 4)
+    s.step(50)
+    st = s.state()
+    xr, vr = twobody_ref.propagate(ics.G_GAUSS, xh, vh, 300.0)
+    assert np.linalg.norm(st["x"][1] - xr) <= 5e-13 * np.linalg.norm(xr) * 50
+    assert np.linalg.norm(st["v"][1] - vr) <= 5e-13 * np.linalg.norm(vr) * 50
+
+
+def test_merger_in_full_step_matches_oracle():
+    """Two bodies on a collision course inside a small system: the merger happens inside BS."""
+    d = ics.disk32(4, n=8)
+    d["x"][1] = d["x"][0] + np.array([0.0005, 0.0, 0.0])
+    d["v"][1] = d["v"][0] - np.array([0.0002, 0.0, 0.0])
+    d["R"][:2] = 3e-5
+    g, o = pair_sims(d, 2, steps=2)
+    assert len(o.collisions()) == 1
+    err, same = rel_state_error(g, o)
+    assert same and err <= 1e-10, err
+    gs, os_ = g.state(), o.state()
+    np.testing.assert_allclose(gs["m"][1:], os_["m"], rtol=1e-15)
+    _, U = g.energy()
+    _, Uo = o.energy()
+    assert U == pytest.approx(Uo, rel=1e-8)
+    code, cnt = g.status()
+    assert cnt["mergers"] == 1
+
+
+def test_set_state_matches_fresh_start():
+    d = ics.disk32(8)
+    m, R, x, v = with_central(d)
+    a = genga.Genga(m, R, x, v, d["G"], d["dt"], 2)
+    a.step(10)
+    mid = a.state()
+    b = genga.Genga(m, R, x, v, d["G"], d["dt"], 2)
+    b.set_state(mid["x"], mid["v"])
+    c = genga.Genga(mid["m"], mid["R"], mid["x"], mid["v"], d["G"], d["dt"], 2)
+    b.step(5)
+    c.step(5)
+    sb, sc = b.state(), c.state()
+    np.testing.assert_allclose(sb["x"], sc["x"], rtol=1e-14, atol=1e-16)
+    np.testing.assert_allclose(sb["v"], sc["v"], rtol=1e-14, atol=1e-18)
