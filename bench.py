@@ -1,0 +1,302 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 FP64 hybrid symplectic step (GENGA, arXiv:1404.2324).
+
+Workload: the 2048-planetesimal disk (0.5-4 AU, total mass 2 Earth masses, seed 2), 4th-order
+(Yoshida) hybrid scheme with close encounters integrated by Bulirsch-Stoer and perfect merging,
+dt = 6 days. One "step" is one full 4th-order hybrid step of all 2048 bodies through the C ABI
+(genga_step -> one replay of the captured step graph).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+Prints ONE JSON line. value: steps/s with the state resident in HBM, timed with CUDA events per
+step on the launching stream, L2 flushed (256 MiB write) before every timed step. e2e: the same
+metric through the public API with host buffers: each step uploads the state from pinned host
+memory (genga_set_state), steps, and reads it back (genga_get_state). roofline: the pairwise
+kick kernel (dominant), FP64-ALU bound. cpu_baseline: the CPU oracle on a bounded sample.
+With --gpus N > 1 (torchrun) every rank runs an independent replica (the method does not shard
+at this N); value counts the steps of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "N=2048 hybrid steps/s & FP64-peak fraction; batched sys-steps/s; adjoint/fwd"
+UNIT = "steps/s"
+N_BODIES = 2048
+ORDER = 4
+SEED = 2
+FMA_LANES_PER_SM_CLK = 2  # FP64 FMA lanes per SM per clock on GB300 (measured: 1.9-2.0 at load clocks)
+FLOPS_PER_PAIR = 20       # algorithmic flops per ordered pair of the kick (sqrt and division count 1)
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "kick_disk2048_ncu.md")
+KICK_SOURCES = [os.path.join(ROOT, "paper_1404_2324_gb300", "csrc", f) for f in ("kick.cu", "genga_dev.cuh")]
+
+
+def workload_config():
+    return {"workload": "disk2048: N=2048 planetesimals, 4th-order hybrid step, BS + merging, dt=6 d",
+            "n_bodies": N_BODIES, "order": ORDER, "dt_days": 6.0, "seed": SEED,
+            "l2": "flushed before every timed step (256 MiB write)",
+            "inputs": "synthetic disk, a U[0.5,4] AU, e~Rayleigh(0.01), i~Rayleigh(0.005), 2 Earth masses"}
+
+
+def make_input():
+    from paper_1404_2324_gb300 import ics
+    d = ics.disk2048(SEED, n=N_BODIES, order=ORDER)
+    m = np.concatenate([[d["m0"]], d["m"]])
+    R = np.concatenate([[0.0], d["R"]])
+    x = np.vstack([np.zeros(3), d["x"]])
+    v = np.vstack([np.zeros(3), d["v"]])
+    return d, m, R, x, v
+
+
+def kick_source_hash():
+    h = hashlib.sha256()
+    for p in KICK_SOURCES:
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic():
+    """DRAM bytes per kick launch from the committed ncu summary, if it was taken on these sources."""
+    try:
+        with open(PROFILE_SUMMARY) as f:
+            txt = f.read()
+    except OSError:
+        return None
+    mh = re.search(r"source_sha256:\s*([0-9a-f]+)", txt)
+    mt = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not mh or not mt or mh.group(1) != kick_source_hash():
+        return None
+    return float(mt.group(1))
+
+
+# ------------------------------------------------------------------------------------ oracle arm
+def run_oracle(steps, warmup):
+    import oracle as O
+    d, *_ = make_input()
+    p = O.params(G=d["G"], m0=d["m0"], dt=d["dt"], order=ORDER)
+    sim = O.Sim(p, d["m"], d["R"], d["x"], d["v"])
+    sim.step(warmup)
+    t0 = time.perf_counter()
+    sim.step(steps)
+    dt = time.perf_counter() - t0
+    sim.close()
+    return steps / dt, dt
+
+
+def cpu_baseline_entry(steps, warmup):
+    rate, secs = run_oracle(steps, warmup)
+    return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} full steps of the same N=2048 4th-order disk after {warmup} warm-up steps, "
+                      f"single-threaded C oracle ({secs:.1f} s)"}
+
+
+# ------------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=10)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------ GPU arm
+def run_gpu(args, rank, world):
+    import torch
+    from paper_1404_2324_gb300 import genga
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    genga.lib()
+    d, m, R, x, v = make_input()
+    ctx = genga.genga_init(m, R, x, v, d["G"], d["dt"], ORDER)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    genga.genga_set_stream(ctx, stream)
+    genga.genga_set_profiling(ctx, True)
+    kernels_per_step = genga.genga_launch_count(ctx)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    genga.genga_step(ctx, args.warmup)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    sampler = ClockSampler(dev)
+    sampler.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    total_ms, kick_ms, kick_launches = 0.0, 0.0, 0
+    for _ in range(args.steps):
+        flush.zero_()
+        ev0.record(stream)
+        genga.genga_step(ctx, 1)
+        ev1.record(stream)
+        ev1.synchronize()
+        total_ms += ev0.elapsed_time(ev1)
+        km, kn = genga.genga_kick_time(ctx)
+        kick_ms += km
+        kick_launches += kn
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    code, counters = genga.genga_status(ctx)
+    t_max = total_ms
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * args.steps / (t_max * 1e-3)
+
+    # end to end through the public API with host buffers (pinned)
+    genga.genga_set_profiling(ctx, False)
+    n = N_BODIES + 1
+    hx = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
+    hv = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
+    st = genga.genga_get_state(ctx, n)
+    hx[:] = st["x"]
+    hv[:] = st["v"]
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    genga.genga_step(ctx, 1)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        genga.genga_set_state(ctx, hx, hv)
+        genga.genga_step(ctx, 1)
+        genga.lib().genga_get_state(ctx, hx.ctypes.data_as(genga._D), hv.ctypes.data_as(genga._D), None, None, None)
+    t_e2e = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e = {"value": world * e2e_steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(hx.nbytes + hv.nbytes),
+           "d2h_bytes_per_step": int(hx.nbytes + hv.nbytes), "steps": e2e_steps,
+           "note": "genga_set_state + genga_step + genga_get_state per step; set_state recomputes the first kick"}
+    genga.genga_free(ctx)
+
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = clocks.get("sm_max_mhz") or 2070.0
+    peak_tflops = props.multi_processor_count * FMA_LANES_PER_SM_CLK * 2 * sm_max * 1e6 / 1e12
+    kick_avg_s = (kick_ms / max(kick_launches, 1)) * 1e-3
+    algo_flops = FLOPS_PER_PAIR * N_BODIES * (N_BODIES - 1)
+    achieved = algo_flops / kick_avg_s / 1e12
+    traffic = committed_traffic()
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": traffic,
+                "kernel": "k_kick (pairwise K-weighted kick + precheck)", "kick_avg_us": kick_avg_s * 1e6,
+                "kick_launches": kick_launches,
+                "peak_basis": f"FP64: {props.multi_processor_count} SMs x {FMA_LANES_PER_SM_CLK} FMA/clk x 2 flop x "
+                              f"{sm_max:.0f} MHz (derived)",
+                "achieved_basis": f"{FLOPS_PER_PAIR} flop x N(N-1) ordered pairs per launch"}
+    res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": workload_config(), "roofline": roofline, "e2e": e2e,
+           "gpu_launches": kernels_per_step * args.steps, "kernels_per_step": kernels_per_step,
+           "clocks": clocks, "status": code, "counters": counters}
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--e2e-steps", type=int, default=500)
+    ap.add_argument("--cpu-steps", type=int, default=40, help="oracle steps in the CPU-baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 0 or args.steps < 1:
+        ap.error("need --steps >= 1 and --warmup >= 0")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        import oracle
+        oracle.build()
+        ref_steps = min(args.steps, args.cpu_steps)
+        ref_warm = min(args.warmup, 2)
+        cb = cpu_baseline_entry(ref_steps, ref_warm)
+        res = {"metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": 1e3 / cb["value"], "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": workload_config(), "impl": "reference", "cpu_baseline": cb,
+               "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(res))
+        return 0
+
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    res = run_gpu(args, rank, world)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            import oracle
+            oracle.build()
+            res["cpu_baseline"] = cpu_baseline_entry(args.cpu_steps, 2)
+        else:
+            res["cpu_baseline"] = None
+        print(json.dumps(res))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -116,6 +116,18 @@ int genga_encounters(genga_ctx *ctx, int substep, int *pairs, int cap, int *n_pa
  * [7] full-kick recomputes (8 entries). Waits for the stream. */
 int genga_status(genga_ctx *ctx, int *code, long long *detail);
 
+/* Enables (1) or disables (0) CUDA-event timing of the pairwise kick kernels inside the captured
+ * step graph (event-record nodes around each kick launch; the next genga_step recaptures). */
+int genga_set_profiling(genga_ctx *ctx, int on);
+
+/* Waits for the stream, then returns in *ms the summed device time of the pairwise kick launches
+ * of the most recent step and in *launches their number (profiling must be on). */
+int genga_kick_time(genga_ctx *ctx, float *ms, int *launches);
+
+/* Number of kernel launches one genga_step enqueues (kernel nodes of the captured step graph;
+ * captures it if needed). */
+int genga_launch_count(genga_ctx *ctx, int *kernels_per_step);
+
 /* Frees the context and every device buffer it owns. */
 void genga_free(genga_ctx *ctx);
 

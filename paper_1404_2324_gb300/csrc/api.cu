@@ -136,6 +136,9 @@ struct genga_ctx {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int bs_grid = 1;
+  bool profiling = false;
+  cudaEvent_t kev[2 * 7] = {};
+  int nkev = 0;
   // staging
   double *sx = nullptr, *sv = nullptr, *sm = nullptr, *sR = nullptr, *scratch = nullptr, *sE = nullptr;
   int *salive = nullptr, *spairs = nullptr, *scount = nullptr;
@@ -184,19 +187,30 @@ void enqueue_step(genga_ctx *c, cudaStream_t st) {
     launch_encounter(S, tau, S.ebm + (size_t)j * S.npad * S.W, st);
     launch_group(S, st);
     launch_bs(S, P, tau, c->bs_grid, st);
+    if (c->profiling) cudaEventRecordWithFlags(c->kev[2 * j], st, cudaEventRecordExternal);
     launch_kick(S, P, false, precise, st);
+    if (c->profiling) cudaEventRecordWithFlags(c->kev[2 * j + 1], st, cudaEventRecordExternal);
     const double h2 = (j + 1 < c->nsub) ? 0.5 * c->w[j + 1] * dt : 0.0;
     launch_fin(S, P, FIN_CLOSE, 0.5 * tau, h2, nullptr, st);
   }
   launch_hc(S, 0.5 * c->w[c->nsub - 1] * dt * inv_m0, st);
 }
 
+// Captured on the context's own stream (the caller's stream may be the legacy default stream,
+// which cannot be captured); the executable graph is then launched on whichever stream is set.
 int build_graph(genga_ctx *c) {
   drop_graph(c);
-  CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-  enqueue_step(c, c->stream);
+  if (c->stream != c->own) {  // the capture must see everything the caller enqueued so far
+    cudaEvent_t ev;
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    CK(cudaEventRecord(ev, c->stream));
+    CK(cudaStreamWaitEvent(c->own, ev, 0));
+    CK(cudaEventDestroy(ev));
+  }
+  CK(cudaStreamBeginCapture(c->own, cudaStreamCaptureModeThreadLocal));
+  enqueue_step(c, c->own);
   cudaGraph_t g = nullptr;
-  cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+  cudaError_t e = cudaStreamEndCapture(c->own, &g);
   if (e != cudaSuccess || !g) return GENGA_ECUDA;
   c->graph = g;
   CK(cudaGraphInstantiate(&c->gexec, c->graph, 0));
@@ -380,10 +394,56 @@ int genga_status(genga_ctx *c, int *code, long long *detail) {
   return GENGA_OK;
 }
 
+int genga_set_profiling(genga_ctx *c, int on) {
+  if (!c) return GENGA_EINVAL;
+  if (on && !c->nkev) {
+    for (int k = 0; k < 2 * c->nsub; ++k) CK(cudaEventCreate(&c->kev[k]));
+    c->nkev = 2 * c->nsub;
+  }
+  c->profiling = on != 0;
+  drop_graph(c);
+  return GENGA_OK;
+}
+
+int genga_kick_time(genga_ctx *c, float *ms, int *launches) {
+  if (!c || !ms || !c->profiling || !c->nkev) return GENGA_EINVAL;
+  CK(cudaStreamSynchronize(c->stream));
+  float tot = 0.0f;
+  for (int j = 0; j < c->nsub; ++j) {
+    float t = 0.0f;
+    CK(cudaEventElapsedTime(&t, c->kev[2 * j], c->kev[2 * j + 1]));
+    tot += t;
+  }
+  *ms = tot;
+  if (launches) *launches = c->nsub;
+  return GENGA_OK;
+}
+
+int genga_launch_count(genga_ctx *c, int *kernels_per_step) {
+  if (!c || !kernels_per_step) return GENGA_EINVAL;
+  if (!c->gexec) {
+    int rc = build_graph(c);
+    if (rc != GENGA_OK) return rc;
+  }
+  size_t nn = 0;
+  CK(cudaGraphGetNodes(c->graph, nullptr, &nn));
+  std::vector<cudaGraphNode_t> nodes(nn);
+  CK(cudaGraphGetNodes(c->graph, nodes.data(), &nn));
+  int k = 0;
+  for (auto nd : nodes) {
+    cudaGraphNodeType t;
+    CK(cudaGraphNodeGetType(nd, &t));
+    if (t == cudaGraphNodeTypeKernel) k++;
+  }
+  *kernels_per_step = k;
+  return GENGA_OK;
+}
+
 void genga_free(genga_ctx *c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   drop_graph(c);
+  for (int k = 0; k < c->nkev; ++k) cudaEventDestroy(c->kev[k]);
   c->mem.release();
   if (c->own) cudaStreamDestroy(c->own);
   delete c;

@@ -59,6 +59,9 @@ _SIGS = {
     "genga_encounters": (C.c_int, [_V, C.c_int, _I, C.c_int, _I]),
     "genga_status": (C.c_int, [_V, _I, C.POINTER(C.c_longlong)]),
     "genga_free": (None, [_V]),
+    "genga_set_profiling": (C.c_int, [_V, C.c_int]),
+    "genga_kick_time": (C.c_int, [_V, C.POINTER(C.c_float), _I]),
+    "genga_launch_count": (C.c_int, [_V, _I]),
     "genga_phase_rcrit": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
                                     _V, _V, _V, _V, _V, _V]),
     "genga_phase_kick": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_int, C.c_int, _V, _V, _V, _V, _V,
@@ -206,6 +209,22 @@ def genga_status(ctx):
     det = (C.c_longlong * 8)()
     _check(lib().genga_status(ctx, C.byref(code), det), "genga_status")
     return code.value, dict(zip(COUNTER_NAMES, list(det)))
+
+
+def genga_set_profiling(ctx, on=True):
+    return _check(lib().genga_set_profiling(ctx, int(bool(on))), "genga_set_profiling")
+
+
+def genga_kick_time(ctx):
+    ms, n = C.c_float(0.0), C.c_int(0)
+    _check(lib().genga_kick_time(ctx, C.byref(ms), C.byref(n)), "genga_kick_time")
+    return ms.value, n.value
+
+
+def genga_launch_count(ctx):
+    k = C.c_int(0)
+    _check(lib().genga_launch_count(ctx, C.byref(k)), "genga_launch_count")
+    return k.value
 
 
 def genga_free(ctx):

@@ -127,3 +127,17 @@ def test_set_state_matches_fresh_start():
     sb, sc = b.state(), c.state()
     np.testing.assert_allclose(sb["x"], sc["x"], rtol=1e-14, atol=1e-16)
     np.testing.assert_allclose(sb["v"], sc["v"], rtol=1e-14, atol=1e-18)
+
+
+def test_profiling_events_and_launch_count():
+    d = ics.disk32(9)
+    m, R, x, v = with_central(d)
+    for order, nsub in ((2, 1), (4, 3)):
+        s = genga.Genga(m, R, x, v, d["G"], d["dt"], order)
+        genga.genga_set_profiling(s.ctx, True)
+        assert genga.genga_launch_count(s.ctx) == 4 + 6 * nsub
+        s.step(2)
+        ms, n = genga.genga_kick_time(s.ctx)
+        assert n == nsub and 0.0 < ms < 50.0
+        genga.genga_set_profiling(s.ctx, False)
+        s.close()
