@@ -39,6 +39,7 @@ extern "C" {
 #define GENGA_ECUDA (-2)       /* a CUDA runtime call failed */
 #define GENGA_ENOMEM (-3)      /* device allocation failed */
 #define GENGA_ECAP (-4)        /* output capacity too small */
+#define GENGA_ESIZE (-5)       /* n above the fixed maximum of genga_kick_noalloc (1024) */
 
 /* status bits accumulated on the device (genga_status); none of them stops the integration */
 #define GENGA_ST_KEPLER_FALLBACK 1   /* a Kepler solve did not converge; that body went to BS */
@@ -179,6 +180,24 @@ int genga_phase_bs(int n, double G, double m0, double tau, double bs_eps, int bs
 /* Energy of the live bodies in democratic coordinates (x heliocentric, v barycentric), (Sect. 4.1). */
 int genga_phase_energy(int n, double G, double m0, const double *m, const int *alive,
                        const double *x, const double *v, double *E, void *stream);
+
+/* Kick phase that allocates no device memory (the paper has no counterpart: this is a service for
+ * callers that cannot allocate). cudaMalloc may block on the driver's allocator and cudaFree
+ * synchronises the whole device, so code in a latency-critical loop, or in a process whose device
+ * memory belongs to another allocator or to a fixed budget, cannot use the entry points above,
+ * which allocate temporaries. This one computes exactly what genga_phase_kick computes (same
+ * kernels) but keeps its scratch in one file-scope device array of about 1.9 MB, which every GPU
+ * that loads the library holds until the process exits.
+ *   n <= 1024 (GENGA_ESIZE otherwise); m, alive, x, rc, a, cand as in genga_phase_kick (device);
+ *   ncand is a DEVICE int that receives the candidate count (nothing is copied to the host).
+ * Only cudaMemsetAsync, kernel launches and a device-to-device copy are enqueued on stream. The
+ * first call on a device looks up the scratch array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture. All calls share the one
+ * array, which keeps the last call's contents: calls that overlap on the GPU (different streams
+ * without ordering between them) race on it. */
+int genga_kick_noalloc(int n, double G, double pc, int kmode, int precise_div, const double *m,
+                       const int *alive, const double *x, const double *rc, double *a, int *cand,
+                       int cap, int *ncand, void *stream);
 
 /* Self-test of the device arithmetic helpers: out[i] = f(in[i]) for which = 0: x^(-1/2),
  * 1: x^(-3/2), 2: 1/x (the refined estimates used by the kernels). Device arrays. */

@@ -22,6 +22,7 @@ GENGA_EINVAL = -1
 GENGA_ECUDA = -2
 GENGA_ENOMEM = -3
 GENGA_ECAP = -4
+GENGA_ESIZE = -5
 ST_KEPLER_FALLBACK = 1
 ST_BS_FAILED = 2
 ST_REUSE_FULLKICK = 4
@@ -74,6 +75,8 @@ _SIGS = {
                                  C.c_int, C.c_int, C.c_int, _V, _V, _V, _V, _V, _V, _V, _V, _D, _V]),
     "genga_phase_energy": (C.c_int, [C.c_int, C.c_double, C.c_double, _V, _V, _V, _V, _D, _V]),
     "genga_phase_mathcheck": (C.c_int, [C.c_int, C.c_int, _V, _V, _V]),
+    "genga_kick_noalloc": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_int, C.c_int, _V, _V, _V, _V, _V,
+                                     _V, C.c_int, _V, _V]),
 }
 
 EXPORTED = sorted(_SIGS)
@@ -286,6 +289,13 @@ def genga_phase_energy(n, G, m0, m, alive, x, v, stream=None):
 def genga_phase_mathcheck(n, which, inp, out, stream=None):
     return _check(lib().genga_phase_mathcheck(n, which, _tp(inp), _tp(out), _stream_ptr(stream)),
                   "genga_phase_mathcheck")
+
+
+def genga_kick_noalloc(n, G, pc, kmode, precise_div, m, alive, x, rc, a, cand, cap, ncand, stream=None):
+    """The kick phase without device allocation; ncand is a one-element int32 CUDA tensor."""
+    return _check(lib().genga_kick_noalloc(n, G, pc, kmode, precise_div, _tp(m), _tp(alive), _tp(x), _tp(rc), _tp(a),
+                                           _tp(cand), int(cap), _tp(ncand), _stream_ptr(stream)),
+                  "genga_kick_noalloc")
 
 
 # ------------------------------------------------------------------------------------ convenience
