@@ -186,7 +186,7 @@ int genga_phase_energy(int n, double G, double m0, const double *m, const int *a
  * synchronises the whole device, so code in a latency-critical loop, or in a process whose device
  * memory belongs to another allocator or to a fixed budget, cannot use the entry points above,
  * which allocate temporaries. This one computes exactly what genga_phase_kick computes (same
- * kernels) but keeps its scratch in one file-scope device array of about 1.9 MB, which every GPU
+ * kernels) but keeps its scratch in one file-scope device array of about 2 MB, which every GPU
  * that loads the library holds until the process exits.
  *   n <= 1024 (GENGA_ESIZE otherwise); m, alive, x, rc, a, cand as in genga_phase_kick (device);
  *   ncand is a DEVICE int that receives the candidate count (nothing is copied to the host).

@@ -61,6 +61,7 @@ bool alloc_sim(Sim &S, DevMem &mem, int n, int nsub) {
   S.part = mem.get<double>(nt * nt * 2 * 96);
   S.pkick = mem.get<double>(nt * 3); S.pfin = mem.get<double>(nt * 3);
   S.cbm = mem.get<unsigned>(np * W); S.rowany = mem.get<unsigned>(W);
+  S.ccnt = mem.get<int>(np); S.clist = mem.get<int>(np * CCAP);
   S.ebm = mem.get<unsigned>((size_t)nsub * np * W);
   const size_t ecap = np * (np - 1) / 2 + 1;
   S.edges = mem.get<int>(2 * ecap); S.nedges = mem.get<int>(1);
@@ -161,6 +162,7 @@ int first_kick(genga_ctx *c) {
   cudaStream_t st = c->stream;
   CK(cudaMemsetAsync(S.cbm, 0, (size_t)S.npad * S.W * sizeof(unsigned), st));
   CK(cudaMemsetAsync(S.rowany, 0, (size_t)S.W * sizeof(unsigned), st));
+  CK(cudaMemsetAsync(S.ccnt, 0, (size_t)S.npad * sizeof(int), st));
   CK(cudaMemsetAsync(S.flags, 0, 4 * sizeof(int), st));
   CK(cudaMemsetAsync(S.nedges, 0, sizeof(int), st));
   CK(cudaMemsetAsync(S.nfail, 0, sizeof(int), st));

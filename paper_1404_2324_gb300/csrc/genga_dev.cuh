@@ -19,6 +19,7 @@ constexpr int BS_LEVELS = 8;      // Bulirsch-Stoer levels, substep sequence n_k
 constexpr int BS_GMAX = 32;       // largest encounter group integrated in one CTA
 constexpr int BS_THREADS = 256;
 constexpr int NCOUNTERS = 8;
+constexpr int CCAP = 32;          // candidate-list slots per body (more: the bitmap row is scanned)
 constexpr double PARK = 1.0e8;    // ghosts are parked this far out (AU) so no pair ever sees them
 
 // status bits (mirrors genga.h)
@@ -51,6 +52,7 @@ struct Sim {
   double *part;                  // [nt * nt * 2 * 3 * 32] kick partial sums
   double *pkick, *pfin;          // [nt * 3] per-tile momentum partials
   unsigned *cbm, *rowany;        // candidate bitmap [npad * W], row-nonempty bits [W]
+  int *ccnt, *clist;             // per-body candidate count [npad] and partners [npad * CCAP]
   unsigned *ebm;                 // encounter bitmaps [nsub * npad * W] (upper triangle)
   int *edges, *nedges;           // edge list [2 * cap] and its count
   int *fail, *nfail;             // Kepler-fallback bodies [npad] and count

@@ -125,6 +125,9 @@ __global__ void __launch_bounds__(128) k_kick(Sim S, DevParams P) {
         atomicOr(&S.cbm[(size_t)j * W + (i >> 5)], 1u << (i & 31));
         atomicOr(&S.rowany[i >> 5], 1u << (i & 31));
         atomicOr(&S.rowany[j >> 5], 1u << (j & 31));
+        const int ki = atomicAdd(&S.ccnt[i], 1), kj = atomicAdd(&S.ccnt[j], 1);
+        if (ki < CCAP) S.clist[i * CCAP + ki] = j;
+        if (kj < CCAP) S.clist[j * CCAP + kj] = i;
         atomicAdd((unsigned long long *)&S.counters[C_CAND], 1ULL);
       }
       const double fi = gj * w3, fj = gi * w3;
@@ -183,6 +186,18 @@ __device__ double near_accel(const Sim &S, const DevParams &P, int i, int c) {
   return acc;
 }
 
+// Component c of the near-pair pull of partner j on body i with the current critical radii
+// (refined inverse square root; the changeover weight as in the kick).
+__device__ __forceinline__ double near_term(const Sim &S, const DevParams &P, int i, int j, int c) {
+  const int np = S.npad;
+  const double dx = S.x[j] - S.x[i], dy = S.x[np + j] - S.x[np + i], dz = S.x[2 * np + j] - S.x[2 * np + i];
+  const double r2 = __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx)));
+  const double yr = rsqrt_refined(r2);
+  double wB = 1.0, wA;
+  if (dbits(r2) < umax64(S.rcsq[i], S.rcsq[j])) changeover_w(r2 * yr, pmin(S.A[i], S.A[j]), P.kmode, wB, wA);
+  return S.gm[j] * wB * (yr * yr * yr) * (c == 0 ? dx : (c == 1 ? dy : dz));
+}
+
 // ---------------------------------------------------------------------------------------------
 // Finalisation, one CTA per (body tile, component):
 //   CLOSE: a = sum of the pair partials (far field, stored for reuse) + near pairs;
@@ -193,6 +208,8 @@ __device__ double near_accel(const Sim &S, const DevParams &P, int i, int c) {
 //   OPEN : first kick of a full step with the new critical radii: a = stored far field + near
 //          pairs recomputed (KickA; KickB when there are none), or the full recompute's partials.
 //   INIT : the very first kick: store the far field (and a = far + near into aout if given).
+// The near pairs of the tile's 32 bodies are gathered from the candidate lists, sorted per body,
+// evaluated one per thread across the CTA and summed per body in partner order.
 // Also writes the per-tile momentum of the new velocities for the next Sun drift.
 // ---------------------------------------------------------------------------------------------
 template <int MODE>
@@ -200,7 +217,11 @@ __global__ void __launch_bounds__(128) k_fin(Sim S, DevParams P, double h1, doub
   const int B = blockIdx.x, c = blockIdx.y, wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int np = S.npad, nt = S.nt, i = B * 32 + lane;
   __shared__ double red[4][32];
+  __shared__ int ent[32 * CCAP];
+  __shared__ double contrib[32 * CCAP];
+  __shared__ int off[33];
   const bool use_part = (MODE != FIN_OPEN) || (S.flags[0] != 0);
+  const bool full_open = (MODE == FIN_OPEN) && (S.flags[0] != 0);
   if (use_part) {
     const int nslot = 2 * nt, s0 = wi * nslot / 4, s1 = (wi + 1) * nslot / 4;
     const double *base = S.part + (size_t)B * nt * 2 * 96 + c * 32 + lane;
@@ -208,12 +229,44 @@ __global__ void __launch_bounds__(128) k_fin(Sim S, DevParams P, double h1, doub
     for (int s = s0; s < s1; ++s) acc += base[(size_t)s * 96];
     red[wi][lane] = acc;
   }
+  // gather this tile's candidate partners (warp 0), each body's list sorted ascending
+  int cnt = 0;
+  bool overflow = false;
+  if (wi == 0) {
+    const bool any = !full_open && ((S.rowany[i >> 5] >> (i & 31)) & 1u);
+    cnt = any ? S.ccnt[i] : 0;
+    overflow = cnt > CCAP;
+    if (overflow) cnt = 0;
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int o0 = incl - cnt;
+    off[lane + 1] = incl;
+    if (lane == 0) off[0] = 0;
+    for (int k = 0; k < cnt; ++k) {  // insertion into place: ascending partner index
+      const int j = S.clist[i * CCAP + k];
+      int q = o0 + k;
+      while (q > o0 && ent[q - 1] > j) { ent[q] = ent[q - 1]; q--; }
+      ent[q] = j;
+    }
+  }
+  __syncthreads();
+  const int M = off[32];
+  for (int k = threadIdx.x; k < M; k += 128) {
+    int b = 0;  // owner: the last body whose offset is <= k
+    for (int s = 16; s > 0; s >>= 1)
+      if (b + s <= 32 && off[b + s] <= k) b += s;
+    contrib[k] = near_term(S, P, B * 32 + b, ent[k], c);
+  }
   __syncthreads();
   if (wi != 0) return;
   double a = use_part ? (red[0][lane] + red[1][lane]) + (red[2][lane] + red[3][lane]) : S.afar[c * np + i];
   if (MODE != FIN_OPEN) S.afar[c * np + i] = a;
-  const bool full_open = (MODE == FIN_OPEN) && (S.flags[0] != 0);
-  if (!full_open && ((S.rowany[i >> 5] >> (i & 31)) & 1u)) a += near_accel(S, P, i, c);
+  for (int k = off[lane]; k < off[lane + 1]; ++k) a += contrib[k];
+  if (overflow) a += near_accel(S, P, i, c);
   if (aout) aout[c * np + i] = a;
   if (MODE == FIN_INIT) return;
   const bool alive = S.alive[i] != 0;

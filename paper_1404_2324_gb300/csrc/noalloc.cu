@@ -6,7 +6,7 @@
 // is owned by another allocator (a framework's caching allocator, an embedding application with
 // a fixed memory budget), cannot call entry points that allocate. This variant keeps all of its
 // scratch in one file-scope __device__ array instead: every GPU that loads the library holds it
-// (about 1.9 MB) until the process exits. The caller still provides the inputs and outputs.
+// (about 2 MB) until the process exits. The caller still provides the inputs and outputs.
 #include <cstring>
 
 #include "../../include/genga.h"
@@ -40,7 +40,9 @@ constexpr size_t O_PKICK = O_PART + align256((size_t)NA_NT * NA_NT * 2 * 96 * si
 constexpr size_t O_PFIN = O_PKICK + align256(NA_NT * 3 * sizeof(double));
 constexpr size_t O_CBM = O_PFIN + align256(NA_NT * 3 * sizeof(double));
 constexpr size_t O_ROWANY = O_CBM + align256((size_t)NA_NMAX * NA_W * sizeof(unsigned));
-constexpr size_t O_ITEMS = O_ROWANY + align256(NA_W * sizeof(unsigned));
+constexpr size_t O_CCNT = O_ROWANY + align256(NA_W * sizeof(unsigned));
+constexpr size_t O_CLIST = O_CCNT + align256(NA_NMAX * sizeof(int));
+constexpr size_t O_ITEMS = O_CLIST + align256((size_t)NA_NMAX * CCAP * sizeof(int));
 constexpr size_t O_FLAGS = O_ITEMS + align256((size_t)NA_NT * NA_NT * sizeof(int));
 constexpr size_t O_STATUS = O_FLAGS + align256(4 * sizeof(int));
 constexpr size_t O_COUNTERS = O_STATUS + align256(sizeof(int));
@@ -113,6 +115,7 @@ extern "C" int genga_kick_noalloc(int n, double G, double pc, int kmode, int pre
   S.afar = (double *)(base + O_AFAR); S.part = (double *)(base + O_PART);
   S.pkick = (double *)(base + O_PKICK); S.pfin = (double *)(base + O_PFIN);
   S.cbm = (unsigned *)(base + O_CBM); S.rowany = (unsigned *)(base + O_ROWANY);
+  S.ccnt = (int *)(base + O_CCNT); S.clist = (int *)(base + O_CLIST);
   S.items = (int *)(base + O_ITEMS);
   S.nitems = S.nt * S.nt;
   S.nwarps = S.nitems < 4 * sms ? S.nitems : 4 * sms;
@@ -134,6 +137,7 @@ extern "C" int genga_kick_noalloc(int n, double G, double pc, int kmode, int pre
   // the array keeps the previous call's contents: clear what must start at zero
   if (cudaMemsetAsync(S.cbm, 0, (size_t)S.npad * S.W * sizeof(unsigned), st) != cudaSuccess ||
       cudaMemsetAsync(S.rowany, 0, (size_t)S.W * sizeof(unsigned), st) != cudaSuccess ||
+      cudaMemsetAsync(S.ccnt, 0, (size_t)S.npad * sizeof(int), st) != cudaSuccess ||
       cudaMemsetAsync(S.flags, 0, 4 * sizeof(int), st) != cudaSuccess ||
       cudaMemsetAsync(S.status, 0, sizeof(int), st) != cudaSuccess ||
       cudaMemsetAsync(S.counters, 0, NCOUNTERS * sizeof(long long), st) != cudaSuccess)

@@ -78,37 +78,52 @@ __global__ void __launch_bounds__(128) k_encounter(Sim S, double tau, unsigned *
   const double rci = S.rc[i];
   const bool ai = S.alive[i] != 0;
   int found = 0;
-  for (int w = lane; w < W; w += 32) {
-    unsigned bits = crow[w];
-    crow[w] = 0u;
-    // keep j > i only
-    const int lo = w * 32;
-    if (lo + 31 <= i) bits = 0u;
-    else if (lo <= i) bits &= (i - lo + 1 >= 32) ? 0u : (0xffffffffu << (i - lo + 1));
-    unsigned eb = 0u;
-    while (bits) {
-      const int b = __ffs(bits) - 1;
-      bits &= bits - 1;
-      const int j = lo + b;
-      if (!ai || !S.alive[j]) continue;
-      const double dmin = hermite_min_exact(
-          __dsub_rn(S.x0[j], x0i), __dsub_rn(S.x0[np + j], y0i), __dsub_rn(S.x0[2 * np + j], z0i),
-          __dsub_rn(S.v0[j], u0i), __dsub_rn(S.v0[np + j], v0i), __dsub_rn(S.v0[2 * np + j], w0i),
-          __dsub_rn(S.x[j], x1i), __dsub_rn(S.x[np + j], y1i), __dsub_rn(S.x[2 * np + j], z1i),
-          __dsub_rn(S.v[j], u1i), __dsub_rn(S.v[np + j], v1i), __dsub_rn(S.v[2 * np + j], w1i), tau);
-      const double rcij = pmax(rci, S.rc[j]);
-      if (dmin < __dmul_rn(rcij, rcij)) {
-        eb |= 1u << b;
-        const int e = atomicAdd(S.nedges, 1);
-        S.edges[2 * e] = i;
-        S.edges[2 * e + 1] = j;
-        found++;
+  // Hermite test of candidate (i, j), j > i; sets the pair's bit in this row and lists the edge
+  auto test = [&](int j) {
+    if (!ai || !S.alive[j]) return;
+    const double dmin = hermite_min_exact(
+        __dsub_rn(S.x0[j], x0i), __dsub_rn(S.x0[np + j], y0i), __dsub_rn(S.x0[2 * np + j], z0i),
+        __dsub_rn(S.v0[j], u0i), __dsub_rn(S.v0[np + j], v0i), __dsub_rn(S.v0[2 * np + j], w0i),
+        __dsub_rn(S.x[j], x1i), __dsub_rn(S.x[np + j], y1i), __dsub_rn(S.x[2 * np + j], z1i),
+        __dsub_rn(S.v[j], u1i), __dsub_rn(S.v[np + j], v1i), __dsub_rn(S.v[2 * np + j], w1i), tau);
+    const double rcij = pmax(rci, S.rc[j]);
+    if (dmin < __dmul_rn(rcij, rcij)) {
+      atomicOr(&erow[j >> 5], 1u << (j & 31));
+      const int e = atomicAdd(S.nedges, 1);
+      S.edges[2 * e] = i;
+      S.edges[2 * e + 1] = j;
+      found++;
+    }
+  };
+  for (int w = lane; w < W; w += 32) erow[w] = 0u;
+  __syncwarp();
+  const int cnt = S.ccnt[i];
+  if (cnt <= CCAP) {  // partners from the list, one per lane
+    for (int k = lane; k < cnt; k += 32) {
+      const int j = S.clist[i * CCAP + k];
+      if (j > i) test(j);
+    }
+    for (int w = lane; w < W; w += 32) crow[w] = 0u;
+  } else {  // list overflowed: scan the bitmap row
+    for (int w = lane; w < W; w += 32) {
+      unsigned bits = crow[w];
+      crow[w] = 0u;
+      const int lo = w * 32;
+      if (lo + 31 <= i) bits = 0u;
+      else if (lo <= i) bits &= (i - lo + 1 >= 32) ? 0u : (0xffffffffu << (i - lo + 1));
+      while (bits) {
+        const int b = __ffs(bits) - 1;
+        bits &= bits - 1;
+        test(lo + b);
       }
     }
-    erow[w] = eb;
   }
+  __syncwarp();
   if (found) atomicAdd((unsigned long long *)&S.counters[C_ENC], (unsigned long long)found);
-  if (lane == 0) atomicAnd(&S.rowany[i >> 5], ~(1u << (i & 31)));
+  if (lane == 0) {
+    S.ccnt[i] = 0;
+    atomicAnd(&S.rowany[i >> 5], ~(1u << (i & 31)));
+  }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -236,6 +251,9 @@ __global__ void k_pairs_to_bitmap(Sim S, const int *pairs, int npairs) {
   atomicOr(&S.cbm[(size_t)j * S.W + (i >> 5)], 1u << (i & 31));
   atomicOr(&S.rowany[i >> 5], 1u << (i & 31));
   atomicOr(&S.rowany[j >> 5], 1u << (j & 31));
+  const int ki = atomicAdd(&S.ccnt[i], 1), kj = atomicAdd(&S.ccnt[j], 1);
+  if (ki < CCAP) S.clist[i * CCAP + ki] = j;
+  if (kj < CCAP) S.clist[j * CCAP + kj] = i;
 }
 
 // Pairs (i < j) of a bitmap, ascending, into out[2*cap]; *count receives the total.
