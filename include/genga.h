@@ -133,6 +133,38 @@ int genga_launch_count(genga_ctx *ctx, int *kernels_per_step);
 void genga_free(genga_ctx *ctx);
 
 /* ------------------------------------------------------------------------------------------ */
+/* Batched many-systems mode (Sect. 3.4, multi-simulation mode)                                  */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Creates a context that advances n_sys independent planetary systems together. System s owns the
+ * orbiting bodies offsets[s] .. offsets[s+1]-1 of the flat host arrays (offsets[0] = 0, 1 to 64
+ * bodies per system; the central masses are NOT in the flat arrays) and has central mass m0[s].
+ *   masses, radii [N], x, v [3N] heliocentric (N = offsets[n_sys]); G, dt, order as genga_init.
+ *   steps_per_launch: steps captured in one CUDA-graph launch (genga_step runs whole launches,
+ *   then single steps for the remainder).
+ * Each system follows exactly the single-system step of genga_init (same parameters for all
+ * systems except m0, Sect. 3.4). The kick's tile shape is autotuned here on the first kick
+ * (genga_batch_info reports it). Returns 0 or a negative code; *ctx is NULL on failure. */
+int genga_init_batch(genga_ctx **ctx, int n_sys, const int *offsets, const double *m0, const double *masses,
+                     const double *radii, const double *x, const double *v, double G, double dt, int order,
+                     int steps_per_launch);
+
+/* Autotuned kick shape (threads per body, threads per CTA) and steps per graph launch. */
+int genga_batch_info(genga_ctx *ctx, int *split, int *block, int *steps_per_launch);
+
+/* Flat heliocentric state in the caller's body order (waits for the stream); pointers may be NULL.
+ * x, v [3N]; m, R [N]; alive [N] (0 for a ghost left by a merger). */
+int genga_get_state_batch(genga_ctx *ctx, double *x, double *v, double *m, double *R, int *alive);
+
+/* Replaces positions and velocities of the live bodies (flat, heliocentric, caller order); the next
+ * step recomputes the first kick. */
+int genga_set_state_batch(genga_ctx *ctx, const double *x, const double *v);
+
+/* Energy of every system (E [n_sys], caller order, democratic coordinates, Sect. 4.1) and the
+ * internal energy U of all mergers so far. Waits for the stream. */
+int genga_energy_batch(genga_ctx *ctx, double *E, double *U);
+
+/* ------------------------------------------------------------------------------------------ */
 /* Phase entry points: one step of the method on caller-provided device arrays (SoA layout).     */
 /* n counts orbiting bodies only (no central mass); 1 <= n <= 2048. alive: int [n] (0 = ghost).  */
 /* ------------------------------------------------------------------------------------------ */

@@ -3,6 +3,7 @@
 // state I/O and the phase entry points.
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -138,6 +139,13 @@ struct genga_ctx {
   cudaGraphExec_t gexec = nullptr;
   int bs_grid = 1;
   bool profiling = false;
+  // batched mode
+  bool batched = false;
+  int nsys = 0, b_split = 1, b_block = 128, steps_per_launch = 1;
+  int *perm = nullptr, *sys_user = nullptr;  // device: internal body -> user body, internal system -> user system
+  double *sysE = nullptr;
+  cudaGraphExec_t gexec1 = nullptr;  // one-step graph for remainders
+  cudaGraph_t graph1 = nullptr;
   cudaEvent_t kev[2 * 7] = {};
   int nkev = 0;
   // staging
@@ -151,8 +159,12 @@ namespace {
 void drop_graph(genga_ctx *c) {
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   if (c->graph) cudaGraphDestroy(c->graph);
+  if (c->gexec1) cudaGraphExecDestroy(c->gexec1);
+  if (c->graph1) cudaGraphDestroy(c->graph1);
   c->gexec = nullptr;
   c->graph = nullptr;
+  c->gexec1 = nullptr;
+  c->graph1 = nullptr;
 }
 
 // The first kick (Sect. 2.2): critical radii, far-field accelerations and candidates of the
@@ -171,6 +183,39 @@ int first_kick(genga_ctx *c) {
   launch_fin(S, c->P, FIN_INIT, 0.0, 0.0, nullptr, st);
   CK(cudaGetLastError());
   return GENGA_OK;
+}
+
+// Batched mode: first kick of every system (critical radii, far field, candidates).
+int first_kick_batch(genga_ctx *c) {
+  Sim &S = c->S;
+  cudaStream_t st = c->stream;
+  CK(cudaMemsetAsync(S.sys_flag, 0, (size_t)c->nsys * sizeof(int), st));
+  launch_b_rcrit(S, c->P, std::fabs(c->dt), 0, st);
+  launch_b_kick(S, c->P, FIN_INIT, 0.0, 0.0, c->b_split, c->b_block, st);
+  CK(cudaGetLastError());
+  return GENGA_OK;
+}
+
+// Batched mode: one full step of every system (the same sequence as the single system, with
+// per-system momenta and central masses).
+void enqueue_step_batch(genga_ctx *c, cudaStream_t st) {
+  const Sim &S = c->S;
+  const DevParams &P = c->P;
+  const double dt = c->dt;
+  launch_b_rcrit(S, P, std::fabs(dt), 1, st);
+  launch_b_kick(S, P, FIN_OPEN, 0.5 * c->w[0] * dt, 0.0, c->b_split, c->b_block, st);
+  for (int j = 0; j < c->nsub; ++j) {
+    const double tau = c->w[j] * dt;
+    launch_b_momentum(S, S.sys_ppost, st);
+    launch_b_drift(S, P, tau, 0.5 * tau, j > 0 ? 0.5 * c->w[j - 1] * dt : 0.0, j == 0, st);
+    launch_b_encounter(S, tau, st);
+    launch_b_group(S, st);
+    launch_bs(S, P, tau, c->bs_grid, st);
+    launch_b_momentum(S, S.sys_ppre, st);
+    const double h2 = (j + 1 < c->nsub) ? 0.5 * c->w[j + 1] * dt : 0.0;
+    launch_b_kick(S, P, FIN_CLOSE, 0.5 * tau, h2, c->b_split, c->b_block, st);
+  }
+  launch_b_hc(S, 0.5 * c->w[c->nsub - 1] * dt, st);
 }
 
 // One full step (Sect. 2.2 second list, composed per Sect. 2.3).
@@ -209,13 +254,24 @@ int build_graph(genga_ctx *c) {
     CK(cudaStreamWaitEvent(c->own, ev, 0));
     CK(cudaEventDestroy(ev));
   }
-  CK(cudaStreamBeginCapture(c->own, cudaStreamCaptureModeThreadLocal));
-  enqueue_step(c, c->own);
-  cudaGraph_t g = nullptr;
-  cudaError_t e = cudaStreamEndCapture(c->own, &g);
-  if (e != cudaSuccess || !g) return GENGA_ECUDA;
-  c->graph = g;
-  CK(cudaGraphInstantiate(&c->gexec, c->graph, 0));
+  for (int pass = 0; pass < (c->batched && c->steps_per_launch > 1 ? 2 : 1); ++pass) {
+    const int nst = pass == 0 ? c->steps_per_launch : 1;
+    CK(cudaStreamBeginCapture(c->own, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < nst; ++k) {
+      if (c->batched) enqueue_step_batch(c, c->own);
+      else enqueue_step(c, c->own);
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->own, &g);
+    if (e != cudaSuccess || !g) return GENGA_ECUDA;
+    if (pass == 0) {
+      c->graph = g;
+      CK(cudaGraphInstantiate(&c->gexec, c->graph, 0));
+    } else {
+      c->graph1 = g;
+      CK(cudaGraphInstantiate(&c->gexec1, c->graph1, 0));
+    }
+  }
   return GENGA_OK;
 }
 
@@ -287,6 +343,175 @@ int genga_init(genga_ctx **out, int n, const double *masses, const double *radii
   return GENGA_OK;
 }
 
+int genga_init_batch(genga_ctx **out, int n_sys, const int *offsets, const double *m0, const double *masses,
+                     const double *radii, const double *x, const double *v, double G, double dt, int order,
+                     int steps_per_launch) {
+  if (!out) return GENGA_EINVAL;
+  *out = nullptr;
+  if (n_sys < 1 || !offsets || !m0 || !masses || !radii || !x || !v || steps_per_launch < 1) return GENGA_EINVAL;
+  if (!(G > 0.0) || !std::isfinite(G) || !std::isfinite(dt) || dt == 0.0) return GENGA_EINVAL;
+  if (order != 2 && order != 4 && order != 6) return GENGA_EINVAL;
+  if (offsets[0] != 0) return GENGA_EINVAL;
+  for (int s = 0; s < n_sys; ++s) {
+    const int ns = offsets[s + 1] - offsets[s];
+    if (ns < 1 || ns > 64 || !(m0[s] > 0.0) || !std::isfinite(m0[s])) return GENGA_EINVAL;
+  }
+  const int n = offsets[n_sys];
+  if (n > (1 << 26)) return GENGA_EINVAL;
+  if (!finite_all(masses, n) || !finite_all(radii, n) || !finite_all(x, 3 * (size_t)n) || !finite_all(v, 3 * (size_t)n))
+    return GENGA_EINVAL;
+  for (int i = 0; i < n; ++i)
+    if (masses[i] < 0.0 || radii[i] < 0.0) return GENGA_EINVAL;
+  genga_ctx *c = new genga_ctx();
+  c->batched = true;
+  c->n = n;
+  c->nsys = n_sys;
+  c->steps_per_launch = steps_per_launch;
+  c->G = G; c->m0 = 1.0; c->dt = dt; c->order = order;
+  c->nsub = substep_weights(order, c->w);
+  genga_default_params(&c->prm);
+  c->P = make_params(G, 1.0, c->prm);
+  if (cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking) != cudaSuccess) { delete c; return GENGA_ECUDA; }
+  c->stream = c->own;
+  // internal order: systems by size (largest first), bodies of a system contiguous
+  std::vector<int> order_s(n_sys);
+  for (int s = 0; s < n_sys; ++s) order_s[s] = s;
+  std::stable_sort(order_s.begin(), order_s.end(), [&](int a, int b) {
+    return offsets[a + 1] - offsets[a] > offsets[b + 1] - offsets[b];
+  });
+  std::vector<int> start(n_sys + 1), sys_of, perm, sys_user(n_sys);
+  std::vector<double> sm0(n_sys);
+  start[0] = 0;
+  for (int k = 0; k < n_sys; ++k) {
+    const int s = order_s[k], ns = offsets[s + 1] - offsets[s];
+    start[k + 1] = start[k] + ns;
+    sys_user[k] = s;
+    sm0[k] = m0[s];
+    for (int q = 0; q < ns; ++q) { perm.push_back(offsets[s] + q); sys_of.push_back(k); }
+  }
+  Sim &S = c->S;
+  DevMem &mem = c->mem;
+  memset(&S, 0, sizeof(S));
+  S.n = n;
+  S.npad = ((n + 31) / 32) * 32;
+  S.nt = S.npad / 32;
+  S.W = 0;
+  const size_t np = S.npad;
+  S.x = mem.get<double>(3 * np); S.v = mem.get<double>(3 * np);
+  S.x0 = mem.get<double>(3 * np); S.v0 = mem.get<double>(3 * np);
+  S.m = mem.get<double>(np); S.gm = mem.get<double>(np); S.R = mem.get<double>(np); S.hill = mem.get<double>(np);
+  S.alive = mem.get<int>(np);
+  S.rc = mem.get<double>(np); S.A = mem.get<double>(np);
+  S.T = mem.get<u64>(np); S.rcsq = mem.get<u64>(np);
+  S.afar = mem.get<double>(3 * np);
+  S.fail = mem.get<int>(np); S.nfail = mem.get<int>(1);
+  S.gstart = mem.get<int>(np + 1); S.gmem = mem.get<int>(np); S.ngroups = mem.get<int>(1);
+  S.gsize = mem.get<int>(np + 1); S.gtotal = mem.get<int>(1);
+  S.flags = mem.get<int>(4); S.status = mem.get<int>(1);
+  S.counters = mem.get<long long>(NCOUNTERS); S.U = mem.get<double>(1);
+  S.nsys = n_sys;
+  S.sys_of = mem.get<int>(np); S.sys_start = mem.get<int>(n_sys + 1);
+  S.sys_m0 = mem.get<double>(n_sys); S.sys_ppre = mem.get<double>(3 * (size_t)n_sys);
+  S.sys_ppost = mem.get<double>(3 * (size_t)n_sys); S.sys_flag = mem.get<int>(n_sys);
+  S.bmask = mem.get<u64>(np); S.emask = mem.get<u64>(np);
+  c->perm = mem.get<int>(n); c->sys_user = mem.get<int>(n_sys); c->sysE = mem.get<double>(n_sys);
+  c->sx = mem.get<double>(3 * (size_t)n); c->sv = mem.get<double>(3 * (size_t)n);
+  c->sm = mem.get<double>(n); c->sR = mem.get<double>(n); c->salive = mem.get<int>(n);
+  if (mem.err != cudaSuccess) { genga_free(c); return GENGA_ENOMEM; }
+  c->bs_grid = 2 * num_sms();
+  sys_of.resize(np, 0);  // padding bodies: never alive
+  cudaStream_t st = c->stream;
+  if (cudaMemcpy(S.sys_of, sys_of.data(), np * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(S.sys_start, start.data(), (n_sys + 1) * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(S.sys_m0, sm0.data(), n_sys * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->perm, perm.data(), n * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->sys_user, sys_user.data(), n_sys * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpyAsync(c->sx, x, 3 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(c->sv, v, 3 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(c->sm, masses, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(c->sR, radii, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess) {
+    genga_free(c);
+    return GENGA_ECUDA;
+  }
+  bs_init_constants();
+  launch_b_from_helio(S, c->P, c->perm, c->sx, c->sv, c->sm, c->sR, 0, st);
+  // autotune the kick's tile shape (threads per body x block size) on the first kick
+  launch_b_rcrit(S, c->P, std::fabs(dt), 0, st);
+  {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    const int splits[3] = {1, 2, 4}, blocks[3] = {64, 128, 256};
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        launch_b_kick(S, c->P, FIN_INIT, 0.0, 0.0, splits[a], blocks[b], st);  // warm
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 3; ++r) launch_b_kick(S, c->P, FIN_INIT, 0.0, 0.0, splits[a], blocks[b], st);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; c->b_split = splits[a]; c->b_block = blocks[b]; }
+      }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  int rc = first_kick_batch(c);
+  if (rc == GENGA_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = GENGA_ECUDA;
+  if (rc != GENGA_OK) { genga_free(c); return rc; }
+  *out = c;
+  return GENGA_OK;
+}
+
+int genga_batch_info(genga_ctx *c, int *split, int *block, int *steps_per_launch) {
+  if (!c || !c->batched) return GENGA_EINVAL;
+  if (split) *split = c->b_split;
+  if (block) *block = c->b_block;
+  if (steps_per_launch) *steps_per_launch = c->steps_per_launch;
+  return GENGA_OK;
+}
+
+int genga_get_state_batch(genga_ctx *c, double *x, double *v, double *m, double *R, int *alive) {
+  if (!c || !c->batched) return GENGA_EINVAL;
+  const size_t n = (size_t)c->n;
+  cudaStream_t st = c->stream;
+  launch_b_to_helio(c->S, c->perm, x ? c->sx : nullptr, v ? c->sv : nullptr, m ? c->sm : nullptr,
+                    R ? c->sR : nullptr, alive ? c->salive : nullptr, st);
+  CK(cudaGetLastError());
+  if (x) CK(cudaMemcpyAsync(x, c->sx, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (v) CK(cudaMemcpyAsync(v, c->sv, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (m) CK(cudaMemcpyAsync(m, c->sm, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (R) CK(cudaMemcpyAsync(R, c->sR, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (alive) CK(cudaMemcpyAsync(alive, c->salive, n * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return GENGA_OK;
+}
+
+int genga_set_state_batch(genga_ctx *c, const double *x, const double *v) {
+  if (!c || !c->batched || !x || !v) return GENGA_EINVAL;
+  const size_t n = (size_t)c->n;
+  cudaStream_t st = c->stream;
+  CK(cudaMemcpyAsync(c->sx, x, 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(c->sv, v, 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
+  launch_b_from_helio(c->S, c->P, c->perm, c->sx, c->sv, nullptr, nullptr, 1, st);
+  CK(cudaGetLastError());
+  return first_kick_batch(c);
+}
+
+int genga_energy_batch(genga_ctx *c, double *E, double *U) {
+  if (!c || !c->batched || !E) return GENGA_EINVAL;
+  cudaStream_t st = c->stream;
+  launch_b_energy(c->S, c->P, c->sys_user, c->sysE, st);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(E, c->sysE, (size_t)c->nsys * sizeof(double), cudaMemcpyDeviceToHost, st));
+  double u = 0.0;
+  CK(cudaMemcpyAsync(&u, c->S.U, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (U) *U = u;
+  return GENGA_OK;
+}
+
 int genga_set_params(genga_ctx *c, const genga_params *p) {
   if (!c || !p) return GENGA_EINVAL;
   if (!(p->n1 >= 0.0) || !(p->n2 >= 0.0) || !(p->pc >= 1.0) || !(p->bs_eps > 0.0) || p->bs_kmax < 2 ||
@@ -295,7 +520,7 @@ int genga_set_params(genga_ctx *c, const genga_params *p) {
   c->prm = *p;
   c->P = make_params(c->G, c->m0, c->prm);
   drop_graph(c);
-  return first_kick(c);
+  return c->batched ? first_kick_batch(c) : first_kick(c);
 }
 
 int genga_set_stream(genga_ctx *c, void *stream) {
@@ -312,6 +537,11 @@ int genga_step(genga_ctx *c, int n_steps) {
     int rc = build_graph(c);
     if (rc != GENGA_OK) return rc;
   }
+  if (c->batched && c->steps_per_launch > 1) {
+    for (int k = 0; k < n_steps / c->steps_per_launch; ++k) CK(cudaGraphLaunch(c->gexec, c->stream));
+    for (int k = 0; k < n_steps % c->steps_per_launch; ++k) CK(cudaGraphLaunch(c->gexec1, c->stream));
+    return GENGA_OK;
+  }
   for (int k = 0; k < n_steps; ++k) CK(cudaGraphLaunch(c->gexec, c->stream));
   return GENGA_OK;
 }
@@ -326,6 +556,7 @@ int genga_sync(genga_ctx *c) {
 
 int genga_set_state(genga_ctx *c, const double *x, const double *v) {
   if (!c || !x || !v) return GENGA_EINVAL;
+  if (c->batched) return GENGA_EINVAL;
   const size_t nn = (size_t)c->n + 1;
   cudaStream_t st = c->stream;
   CK(cudaMemcpyAsync(c->sx, x, 3 * nn * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -338,6 +569,7 @@ int genga_set_state(genga_ctx *c, const double *x, const double *v) {
 
 int genga_get_state(genga_ctx *c, double *x, double *v, double *m, double *R, int *alive) {
   if (!c) return GENGA_EINVAL;
+  if (c->batched) return GENGA_EINVAL;
   const size_t nn = (size_t)c->n + 1;
   cudaStream_t st = c->stream;
   launch_to_helio(c->S, c->P, x ? c->sx : nullptr, v ? c->sv : nullptr, m ? c->sm : nullptr,
@@ -354,6 +586,7 @@ int genga_get_state(genga_ctx *c, double *x, double *v, double *m, double *R, in
 
 int genga_energy(genga_ctx *c, double *E, double *U) {
   if (!c) return GENGA_EINVAL;
+  if (c->batched) return GENGA_EINVAL;
   cudaStream_t st = c->stream;
   launch_energy(c->S, c->P, c->scratch, c->sE, st);
   CK(cudaGetLastError());
@@ -367,7 +600,7 @@ int genga_energy(genga_ctx *c, double *E, double *U) {
 }
 
 int genga_encounters(genga_ctx *c, int substep, int *pairs, int cap, int *n_pairs) {
-  if (!c || cap < 0) return GENGA_EINVAL;
+  if (!c || cap < 0 || c->batched) return GENGA_EINVAL;
   if (substep < 0) substep = c->nsub - 1;
   if (substep >= c->nsub) return GENGA_EINVAL;
   cudaStream_t st = c->stream;
@@ -397,7 +630,7 @@ int genga_status(genga_ctx *c, int *code, long long *detail) {
 }
 
 int genga_set_profiling(genga_ctx *c, int on) {
-  if (!c) return GENGA_EINVAL;
+  if (!c || c->batched) return GENGA_EINVAL;
   if (on && !c->nkev) {
     for (int k = 0; k < 2 * c->nsub; ++k) CK(cudaEventCreate(&c->kev[k]));
     c->nkev = 2 * c->nsub;
@@ -437,7 +670,7 @@ int genga_launch_count(genga_ctx *c, int *kernels_per_step) {
     CK(cudaGraphNodeGetType(nd, &t));
     if (t == cudaGraphNodeTypeKernel) k++;
   }
-  *kernels_per_step = k;
+  *kernels_per_step = c->batched ? k / c->steps_per_launch : k;
   return GENGA_OK;
 }
 

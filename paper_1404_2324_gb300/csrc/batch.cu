@@ -1,0 +1,423 @@
+// batch.cu -- many independent planetary systems advanced together (Sect. 3.4, multi-simulation
+// mode), each system with its own central mass and up to 64 orbiting bodies.
+//
+// Bodies of one system are contiguous and systems are ordered by size, so neighbouring lanes
+// loop over partner sets of similar length (the paper masks "false interactions" of a thread
+// that runs past its system; here no lane ever reads another system). Every kick thread (or
+// SPLIT threads, autotuned) sums the whole acceleration of its body, so no partial-sum buffers
+// or atomics are needed. Candidate and encounter partners are per-body 64-bit masks (bit = index
+// within the system). Groups are found by one warp per system and integrated by the
+// Bulirsch-Stoer kernel of the single-system mode, which reads the group's central mass.
+#include "genga_launch.h"
+
+namespace genga {
+
+__device__ __forceinline__ double sys_inv(double m0) { return rcp_refined(m0); }
+
+// Critical radii with the body's own central mass; the kick-reuse test is per system.
+__global__ void k_b_rcrit(Sim S, DevParams P, double tau_abs, int check_reuse) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (check_reuse && i == 0) atomicAdd((unsigned long long *)&S.counters[C_STEPS], 1ULL);
+  if (i >= S.npad) return;
+  const int np = S.npad;
+  if (!S.alive[i]) {
+    S.rc[i] = 0.0; S.A[i] = 0.0; S.T[i] = 0ULL; S.rcsq[i] = 0ULL;
+    return;
+  }
+  const int s = S.sys_of[i];
+  const double mu = P.G * S.sys_m0[s];
+  const double x = S.x[i], y = S.x[np + i], z = S.x[2 * np + i];
+  const double vx = S.v[i], vy = S.v[np + i], vz = S.v[2 * np + i];
+  const double r2 = fma(z, z, fma(y, y, x * x));
+  const double ir = rsqrt_refined(r2);
+  const double v2 = fma(vz, vz, fma(vy, vy, vx * vx));
+  const double inva = fma(2.0, ir, -v2 * sys_inv(mu));
+  const double asemi = is_neg_or_zero(inva) ? r2 * ir : rcp_refined(inva);
+  const double rh = asemi * S.hill[i];
+  const double vabs = (dbits(v2) == 0ULL) ? 0.0 : v2 * rsqrt_refined(v2);
+  const double rc = pmax(P.n1 * rh, (P.n2 * tau_abs) * vabs);
+  if (check_reuse && dbits(rc) > dbits(P.pc * S.rc[i])) {
+    S.sys_flag[s] = 1;
+    atomicOr(S.status, ST_REUSE_FULLKICK);
+    atomicAdd((unsigned long long *)&S.counters[C_FULLKICK], 1ULL);
+  }
+  S.rc[i] = rc;
+  const double t = __dmul_rn(P.pc, rc);
+  S.T[i] = dbits(__dmul_rn(t, t));
+  S.rcsq[i] = dbits(__dmul_rn(rc, rc));
+  S.A[i] = (dbits(rc) == 0ULL) ? 0.0 : rcp_refined(0.9 * rc);
+}
+
+// Kick with the prechecker. CLOSE: far pairs + candidates (recorded) with the current critical
+// radii, v += h1 a (+ h2 a). OPEN: stored far field + candidates with the new radii (or every
+// pair when the system failed the reuse test). INIT: far field and candidates only.
+template <int MODE, int SPLIT>
+__global__ void k_b_kick(Sim S, DevParams P, double h1, double h2) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = t / SPLIT, sub = t % SPLIT;
+  const int np = S.npad;
+  const bool live = i < np && S.alive[i];
+  double fx = 0, fy = 0, fz = 0, nx = 0, ny = 0, nz = 0;
+  u64 mask = 0ULL;
+  bool full = false;
+  if (live) {
+    const int s = S.sys_of[i], st = S.sys_start[s], en = S.sys_start[s + 1];
+    full = (MODE == FIN_OPEN) && S.sys_flag[s] != 0;
+    const double xi = S.x[i], yi = S.x[np + i], zi = S.x[2 * np + i];
+    const u64 Ti = S.T[i], Qi = S.rcsq[i];
+    const double Ai = S.A[i];
+    if (MODE != FIN_OPEN || full) {
+      for (int j = st + sub; j < en; j += SPLIT) {
+        if (j == i || !S.alive[j]) continue;
+        const double dx = S.x[j] - xi, dy = S.x[np + j] - yi, dz = S.x[2 * np + j] - zi;
+        const double r2 = __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx)));
+        const double w3 = rcube_refined(r2);
+        const u64 rb = dbits(r2);
+        const bool cand = (MODE != FIN_OPEN) && rb < umax64(Ti, S.T[j]);
+        double g = S.gm[j] * w3;
+        if (cand || full) {
+          if (rb < umax64(Qi, S.rcsq[j])) {
+            double wB, wA;
+            changeover_w(r2 * rsqrt_refined(r2), pmin(Ai, S.A[j]), P.kmode, wB, wA);
+            g *= wB;
+          }
+          if (cand) mask |= 1ULL << (j - st);
+          nx = fma(g, dx, nx); ny = fma(g, dy, ny); nz = fma(g, dz, nz);
+        } else {
+          fx = fma(g, dx, fx); fy = fma(g, dy, fy); fz = fma(g, dz, fz);
+        }
+      }
+    } else {  // KickA: recompute only the candidates with the new critical radii
+      u64 bits = S.bmask[i];
+      int k = 0;
+      while (bits) {
+        const int b = __ffsll((long long)bits) - 1;
+        bits &= bits - 1;
+        if ((k++ % SPLIT) != sub) continue;
+        const int j = st + b;
+        const double dx = S.x[j] - xi, dy = S.x[np + j] - yi, dz = S.x[2 * np + j] - zi;
+        const double r2 = __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx)));
+        const double yr = rsqrt_refined(r2);
+        double g = S.gm[j] * (yr * yr * yr);
+        if (dbits(r2) < umax64(Qi, S.rcsq[j])) {
+          double wB, wA;
+          changeover_w(r2 * yr, pmin(Ai, S.A[j]), P.kmode, wB, wA);
+          g *= wB;
+        }
+        nx = fma(g, dx, nx); ny = fma(g, dy, ny); nz = fma(g, dz, nz);
+      }
+    }
+  }
+#pragma unroll
+  for (int o = SPLIT >> 1; o > 0; o >>= 1) {
+    fx += __shfl_xor_sync(0xffffffffu, fx, o); fy += __shfl_xor_sync(0xffffffffu, fy, o);
+    fz += __shfl_xor_sync(0xffffffffu, fz, o); nx += __shfl_xor_sync(0xffffffffu, nx, o);
+    ny += __shfl_xor_sync(0xffffffffu, ny, o); nz += __shfl_xor_sync(0xffffffffu, nz, o);
+    mask |= __shfl_xor_sync(0xffffffffu, mask, o);
+  }
+  if (!live || sub != 0) return;
+  double ax, ay, az;
+  if (MODE == FIN_OPEN) {
+    if (full) { ax = nx; ay = ny; az = nz; }
+    else { ax = S.afar[i] + nx; ay = S.afar[np + i] + ny; az = S.afar[2 * np + i] + nz; }
+  } else {
+    S.afar[i] = fx; S.afar[np + i] = fy; S.afar[2 * np + i] = fz;
+    S.bmask[i] = mask;
+    if (mask) atomicAdd((unsigned long long *)&S.counters[C_CAND], (unsigned long long)__popcll(mask));
+    ax = fx + nx; ay = fy + ny; az = fz + nz;
+  }
+  if (MODE == FIN_INIT) return;
+  double vx = fma(h1, ax, S.v[i]), vy = fma(h1, ay, S.v[np + i]), vz = fma(h1, az, S.v[2 * np + i]);
+  if (h2 != 0.0) { vx = fma(h2, ax, vx); vy = fma(h2, ay, vy); vz = fma(h2, az, vz); }
+  S.v[i] = vx; S.v[np + i] = vy; S.v[2 * np + i] = vz;
+}
+
+// Momentum of every system (one warp per system, fixed order).
+__global__ void k_b_momentum(Sim S, double *out) {
+  const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (s >= S.nsys) return;
+  const int st = S.sys_start[s], en = S.sys_start[s + 1], np = S.npad;
+  double p[3] = {0.0, 0.0, 0.0};
+  for (int j = st + lane; j < en; j += 32)
+    if (S.alive[j]) for (int c = 0; c < 3; ++c) p[c] = fma(S.m[j], S.v[c * np + j], p[c]);
+  for (int c = 0; c < 3; ++c) {
+    const double q = warp_sum(p[c]);
+    if (lane == 0) out[3 * s + c] = q;
+  }
+}
+
+// Sun drifts (this substep's first with the momentum after the opening kick, and the previous
+// substep's second with the momentum before its closing kick), then the Kepler drift.
+__global__ void k_b_drift(Sim S, DevParams P, double tau, double h1, double h2, int first) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) { *S.ngroups = 0; *S.gtotal = 0; }
+  if (i >= S.npad) return;
+  const int np = S.npad;
+  const int s = S.sys_of[i];
+  if (first && S.alive[i] && i == S.sys_start[s]) S.sys_flag[s] = 0;  // the opening kick used it
+  S.fail[i] = 0;
+  if (!S.alive[i]) return;
+  const double m0 = S.sys_m0[s], im0 = sys_inv(m0), mu = P.G * m0;
+  double sh[3];
+  for (int c = 0; c < 3; ++c) {
+    double a = h1 * S.sys_ppost[3 * s + c];
+    if (h2 != 0.0) a = fma(h2, S.sys_ppre[3 * s + c], a);
+    sh[c] = a * im0;
+  }
+  double x = S.x[i] + sh[0], y = S.x[np + i] + sh[1], z = S.x[2 * np + i] + sh[2];
+  double vx = S.v[i], vy = S.v[np + i], vz = S.v[2 * np + i];
+  S.x0[i] = x; S.x0[np + i] = y; S.x0[2 * np + i] = z;
+  S.v0[i] = vx; S.v0[np + i] = vy; S.v0[2 * np + i] = vz;
+  int it = 0;
+  if (kepler_drift_dev(mu, 2.0 * mu, x, y, z, vx, vy, vz, tau, P.kepler_maxit, &it)) {
+    atomicOr(S.status, ST_KEPLER_FALLBACK);
+    atomicAdd((unsigned long long *)&S.counters[C_KFALL], 1ULL);
+    S.fail[i] = 1;
+  }
+  S.x[i] = x; S.x[np + i] = y; S.x[2 * np + i] = z;
+  S.v[i] = vx; S.v[np + i] = vy; S.v[2 * np + i] = vz;
+}
+
+// Encounter search over each body's candidates with a larger index (Hermite, bit-exact).
+__global__ void k_b_encounter(Sim S, double tau) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= S.npad) return;
+  const int np = S.npad;
+  u64 em = 0ULL;
+  if (S.alive[i]) {
+    const int s = S.sys_of[i], st = S.sys_start[s], li = i - st;
+    u64 bits = S.bmask[i] & (li >= 63 ? 0ULL : (~0ULL << (li + 1)));
+    const double x0i = S.x0[i], y0i = S.x0[np + i], z0i = S.x0[2 * np + i];
+    const double u0i = S.v0[i], v0i = S.v0[np + i], w0i = S.v0[2 * np + i];
+    const double x1i = S.x[i], y1i = S.x[np + i], z1i = S.x[2 * np + i];
+    const double u1i = S.v[i], v1i = S.v[np + i], w1i = S.v[2 * np + i];
+    while (bits) {
+      const int b = __ffsll((long long)bits) - 1;
+      bits &= bits - 1;
+      const int j = st + b;
+      if (!S.alive[j]) continue;
+      const double dmin = hermite_min_exact(
+          __dsub_rn(S.x0[j], x0i), __dsub_rn(S.x0[np + j], y0i), __dsub_rn(S.x0[2 * np + j], z0i),
+          __dsub_rn(S.v0[j], u0i), __dsub_rn(S.v0[np + j], v0i), __dsub_rn(S.v0[2 * np + j], w0i),
+          __dsub_rn(S.x[j], x1i), __dsub_rn(S.x[np + j], y1i), __dsub_rn(S.x[2 * np + j], z1i),
+          __dsub_rn(S.v[j], u1i), __dsub_rn(S.v[np + j], v1i), __dsub_rn(S.v[2 * np + j], w1i), tau);
+      const double rcij = pmax(S.rc[i], S.rc[j]);
+      if (dmin < __dmul_rn(rcij, rcij)) em |= 1ULL << b;
+    }
+    if (em) atomicAdd((unsigned long long *)&S.counters[C_ENC], (unsigned long long)__popcll(em));
+  }
+  S.emask[i] = em;
+}
+
+// Groups of one system per warp: union of encounter pairs by atomicMin on local links, then
+// each root becomes a group (members ascending) appended to the global group list.
+constexpr int BG_WARPS = 4;
+__global__ void __launch_bounds__(32 * BG_WARPS) k_b_group(Sim S) {
+  __shared__ int link_s[BG_WARPS][64];
+  __shared__ int cnt_s[BG_WARPS][64];
+  __shared__ int pos_s[BG_WARPS][64];
+  __shared__ unsigned char part_s[BG_WARPS][64];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = blockIdx.x * BG_WARPS + w;
+  if (s >= S.nsys) return;  // warp-uniform
+  int *link = link_s[w], *cnt = cnt_s[w], *pos = pos_s[w];
+  unsigned char *part = part_s[w];
+  const int st = S.sys_start[s], n = S.sys_start[s + 1] - st;
+  for (int k = lane; k < 64; k += 32) { link[k] = k; cnt[k] = 0; part[k] = 0; }
+  __syncwarp();
+  for (int k = lane; k < n; k += 32) {
+    const u64 em = S.emask[st + k];
+    if (em || S.fail[st + k]) part[k] = 1;
+    u64 bits = em;
+    while (bits) { const int b = __ffsll((long long)bits) - 1; bits &= bits - 1; part[b] = 1; }
+  }
+  __syncwarp();
+  bool any = false;
+  for (int k = lane; k < n; k += 32) any |= part[k] != 0;
+  if (!__any_sync(0xffffffffu, any)) return;
+  for (int round = 0; round < 64; ++round) {
+    bool ch = false;
+    for (int k = lane; k < n; k += 32) {
+      u64 bits = S.emask[st + k];
+      while (bits) {
+        const int b = __ffsll((long long)bits) - 1;
+        bits &= bits - 1;
+        int ru = k, rv = b;
+        for (int q = 0; q < 66 && link[ru] != ru; ++q) ru = link[ru];
+        for (int q = 0; q < 66 && link[rv] != rv; ++q) rv = link[rv];
+        if (ru != rv) { atomicMin(&link[ru > rv ? ru : rv], ru < rv ? ru : rv); ch = true; }
+      }
+    }
+    __syncwarp();
+    for (int k = lane; k < n; k += 32) {
+      int r = k;
+      for (int q = 0; q < 66 && link[r] != r; ++q) r = link[r];
+      link[k] = r;
+    }
+    __syncwarp();
+    if (!__any_sync(0xffffffffu, ch)) break;
+  }
+  for (int k = lane; k < n; k += 32)
+    if (part[k]) atomicAdd(&cnt[link[k]], 1);
+  __syncwarp();
+  if (lane == 0) {
+    int ng = 0;
+    for (int r = 0; r < n; ++r)
+      if (part[r] && link[r] == r) {
+        const int g = atomicAdd(S.ngroups, 1);
+        const int p = atomicAdd(S.gtotal, cnt[r]);
+        S.gstart[g] = p;
+        S.gsize[g] = cnt[r];
+        pos[r] = p;
+        ng++;
+      }
+    if (ng) atomicAdd((unsigned long long *)&S.counters[C_GROUPS], (unsigned long long)ng);
+  }
+  __syncwarp();
+  for (int k = lane; k < n; k += 32) {
+    if (!part[k]) continue;
+    const int r = link[k];
+    int rank = 0;
+    for (int q = 0; q < k; ++q) rank += (part[q] && link[q] == r) ? 1 : 0;
+    S.gmem[pos[r] + rank] = st + k;
+  }
+}
+
+// Second Sun drift of the last substep.
+__global__ void k_b_hc(Sim S, double h) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= S.npad || !S.alive[i]) return;
+  const int s = S.sys_of[i], np = S.npad;
+  const double im0 = sys_inv(S.sys_m0[s]);
+  for (int c = 0; c < 3; ++c) S.x[c * np + i] = fma(h * S.sys_ppre[3 * s + c], im0, S.x[c * np + i]);
+}
+
+// State conversions (user order <-> internal order, heliocentric <-> democratic), one warp per
+// system. perm[internal body] = user body, sys_user[internal system] = user system.
+__global__ void k_b_from_helio(Sim S, DevParams P, const int *perm, const double *xh, const double *vh,
+                               const double *m_in, const double *R_in, int keep) {
+  const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (s >= S.nsys) return;
+  const int st = S.sys_start[s], en = S.sys_start[s + 1], np = S.npad;
+  const double m0 = S.sys_m0[s];
+  double p[3] = {0.0, 0.0, 0.0}, mt = 0.0;
+  for (int j = st + lane; j < en; j += 32) {
+    const int u = perm[j];
+    const double mj = keep ? (S.alive[j] ? S.m[j] : 0.0) : m_in[u];
+    mt += mj;
+    for (int c = 0; c < 3; ++c) p[c] = fma(mj, vh[3 * u + c], p[c]);
+  }
+  mt = warp_sum(mt);
+  for (int c = 0; c < 3; ++c) p[c] = warp_sum(p[c]) / (m0 + mt);
+  for (int j = st + lane; j < en; j += 32) {
+    const int u = perm[j];
+    if (keep && !S.alive[j]) continue;
+    for (int c = 0; c < 3; ++c) {
+      S.x[c * np + j] = xh[3 * u + c];
+      S.v[c * np + j] = vh[3 * u + c] - p[c];
+    }
+    if (!keep) {
+      const double mj = m_in[u];
+      S.m[j] = mj; S.gm[j] = P.G * mj; S.R[j] = R_in[u];
+      S.hill[j] = cbrt(mj / (3.0 * m0));
+      S.alive[j] = 1;
+    }
+  }
+}
+
+__global__ void k_b_to_helio(Sim S, const int *perm, double *xh, double *vh, double *m_out, double *R_out,
+                             int *alive_out) {
+  const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (s >= S.nsys) return;
+  const int st = S.sys_start[s], en = S.sys_start[s + 1], np = S.npad;
+  const double im0 = 1.0 / S.sys_m0[s];
+  double p[3] = {0.0, 0.0, 0.0};
+  for (int j = st + lane; j < en; j += 32)
+    if (S.alive[j]) for (int c = 0; c < 3; ++c) p[c] = fma(S.m[j], S.v[c * np + j], p[c]);
+  for (int c = 0; c < 3; ++c) p[c] = warp_sum(p[c]);
+  for (int j = st + lane; j < en; j += 32) {
+    const int u = perm[j];
+    for (int c = 0; c < 3; ++c) {
+      if (xh) xh[3 * u + c] = S.x[c * np + j];
+      if (vh) vh[3 * u + c] = fma(p[c], im0, S.v[c * np + j]);
+    }
+    if (m_out) m_out[u] = S.m[j];
+    if (R_out) R_out[u] = S.R[j];
+    if (alive_out) alive_out[u] = S.alive[j];
+  }
+}
+
+// Energy of each system in democratic coordinates (one warp per system, fixed order).
+__global__ void k_b_energy(Sim S, DevParams P, const int *sys_user, double *E) {
+  const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (s >= S.nsys) return;
+  const int st = S.sys_start[s], en = S.sys_start[s + 1], n = en - st, np = S.npad;
+  const double m0 = S.sys_m0[s];
+  double e = 0.0, p[3] = {0.0, 0.0, 0.0};
+  for (int j = st + lane; j < en; j += 32) {
+    if (!S.alive[j]) continue;
+    const double x = S.x[j], y = S.x[np + j], z = S.x[2 * np + j];
+    const double vx = S.v[j], vy = S.v[np + j], vz = S.v[2 * np + j];
+    e += 0.5 * S.m[j] * (vx * vx + vy * vy + vz * vz) - P.G * m0 * S.m[j] / sqrt(x * x + y * y + z * z);
+    p[0] = fma(S.m[j], vx, p[0]); p[1] = fma(S.m[j], vy, p[1]); p[2] = fma(S.m[j], vz, p[2]);
+  }
+  for (int k = lane; k < n * n; k += 32) {
+    const int a = k / n, b = k % n;
+    if (b <= a) continue;
+    const int ja = st + a, jb = st + b;
+    if (!S.alive[ja] || !S.alive[jb]) continue;
+    const double dx = S.x[jb] - S.x[ja], dy = S.x[np + jb] - S.x[np + ja], dz = S.x[2 * np + jb] - S.x[2 * np + ja];
+    e -= P.G * S.m[ja] * S.m[jb] / sqrt(dx * dx + dy * dy + dz * dz);
+  }
+  e = warp_sum(e);
+  for (int c = 0; c < 3; ++c) p[c] = warp_sum(p[c]);
+  if (lane == 0) E[sys_user[s]] = e + (p[0] * p[0] + p[1] * p[1] + p[2] * p[2]) / (2.0 * m0);
+}
+
+// ---------------------------------------------------------------------------------------------
+void launch_b_rcrit(const Sim &S, const DevParams &P, double tau_abs, int check, cudaStream_t st) {
+  k_b_rcrit<<<(S.npad + 127) / 128, 128, 0, st>>>(S, P, tau_abs, check);
+}
+
+template <int MODE>
+static void b_kick_split(const Sim &S, const DevParams &P, double h1, double h2, int split, int block, cudaStream_t st) {
+  const long threads = (long)S.npad * split;
+  const int grid = (int)((threads + block - 1) / block);
+  if (split == 1) k_b_kick<MODE, 1><<<grid, block, 0, st>>>(S, P, h1, h2);
+  else if (split == 2) k_b_kick<MODE, 2><<<grid, block, 0, st>>>(S, P, h1, h2);
+  else k_b_kick<MODE, 4><<<grid, block, 0, st>>>(S, P, h1, h2);
+}
+
+void launch_b_kick(const Sim &S, const DevParams &P, FinMode mode, double h1, double h2, int split, int block,
+                   cudaStream_t st) {
+  if (mode == FIN_CLOSE) b_kick_split<FIN_CLOSE>(S, P, h1, h2, split, block, st);
+  else if (mode == FIN_OPEN) b_kick_split<FIN_OPEN>(S, P, h1, h2, split, block, st);
+  else b_kick_split<FIN_INIT>(S, P, h1, h2, split, block, st);
+}
+
+void launch_b_momentum(const Sim &S, double *out, cudaStream_t st) {
+  k_b_momentum<<<(S.nsys * 32 + 127) / 128, 128, 0, st>>>(S, out);
+}
+void launch_b_drift(const Sim &S, const DevParams &P, double tau, double h1, double h2, int first, cudaStream_t st) {
+  k_b_drift<<<(S.npad + 127) / 128, 128, 0, st>>>(S, P, tau, h1, h2, first);
+}
+void launch_b_encounter(const Sim &S, double tau, cudaStream_t st) {
+  k_b_encounter<<<(S.npad + 127) / 128, 128, 0, st>>>(S, tau);
+}
+void launch_b_group(const Sim &S, cudaStream_t st) {
+  k_b_group<<<(S.nsys + BG_WARPS - 1) / BG_WARPS, 32 * BG_WARPS, 0, st>>>(S);
+}
+void launch_b_hc(const Sim &S, double h, cudaStream_t st) { k_b_hc<<<(S.npad + 127) / 128, 128, 0, st>>>(S, h); }
+void launch_b_from_helio(const Sim &S, const DevParams &P, const int *perm, const double *xh, const double *vh,
+                         const double *m_in, const double *R_in, int keep, cudaStream_t st) {
+  k_b_from_helio<<<(S.nsys * 32 + 127) / 128, 128, 0, st>>>(S, P, perm, xh, vh, m_in, R_in, keep);
+}
+void launch_b_to_helio(const Sim &S, const int *perm, double *xh, double *vh, double *m_out, double *R_out,
+                       int *alive_out, cudaStream_t st) {
+  k_b_to_helio<<<(S.nsys * 32 + 127) / 128, 128, 0, st>>>(S, perm, xh, vh, m_out, R_out, alive_out);
+}
+void launch_b_energy(const Sim &S, const DevParams &P, const int *sys_user, double *E, cudaStream_t st) {
+  k_b_energy<<<(S.nsys * 32 + 127) / 128, 128, 0, st>>>(S, P, sys_user, E);
+}
+
+}  // namespace genga

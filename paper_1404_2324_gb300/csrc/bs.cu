@@ -29,15 +29,16 @@ struct BsShared {
 
 // Acceleration terms of member q assigned to this thread: term p == q is the central mass, any
 // other p the (1 - K)-weighted pull of partner p (H_A, Eq. Ha). Summed over the slot's threads.
-__device__ __forceinline__ void bs_terms(const BsShared &sh, const DevParams &P, int g, int q, int sub, int tps,
-                                         const double (*pos)[3], bool q_alive, double &ax, double &ay, double &az) {
+__device__ __forceinline__ void bs_terms(const BsShared &sh, const DevParams &P, double Gm0, int g, int q, int sub,
+                                         int tps, const double (*pos)[3], bool q_alive, double &ax, double &ay,
+                                         double &az) {
   ax = ay = az = 0.0;
   const double xq = pos[q][0], yq = pos[q][1], zq = pos[q][2];
   if (q_alive) {
     for (int p = sub; p < g; p += tps) {
       if (p == q) {
         const double r2 = fma(zq, zq, fma(yq, yq, xq * xq));
-        const double f = -P.Gm0 * rcube_refined(r2);
+        const double f = -Gm0 * rcube_refined(r2);
         ax = fma(f, xq, ax); ay = fma(f, yq, ay); az = fma(f, zq, az);
       } else if (sh.alive[p]) {
         const double dx = pos[p][0] - xq, dy = pos[p][1] - yq, dz = pos[p][2] - zq;
@@ -65,7 +66,10 @@ __global__ void __launch_bounds__(BS_THREADS) k_bs(Sim S, DevParams P, double ta
   const int np = S.npad;
   const int ngroups = *S.ngroups;
   for (int gidx = blockIdx.x; gidx < ngroups; gidx += gridDim.x) {
-    const int g0 = S.gstart[gidx], g = S.gstart[gidx + 1] - g0;
+    const int g0 = S.gstart[gidx], g = S.gsize ? S.gsize[gidx] : S.gstart[gidx + 1] - g0;
+    // central mass of the group's system (batched mode) or of the single system
+    const double m0 = S.sys_of ? S.sys_m0[S.sys_of[S.gmem[g0]]] : P.m0;
+    const double Gm0 = P.G * m0;
     if (g > BS_GMAX) {
       if (tid == 0) atomicOr(S.status, ST_GROUP_TOO_LARGE);
       continue;  // uniform across the CTA
@@ -111,7 +115,7 @@ __global__ void __launch_bounds__(BS_THREADS) k_bs(Sim S, DevParams P, double ta
       double ax = 0.0, ay = 0.0, az = 0.0;
       // every lane of a warp that holds any active slot takes part (the term sums shuffle across
       // lanes); warps without active slots stay off the FP64 pipe
-      if (__any_sync(0xffffffffu, act)) bs_terms(sh, P, g, q, sub, tps, sh.pos[0][lev], qa, ax, ay, az);
+      if (__any_sync(0xffffffffu, act)) bs_terms(sh, P, Gm0, g, q, sub, tps, sh.pos[0][lev], qa, ax, ay, az);
       if (qa) {
         zB[0] = fma(h, zA[3], zA[0]); zB[1] = fma(h, zA[4], zA[1]); zB[2] = fma(h, zA[5], zA[2]);
         zB[3] = fma(h, ax, zA[3]); zB[4] = fma(h, ay, zA[4]); zB[5] = fma(h, az, zA[5]);
@@ -123,7 +127,7 @@ __global__ void __launch_bounds__(BS_THREADS) k_bs(Sim S, DevParams P, double ta
         const bool lv = act && e <= nk;
         if (lv && sub == 0) for (int c = 0; c < 3; ++c) sh.pos[b][lev][q][c] = zB[c];
         __syncthreads();
-        if (__any_sync(0xffffffffu, lv)) bs_terms(sh, P, g, q, sub, tps, sh.pos[b][lev], qa, ax, ay, az);
+        if (__any_sync(0xffffffffu, lv)) bs_terms(sh, P, Gm0, g, q, sub, tps, sh.pos[b][lev], qa, ax, ay, az);
         if (lv) {
           if (qa) {
             if (e < nk) {
@@ -217,7 +221,7 @@ __global__ void __launch_bounds__(BS_THREADS) k_bs(Sim S, DevParams P, double ta
                 sh.m[s] = M; sh.gm[s] = P.G * M;
                 sh.m[d] = 0.0; sh.gm[d] = 0.0; sh.R[d] = 0.0; sh.alive[d] = 0;
                 const int is = sh.idx[s], idd = sh.idx[d];
-                S.m[is] = M; S.gm[is] = P.G * M; S.R[is] = sh.R[s]; S.hill[is] = cbrt(M / (3.0 * P.m0));
+                S.m[is] = M; S.gm[is] = P.G * M; S.R[is] = sh.R[s]; S.hill[is] = cbrt(M / (3.0 * m0));
                 S.m[idd] = 0.0; S.gm[idd] = 0.0; S.R[idd] = 0.0; S.hill[idd] = 0.0; S.alive[idd] = 0;
                 S.T[idd] = 0ULL; S.rcsq[idd] = 0ULL;
                 atomicAdd((unsigned long long *)&S.counters[C_MERGE], 1ULL);

@@ -58,6 +58,14 @@ struct Sim {
   int *fail, *nfail;             // Kepler-fallback bodies [npad] and count
   int *gstart, *gmem, *ngroups;  // groups
   int *items, nitems, nwarps;    // kick work list
+  // batched mode (independent systems; null in the single-system mode)
+  int nsys;
+  int *sys_of, *sys_start;       // system of each body [npad]; body range of each system [nsys+1]
+  double *sys_m0, *sys_ppre, *sys_ppost;  // central masses [nsys], momenta [3 nsys]
+  int *sys_flag;                 // per system: opening kick must be recomputed in full
+  u64 *bmask, *emask;            // per body: candidate / encounter partners (bit = index in system)
+  int *gsize;                    // batched groups: member count per group (gstart = first member)
+  int *gtotal;                   // batched groups: members placed so far
   int *flags;                    // [0] full opening kick needed
   int *status;                   // status bits
   long long *counters;           // [NCOUNTERS]

@@ -32,6 +32,21 @@ void launch_copy_edges(const Sim &S, const int *pairs, int npairs, cudaStream_t 
 void bs_init_constants();  // once per device, before any capture
 void launch_bs(const Sim &S, const DevParams &P, double tau, int max_groups, cudaStream_t st);
 
+// batch.cu
+void launch_b_rcrit(const Sim &S, const DevParams &P, double tau_abs, int check, cudaStream_t st);
+void launch_b_kick(const Sim &S, const DevParams &P, FinMode mode, double h1, double h2, int split, int block,
+                   cudaStream_t st);
+void launch_b_momentum(const Sim &S, double *out, cudaStream_t st);
+void launch_b_drift(const Sim &S, const DevParams &P, double tau, double h1, double h2, int first, cudaStream_t st);
+void launch_b_encounter(const Sim &S, double tau, cudaStream_t st);
+void launch_b_group(const Sim &S, cudaStream_t st);
+void launch_b_hc(const Sim &S, double h, cudaStream_t st);
+void launch_b_from_helio(const Sim &S, const DevParams &P, const int *perm, const double *xh, const double *vh,
+                         const double *m_in, const double *R_in, int keep, cudaStream_t st);
+void launch_b_to_helio(const Sim &S, const int *perm, double *xh, double *vh, double *m_out, double *R_out,
+                       int *alive_out, cudaStream_t st);
+void launch_b_energy(const Sim &S, const DevParams &P, const int *sys_user, double *E, cudaStream_t st);
+
 // io.cu
 void launch_from_helio(const Sim &S, const DevParams &P, const double *xh, const double *vh,
                        const double *m_in, const double *R_in, cudaStream_t st);

@@ -75,6 +75,12 @@ _SIGS = {
                                  C.c_int, C.c_int, C.c_int, _V, _V, _V, _V, _V, _V, _V, _V, _D, _V]),
     "genga_phase_energy": (C.c_int, [C.c_int, C.c_double, C.c_double, _V, _V, _V, _V, _D, _V]),
     "genga_phase_mathcheck": (C.c_int, [C.c_int, C.c_int, _V, _V, _V]),
+    "genga_init_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, _I, _D, _D, _D, _D, _D, C.c_double,
+                                   C.c_double, C.c_int, C.c_int]),
+    "genga_batch_info": (C.c_int, [_V, _I, _I, _I]),
+    "genga_get_state_batch": (C.c_int, [_V, _D, _D, _D, _D, _I]),
+    "genga_set_state_batch": (C.c_int, [_V, _D, _D]),
+    "genga_energy_batch": (C.c_int, [_V, _D, _D]),
     "genga_kick_noalloc": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_int, C.c_int, _V, _V, _V, _V, _V,
                                      _V, C.c_int, _V, _V]),
 }
@@ -233,6 +239,49 @@ def genga_launch_count(ctx):
 def genga_free(ctx):
     if ctx:
         lib().genga_free(ctx)
+
+
+# ------------------------------------------------------------------------------------ batched mode
+def genga_init_batch(offsets, m0, masses, radii, x, v, G, dt, order=2, steps_per_launch=100):
+    off = np.ascontiguousarray(offsets, np.int32)
+    m0a = np.ascontiguousarray(m0, np.float64)
+    m = np.ascontiguousarray(masses, np.float64)
+    R = np.ascontiguousarray(radii, np.float64)
+    xx = np.ascontiguousarray(x, np.float64).reshape(-1)
+    vv = np.ascontiguousarray(v, np.float64).reshape(-1)
+    nsys = len(off) - 1
+    if len(m0a) != nsys or len(m) != off[-1] or len(xx) != 3 * len(m) or len(vv) != 3 * len(m) or len(R) != len(m):
+        raise GengaError("genga_init_batch: array sizes disagree")
+    h = C.c_void_p()
+    _check(lib().genga_init_batch(C.byref(h), nsys, _ip(off), _dp(m0a), _dp(m), _dp(R), _dp(xx), _dp(vv), float(G),
+                                  float(dt), int(order), int(steps_per_launch)), "genga_init_batch")
+    return h
+
+
+def genga_batch_info(ctx):
+    a, b, c = C.c_int(), C.c_int(), C.c_int()
+    _check(lib().genga_batch_info(ctx, C.byref(a), C.byref(b), C.byref(c)), "genga_batch_info")
+    return a.value, b.value, c.value
+
+
+def genga_get_state_batch(ctx, n):
+    x, v, m, R = np.empty((n, 3)), np.empty((n, 3)), np.empty(n), np.empty(n)
+    alive = np.empty(n, np.int32)
+    _check(lib().genga_get_state_batch(ctx, _dp(x), _dp(v), _dp(m), _dp(R), _ip(alive)), "genga_get_state_batch")
+    return dict(x=x, v=v, m=m, R=R, alive=alive)
+
+
+def genga_set_state_batch(ctx, x, v):
+    xx = np.ascontiguousarray(x, np.float64).reshape(-1)
+    vv = np.ascontiguousarray(v, np.float64).reshape(-1)
+    return _check(lib().genga_set_state_batch(ctx, _dp(xx), _dp(vv)), "genga_set_state_batch")
+
+
+def genga_energy_batch(ctx, nsys):
+    E = np.empty(nsys)
+    U = C.c_double()
+    _check(lib().genga_energy_batch(ctx, _dp(E), C.byref(U)), "genga_energy_batch")
+    return E, U.value
 
 
 # ------------------------------------------------------------------------------------ phases
