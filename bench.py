@@ -149,6 +149,92 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ------------------------------------------------------------------------------------ batched mode
+BATCH_SYSTEMS = 8192
+BATCH_SEED = 4
+
+
+def run_batched(args):
+    """Many-systems mode: 8192 systems of 4..64 bodies (incl. the star), 2nd order, graph launches of
+    100 steps; compared with one system per launch (a main-mode context per system) on a sample."""
+    import torch
+    from paper_1404_2324_gb300 import genga, ics
+    b = ics.batch(BATCH_SEED, n_sys=BATCH_SYSTEMS)
+    n = int(b["offsets"][-1])
+    spl = 100
+    h = genga.genga_init_batch(b["offsets"], b["m0"], b["m"], b["R"], b["x"], b["v"], b["G"], b["dt"], 2, spl)
+    stream = torch.cuda.current_stream()
+    genga.genga_set_stream(h, stream)
+    split, block, _ = genga.genga_batch_info(h)
+    kps = genga.genga_launch_count(h)
+    genga.genga_step(h, spl)  # warm-up launch
+    torch.cuda.synchronize()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = max(1, args.batch_launches)
+    tot = 0.0
+    for _ in range(launches):
+        flush.zero_()
+        ev0.record(stream)
+        genga.genga_step(h, spl)
+        ev1.record(stream)
+        ev1.synchronize()
+        tot += ev0.elapsed_time(ev1)
+    code, cnt = genga.genga_status(h)
+    genga.genga_free(h)
+    value = BATCH_SYSTEMS * spl * launches / (tot * 1e-3)
+    # one system per launch: a main-mode context per system, one step graph per system per step
+    nsamp, ksteps = 64, 20
+    ctxs = []
+    for s in range(nsamp):
+        o0, o1 = b["offsets"][s], b["offsets"][s + 1]
+        m = np.concatenate([[b["m0"][s]], b["m"][o0:o1]])
+        R = np.concatenate([[0.0], b["R"][o0:o1]])
+        x = np.vstack([np.zeros(3), b["x"][o0:o1]])
+        v = np.vstack([np.zeros(3), b["v"][o0:o1]])
+        c = genga.genga_init(m, R, x, v, b["G"], b["dt"], 2)
+        genga.genga_set_stream(c, stream)
+        genga.genga_step(c, 1)
+        ctxs.append(c)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(ksteps):
+        for c in ctxs:
+            genga.genga_step(c, 1)
+    ev1.record(stream)
+    ev1.synchronize()
+    t_one = ev0.elapsed_time(ev1)
+    for c in ctxs:
+        genga.genga_free(c)
+    one_value = nsamp * ksteps / (t_one * 1e-3)
+    return {"metric": "batched system-steps/s", "value": value, "unit": "system-steps/s",
+            "n_systems": BATCH_SYSTEMS, "bodies": n, "steps": spl * launches, "steps_per_launch": spl,
+            "ms_per_launch": tot / launches, "gpu_launches": kps * spl * launches,
+            "autotuned": {"threads_per_body": split, "block": block},
+            "one_system_per_launch": {"value": one_value, "unit": "system-steps/s",
+                                      "sample": f"{nsamp} systems x {ksteps} steps, one step graph per system"},
+            "speedup_vs_one_per_launch": value / one_value, "status": code, "counters": cnt,
+            "config": f"batch recipe seed {BATCH_SEED}: N_s ~ U{{4..64}} incl. star, m log-U[1e-7,1e-4], "
+                      f"a U[0.1,5], e~Rayleigh(0.02), i~Rayleigh(0.01), 2nd order, dt 6 d; L2 flushed per launch"}
+
+
+def batched_cpu_baseline(nsys=24, steps=20):
+    import oracle as O
+    from paper_1404_2324_gb300 import ics
+    b = ics.batch(BATCH_SEED, n_sys=BATCH_SYSTEMS)
+    off = b["offsets"]
+    t0 = time.perf_counter()
+    for s in range(nsys):
+        sl = slice(off[s], off[s + 1])
+        p = O.params(G=b["G"], m0=b["m0"][s], dt=b["dt"], order=2)
+        sim = O.Sim(p, b["m"][sl], b["R"][sl], b["x"][sl], b["v"][sl])
+        sim.step(steps)
+        sim.close()
+    dt = time.perf_counter() - t0
+    return {"value": nsys * steps / dt, "unit": "system-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {nsys} systems of the batch x {steps} steps ({dt:.1f} s)"}
+
+
 # ------------------------------------------------------------------------------------ GPU arm
 def run_gpu(args, rank, world):
     import torch
@@ -257,6 +343,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=500)
     ap.add_argument("--cpu-steps", type=int, default=40, help="oracle steps in the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-launches", type=int, default=5, help="timed 100-step launches of the batched mode")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     if args.warmup < 0 or args.steps < 1:
         ap.error("need --steps >= 1 and --warmup >= 0")
@@ -284,11 +372,15 @@ def main():
         import torch
         torch.distributed.init_process_group("nccl")
     res = run_gpu(args, rank, world)
+    if not args.no_batched:
+        res["batched"] = run_batched(args)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             import oracle
             oracle.build()
             res["cpu_baseline"] = cpu_baseline_entry(args.cpu_steps, 2)
+            if "batched" in res:
+                res["batched"]["cpu_baseline"] = batched_cpu_baseline()
         else:
             res["cpu_baseline"] = None
         print(json.dumps(res))
