@@ -92,6 +92,12 @@ def lib():
                 "orc_get_groups": (C.c_int, [C.c_void_p, C.c_int, _I, _I, C.c_int]),
                 "orc_get_stats": (None, [C.c_void_p, C.POINTER(C.c_longlong), C.c_int]),
                 "orc_get_collisions": (C.c_int, [C.c_void_p, _I, C.c_int]),
+                "orc_tp_create": (C.c_void_p, [C.c_int, _P, _D, _D, _D, _D, C.c_int, _D, _D, _D]),
+                "orc_tp_free": (None, [C.c_void_p]),
+                "orc_tp_step": (C.c_int, [C.c_void_p, C.c_int]),
+                "orc_tp_get_state": (None, [C.c_void_p, _D, _D, _D, _I, _D, _D, _I]),
+                "orc_tp_get_stats": (None, [C.c_void_p, C.POINTER(C.c_longlong), C.c_int]),
+                "orc_tp_get_encounters": (C.c_int, [C.c_void_p, C.c_int, _I, C.c_int]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -320,3 +326,50 @@ class Sim:
         out, po = _iout(2 * max(cnt, 1))
         lib().orc_get_collisions(self._h, po, cnt)
         return out[: 2 * cnt].reshape(-1, 2)
+
+
+TP_STAT_NAMES = ["tp_candidates", "tp_encounters", "tp_bs_steps", "tp_removed", "tp_bs_failed", "u5", "u6", "u7"]
+
+
+class TPSim:
+    """Test-particle mode on the oracle: massive bodies (<= 32) plus massless test particles."""
+
+    def __init__(self, p: Params, m, R, xh, vh, xt, vt, Rt=None):
+        self.p = p
+        self.n = len(m)
+        self.nt = len(xt)
+        m, pm = _d(m); R, pR = _d(R); xh, px = _d(xh); vh, pv = _d(vh)
+        xt, pxt = _d(xt); vt, pvt = _d(vt)
+        Rt, pRt = _d(np.zeros(self.nt) if Rt is None else Rt)
+        self._h = lib().orc_tp_create(self.n, C.byref(p), pm, pR, px, pv, self.nt, pxt, pvt, pRt)
+        if not self._h:
+            raise RuntimeError("orc_tp_create failed")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().orc_tp_free(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def step(self, nsteps=1):
+        return lib().orc_tp_step(self._h, int(nsteps))
+
+    def state(self):
+        n, nt = self.n, self.nt
+        x, px = _dout(3 * n); v, pv = _dout(3 * n); m, pm = _dout(n); al, pa = _iout(n)
+        xt, pxt = _dout(3 * nt); vt, pvt = _dout(3 * nt); at, pat = _iout(nt)
+        lib().orc_tp_get_state(self._h, px, pv, pm, pa, pxt, pvt, pat)
+        return dict(x=x.reshape(n, 3), v=v.reshape(n, 3), m=m, alive=al, xt=xt.reshape(nt, 3), vt=vt.reshape(nt, 3),
+                    tp_alive=at)
+
+    def stats(self):
+        arr = (C.c_longlong * 8)()
+        lib().orc_tp_get_stats(self._h, arr, 8)
+        return dict(zip(TP_STAT_NAMES, list(arr)))
+
+    def encounters(self, substep=-1):
+        cnt = lib().orc_tp_get_encounters(self._h, substep, None, 0)
+        out, po = _iout(2 * max(cnt, 1))
+        lib().orc_tp_get_encounters(self._h, substep, po, cnt)
+        return out[: 2 * cnt].reshape(cnt, 2)

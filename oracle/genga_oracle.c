@@ -885,3 +885,385 @@ int orc_get_collisions(const orc_sim *s, int *pairs, int cap) {
   if (pairs) memcpy(pairs, s->coll, sizeof(int) * 2 * (size_t)c);
   return s->ncoll;
 }
+
+/* ------------------------------------------------------------------------------------------ */
+/* Sect. 3.3: test-particle mode                                                               */
+/* ------------------------------------------------------------------------------------------ */
+/*
+ * Massless test particles (TPs) are perturbed by the massive bodies and never by each other; the
+ * massive bodies evolve exactly as without TPs. Each TP takes the same operators as a massive body
+ * (K-weighted kick with the prechecker, Sun drift with the momentum of the massive bodies, Kepler
+ * drift). A TP whose Hermite test confirms an encounter with a planet is integrated by BS alone,
+ * from its pre-drift state, in the field of m0 and the (1 - W_B)-weighted pull of the planets it
+ * encounters; those planets keep their Kepler-drift ("FG") path, evaluated at the BS times by a
+ * Kepler drift from their pre-drift state (Sect. 3.3: only the TP is updated, the planetesimal
+ * keeps the coordinates from the FG kernel). A TP whose BS substep brings it within R_tp + R_p of
+ * an encountered planet (Hermite contact test) is removed. The TP critical radius has no Hill term
+ * (m = 0): rc_tp = n2 |tau| |v_tp|; a TP-planet pair uses max(rc_tp, rc_p).
+ */
+#define ORC_TP_NSTATS 8
+#define ORC_TP_MAXPL 32
+
+static void tp_rcrit(orc_tpsim *T);
+static void tp_accel(const orc_sim *s, const double *x, double rct, double *a);
+static unsigned tp_precheck(const orc_sim *s, const double *x, double rct);
+
+struct orc_tpsim {
+  orc_sim *s;
+  int nt;
+  double *x, *v, *x0, *v0, *R, *rc, *a;
+  int *alive;
+  unsigned *cmask;               /* per TP: planets flagged by the last closing kick's precheck */
+  double *xp0, *vp0, *xpf, *vpf; /* planets: pre-drift state, Kepler-drift result */
+  int *enc[ORC_MAXSUB], nenc[ORC_MAXSUB];
+  long long stats[ORC_TP_NSTATS]; /* candidates, encounters, BS steps, removed, BS failures */
+};
+
+orc_tpsim *orc_tp_create(int n, const orc_params *p, const double *m, const double *R, const double *xh,
+                         const double *vh, int ntp, const double *xt, const double *vt, const double *Rt) {
+  if (n > ORC_TP_MAXPL) return NULL;
+  orc_tpsim *t = (orc_tpsim *)xcalloc(1, sizeof(orc_tpsim));
+  t->s = orc_create(n, p, m, R, xh, vh);
+  t->nt = ntp;
+  t->x = (double *)xcalloc((size_t)3 * ntp, sizeof(double));
+  t->v = (double *)xcalloc((size_t)3 * ntp, sizeof(double));
+  t->x0 = (double *)xcalloc((size_t)3 * ntp, sizeof(double));
+  t->v0 = (double *)xcalloc((size_t)3 * ntp, sizeof(double));
+  t->a = (double *)xcalloc((size_t)3 * ntp, sizeof(double));
+  t->R = (double *)xcalloc((size_t)ntp, sizeof(double));
+  t->rc = (double *)xcalloc((size_t)ntp, sizeof(double));
+  t->alive = (int *)xcalloc((size_t)ntp, sizeof(int));
+  t->cmask = (unsigned *)xcalloc((size_t)ntp + 1, sizeof(unsigned));
+  t->xp0 = (double *)xcalloc((size_t)3 * n + 3, sizeof(double));
+  t->vp0 = (double *)xcalloc((size_t)3 * n + 3, sizeof(double));
+  t->xpf = (double *)xcalloc((size_t)3 * n + 3, sizeof(double));
+  t->vpf = (double *)xcalloc((size_t)3 * n + 3, sizeof(double));
+  for (int k = 0; k < ORC_MAXSUB; k++) t->enc[k] = (int *)xcalloc((size_t)2 * ntp * (n > 0 ? n : 1) + 2, sizeof(int));
+  /* the TPs' velocities become barycentric with the same shift as the massive bodies (Sect. 2.1):
+   * v_b = v_h - sum m v_h / (m0 + sum m) over the massive bodies */
+  double M = p->m0, Pm[3] = {0, 0, 0};
+  for (int i = 0; i < n; i++) {
+    M += m[i];
+    for (int k = 0; k < 3; k++) Pm[k] += m[i] * vh[3 * i + k];
+  }
+  for (int i = 0; i < ntp; i++) {
+    t->alive[i] = 1;
+    t->R[i] = Rt ? Rt[i] : 0.0;
+    for (int k = 0; k < 3; k++) { t->x[3 * i + k] = xt[3 * i + k]; t->v[3 * i + k] = vt[3 * i + k] - Pm[k] / M; }
+  }
+  /* the very first TP kick: accelerations and candidates with the initial critical radii */
+  tp_rcrit(t);
+  for (int i = 0; i < ntp; i++) {
+    tp_accel(t->s, t->x + 3 * i, t->rc[i], t->a + 3 * i);
+    t->cmask[i] = tp_precheck(t->s, t->x + 3 * i, t->rc[i]);
+  }
+  return t;
+}
+
+void orc_tp_free(orc_tpsim *t) {
+  if (!t) return;
+  orc_free(t->s);
+  free(t->x); free(t->v); free(t->x0); free(t->v0); free(t->a); free(t->R); free(t->rc); free(t->alive);
+  free(t->cmask);
+  free(t->xp0); free(t->vp0); free(t->xpf); free(t->vpf);
+  for (int k = 0; k < ORC_MAXSUB; k++) free(t->enc[k]);
+  free(t);
+}
+
+/* TP precheck (Sect. 2.2): planet j is a candidate if r^2 < max((pc rc_tp)^2, (pc rc_j)^2). */
+static unsigned tp_precheck(const orc_sim *s, const double *x, double rct) {
+  unsigned mask = 0;
+  double t = s->p.pc * rct, Tt = t * t;
+  for (int j = 0; j < s->n; j++) {
+    if (!s->alive[j]) continue;
+    double tj = s->p.pc * s->rc[j], Tj = tj * tj;
+    double T = Tt > Tj ? Tt : Tj;
+    double dx = s->x[3 * j] - x[0], dy = s->x[3 * j + 1] - x[1], dz = s->x[3 * j + 2] - x[2];
+    if (pair_r2(dx, dy, dz) < T) mask |= 1u << j;
+  }
+  return mask;
+}
+
+/* TP acceleration: a = sum_p G m_p W_B(r, max(rc_tp, rc_p)) (x_p - x)/r^3 over the live planets. */
+static void tp_accel(const orc_sim *s, const double *x, double rct, double *a) {
+  const orc_params *p = &s->p;
+  a[0] = a[1] = a[2] = 0.0;
+  for (int j = 0; j < s->n; j++) {
+    if (!s->alive[j]) continue;
+    double dx = s->x[3 * j] - x[0], dy = s->x[3 * j + 1] - x[1], dz = s->x[3 * j + 2] - x[2];
+    double r2 = pair_r2(dx, dy, dz);
+    double rcij = rct > s->rc[j] ? rct : s->rc[j];
+    double w = orc_weight_B(r2, rcij, p->kmode);
+    double r = sqrt(r2);
+    double f = p->G * s->m[j] * w / (r2 * r);
+    a[0] += f * dx; a[1] += f * dy; a[2] += f * dz;
+  }
+}
+
+/* Right-hand side of a TP in BS at time t within the substep: central mass plus the (1 - W_B) pull
+ * of the encountered planets (mask) on their Kepler paths from the pre-drift state. */
+static void tp_bs_deriv(const orc_tpsim *T, unsigned mask, double rct, double t, const double *y, double *dy) {
+  const orc_sim *s = T->s;
+  const orc_params *p = &s->p;
+  dy[0] = y[3]; dy[1] = y[4]; dy[2] = y[5];
+  double r2 = y[0] * y[0] + y[1] * y[1] + y[2] * y[2];
+  double r = sqrt(r2);
+  double f = p->G * p->m0 / (r2 * r);
+  double ax = -f * y[0], ay = -f * y[1], az = -f * y[2];
+  for (int j = 0; j < s->n; j++) {
+    if (!(mask & (1u << j))) continue;
+    double xp[3] = {T->xp0[3 * j], T->xp0[3 * j + 1], T->xp0[3 * j + 2]};
+    double vp[3] = {T->vp0[3 * j], T->vp0[3 * j + 1], T->vp0[3 * j + 2]};
+    orc_kepler_drift(p->G * p->m0, xp, vp, t, p->kepler_maxit, NULL);
+    double dx = xp[0] - y[0], dyy = xp[1] - y[1], dz = xp[2] - y[2];
+    double pr2 = pair_r2(dx, dyy, dz);
+    double rcij = rct > s->rc[j] ? rct : s->rc[j];
+    double wa = 1.0 - orc_weight_B(pr2, rcij, p->kmode);
+    if (wa == 0.0) continue;
+    double pr = sqrt(pr2);
+    double fp = p->G * s->m[j] * wa / (pr2 * pr);
+    ax += fp * dx; ay += fp * dyy; az += fp * dz;
+  }
+  dy[3] = ax; dy[4] = ay; dy[5] = az;
+}
+
+/* BS of one TP over tau from (x, v): the same controller as orc_bs_group (n_k = 2k, Neville in
+ * h^2, error |dx|/|x| and |dv|/|v| <= eps, halving on failure, doubling after acceptance), then the
+ * contact test against the encountered planets after every accepted substep. Returns 0, 1 (removed
+ * by a collision) or ORC_ST_BS_FAILED. */
+static int tp_bs(orc_tpsim *T, int it, unsigned mask, double tau, int *steps) {
+  const orc_sim *s = T->s;
+  const orc_params *p = &s->p;
+  const int kmax = p->bs_kmax;
+  double y[6], yn[6], dy0[6], za[6], zb[6], f[6], sc[6];
+  double Tt[9][9][6];
+  for (int k = 0; k < 3; k++) { y[k] = T->x0[3 * it + k]; y[3 + k] = T->v0[3 * it + k]; }
+  double rct = T->rc[it], t0 = 0.0, remaining = tau, H = tau;
+  int halvings = 0;
+  while (remaining != 0.0) {
+    if (fabs(H) > fabs(remaining)) H = remaining;
+    tp_bs_deriv(T, mask, rct, t0, y, dy0);
+    double sx = sqrt(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]), sv = sqrt(y[3] * y[3] + y[4] * y[4] + y[5] * y[5]);
+    if (!(sx > 0.0)) sx = DBL_MIN;
+    if (!(sv > 0.0)) sv = DBL_MIN;
+    for (int k = 0; k < 3; k++) { sc[k] = sx; sc[3 + k] = sv; }
+    int acc = 0;
+    for (int k = 1; k <= kmax && !acc; k++) {
+      int nk = 2 * k;
+      double h = H / nk;
+      for (int e = 0; e < 6; e++) { za[e] = y[e]; zb[e] = y[e] + h * dy0[e]; }
+      for (int m = 1; m < nk; m++) {
+        tp_bs_deriv(T, mask, rct, t0 + m * h, zb, f);
+        for (int e = 0; e < 6; e++) { double tt = za[e] + 2.0 * h * f[e]; za[e] = zb[e]; zb[e] = tt; }
+      }
+      tp_bs_deriv(T, mask, rct, t0 + H, zb, f);
+      for (int e = 0; e < 6; e++) Tt[k][1][e] = 0.5 * (zb[e] + za[e] + h * f[e]);
+      for (int j = 1; j < k; j++) {
+        double ratio = (double)k / (double)(k - j), fac = ratio * ratio - 1.0;
+        for (int e = 0; e < 6; e++) Tt[k][j + 1][e] = Tt[k][j][e] + (Tt[k][j][e] - Tt[k - 1][j][e]) / fac;
+      }
+      if (k >= 2) {
+        double err = 0.0;
+        for (int e = 0; e < 6; e++) {
+          double ee = fabs(Tt[k][k][e] - Tt[k][k - 1][e]) / sc[e];
+          if (!(ee <= err)) err = ee;
+        }
+        if (err <= p->bs_eps) { memcpy(yn, Tt[k][k], sizeof yn); acc = 1; }
+      }
+    }
+    if (!acc) {
+      H *= 0.5;
+      if (++halvings > p->bs_max_halvings) {
+        for (int k = 0; k < 3; k++) { T->x[3 * it + k] = y[k]; T->v[3 * it + k] = y[3 + k]; }
+        return ORC_ST_BS_FAILED;
+      }
+      continue;
+    }
+    halvings = 0;
+    (*steps)++;
+    if (p->collisions) { /* contact with an encountered planet during the substep: the TP is removed */
+      for (int j = 0; j < s->n; j++) {
+        if (!(mask & (1u << j))) continue;
+        double xa[3] = {T->xp0[3 * j], T->xp0[3 * j + 1], T->xp0[3 * j + 2]}, va[3] = {T->vp0[3 * j], T->vp0[3 * j + 1], T->vp0[3 * j + 2]};
+        double xb[3] = {xa[0], xa[1], xa[2]}, vb[3] = {va[0], va[1], va[2]};
+        orc_kepler_drift(p->G * p->m0, xa, va, t0, p->kepler_maxit, NULL);
+        orc_kepler_drift(p->G * p->m0, xb, vb, t0 + H, p->kepler_maxit, NULL);
+        double dx0[3], dv0[3], dx1[3], dv1[3];
+        for (int e = 0; e < 3; e++) {
+          dx0[e] = xa[e] - y[e]; dv0[e] = va[e] - y[3 + e];
+          dx1[e] = xb[e] - yn[e]; dv1[e] = vb[e] - yn[3 + e];
+        }
+        double rr = T->R[it] + s->R[j];
+        if (orc_hermite_min(dx0, dv0, dx1, dv1, H) < rr * rr) {
+          T->alive[it] = 0;
+          for (int k = 0; k < 3; k++) { T->x[3 * it + k] = yn[k]; T->v[3 * it + k] = yn[3 + k]; }
+          return 1;
+        }
+      }
+    }
+    memcpy(y, yn, sizeof y);
+    t0 += H;
+    remaining -= H;
+    H *= 2.0;
+  }
+  for (int k = 0; k < 3; k++) { T->x[3 * it + k] = y[k]; T->v[3 * it + k] = y[3 + k]; }
+  return 0;
+}
+
+/* One 2nd-order substep of the massive bodies (as in substep()) with the TPs interleaved. */
+static int tp_substep(orc_tpsim *T, int js, double tau) {
+  orc_sim *s = T->s;
+  orc_params *p = &s->p;
+  int n = s->n, st = 0;
+  double h = 0.5 * tau, P[3];
+  /* opening kicks */
+  for (int k = 0; k < 3 * n; k++) s->v[k] += h * s->a[k];
+  for (int k = 0; k < 3 * T->nt; k++) T->v[k] += h * T->a[k];
+  /* Sun drift with the massive momentum */
+  orc_momentum(n, s->m, s->alive, s->v, P);
+  orc_sun_drift(n, p, s->alive, s->x, P, h);
+  orc_sun_drift(T->nt, p, T->alive, T->x, P, h);
+  /* Kepler drifts, keeping the pre-drift states */
+  memcpy(s->x0, s->x, sizeof(double) * 3 * n);
+  memcpy(s->v0, s->v, sizeof(double) * 3 * n);
+  memcpy(T->x0, T->x, sizeof(double) * 3 * T->nt);
+  memcpy(T->v0, T->v, sizeof(double) * 3 * T->nt);
+  double mu = p->G * p->m0;
+  for (int i = 0; i < n; i++) {
+    s->fail[i] = 0;
+    if (!s->alive[i]) continue;
+    int it = 0;
+    if (orc_kepler_drift(mu, s->x + 3 * i, s->v + 3 * i, tau, p->kepler_maxit, &it)) { s->fail[i] = 1; st |= ORC_ST_KEPLER_FALLBACK; }
+  }
+  memcpy(T->xp0, s->x0, sizeof(double) * 3 * n);
+  memcpy(T->vp0, s->v0, sizeof(double) * 3 * n);
+  memcpy(T->xpf, s->x, sizeof(double) * 3 * n);
+  memcpy(T->vpf, s->v, sizeof(double) * 3 * n);
+  int *tfail = (int *)xcalloc((size_t)T->nt + 1, sizeof(int));
+  for (int i = 0; i < T->nt; i++) {
+    if (!T->alive[i]) continue;
+    if (orc_kepler_drift(mu, T->x + 3 * i, T->v + 3 * i, tau, p->kepler_maxit, NULL)) { tfail[i] = 1; st |= ORC_ST_KEPLER_FALLBACK; }
+  }
+  /* massive encounters, groups, BS (as in substep()) */
+  int ne = orc_encounters(n, s->alive, s->x0, s->v0, s->x, s->v, s->rc, s->cand, s->ncand, tau, s->enc[js], s->cand_cap);
+  s->nenc[js] = ne;
+  int ng = orc_groups(n, s->enc[js], ne, s->fail, s->gstart[js], s->gmem[js]);
+  s->ngroups[js] = ng;
+  for (int gk = 0; gk < ng; gk++) {
+    int g0 = s->gstart[js][gk], g = s->gstart[js][gk + 1] - g0;
+    const int *idx = s->gmem[js] + g0;
+    for (int q = 0; q < g; q++)
+      for (int c = 0; c < 3; c++) { s->x[3 * idx[q] + c] = s->x0[3 * idx[q] + c]; s->v[3 * idx[q] + c] = s->v0[3 * idx[q] + c]; }
+    int bs_steps = 0;
+    st |= orc_bs_group(n, p, g, idx, tau, s->m, s->R, s->alive, s->x, s->v, s->rc, &s->U, &s->ncoll, s->coll, s->coll_cap, &bs_steps);
+  }
+  /* TP encounters with planets (candidates from the previous closing TP kick), then BS of every
+   * TP with an encounter (or a failed Kepler solve) */
+  int nte = 0;
+  for (int i = 0; i < T->nt; i++) {
+    if (!T->alive[i]) continue;
+    unsigned emask = 0;
+    for (int j = 0; j < n; j++) {
+      if (!(T->cmask[i] & (1u << j)) || !s->alive[j]) continue;
+      double dx0[3], dv0[3], dx1[3], dv1[3];
+      for (int c = 0; c < 3; c++) {
+        dx0[c] = T->xp0[3 * j + c] - T->x0[3 * i + c];
+        dv0[c] = T->vp0[3 * j + c] - T->v0[3 * i + c];
+        dx1[c] = T->xpf[3 * j + c] - T->x[3 * i + c];
+        dv1[c] = T->vpf[3 * j + c] - T->v[3 * i + c];
+      }
+      double dmin = orc_hermite_min(dx0, dv0, dx1, dv1, tau);
+      double rcij = T->rc[i] > s->rc[j] ? T->rc[i] : s->rc[j];
+      if (dmin < rcij * rcij) {
+        emask |= 1u << j;
+        T->enc[js][2 * nte] = i;
+        T->enc[js][2 * nte + 1] = j;
+        nte++;
+      }
+    }
+    if (emask || tfail[i]) {
+      int steps = 0;
+      int r = tp_bs(T, i, emask, tau, &steps);
+      T->stats[2] += steps;
+      if (r == 1) T->stats[3]++;
+      else if (r) { st |= r; T->stats[4]++; }
+    }
+  }
+  T->nenc[js] = nte;
+  T->stats[1] += nte;
+  free(tfail);
+  /* Sun drift tau/2 */
+  orc_momentum(n, s->m, s->alive, s->v, P);
+  orc_sun_drift(n, p, s->alive, s->x, P, h);
+  orc_sun_drift(T->nt, p, T->alive, T->x, P, h);
+  /* closing kicks */
+  orc_accel_B(n, p, s->m, s->alive, s->x, s->rc, s->a);
+  for (int k = 0; k < 3 * n; k++) s->v[k] += h * s->a[k];
+  s->ncand = orc_precheck(n, p, s->alive, s->x, s->rc, s->cand, s->cand_cap);
+  for (int i = 0; i < T->nt; i++) {
+    T->cmask[i] = 0;
+    if (!T->alive[i]) { T->a[3 * i] = T->a[3 * i + 1] = T->a[3 * i + 2] = 0.0; continue; }
+    tp_accel(s, T->x + 3 * i, T->rc[i], T->a + 3 * i);
+    for (int k = 0; k < 3; k++) T->v[3 * i + k] += h * T->a[3 * i + k];
+    T->cmask[i] = tp_precheck(s, T->x + 3 * i, T->rc[i]);
+    T->stats[0] += __builtin_popcount(T->cmask[i]);
+  }
+  return st;
+}
+
+/* TP critical radii: Eq. rcrit with m = 0 (no Hill term): n2 |tau| |v|. */
+static void tp_rcrit(orc_tpsim *T) {
+  orc_sim *s = T->s;
+  double *m0s = (double *)xcalloc((size_t)T->nt + 1, sizeof(double));
+  orc_rcrit(T->nt, &s->p, fabs(s->p.dt), m0s, T->alive, T->x, T->v, T->rc);
+  free(m0s);
+}
+
+int orc_tp_step(orc_tpsim *T, int nsteps) {
+  orc_sim *s = T->s;
+  int n = s->n, st = 0;
+  double w[ORC_MAXSUB];
+  int nsub = substep_weights(s->p.order, w);
+  for (int it = 0; it < nsteps; it++) {
+    orc_rcrit(n, &s->p, fabs(s->p.dt), s->m, s->alive, s->x, s->v, s->rc);
+    tp_rcrit(T);
+    /* opening kicks of the step: plain definition, all pairs with the new critical radii */
+    orc_accel_B(n, &s->p, s->m, s->alive, s->x, s->rc, s->a);
+    for (int i = 0; i < T->nt; i++) {
+      if (T->alive[i]) tp_accel(s, T->x + 3 * i, T->rc[i], T->a + 3 * i);
+      else T->a[3 * i] = T->a[3 * i + 1] = T->a[3 * i + 2] = 0.0;
+    }
+    for (int js = 0; js < nsub; js++) st |= tp_substep(T, js, w[js] * s->p.dt);
+    s->nsub_last = nsub;
+    s->stats[0]++;
+  }
+  return st;
+}
+
+void orc_tp_get_state(const orc_tpsim *T, double *xh, double *vh, double *m, int *alive, double *xt,
+                      double *vt, int *tp_alive) {
+  const orc_sim *s = T->s;
+  orc_get_state(s, xh, vh, m, NULL, alive);
+  double P[3];
+  orc_momentum(s->n, s->m, s->alive, s->v, P);
+  for (int i = 0; i < T->nt; i++) {
+    for (int k = 0; k < 3; k++) {
+      if (xt) xt[3 * i + k] = T->x[3 * i + k];
+      if (vt) vt[3 * i + k] = T->v[3 * i + k] + P[k] / s->p.m0;
+    }
+    if (tp_alive) tp_alive[i] = T->alive[i];
+  }
+}
+
+void orc_tp_get_stats(const orc_tpsim *T, long long *stats, int nstats) {
+  for (int k = 0; k < nstats && k < ORC_TP_NSTATS; k++) stats[k] = T->stats[k];
+}
+
+int orc_tp_get_encounters(const orc_tpsim *T, int substep_idx, int *pairs, int cap) {
+  if (substep_idx < 0) substep_idx = T->s->nsub_last - 1;
+  if (substep_idx < 0 || substep_idx >= T->s->nsub_last) return 0;
+  int ne = T->nenc[substep_idx];
+  int c = ne < cap ? ne : cap;
+  if (pairs) memcpy(pairs, T->enc[substep_idx], sizeof(int) * 2 * (size_t)c);
+  return ne;
+}

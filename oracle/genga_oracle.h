@@ -91,6 +91,17 @@ int orc_get_groups(const orc_sim *s, int substep, int *group_start, int *members
 void orc_get_stats(const orc_sim *s, long long *stats, int nstats);
 int orc_get_collisions(const orc_sim *s, int *pairs, int cap);
 
+/* ---- test-particle mode (Sect. 3.3): massive bodies as above plus massless test particles ---- */
+typedef struct orc_tpsim orc_tpsim;
+orc_tpsim *orc_tp_create(int n, const orc_params *p, const double *m, const double *R, const double *xh,
+                         const double *vh, int ntp, const double *xt, const double *vt, const double *Rt);
+void orc_tp_free(orc_tpsim *t);
+int orc_tp_step(orc_tpsim *t, int nsteps);
+void orc_tp_get_state(const orc_tpsim *t, double *xh, double *vh, double *m, int *alive, double *xt,
+                      double *vt, int *tp_alive);
+void orc_tp_get_stats(const orc_tpsim *t, long long *stats, int nstats);
+int orc_tp_get_encounters(const orc_tpsim *t, int substep, int *pairs, int cap);
+
 #ifdef __cplusplus
 }
 #endif
