@@ -133,6 +133,28 @@ int genga_launch_count(genga_ctx *ctx, int *kernels_per_step);
 void genga_free(genga_ctx *ctx);
 
 /* ------------------------------------------------------------------------------------------ */
+/* Test-particle mode (Sect. 3.3)                                                                */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Creates a context with up to 32 massive bodies (arguments as genga_init, 2 <= n <= 33 including
+ * the central mass) plus n_tp massless test particles: xt, vt [3 n_tp] heliocentric, Rt [n_tp]
+ * physical radii (NULL: 0). Test particles feel the massive bodies (K-weighted kick with the
+ * prechecker, the massive bodies' Sun drift, Kepler drift); a test particle with a confirmed planet
+ * encounter is integrated alone by Bulirsch-Stoer in the field of m0 and the (1 - K) pull of the
+ * planets it meets, which keep their Kepler paths; one that reaches a planet's surface is removed.
+ * The massive bodies evolve exactly as without test particles (genga_get_state, genga_energy). */
+int genga_init_tp(genga_ctx **ctx, int n, const double *masses, const double *radii, const double *x,
+                  const double *v, double G, double dt, int order, int n_tp, const double *xt,
+                  const double *vt, const double *Rt);
+
+/* Test-particle state (heliocentric, host): xt, vt [3 n_tp], tp_alive [n_tp]; any may be NULL. */
+int genga_get_state_tp(genga_ctx *ctx, double *xt, double *vt, int *tp_alive);
+
+/* Test-particle counters since genga_init_tp: detail[0] (TP, planet) candidate pairs recorded by the
+ * closing kicks, [1] confirmed encounter pairs, [2] accepted BS substeps, [3] particles removed. */
+int genga_tp_status(genga_ctx *ctx, long long *detail);
+
+/* ------------------------------------------------------------------------------------------ */
 /* Batched many-systems mode (Sect. 3.4, multi-simulation mode)                                  */
 /* ------------------------------------------------------------------------------------------ */
 

@@ -144,6 +144,11 @@ struct genga_ctx {
   int nsys = 0, b_split = 1, b_block = 128, steps_per_launch = 1;
   int *perm = nullptr, *sys_user = nullptr;  // device: internal body -> user body, internal system -> user system
   double *sysE = nullptr;
+  // test-particle mode
+  bool tpmode = false;
+  TPSet T{};
+  double *stx = nullptr, *stv = nullptr;
+  int *stalive = nullptr;
   cudaGraphExec_t gexec1 = nullptr;  // one-step graph for remainders
   cudaGraph_t graph1 = nullptr;
   cudaEvent_t kev[2 * 7] = {};
@@ -181,6 +186,10 @@ int first_kick(genga_ctx *c) {
   launch_rcrit(S, c->P, std::fabs(c->dt), 0, st);
   launch_kick(S, c->P, false, c->prm.precise_div != 0, st);
   launch_fin(S, c->P, FIN_INIT, 0.0, 0.0, nullptr, st);
+  if (c->tpmode) {
+    launch_tp_rcrit(c->T, c->P, std::fabs(c->dt), 0, st);
+    launch_tp_kick(S, c->T, c->P, FIN_INIT, 0.0, 0.0, st);
+  }
   CK(cudaGetLastError());
   return GENGA_OK;
 }
@@ -224,23 +233,35 @@ void enqueue_step(genga_ctx *c, cudaStream_t st) {
   const DevParams &P = c->P;
   const bool precise = c->prm.precise_div != 0;
   const double dt = c->dt, inv_m0 = 1.0 / c->m0;
+  const bool tp = c->tpmode;
+  const TPSet &T = c->T;
   launch_rcrit(S, P, std::fabs(dt), 1, st);
+  if (tp) launch_tp_rcrit(T, P, std::fabs(dt), 1, st);
   launch_kick(S, P, true, precise, st);  // runs only if the critical radii grew too much
   launch_fin(S, P, FIN_OPEN, 0.5 * c->w[0] * dt, 0.0, nullptr, st);
+  if (tp) launch_tp_kick(S, T, P, FIN_OPEN, 0.5 * c->w[0] * dt, 0.0, st);
   for (int j = 0; j < c->nsub; ++j) {
     const double tau = c->w[j] * dt;
     const double hcm2 = j > 0 ? 0.5 * c->w[j - 1] * dt * inv_m0 : 0.0;
-    launch_drift(S, P, tau, 0.5 * tau * inv_m0, hcm2, j == 0, st);
+    if (tp) launch_tp_drift(S, T, P, tau, 0.5 * tau * inv_m0, hcm2, st);  // before the massive drift
+    launch_drift(S, P, tau, 0.5 * tau * inv_m0, hcm2, j == 0, st);        // clears the reuse flag
+    if (tp) launch_planet_table(S, T, P, tau, st);
     launch_encounter(S, tau, S.ebm + (size_t)j * S.npad * S.W, st);
     launch_group(S, st);
     launch_bs(S, P, tau, c->bs_grid, st);
+    if (tp) {
+      launch_tp_encounter(S, T, tau, st);
+      launch_tp_bs(S, T, P, tau, c->bs_grid, st);
+    }
     if (c->profiling) cudaEventRecordWithFlags(c->kev[2 * j], st, cudaEventRecordExternal);
     launch_kick(S, P, false, precise, st);
     if (c->profiling) cudaEventRecordWithFlags(c->kev[2 * j + 1], st, cudaEventRecordExternal);
     const double h2 = (j + 1 < c->nsub) ? 0.5 * c->w[j + 1] * dt : 0.0;
     launch_fin(S, P, FIN_CLOSE, 0.5 * tau, h2, nullptr, st);
+    if (tp) launch_tp_kick(S, T, P, FIN_CLOSE, 0.5 * tau, h2, st);
   }
   launch_hc(S, 0.5 * c->w[c->nsub - 1] * dt * inv_m0, st);
+  if (tp) launch_tp_hc(S, T, 0.5 * c->w[c->nsub - 1] * dt * inv_m0, st);
 }
 
 // Captured on the context's own stream (the caller's stream may be the legacy default stream,
@@ -340,6 +361,73 @@ int genga_init(genga_ctx **out, int n, const double *masses, const double *radii
   if (rc == GENGA_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = GENGA_ECUDA;
   if (rc != GENGA_OK) { genga_free(c); return rc; }
   *out = c;
+  return GENGA_OK;
+}
+
+int genga_init_tp(genga_ctx **out, int n, const double *masses, const double *radii, const double *x,
+                  const double *v, double G, double dt, int order, int n_tp, const double *xt, const double *vt,
+                  const double *Rt) {
+  if (!out) return GENGA_EINVAL;
+  *out = nullptr;
+  if (n < 2 || n > 33 || n_tp < 1 || n_tp > (1 << 26) || !xt || !vt) return GENGA_EINVAL;
+  if (!finite_all(xt, 3 * (size_t)n_tp) || !finite_all(vt, 3 * (size_t)n_tp) || (Rt && !finite_all(Rt, n_tp)))
+    return GENGA_EINVAL;
+  genga_ctx *c = nullptr;
+  int rc = genga_init(&c, n, masses, radii, x, v, G, dt, order, GENGA_MODE_MASSIVE);
+  if (rc != GENGA_OK) return rc;
+  TPSet &T = c->T;
+  DevMem &mem = c->mem;
+  T.n = n_tp;
+  T.npad = ((n_tp + 31) / 32) * 32;
+  const size_t np = T.npad;
+  T.x = mem.get<double>(3 * np); T.v = mem.get<double>(3 * np);
+  T.x0 = mem.get<double>(3 * np); T.v0 = mem.get<double>(3 * np);
+  T.R = mem.get<double>(np); T.rc = mem.get<double>(np); T.A = mem.get<double>(np);
+  T.afar = mem.get<double>(3 * np);
+  T.T = mem.get<u64>(np); T.rcsq = mem.get<u64>(np);
+  T.alive = mem.get<int>(np); T.full = mem.get<int>(np); T.fail = mem.get<int>(np);
+  T.cmask = mem.get<unsigned>(np); T.emask = mem.get<unsigned>(np);
+  T.bslist = mem.get<int>(np); T.nbs = mem.get<int>(1);
+  T.ptab = mem.get<double>(32 * 80 * 6);
+  T.counters = mem.get<long long>(8);
+  c->stx = mem.get<double>(3 * (size_t)n_tp); c->stv = mem.get<double>(3 * (size_t)n_tp);
+  c->stalive = mem.get<int>(n_tp);
+  double *sR = mem.get<double>(n_tp);
+  if (mem.err != cudaSuccess) { genga_free(c); return GENGA_ENOMEM; }
+  cudaStream_t st = c->stream;
+  if (cudaMemcpyAsync(c->stx, xt, 3 * (size_t)n_tp * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(c->stv, vt, 3 * (size_t)n_tp * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      (Rt && cudaMemcpyAsync(sR, Rt, (size_t)n_tp * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess)) {
+    genga_free(c);
+    return GENGA_ECUDA;
+  }
+  // the staging arrays still hold the massive heliocentric input of genga_init
+  launch_tp_from_helio(T, n, c->sm, c->sv, c->stx, c->stv, Rt ? sR : nullptr, 0, st);
+  c->tpmode = true;
+  rc = first_kick(c);
+  if (rc == GENGA_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = GENGA_ECUDA;
+  if (rc != GENGA_OK) { genga_free(c); return rc; }
+  *out = c;
+  return GENGA_OK;
+}
+
+int genga_get_state_tp(genga_ctx *c, double *xt, double *vt, int *tp_alive) {
+  if (!c || !c->tpmode) return GENGA_EINVAL;
+  const size_t n = (size_t)c->T.n;
+  cudaStream_t st = c->stream;
+  launch_tp_to_helio(c->S, c->T, c->P, xt ? c->stx : nullptr, vt ? c->stv : nullptr, tp_alive ? c->stalive : nullptr, st);
+  CK(cudaGetLastError());
+  if (xt) CK(cudaMemcpyAsync(xt, c->stx, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (vt) CK(cudaMemcpyAsync(vt, c->stv, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (tp_alive) CK(cudaMemcpyAsync(tp_alive, c->stalive, n * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return GENGA_OK;
+}
+
+int genga_tp_status(genga_ctx *c, long long *detail) {
+  if (!c || !c->tpmode || !detail) return GENGA_EINVAL;
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpy(detail, c->T.counters, 4 * sizeof(long long), cudaMemcpyDeviceToHost));
   return GENGA_OK;
 }
 
@@ -556,7 +644,7 @@ int genga_sync(genga_ctx *c) {
 
 int genga_set_state(genga_ctx *c, const double *x, const double *v) {
   if (!c || !x || !v) return GENGA_EINVAL;
-  if (c->batched) return GENGA_EINVAL;
+  if (c->batched || c->tpmode) return GENGA_EINVAL;
   const size_t nn = (size_t)c->n + 1;
   cudaStream_t st = c->stream;
   CK(cudaMemcpyAsync(c->sx, x, 3 * nn * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -630,7 +718,7 @@ int genga_status(genga_ctx *c, int *code, long long *detail) {
 }
 
 int genga_set_profiling(genga_ctx *c, int on) {
-  if (!c || c->batched) return GENGA_EINVAL;
+  if (!c || c->batched || c->tpmode) return GENGA_EINVAL;
   if (on && !c->nkev) {
     for (int k = 0; k < 2 * c->nsub; ++k) CK(cudaEventCreate(&c->kev[k]));
     c->nkev = 2 * c->nsub;

@@ -72,6 +72,20 @@ struct Sim {
   double *U;                     // internal energy of mergers
 };
 
+// Test particles (massless, perturbed by the massive bodies of a Sim; Sect. 3.3). SoA with
+// leading dimension npad; planet quantities are indexed by the planet's body index (< 32).
+struct TPSet {
+  int n, npad;
+  double *x, *v, *x0, *v0;       // [3 npad]
+  double *R, *rc, *A, *afar;     // [npad] (afar [3 npad])
+  u64 *T, *rcsq;                 // [npad]
+  int *alive, *full, *fail;      // [npad]
+  unsigned *cmask, *emask;       // candidate / encountered planets per TP
+  int *bslist, *nbs;             // TPs that need Bulirsch-Stoer this substep
+  double *ptab;                  // planets' Kepler paths at the BS midpoint times [32 * 80 * 6]
+  long long *counters;           // candidates, encounters, BS steps, removed
+};
+
 // ---------------------------------------------------------------------------------------------
 // Integer-pipe helpers
 // ---------------------------------------------------------------------------------------------

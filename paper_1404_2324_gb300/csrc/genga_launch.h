@@ -47,6 +47,19 @@ void launch_b_to_helio(const Sim &S, const int *perm, double *xh, double *vh, do
                        int *alive_out, cudaStream_t st);
 void launch_b_energy(const Sim &S, const DevParams &P, const int *sys_user, double *E, cudaStream_t st);
 
+// tp.cu
+void launch_tp_rcrit(const TPSet &T, const DevParams &P, double tau_abs, int check, cudaStream_t st);
+void launch_tp_kick(const Sim &S, const TPSet &T, const DevParams &P, FinMode mode, double h1, double h2, cudaStream_t st);
+void launch_tp_drift(const Sim &S, const TPSet &T, const DevParams &P, double tau, double hcm1, double hcm2, cudaStream_t st);
+void launch_planet_table(const Sim &S, const TPSet &T, const DevParams &P, double tau, cudaStream_t st);
+void launch_tp_encounter(const Sim &S, const TPSet &T, double tau, cudaStream_t st);
+void launch_tp_bs(const Sim &S, const TPSet &T, const DevParams &P, double tau, int blocks, cudaStream_t st);
+void launch_tp_hc(const Sim &S, const TPSet &T, double hcm, cudaStream_t st);
+void launch_tp_from_helio(const TPSet &T, int nmass, const double *mh, const double *vmh, const double *xh,
+                          const double *vh, const double *Rh, int keep, cudaStream_t st);
+void launch_tp_to_helio(const Sim &S, const TPSet &T, const DevParams &P, double *xh, double *vh, int *alive,
+                        cudaStream_t st);
+
 // io.cu
 void launch_from_helio(const Sim &S, const DevParams &P, const double *xh, const double *vh,
                        const double *m_in, const double *R_in, cudaStream_t st);

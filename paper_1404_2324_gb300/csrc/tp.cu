@@ -1,0 +1,445 @@
+// tp.cu -- test-particle mode (Sect. 3.3): up to 32 massive bodies (integrated by the
+// single-system kernels) plus massless test particles (TPs) that they perturb.
+//
+// One thread per TP for the kick (K-weighted, prechecker against every planet, planets staged in
+// shared memory), the Sun drift with the massive momentum, the Kepler drift and the Hermite test.
+// A TP with a confirmed planet encounter (or a failed Kepler solve) is integrated alone by
+// Bulirsch-Stoer on one warp, lanes = extrapolation levels, in the field of m0 and the (1 - K)
+// pull of the encountered planets, which move on their Kepler paths from the pre-drift state
+// (Sect. 3.3: only the test particle is updated). The planets' positions at every midpoint time of
+// a full-length BS attempt come from a table computed once per substep; shorter attempts (after a
+// halving) solve Kepler's equation on the fly. A TP whose BS substep reaches a planet's surface is
+// removed.
+#include "genga_launch.h"
+
+namespace genga {
+
+constexpr int TP_MAXPL = 32;
+constexpr int TP_TAB = 80;  // sum over k = 1..8 of (2k + 1) midpoint times
+
+__device__ __forceinline__ int tab_index(int k, int m) { return k * k - 1 + m; }  // level k >= 1, m = 0..2k
+
+// Critical radii of the TPs (Eq. rcrit with m = 0: n2 |tau| |v|) and the per-TP reuse test.
+__global__ void k_tp_rcrit(TPSet T, DevParams P, double tau_abs, int check_reuse) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= T.n) return;
+  if (!T.alive[i]) { T.rc[i] = 0.0; T.A[i] = 0.0; T.T[i] = 0ULL; T.rcsq[i] = 0ULL; return; }
+  const int np = T.npad;
+  const double vx = T.v[i], vy = T.v[np + i], vz = T.v[2 * np + i];
+  const double v2 = fma(vz, vz, fma(vy, vy, vx * vx));
+  const double vabs = (dbits(v2) == 0ULL) ? 0.0 : v2 * rsqrt_refined(v2);
+  const double rc = (P.n2 * tau_abs) * vabs;
+  T.full[i] = check_reuse && dbits(rc) > dbits(P.pc * T.rc[i]);
+  T.rc[i] = rc;
+  const double t = __dmul_rn(P.pc, rc);
+  T.T[i] = dbits(__dmul_rn(t, t));
+  T.rcsq[i] = dbits(__dmul_rn(rc, rc));
+  T.A[i] = (dbits(rc) == 0ULL) ? 0.0 : rcp_refined(0.9 * rc);
+}
+
+struct PlanetSm {
+  double x[TP_MAXPL], y[TP_MAXPL], z[TP_MAXPL], gm[TP_MAXPL], A[TP_MAXPL];
+  u64 T[TP_MAXPL], Q[TP_MAXPL];
+  int alive[TP_MAXPL];
+};
+
+__device__ void load_planets(const Sim &S, PlanetSm &ps) {
+  const int np = S.npad;
+  for (int j = threadIdx.x; j < TP_MAXPL; j += blockDim.x) {
+    const bool ok = j < S.n && S.alive[j];
+    ps.alive[j] = ok;
+    ps.x[j] = ok ? S.x[j] : 0.0; ps.y[j] = ok ? S.x[np + j] : 0.0; ps.z[j] = ok ? S.x[2 * np + j] : 0.0;
+    ps.gm[j] = ok ? S.gm[j] : 0.0; ps.A[j] = ok ? S.A[j] : 0.0;
+    ps.T[j] = ok ? S.T[j] : 0ULL; ps.Q[j] = ok ? S.rcsq[j] : 0ULL;
+  }
+  __syncthreads();
+}
+
+// TP kick. CLOSE / INIT: all planets with the changeover weight, far field stored, candidates
+// recorded. OPEN: stored far field + candidates with the new radii, or every planet when the TP
+// or any planet failed the reuse test.
+template <int MODE>
+__global__ void __launch_bounds__(128) k_tp_kick(Sim S, TPSet T, DevParams P, double h1, double h2) {
+  __shared__ PlanetSm ps;
+  load_planets(S, ps);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= T.n || !T.alive[i]) return;
+  const int np = T.npad, npl = S.n;
+  const double xi = T.x[i], yi = T.x[np + i], zi = T.x[2 * np + i];
+  const u64 Ti = T.T[i], Qi = T.rcsq[i];
+  const double Ai = T.A[i];
+  const bool full = (MODE == FIN_OPEN) && (T.full[i] || S.flags[0]);
+  double fx = 0, fy = 0, fz = 0, nx = 0, ny = 0, nz = 0;
+  unsigned cm = 0u;
+  const unsigned scan = (MODE == FIN_OPEN && !full) ? T.cmask[i] : 0xffffffffu;
+  for (int j = 0; j < npl; ++j) {
+    if (!ps.alive[j] || !((scan >> j) & 1u)) continue;
+    const double dx = ps.x[j] - xi, dy = ps.y[j] - yi, dz = ps.z[j] - zi;
+    const double r2 = __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx)));
+    const double yr = rsqrt_refined(r2);
+    const u64 rb = dbits(r2);
+    double g = ps.gm[j] * (yr * yr * yr);
+    const bool cand = (MODE != FIN_OPEN) && rb < umax64(Ti, ps.T[j]);
+    if (MODE == FIN_OPEN || cand) {
+      if (rb < umax64(Qi, ps.Q[j])) {
+        double wB, wA;
+        changeover_w(r2 * yr, pmin(Ai, ps.A[j]), P.kmode, wB, wA);
+        g *= wB;
+      }
+      if (cand) cm |= 1u << j;
+      nx = fma(g, dx, nx); ny = fma(g, dy, ny); nz = fma(g, dz, nz);
+    } else {
+      fx = fma(g, dx, fx); fy = fma(g, dy, fy); fz = fma(g, dz, fz);
+    }
+  }
+  double ax, ay, az;
+  if (MODE == FIN_OPEN) {
+    if (full) { ax = nx; ay = ny; az = nz; }
+    else { ax = T.afar[i] + nx; ay = T.afar[np + i] + ny; az = T.afar[2 * np + i] + nz; }
+  } else {
+    T.afar[i] = fx; T.afar[np + i] = fy; T.afar[2 * np + i] = fz;
+    T.cmask[i] = cm;
+    if (MODE == FIN_CLOSE && cm) atomicAdd((unsigned long long *)&T.counters[0], (unsigned long long)__popc(cm));
+    ax = fx + nx; ay = fy + ny; az = fz + nz;
+  }
+  if (MODE == FIN_INIT) return;
+  double vx = fma(h1, ax, T.v[i]), vy = fma(h1, ay, T.v[np + i]), vz = fma(h1, az, T.v[2 * np + i]);
+  if (h2 != 0.0) { vx = fma(h2, ax, vx); vy = fma(h2, ay, vy); vz = fma(h2, az, vz); }
+  T.v[i] = vx; T.v[np + i] = vy; T.v[2 * np + i] = vz;
+}
+
+// Sun drifts with the massive momentum (the same partials the massive drift reads), keep the
+// pre-drift state, Kepler drift.
+__global__ void k_tp_drift(Sim S, TPSet T, DevParams P, double tau, double hcm1, double hcm2) {
+  __shared__ double sh[3];
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      double a = 0.0, b = 0.0;
+      for (int t = lane; t < S.nt; t += 32) {
+        a += S.pfin[t * 3 + c];
+        if (hcm2 != 0.0) b += S.pkick[t * 3 + c];
+      }
+      a = warp_sum(a);
+      double v = hcm1 * a;
+      if (hcm2 != 0.0) v = fma(hcm2, warp_sum(b), v);
+      if (lane == 0) sh[c] = v;
+    }
+  }
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) *T.nbs = 0;
+  if (i >= T.n) return;
+  T.fail[i] = 0;
+  if (!T.alive[i]) return;
+  const int np = T.npad;
+  double x = T.x[i] + sh[0], y = T.x[np + i] + sh[1], z = T.x[2 * np + i] + sh[2];
+  double vx = T.v[i], vy = T.v[np + i], vz = T.v[2 * np + i];
+  T.x0[i] = x; T.x0[np + i] = y; T.x0[2 * np + i] = z;
+  T.v0[i] = vx; T.v0[np + i] = vy; T.v0[2 * np + i] = vz;
+  int it = 0;
+  if (kepler_drift_dev(P.G * P.m0, P.mu2, x, y, z, vx, vy, vz, tau, P.kepler_maxit, &it)) {
+    T.fail[i] = 1;
+    atomicOr(S.status, ST_KEPLER_FALLBACK);
+  }
+  T.x[i] = x; T.x[np + i] = y; T.x[2 * np + i] = z;
+  T.v[i] = vx; T.v[np + i] = vy; T.v[2 * np + i] = vz;
+}
+
+// Kepler path of every planet from its pre-drift state at all midpoint times of a full-length BS
+// attempt (t = m * (tau / 2k), and t = tau at m = 2k), plus the drift result itself.
+__global__ void k_planet_table(Sim S, TPSet T, DevParams P, double tau) {
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = id / TP_TAB, e = id % TP_TAB;
+  if (j >= S.n) return;
+  int k = 1;
+  while (tab_index(k + 1, 0) <= e) k++;
+  const int m = e - tab_index(k, 0), nk = 2 * k;
+  const double t = (m == nk) ? tau : (double)m * __ddiv_rn(tau, (double)nk);
+  const int np = S.npad;
+  double x = S.x0[j], y = S.x0[np + j], z = S.x0[2 * np + j];
+  double vx = S.v0[j], vy = S.v0[np + j], vz = S.v0[2 * np + j];
+  if (m > 0) kepler_drift_dev(P.G * P.m0, P.mu2, x, y, z, vx, vy, vz, t, P.kepler_maxit, nullptr);
+  double *o = T.ptab + ((size_t)j * TP_TAB + e) * 6;
+  o[0] = x; o[1] = y; o[2] = z; o[3] = vx; o[4] = vy; o[5] = vz;
+}
+
+// Hermite test of each TP against its candidate planets over the drift (bit-exact with the
+// oracle); TPs with an encounter or a failed Kepler solve are listed for BS.
+__global__ void k_tp_encounter(Sim S, TPSet T, double tau) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= T.n || !T.alive[i]) return;
+  const unsigned cm = T.cmask[i];
+  unsigned em = 0u;
+  if (cm) {
+    const int np = T.npad, pp = S.npad;
+    const double x0 = T.x0[i], y0 = T.x0[np + i], z0 = T.x0[2 * np + i];
+    const double u0 = T.v0[i], v0 = T.v0[np + i], w0 = T.v0[2 * np + i];
+    const double x1 = T.x[i], y1 = T.x[np + i], z1 = T.x[2 * np + i];
+    const double u1 = T.v[i], v1 = T.v[np + i], w1 = T.v[2 * np + i];
+    for (int j = 0; j < S.n; ++j) {
+      if (!((cm >> j) & 1u) || !S.alive[j]) continue;
+      const double *pf = T.ptab + ((size_t)j * TP_TAB + tab_index(1, 2)) * 6;  // t = tau
+      const double dmin = hermite_min_exact(
+          __dsub_rn(S.x0[j], x0), __dsub_rn(S.x0[pp + j], y0), __dsub_rn(S.x0[2 * pp + j], z0),
+          __dsub_rn(S.v0[j], u0), __dsub_rn(S.v0[pp + j], v0), __dsub_rn(S.v0[2 * pp + j], w0),
+          __dsub_rn(pf[0], x1), __dsub_rn(pf[1], y1), __dsub_rn(pf[2], z1),
+          __dsub_rn(pf[3], u1), __dsub_rn(pf[4], v1), __dsub_rn(pf[5], w1), tau);
+      const double rcij = pmax(T.rc[i], S.rc[j]);
+      if (dmin < __dmul_rn(rcij, rcij)) em |= 1u << j;
+    }
+  }
+  T.emask[i] = em;
+  if (em) atomicAdd((unsigned long long *)&T.counters[1], (unsigned long long)__popc(em));
+  if (em || T.fail[i]) T.bslist[atomicAdd(T.nbs, 1)] = i;
+}
+
+// Planet j's position on its Kepler path at time t of the substep (table for full-length
+// attempts, otherwise a Kepler solve from the pre-drift state).
+__device__ __forceinline__ void planet_at(const Sim &S, const TPSet &T, const DevParams &P, int j, bool table,
+                                          int k, int m, double t, double &px, double &py, double &pz) {
+  if (table) {
+    const double *o = T.ptab + ((size_t)j * TP_TAB + tab_index(k, m)) * 6;
+    px = o[0]; py = o[1]; pz = o[2];
+    return;
+  }
+  const int pp = S.npad;
+  double x = S.x0[j], y = S.x0[pp + j], z = S.x0[2 * pp + j];
+  double vx = S.v0[j], vy = S.v0[pp + j], vz = S.v0[2 * pp + j];
+  if (dbits(t) != 0ULL) kepler_drift_dev(P.G * P.m0, P.mu2, x, y, z, vx, vy, vz, t, P.kepler_maxit, nullptr);
+  px = x; py = y; pz = z;
+}
+
+// Acceleration of the TP at y (central + (1 - W_B) pull of the encountered planets at time t).
+__device__ __forceinline__ void tp_force(const Sim &S, const TPSet &T, const DevParams &P, int i, unsigned em, bool table,
+                                         int k, int m, double t, const double *y, double &ax, double &ay, double &az) {
+  const double r2 = fma(y[2], y[2], fma(y[1], y[1], y[0] * y[0]));
+  const double f = -P.Gm0 * rcube_refined(r2);
+  ax = f * y[0]; ay = f * y[1]; az = f * y[2];
+  unsigned bits = em;
+  while (bits) {
+    const int j = __ffs(bits) - 1;
+    bits &= bits - 1;
+    double px, py, pz;
+    planet_at(S, T, P, j, table, k, m, t, px, py, pz);
+    const double dx = px - y[0], dy = py - y[1], dz = pz - y[2];
+    const double pr2 = fma(dz, dz, fma(dy, dy, dx * dx));
+    if (dbits(pr2) >= umax64(T.rcsq[i], S.rcsq[j])) continue;
+    const double yr = rsqrt_refined(pr2);
+    double wB, wA;
+    changeover_w(pr2 * yr, pmin(T.A[i], S.A[j]), P.kmode, wB, wA);
+    const double g = S.gm[j] * wA * (yr * yr * yr);
+    ax = fma(g, dx, ax); ay = fma(g, dy, ay); az = fma(g, dz, az);
+  }
+}
+
+// BS of one listed TP per warp; lane L-1 runs level L (n_L = 2L midpoint substeps).
+__global__ void __launch_bounds__(128) k_tp_bs(Sim S, TPSet T, DevParams P, double tau) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarp = (gridDim.x * blockDim.x) >> 5;
+  const int nlist = *T.nbs;
+  const int np = T.npad;
+  for (int w = warp; w < nlist; w += nwarp) {
+    const int i = T.bslist[w];
+    const unsigned em = T.emask[i];
+    const int L = lane < BS_LEVELS ? lane + 1 : 1, nk = 2 * L;
+    double y[6];
+    for (int c = 0; c < 3; ++c) { y[c] = T.x0[c * np + i]; y[3 + c] = T.v0[c * np + i]; }
+    double t0 = 0.0, rem = tau, H = tau;
+    int halvings = 0, steps = 0, attempts = 0;
+    bool removed = false, failed = false;
+    while (absbits(rem) != 0ULL && ++attempts < 100000) {
+      if (absbits(H) > absbits(rem)) H = rem;
+      const bool table = dbits(t0) == 0ULL && dbits(H) == dbits(tau);
+      const double h = __ddiv_rn(H, (double)nk), h2 = 2.0 * h;
+      double za[6], zb[6], out[6], ax, ay, az;
+      for (int c = 0; c < 6; ++c) za[c] = y[c];
+      tp_force(S, T, P, i, em, table, L, 0, t0, y, ax, ay, az);
+      zb[0] = fma(h, y[3], y[0]); zb[1] = fma(h, y[4], y[1]); zb[2] = fma(h, y[5], y[2]);
+      zb[3] = fma(h, ax, y[3]); zb[4] = fma(h, ay, y[4]); zb[5] = fma(h, az, y[5]);
+      for (int m = 1; m <= nk; ++m) {
+        const double t = (m == nk) ? t0 + H : t0 + m * h;
+        tp_force(S, T, P, i, em, table, L, m, t, zb, ax, ay, az);
+        if (m < nk) {
+          double zn[6];
+          zn[0] = fma(h2, zb[3], za[0]); zn[1] = fma(h2, zb[4], za[1]); zn[2] = fma(h2, zb[5], za[2]);
+          zn[3] = fma(h2, ax, za[3]); zn[4] = fma(h2, ay, za[4]); zn[5] = fma(h2, az, za[5]);
+          for (int c = 0; c < 6; ++c) { za[c] = zb[c]; zb[c] = zn[c]; }
+        } else {
+          out[0] = 0.5 * fma(h, zb[3], zb[0] + za[0]); out[1] = 0.5 * fma(h, zb[4], zb[1] + za[1]);
+          out[2] = 0.5 * fma(h, zb[5], zb[2] + za[2]); out[3] = 0.5 * fma(h, ax, zb[3] + za[3]);
+          out[4] = 0.5 * fma(h, ay, zb[4] + za[4]); out[5] = 0.5 * fma(h, az, zb[5] + za[5]);
+        }
+      }
+      // Neville wavefront across lanes: lane L holds row L
+      double Tk[6], Tm1[6];
+      for (int c = 0; c < 6; ++c) { Tk[c] = out[c]; Tm1[c] = out[c]; }
+      for (int j = 1; j < BS_LEVELS; ++j) {
+        double up[6];
+        for (int c = 0; c < 6; ++c) up[c] = __shfl_up_sync(0xffffffffu, Tk[c], 1);
+        if (lane < BS_LEVELS && L > j) {
+          const double ratio = (double)L / (double)(L - j);
+          const double fi = rcp_refined(ratio * ratio - 1.0);
+          if (j == L - 1) for (int c = 0; c < 6; ++c) Tm1[c] = Tk[c];
+          for (int c = 0; c < 6; ++c) Tk[c] = fma(Tk[c] - up[c], fi, Tk[c]);
+        }
+      }
+      const double sx2 = fma(y[2], y[2], fma(y[1], y[1], y[0] * y[0]));
+      const double sv2 = fma(y[5], y[5], fma(y[4], y[4], y[3] * y[3]));
+      const double isx = rsqrt_refined(sx2), isv = dbits(sv2) == 0ULL ? 4.49423283715579e307 : rsqrt_refined(sv2);
+      u64 em_ = 0ULL;
+      for (int c = 0; c < 6; ++c) em_ = umax64(em_, absbits((Tk[c] - Tm1[c]) * (c < 3 ? isx : isv)));
+      const bool conv = lane < BS_LEVELS && L >= 2 && L <= P.bs_kmax && em_ <= dbits(P.bs_eps);
+      const unsigned bal = __ballot_sync(0xffffffffu, conv);
+      if (!bal) {
+        H *= 0.5;
+        if (++halvings > P.bs_max_halvings) { failed = true; break; }
+        continue;
+      }
+      const int src = __ffs(bal) - 1;
+      double yn[6];
+      for (int c = 0; c < 6; ++c) yn[c] = __shfl_sync(0xffffffffu, Tk[c], src);
+      halvings = 0;
+      steps++;
+      if (P.collisions) {  // contact with an encountered planet during the substep removes the TP
+        bool hit = false;
+        unsigned bits = em;
+        while (bits && !hit) {
+          const int j = __ffs(bits) - 1;
+          bits &= bits - 1;
+          const int pp = S.npad;
+          double xa = S.x0[j], ya = S.x0[pp + j], zaa = S.x0[2 * pp + j], ua = S.v0[j], va = S.v0[pp + j], wa = S.v0[2 * pp + j];
+          double xb = xa, yb = ya, zbb = zaa, ub = ua, vb = va, wb = wa;
+          if (dbits(t0) != 0ULL) kepler_drift_dev(P.G * P.m0, P.mu2, xa, ya, zaa, ua, va, wa, t0, P.kepler_maxit, nullptr);
+          kepler_drift_dev(P.G * P.m0, P.mu2, xb, yb, zbb, ub, vb, wb, t0 + H, P.kepler_maxit, nullptr);
+          const double dmin = hermite_min_exact(
+              __dsub_rn(xa, y[0]), __dsub_rn(ya, y[1]), __dsub_rn(zaa, y[2]),
+              __dsub_rn(ua, y[3]), __dsub_rn(va, y[4]), __dsub_rn(wa, y[5]),
+              __dsub_rn(xb, yn[0]), __dsub_rn(yb, yn[1]), __dsub_rn(zbb, yn[2]),
+              __dsub_rn(ub, yn[3]), __dsub_rn(vb, yn[4]), __dsub_rn(wb, yn[5]), H);
+          const double rr = T.R[i] + S.R[j];
+          hit = dmin < rr * rr;
+        }
+        if (hit) { for (int c = 0; c < 6; ++c) y[c] = yn[c]; removed = true; break; }
+      }
+      for (int c = 0; c < 6; ++c) y[c] = yn[c];
+      t0 += H;
+      rem -= H;
+      H *= 2.0;
+    }
+    if (lane == 0) {
+      for (int c = 0; c < 3; ++c) { T.x[c * np + i] = y[c]; T.v[c * np + i] = y[3 + c]; }
+      if (removed) { T.alive[i] = 0; atomicAdd((unsigned long long *)&T.counters[3], 1ULL); }
+      if (failed) atomicOr(S.status, ST_BS_FAILED);
+      atomicAdd((unsigned long long *)&T.counters[2], (unsigned long long)steps);
+    }
+  }
+}
+
+__global__ void k_tp_hc(Sim S, TPSet T, double hcm) {
+  __shared__ double sh[3];
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      double a = 0.0;
+      for (int t = lane; t < S.nt; t += 32) a += S.pkick[t * 3 + c];
+      a = warp_sum(a);
+      if (lane == 0) sh[c] = hcm * a;
+    }
+  }
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= T.n || !T.alive[i]) return;
+  for (int c = 0; c < 3; ++c) T.x[c * T.npad + i] += sh[c];
+}
+
+// TP input (heliocentric AoS) -> democratic SoA: v_b = v_h - sum m v_h / (m0 + sum m) with the
+// massive bodies' heliocentric input (staged as AoS with the central mass in row 0).
+__global__ void k_tp_from_helio(TPSet T, int nmass, const double *mh, const double *vmh, const double *xh,
+                                const double *vh, const double *Rh, int keep) {
+  __shared__ double vcm[3];
+  if (threadIdx.x == 0) {
+    double M = mh[0], p[3] = {0.0, 0.0, 0.0};
+    for (int j = 1; j < nmass; ++j) {
+      M += mh[j];
+      for (int c = 0; c < 3; ++c) p[c] += mh[j] * vmh[3 * j + c];
+    }
+    for (int c = 0; c < 3; ++c) vcm[c] = p[c] / M;
+  }
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= T.npad) return;
+  const int np = T.npad;
+  if (i >= T.n) {  // padding: never alive
+    T.alive[i] = 0;
+    return;
+  }
+  if (keep && !T.alive[i]) return;
+  for (int c = 0; c < 3; ++c) { T.x[c * np + i] = xh[3 * i + c]; T.v[c * np + i] = vh[3 * i + c] - vcm[c]; }
+  if (!keep) { T.R[i] = Rh ? Rh[i] : 0.0; T.alive[i] = 1; }
+}
+
+// TPs back to heliocentric AoS: v_h = v_b + P/m0 with the massive momentum P.
+__global__ void k_tp_to_helio(Sim S, TPSet T, DevParams P, double *xh, double *vh, int *alive) {
+  __shared__ double pm[3];
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x, np = S.npad;
+    for (int c = 0; c < 3; ++c) {
+      double a = 0.0;
+      for (int j = lane; j < S.n; j += 32)
+        if (S.alive[j]) a = fma(S.m[j], S.v[c * np + j], a);
+      a = warp_sum(a);
+      if (lane == 0) pm[c] = a;
+    }
+  }
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= T.n) return;
+  const int np = T.npad;
+  for (int c = 0; c < 3; ++c) {
+    if (xh) xh[3 * i + c] = T.x[c * np + i];
+    if (vh) vh[3 * i + c] = fma(pm[c], P.inv_m0, T.v[c * np + i]);
+  }
+  if (alive) alive[i] = T.alive[i];
+}
+
+// ---------------------------------------------------------------------------------------------
+static int grid_of(int n, int b) { return (n + b - 1) / b; }
+
+void launch_tp_from_helio(const TPSet &T, int nmass, const double *mh, const double *vmh, const double *xh,
+                          const double *vh, const double *Rh, int keep, cudaStream_t st) {
+  k_tp_from_helio<<<grid_of(T.npad, 256), 256, 0, st>>>(T, nmass, mh, vmh, xh, vh, Rh, keep);
+}
+void launch_tp_to_helio(const Sim &S, const TPSet &T, const DevParams &P, double *xh, double *vh, int *alive,
+                        cudaStream_t st) {
+  k_tp_to_helio<<<grid_of(T.n, 256), 256, 0, st>>>(S, T, P, xh, vh, alive);
+}
+
+void launch_tp_rcrit(const TPSet &T, const DevParams &P, double tau_abs, int check, cudaStream_t st) {
+  k_tp_rcrit<<<grid_of(T.n, 256), 256, 0, st>>>(T, P, tau_abs, check);
+}
+void launch_tp_kick(const Sim &S, const TPSet &T, const DevParams &P, FinMode mode, double h1, double h2, cudaStream_t st) {
+  const int g = grid_of(T.n, 128);
+  if (mode == FIN_CLOSE) k_tp_kick<FIN_CLOSE><<<g, 128, 0, st>>>(S, T, P, h1, h2);
+  else if (mode == FIN_OPEN) k_tp_kick<FIN_OPEN><<<g, 128, 0, st>>>(S, T, P, h1, h2);
+  else k_tp_kick<FIN_INIT><<<g, 128, 0, st>>>(S, T, P, h1, h2);
+}
+void launch_tp_drift(const Sim &S, const TPSet &T, const DevParams &P, double tau, double hcm1, double hcm2, cudaStream_t st) {
+  k_tp_drift<<<grid_of(T.n, 128), 128, 0, st>>>(S, T, P, tau, hcm1, hcm2);
+}
+void launch_planet_table(const Sim &S, const TPSet &T, const DevParams &P, double tau, cudaStream_t st) {
+  k_planet_table<<<grid_of(S.n * TP_TAB, 32), 32, 0, st>>>(S, T, P, tau);
+}
+void launch_tp_encounter(const Sim &S, const TPSet &T, double tau, cudaStream_t st) {
+  k_tp_encounter<<<grid_of(T.n, 128), 128, 0, st>>>(S, T, tau);
+}
+void launch_tp_bs(const Sim &S, const TPSet &T, const DevParams &P, double tau, int blocks, cudaStream_t st) {
+  k_tp_bs<<<blocks, 128, 0, st>>>(S, T, P, tau);
+}
+void launch_tp_hc(const Sim &S, const TPSet &T, double hcm, cudaStream_t st) {
+  k_tp_hc<<<grid_of(T.n, 128), 128, 0, st>>>(S, T, hcm);
+}
+
+}  // namespace genga

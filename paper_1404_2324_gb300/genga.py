@@ -75,6 +75,10 @@ _SIGS = {
                                  C.c_int, C.c_int, C.c_int, _V, _V, _V, _V, _V, _V, _V, _V, _D, _V]),
     "genga_phase_energy": (C.c_int, [C.c_int, C.c_double, C.c_double, _V, _V, _V, _V, _D, _V]),
     "genga_phase_mathcheck": (C.c_int, [C.c_int, C.c_int, _V, _V, _V]),
+    "genga_init_tp": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, _D, _D, _D, _D, C.c_double, C.c_double, C.c_int,
+                                C.c_int, _D, _D, _D]),
+    "genga_get_state_tp": (C.c_int, [_V, _D, _D, _I]),
+    "genga_tp_status": (C.c_int, [_V, C.POINTER(C.c_longlong)]),
     "genga_init_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, _I, _D, _D, _D, _D, _D, C.c_double,
                                    C.c_double, C.c_int, C.c_int]),
     "genga_batch_info": (C.c_int, [_V, _I, _I, _I]),
@@ -239,6 +243,34 @@ def genga_launch_count(ctx):
 def genga_free(ctx):
     if ctx:
         lib().genga_free(ctx)
+
+
+# ------------------------------------------------------------------------------------ test particles
+def genga_init_tp(masses, radii, x, v, G, dt, order, xt, vt, Rt=None):
+    m = np.ascontiguousarray(masses, np.float64)
+    R = np.ascontiguousarray(radii, np.float64)
+    xx = np.ascontiguousarray(x, np.float64).reshape(-1)
+    vv = np.ascontiguousarray(v, np.float64).reshape(-1)
+    xtt = np.ascontiguousarray(xt, np.float64).reshape(-1)
+    vtt = np.ascontiguousarray(vt, np.float64).reshape(-1)
+    ntp = len(xtt) // 3
+    Rtt = None if Rt is None else np.ascontiguousarray(Rt, np.float64)
+    h = C.c_void_p()
+    _check(lib().genga_init_tp(C.byref(h), len(m), _dp(m), _dp(R), _dp(xx), _dp(vv), float(G), float(dt), int(order),
+                               ntp, _dp(xtt), _dp(vtt), None if Rtt is None else _dp(Rtt)), "genga_init_tp")
+    return h
+
+
+def genga_get_state_tp(ctx, n_tp):
+    xt, vt, al = np.empty((n_tp, 3)), np.empty((n_tp, 3)), np.empty(n_tp, np.int32)
+    _check(lib().genga_get_state_tp(ctx, _dp(xt), _dp(vt), _ip(al)), "genga_get_state_tp")
+    return dict(xt=xt, vt=vt, tp_alive=al)
+
+
+def genga_tp_status(ctx):
+    d = (C.c_longlong * 4)()
+    _check(lib().genga_tp_status(ctx, d), "genga_tp_status")
+    return dict(zip(["tp_candidates", "tp_encounters", "tp_bs_steps", "tp_removed"], list(d)))
 
 
 # ------------------------------------------------------------------------------------ batched mode
