@@ -163,7 +163,8 @@ def run_batched(args):
     n = int(b["offsets"][-1])
     spl = 100
     h = genga.genga_init_batch(b["offsets"], b["m0"], b["m"], b["R"], b["x"], b["v"], b["G"], b["dt"], 2, spl)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()  # a real stream: the legacy default stream would not order the graph
+    torch.cuda.set_stream(stream)
     genga.genga_set_stream(h, stream)
     split, block, _ = genga.genga_batch_info(h)
     kps = genga.genga_launch_count(h)
@@ -233,6 +234,98 @@ def batched_cpu_baseline(nsys=24, steps=20):
     dt = time.perf_counter() - t0
     return {"value": nsys * steps / dt, "unit": "system-steps/s", "cores": 1, "kind": "oracle",
             "sample": f"first {nsys} systems of the batch x {steps} steps ({dt:.1f} s)"}
+
+
+# ------------------------------------------------------------------------------------ test-particle mode
+TP_COUNT = 1 << 20
+TP_SEED = 3
+TP_STEPS = 200
+TP_BYTES_PER_TP_STEP = 96  # algorithmic HBM traffic: read x, v (48 B) and write x, v (48 B) per particle
+TP_PROFILE = os.path.join(ROOT, "profiles", "tp_pass_ncu.md")
+TP_SOURCES = [os.path.join(ROOT, "paper_1404_2324_gb300", "csrc", f) for f in ("tp.cu", "genga_dev.cuh")]
+
+
+def tp_profile_counts():
+    """FP64 instructions and DRAM bytes per particle-step from the committed ncu summary of the
+    particle kernels, if it was taken from the current sources (else None)."""
+    try:
+        txt = open(TP_PROFILE).read()
+    except OSError:
+        return None
+    h = hashlib.sha256()
+    for f in TP_SOURCES:
+        h.update(open(f, "rb").read())
+    m = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
+    f = re.search(r"fp64_inst_per_tp_step:\s*([0-9.eE+-]+)", txt)
+    b = re.search(r"dram_bytes_per_tp_step:\s*([0-9.eE+-]+)", txt)
+    if not (m and f and b) or m.group(1) != h.hexdigest():
+        return None
+    return float(f.group(1)), float(b.group(1))
+
+
+def run_tp(args, peaks):
+    """Test-particle mode: 8 planets + 2^20 massless particles, 2nd order, dt 6 d. One step = one
+    replay of the step graph (planets and particles). Each timed step follows an L2 flush."""
+    import torch
+    from paper_1404_2324_gb300 import genga, ics
+    d = ics.tp_disk(TP_SEED, n_tp=TP_COUNT)
+    m = np.concatenate([[d["m0"]], d["m"]])
+    R = np.concatenate([[0.0], d["R"]])
+    x = np.vstack([np.zeros(3), d["x"]])
+    v = np.vstack([np.zeros(3), d["v"]])
+    h = genga.genga_init_tp(m, R, x, v, d["G"], d["dt"], 2, d["x_tp"], d["v_tp"], d["R_tp"])
+    stream = torch.cuda.Stream()  # a real stream: the legacy default stream would not order the graph
+    torch.cuda.set_stream(stream)
+    genga.genga_set_stream(h, stream)
+    genga.genga_step(h, max(3, min(args.warmup, 20)))
+    torch.cuda.synchronize()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = max(1, args.tp_steps)
+    tot = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        ev0.record(stream)
+        genga.genga_step(h, 1)
+        ev1.record(stream)
+        ev1.synchronize()
+        tot += ev0.elapsed_time(ev1)
+    kps = genga.genga_launch_count(h)
+    st = genga.genga_tp_status(h)
+    code, _ = genga.genga_status(h)
+    genga.genga_free(h)
+    sec = tot * 1e-3 / steps
+    rate = TP_COUNT / sec
+    gbs = TP_BYTES_PER_TP_STEP * rate / 1e9
+    out = {"metric": "test-particle steps/s", "value": rate, "unit": "TP-steps/s", "n_tp": TP_COUNT,
+           "n_planets": len(d["m"]), "steps": steps, "ms_per_step": tot / steps, "gpu_launches": kps * steps,
+           "hbm": {"achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
+                   "bytes_per_tp_step": TP_BYTES_PER_TP_STEP, "peak_source": peaks["hbm_source"]},
+           "status": code, "counters": st,
+           "config": f"tp_disk seed {TP_SEED}: 8 planets m log-U[1e-7,1e-3], a 0.4-30 AU; 2^20 particles "
+                     f"a U[0.3,5], e U[0,0.3], i U[0,0.2]; 2nd order, dt 6 d; L2 flushed per step"}
+    prof = tp_profile_counts()
+    if prof is not None:
+        inst, dram = prof
+        fl = 2.0 * inst * rate / 1e12  # counting every FP64 pipe instruction as one FMA (upper bound)
+        out["fp64"] = {"pipe_inst_per_tp_step": inst, "achieved_tflops_upper": fl, "peak": peaks["fp64_tflops"],
+                       "frac_upper": fl / peaks["fp64_tflops"], "dram_bytes_per_tp_step": dram}
+    return out
+
+
+def tp_cpu_baseline(n_tp=16384, steps=5):
+    import oracle as O
+    from paper_1404_2324_gb300 import ics
+    d = ics.tp_disk(TP_SEED, n_tp=n_tp)
+    p = O.params(G=d["G"], m0=d["m0"], dt=d["dt"], order=2)
+    sim = O.TPSim(p, d["m"], d["R"], d["x"], d["v"], d["x_tp"], d["v_tp"], d["R_tp"])
+    sim.step(1)
+    t0 = time.perf_counter()
+    sim.step(steps)
+    dt = time.perf_counter() - t0
+    sim.close()
+    return {"value": n_tp * steps / dt, "unit": "TP-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"8 planets + {n_tp} particles of the same recipe x {steps} steps ({dt:.1f} s)"}
 
 
 # ------------------------------------------------------------------------------------ GPU arm
@@ -334,6 +427,17 @@ def run_gpu(args, rank, world):
     return res
 
 
+def measured_peaks(res):
+    """HBM copy bandwidth from the measured-peaks file (fallback 6.8 TB/s) and the derived FP64 peak
+    of the main line's roofline."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            hbm, src = float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        hbm, src = 6800.0, "fallback"
+    return {"hbm_gbs": hbm, "hbm_source": src, "fp64_tflops": res["roofline"]["peak"]}
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -345,6 +449,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-launches", type=int, default=5, help="timed 100-step launches of the batched mode")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--tp-steps", type=int, default=TP_STEPS, help="timed steps of the test-particle mode")
+    ap.add_argument("--no-tp", action="store_true")
     args = ap.parse_args()
     if args.warmup < 0 or args.steps < 1:
         ap.error("need --steps >= 1 and --warmup >= 0")
@@ -374,6 +480,8 @@ def main():
     res = run_gpu(args, rank, world)
     if not args.no_batched:
         res["batched"] = run_batched(args)
+    if not args.no_tp:
+        res["test_particles"] = run_tp(args, measured_peaks(res))
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             import oracle
@@ -381,6 +489,8 @@ def main():
             res["cpu_baseline"] = cpu_baseline_entry(args.cpu_steps, 2)
             if "batched" in res:
                 res["batched"]["cpu_baseline"] = batched_cpu_baseline()
+            if "test_particles" in res:
+                res["test_particles"]["cpu_baseline"] = tp_cpu_baseline()
         else:
             res["cpu_baseline"] = None
         print(json.dumps(res))

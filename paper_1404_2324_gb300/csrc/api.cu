@@ -138,6 +138,7 @@ struct genga_ctx {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int bs_grid = 1;
+  int tp_grid = 1;  // blocks of the test-particle encounter and BS kernels
   bool profiling = false;
   // batched mode
   bool batched = false;
@@ -187,6 +188,7 @@ int first_kick(genga_ctx *c) {
   launch_kick(S, c->P, false, c->prm.precise_div != 0, st);
   launch_fin(S, c->P, FIN_INIT, 0.0, 0.0, nullptr, st);
   if (c->tpmode) {
+    CK(cudaMemsetAsync(c->T.npairs, 0, sizeof(unsigned), st));
     launch_tp_rcrit(c->T, c->P, std::fabs(c->dt), 0, st);
     launch_tp_kick(S, c->T, c->P, FIN_INIT, 0.0, 0.0, st);
   }
@@ -250,8 +252,8 @@ void enqueue_step(genga_ctx *c, cudaStream_t st) {
     launch_group(S, st);
     launch_bs(S, P, tau, c->bs_grid, st);
     if (tp) {
-      launch_tp_encounter(S, T, tau, st);
-      launch_tp_bs(S, T, P, tau, c->bs_grid, st);
+      launch_tp_encounter(S, T, tau, c->tp_grid, st);
+      launch_tp_bs(S, T, P, tau, 3 * num_sms(), st);
     }
     if (c->profiling) cudaEventRecordWithFlags(c->kev[2 * j], st, cudaEventRecordExternal);
     launch_kick(S, P, false, precise, st);
@@ -387,8 +389,10 @@ int genga_init_tp(genga_ctx **out, int n, const double *masses, const double *ra
   T.T = mem.get<u64>(np); T.rcsq = mem.get<u64>(np);
   T.alive = mem.get<int>(np); T.full = mem.get<int>(np); T.fail = mem.get<int>(np);
   T.cmask = mem.get<unsigned>(np); T.emask = mem.get<unsigned>(np);
-  T.bslist = mem.get<int>(np); T.nbs = mem.get<int>(1);
-  T.ptab = mem.get<double>(32 * 80 * 6);
+  T.bslist = mem.get<int>(np); T.nbs = mem.get<int>(1); T.bsnext = mem.get<unsigned>(1);
+  T.pairs = mem.get<unsigned>(np * (size_t)(n - 1)); T.npairs = mem.get<unsigned>(1);
+  T.ptab = mem.get<double>(TP_MAXPL * TP_TAB * 6);
+  T.pcheb = mem.get<double>(TP_MAXPL * 6 * TP_CHEB); T.pcok = mem.get<int>(TP_MAXPL);
   T.counters = mem.get<long long>(8);
   c->stx = mem.get<double>(3 * (size_t)n_tp); c->stv = mem.get<double>(3 * (size_t)n_tp);
   c->stalive = mem.get<int>(n_tp);
@@ -404,6 +408,8 @@ int genga_init_tp(genga_ctx **out, int n, const double *masses, const double *ra
   // the staging arrays still hold the massive heliocentric input of genga_init
   launch_tp_from_helio(T, n, c->sm, c->sv, c->stx, c->stv, Rt ? sR : nullptr, 0, st);
   c->tpmode = true;
+  c->tp_grid = 4 * num_sms();
+  if (tp_init_constants() != 0) { genga_free(c); return GENGA_ECUDA; }
   rc = first_kick(c);
   if (rc == GENGA_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = GENGA_ECUDA;
   if (rc != GENGA_OK) { genga_free(c); return rc; }

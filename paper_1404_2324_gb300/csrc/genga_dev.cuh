@@ -82,9 +82,16 @@ struct TPSet {
   int *alive, *full, *fail;      // [npad]
   unsigned *cmask, *emask;       // candidate / encountered planets per TP
   int *bslist, *nbs;             // TPs that need Bulirsch-Stoer this substep
-  double *ptab;                  // planets' Kepler paths at the BS midpoint times [32 * 80 * 6]
+  unsigned *bsnext;              // next list entry a BS warp takes
+  unsigned *pairs, *npairs;      // candidate (TP, planet) pairs of the last closing kick: i * 32 + j
+  double *ptab;                  // planets' Kepler paths at the BS midpoint times [TP_MAXPL * TP_TAB * 6]
+  double *pcheb;                 // Chebyshev series of the planets' paths over the substep [TP_MAXPL * 6 * TP_CHEB]
+  int *pcok;                     // 1: planet j's series is exact to rounding; 0: solve Kepler instead
   long long *counters;           // candidates, encounters, BS steps, removed
 };
+constexpr int TP_MAXPL = 32;     // planets in test-particle mode
+constexpr int TP_TAB = 80;       // sum over BS levels k = 1..8 of the 2k + 1 midpoint times
+constexpr int TP_CHEB = 16;      // Chebyshev nodes per planet path
 
 // ---------------------------------------------------------------------------------------------
 // Integer-pipe helpers

@@ -48,11 +48,12 @@ void launch_b_to_helio(const Sim &S, const int *perm, double *xh, double *vh, do
 void launch_b_energy(const Sim &S, const DevParams &P, const int *sys_user, double *E, cudaStream_t st);
 
 // tp.cu
+int tp_init_constants();  // Neville factors of the TP Bulirsch-Stoer (call outside stream capture)
 void launch_tp_rcrit(const TPSet &T, const DevParams &P, double tau_abs, int check, cudaStream_t st);
 void launch_tp_kick(const Sim &S, const TPSet &T, const DevParams &P, FinMode mode, double h1, double h2, cudaStream_t st);
 void launch_tp_drift(const Sim &S, const TPSet &T, const DevParams &P, double tau, double hcm1, double hcm2, cudaStream_t st);
 void launch_planet_table(const Sim &S, const TPSet &T, const DevParams &P, double tau, cudaStream_t st);
-void launch_tp_encounter(const Sim &S, const TPSet &T, double tau, cudaStream_t st);
+void launch_tp_encounter(const Sim &S, const TPSet &T, double tau, int blocks, cudaStream_t st);
 void launch_tp_bs(const Sim &S, const TPSet &T, const DevParams &P, double tau, int blocks, cudaStream_t st);
 void launch_tp_hc(const Sim &S, const TPSet &T, double hcm, cudaStream_t st);
 void launch_tp_from_helio(const TPSet &T, int nmass, const double *mh, const double *vmh, const double *xh,

@@ -14,9 +14,6 @@
 
 namespace genga {
 
-constexpr int TP_MAXPL = 32;
-constexpr int TP_TAB = 80;  // sum over k = 1..8 of (2k + 1) midpoint times
-
 __device__ __forceinline__ int tab_index(int k, int m) { return k * k - 1 + m; }  // level k >= 1, m = 0..2k
 
 // Critical radii of the TPs (Eq. rcrit with m = 0: n2 |tau| |v|) and the per-TP reuse test.
@@ -56,60 +53,90 @@ __device__ void load_planets(const Sim &S, PlanetSm &ps) {
 }
 
 // TP kick. CLOSE / INIT: all planets with the changeover weight, far field stored, candidates
-// recorded. OPEN: stored far field + candidates with the new radii, or every planet when the TP
-// or any planet failed the reuse test.
+// recorded (per TP as a mask, and as (TP, planet) pairs appended to the pair list for the next
+// encounter test). OPEN: stored far field + candidates with the new radii, or every planet when the
+// TP or any planet failed the reuse test. Every launch also empties the BS list of the coming
+// substep (its last reader, the previous substep's BS, has finished).
 template <int MODE>
 __global__ void __launch_bounds__(128) k_tp_kick(Sim S, TPSet T, DevParams P, double h1, double h2) {
   __shared__ PlanetSm ps;
   load_planets(S, ps);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= T.n || !T.alive[i]) return;
-  const int np = T.npad, npl = S.n;
-  const double xi = T.x[i], yi = T.x[np + i], zi = T.x[2 * np + i];
-  const u64 Ti = T.T[i], Qi = T.rcsq[i];
-  const double Ai = T.A[i];
-  const bool full = (MODE == FIN_OPEN) && (T.full[i] || S.flags[0]);
-  double fx = 0, fy = 0, fz = 0, nx = 0, ny = 0, nz = 0;
+  if (i == 0) *T.nbs = 0;
+  const bool act = i < T.n && T.alive[i];
   unsigned cm = 0u;
-  const unsigned scan = (MODE == FIN_OPEN && !full) ? T.cmask[i] : 0xffffffffu;
-  for (int j = 0; j < npl; ++j) {
-    if (!ps.alive[j] || !((scan >> j) & 1u)) continue;
-    const double dx = ps.x[j] - xi, dy = ps.y[j] - yi, dz = ps.z[j] - zi;
-    const double r2 = __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx)));
-    const double yr = rsqrt_refined(r2);
-    const u64 rb = dbits(r2);
-    double g = ps.gm[j] * (yr * yr * yr);
-    const bool cand = (MODE != FIN_OPEN) && rb < umax64(Ti, ps.T[j]);
-    if (MODE == FIN_OPEN || cand) {
-      if (rb < umax64(Qi, ps.Q[j])) {
-        double wB, wA;
-        changeover_w(r2 * yr, pmin(Ai, ps.A[j]), P.kmode, wB, wA);
-        g *= wB;
+  if (act) {
+    const int np = T.npad, npl = S.n;
+    const double xi = T.x[i], yi = T.x[np + i], zi = T.x[2 * np + i];
+    const u64 Ti = T.T[i], Qi = T.rcsq[i];
+    const double Ai = T.A[i];
+    const bool full = (MODE == FIN_OPEN) && (T.full[i] || S.flags[0]);
+    double fx = 0, fy = 0, fz = 0, nx = 0, ny = 0, nz = 0;
+    const unsigned scan = (MODE == FIN_OPEN && !full) ? T.cmask[i] : 0xffffffffu;
+    for (int j = 0; j < npl; ++j) {
+      if (!ps.alive[j] || !((scan >> j) & 1u)) continue;
+      const double dx = ps.x[j] - xi, dy = ps.y[j] - yi, dz = ps.z[j] - zi;
+      const double r2 = __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx)));
+      const double yr = rsqrt_refined(r2);
+      const u64 rb = dbits(r2);
+      double g = ps.gm[j] * (yr * yr * yr);
+      const bool cand = (MODE != FIN_OPEN) && rb < umax64(Ti, ps.T[j]);
+      if (MODE == FIN_OPEN || cand) {
+        if (rb < umax64(Qi, ps.Q[j])) {
+          double wB, wA;
+          changeover_w(r2 * yr, pmin(Ai, ps.A[j]), P.kmode, wB, wA);
+          g *= wB;
+        }
+        if (cand) cm |= 1u << j;
+        nx = fma(g, dx, nx); ny = fma(g, dy, ny); nz = fma(g, dz, nz);
+      } else {
+        fx = fma(g, dx, fx); fy = fma(g, dy, fy); fz = fma(g, dz, fz);
       }
-      if (cand) cm |= 1u << j;
-      nx = fma(g, dx, nx); ny = fma(g, dy, ny); nz = fma(g, dz, nz);
+    }
+    double ax, ay, az;
+    if (MODE == FIN_OPEN) {
+      if (full) { ax = nx; ay = ny; az = nz; }
+      else { ax = T.afar[i] + nx; ay = T.afar[np + i] + ny; az = T.afar[2 * np + i] + nz; }
     } else {
-      fx = fma(g, dx, fx); fy = fma(g, dy, fy); fz = fma(g, dz, fz);
+      T.afar[i] = fx; T.afar[np + i] = fy; T.afar[2 * np + i] = fz;
+      T.cmask[i] = cm;
+      ax = fx + nx; ay = fy + ny; az = fz + nz;
+    }
+    if (MODE != FIN_INIT) {
+      double vx = fma(h1, ax, T.v[i]), vy = fma(h1, ay, T.v[np + i]), vz = fma(h1, az, T.v[2 * np + i]);
+      if (h2 != 0.0) { vx = fma(h2, ax, vx); vy = fma(h2, ay, vy); vz = fma(h2, az, vz); }
+      T.v[i] = vx; T.v[np + i] = vy; T.v[2 * np + i] = vz;
+    } else {
+      (void)h1; (void)h2;
     }
   }
-  double ax, ay, az;
-  if (MODE == FIN_OPEN) {
-    if (full) { ax = nx; ay = ny; az = nz; }
-    else { ax = T.afar[i] + nx; ay = T.afar[np + i] + ny; az = T.afar[2 * np + i] + nz; }
-  } else {
-    T.afar[i] = fx; T.afar[np + i] = fy; T.afar[2 * np + i] = fz;
-    T.cmask[i] = cm;
-    if (MODE == FIN_CLOSE && cm) atomicAdd((unsigned long long *)&T.counters[0], (unsigned long long)__popc(cm));
-    ax = fx + nx; ay = fy + ny; az = fz + nz;
+  if (MODE != FIN_OPEN) {  // append this warp's candidate pairs with one atomic
+    const int lane = threadIdx.x & 31;
+    const unsigned cnt = __popc(cm);
+    unsigned incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned base = 0u;
+    if (lane == 31 && total) {
+      base = atomicAdd(T.npairs, total);
+      if (MODE == FIN_CLOSE) atomicAdd((unsigned long long *)&T.counters[0], (unsigned long long)total);
+    }
+    base = __shfl_sync(0xffffffffu, base, 31);
+    unsigned pos = base + incl - cnt;
+    while (cm) {
+      const int j = __ffs(cm) - 1;
+      cm &= cm - 1;
+      T.pairs[pos++] = ((unsigned)i << 5) | (unsigned)j;
+    }
   }
-  if (MODE == FIN_INIT) return;
-  double vx = fma(h1, ax, T.v[i]), vy = fma(h1, ay, T.v[np + i]), vz = fma(h1, az, T.v[2 * np + i]);
-  if (h2 != 0.0) { vx = fma(h2, ax, vx); vy = fma(h2, ay, vy); vz = fma(h2, az, vz); }
-  T.v[i] = vx; T.v[np + i] = vy; T.v[2 * np + i] = vz;
 }
 
 // Sun drifts with the massive momentum (the same partials the massive drift reads), keep the
-// pre-drift state, Kepler drift.
+// pre-drift state, Kepler drift. Clears the encounter masks; a failed solve lists the TP for BS.
 __global__ void k_tp_drift(Sim S, TPSet T, DevParams P, double tau, double hcm1, double hcm2) {
   __shared__ double sh[3];
   if (threadIdx.x < 32) {
@@ -129,9 +156,9 @@ __global__ void k_tp_drift(Sim S, TPSet T, DevParams P, double tau, double hcm1,
   }
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0) *T.nbs = 0;
   if (i >= T.n) return;
   T.fail[i] = 0;
+  T.emask[i] = 0u;
   if (!T.alive[i]) return;
   const int np = T.npad;
   double x = T.x[i] + sh[0], y = T.x[np + i] + sh[1], z = T.x[2 * np + i] + sh[2];
@@ -142,66 +169,120 @@ __global__ void k_tp_drift(Sim S, TPSet T, DevParams P, double tau, double hcm1,
   if (kepler_drift_dev(P.G * P.m0, P.mu2, x, y, z, vx, vy, vz, tau, P.kepler_maxit, &it)) {
     T.fail[i] = 1;
     atomicOr(S.status, ST_KEPLER_FALLBACK);
+    T.bslist[atomicAdd(T.nbs, 1)] = i;  // integrated by BS in the field of m0 alone (unless it meets a planet)
   }
   T.x[i] = x; T.x[np + i] = y; T.x[2 * np + i] = z;
   T.v[i] = vx; T.v[np + i] = vy; T.v[2 * np + i] = vz;
 }
 
-// Kepler path of every planet from its pre-drift state at all midpoint times of a full-length BS
-// attempt (t = m * (tau / 2k), and t = tau at m = 2k), plus the drift result itself.
-__global__ void k_planet_table(Sim S, TPSet T, DevParams P, double tau) {
-  const int id = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = id / TP_TAB, e = id % TP_TAB;
-  if (j >= S.n) return;
-  int k = 1;
-  while (tab_index(k + 1, 0) <= e) k++;
-  const int m = e - tab_index(k, 0), nk = 2 * k;
-  const double t = (m == nk) ? tau : (double)m * __ddiv_rn(tau, (double)nk);
+// Planet paths for the TP Bulirsch-Stoer, one block per planet, from the pre-drift state:
+//  * the Kepler solution at every midpoint time of a full-length attempt (t = m tau/2k, and t = tau
+//    at m = 2k), also the drift result itself;
+//  * a Chebyshev series in s = 2t/tau - 1 of position and velocity through TP_CHEB Kepler solutions
+//    at the Chebyshev nodes, used for the times of shorter attempts. The series stands in for the
+//    Kepler solve only when its last two coefficients are below 2^-60 of |x| (resp. |v|): the
+//    coefficients of a smooth path fall geometrically, so the truncation error is then far below
+//    one rounding of the position. Otherwise pcok = 0 and those times solve Kepler's equation.
+__global__ void __launch_bounds__(128) k_planet_table(Sim S, TPSet T, DevParams P, double tau) {
+  __shared__ double node[TP_CHEB][6];
+  __shared__ double coef[6][TP_CHEB];
+  const int j = blockIdx.x, e = threadIdx.x;
   const int np = S.npad;
-  double x = S.x0[j], y = S.x0[np + j], z = S.x0[2 * np + j];
-  double vx = S.v0[j], vy = S.v0[np + j], vz = S.v0[2 * np + j];
-  if (m > 0) kepler_drift_dev(P.G * P.m0, P.mu2, x, y, z, vx, vy, vz, t, P.kepler_maxit, nullptr);
-  double *o = T.ptab + ((size_t)j * TP_TAB + e) * 6;
-  o[0] = x; o[1] = y; o[2] = z; o[3] = vx; o[4] = vy; o[5] = vz;
+  const double x0 = S.x0[j], y0 = S.x0[np + j], z0 = S.x0[2 * np + j];
+  const double u0 = S.v0[j], v0 = S.v0[np + j], w0 = S.v0[2 * np + j];
+  if (e < TP_TAB) {
+    int k = 1;
+    while (tab_index(k + 1, 0) <= e) k++;
+    const int m = e - tab_index(k, 0), nk = 2 * k;
+    const double t = (m == nk) ? tau : (double)m * __ddiv_rn(tau, (double)nk);
+    double x = x0, y = y0, z = z0, vx = u0, vy = v0, vz = w0;
+    if (m > 0) kepler_drift_dev(P.G * P.m0, P.mu2, x, y, z, vx, vy, vz, t, P.kepler_maxit, nullptr);
+    double *o = T.ptab + ((size_t)j * TP_TAB + e) * 6;
+    o[0] = x; o[1] = y; o[2] = z; o[3] = vx; o[4] = vy; o[5] = vz;
+  } else if (e < TP_TAB + TP_CHEB) {
+    const int q = e - TP_TAB;
+    const double sq = cospi((double)(2 * q + 1) / (double)(2 * TP_CHEB));
+    const double t = 0.5 * tau * (sq + 1.0);
+    double x = x0, y = y0, z = z0, vx = u0, vy = v0, vz = w0;
+    int bad = kepler_drift_dev(P.G * P.m0, P.mu2, x, y, z, vx, vy, vz, t, P.kepler_maxit, nullptr);
+    node[q][0] = x; node[q][1] = y; node[q][2] = z;
+    node[q][3] = bad ? __longlong_as_double(0x7ff8000000000000LL) : vx; node[q][4] = vy; node[q][5] = vz;
+  }
+  __syncthreads();
+  if (e < 6 * TP_CHEB) {
+    const int c = e / TP_CHEB, k = e % TP_CHEB;
+    double acc = 0.0;
+    for (int q = 0; q < TP_CHEB; ++q)
+      acc = fma(node[q][c], cospi((double)(k * (2 * q + 1)) / (double)(2 * TP_CHEB)), acc);
+    acc *= 2.0 / TP_CHEB;
+    coef[c][k] = acc;
+    T.pcheb[((size_t)j * 6 + c) * TP_CHEB + k] = acc;
+  }
+  __syncthreads();
+  if (e == 0) {
+    const double r = sqrt(fma(z0, z0, fma(y0, y0, x0 * x0))), v = sqrt(fma(w0, w0, fma(v0, v0, u0 * u0)));
+    const double lim = 8.673617379884035e-19;  // 2^-60
+    bool ok = true;
+    for (int c = 0; c < 6; ++c) {
+      const double tail = fabs(coef[c][TP_CHEB - 1]) + fabs(coef[c][TP_CHEB - 2]);
+      if (!(tail <= lim * (c < 3 ? r : v))) ok = false;  // NaN (failed node) is not ok
+    }
+    T.pcok[j] = ok;
+  }
 }
 
-// Hermite test of each TP against its candidate planets over the drift (bit-exact with the
-// oracle); TPs with an encounter or a failed Kepler solve are listed for BS.
-__global__ void k_tp_encounter(Sim S, TPSet T, double tau) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= T.n || !T.alive[i]) return;
-  const unsigned cm = T.cmask[i];
-  unsigned em = 0u;
-  if (cm) {
-    const int np = T.npad, pp = S.npad;
-    const double x0 = T.x0[i], y0 = T.x0[np + i], z0 = T.x0[2 * np + i];
-    const double u0 = T.v0[i], v0 = T.v0[np + i], w0 = T.v0[2 * np + i];
-    const double x1 = T.x[i], y1 = T.x[np + i], z1 = T.x[2 * np + i];
-    const double u1 = T.v[i], v1 = T.v[np + i], w1 = T.v[2 * np + i];
-    for (int j = 0; j < S.n; ++j) {
-      if (!((cm >> j) & 1u) || !S.alive[j]) continue;
-      const double *pf = T.ptab + ((size_t)j * TP_TAB + tab_index(1, 2)) * 6;  // t = tau
-      const double dmin = hermite_min_exact(
-          __dsub_rn(S.x0[j], x0), __dsub_rn(S.x0[pp + j], y0), __dsub_rn(S.x0[2 * pp + j], z0),
-          __dsub_rn(S.v0[j], u0), __dsub_rn(S.v0[pp + j], v0), __dsub_rn(S.v0[2 * pp + j], w0),
-          __dsub_rn(pf[0], x1), __dsub_rn(pf[1], y1), __dsub_rn(pf[2], z1),
-          __dsub_rn(pf[3], u1), __dsub_rn(pf[4], v1), __dsub_rn(pf[5], w1), tau);
-      const double rcij = pmax(T.rc[i], S.rc[j]);
-      if (dmin < __dmul_rn(rcij, rcij)) em |= 1u << j;
+// Hermite test of each candidate (TP, planet) pair of the last closing kick over the drift,
+// one pair per thread (bit-exact with the oracle). A TP's first encounter lists it for BS, unless
+// its failed Kepler solve listed it already.
+__global__ void __launch_bounds__(256) k_tp_encounter(Sim S, TPSet T, double tau) {
+  const unsigned npairs = *T.npairs;
+  const int np = T.npad, pp = S.npad;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *T.bsnext = 0u;  // the BS that follows starts at the head
+  for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < npairs; q += gridDim.x * blockDim.x) {
+    const unsigned pr = T.pairs[q];
+    const int i = (int)(pr >> 5), j = (int)(pr & 31u);
+    if (!T.alive[i] || !S.alive[j]) continue;
+    const double *pf = T.ptab + ((size_t)j * TP_TAB + tab_index(1, 2)) * 6;  // t = tau
+    const double dmin = hermite_min_exact(
+        __dsub_rn(S.x0[j], T.x0[i]), __dsub_rn(S.x0[pp + j], T.x0[np + i]), __dsub_rn(S.x0[2 * pp + j], T.x0[2 * np + i]),
+        __dsub_rn(S.v0[j], T.v0[i]), __dsub_rn(S.v0[pp + j], T.v0[np + i]), __dsub_rn(S.v0[2 * pp + j], T.v0[2 * np + i]),
+        __dsub_rn(pf[0], T.x[i]), __dsub_rn(pf[1], T.x[np + i]), __dsub_rn(pf[2], T.x[2 * np + i]),
+        __dsub_rn(pf[3], T.v[i]), __dsub_rn(pf[4], T.v[np + i]), __dsub_rn(pf[5], T.v[2 * np + i]), tau);
+    const double rcij = pmax(T.rc[i], S.rc[j]);
+    if (dmin < __dmul_rn(rcij, rcij)) {
+      const unsigned old = atomicOr(&T.emask[i], 1u << j);
+      atomicAdd((unsigned long long *)&T.counters[1], 1ULL);
+      if (old == 0u && !T.fail[i]) T.bslist[atomicAdd(T.nbs, 1)] = i;
     }
   }
-  T.emask[i] = em;
-  if (em) atomicAdd((unsigned long long *)&T.counters[1], (unsigned long long)__popc(em));
-  if (em || T.fail[i]) T.bslist[atomicAdd(T.nbs, 1)] = i;
 }
 
-// Planet j's position on its Kepler path at time t of the substep (table for full-length
-// attempts, otherwise a Kepler solve from the pre-drift state).
+// Chebyshev series of planet j (components c0 .. c0 + 2) at s in [-1, 1] (Clenshaw).
+__device__ __forceinline__ void cheb3(const double *cf, double s, double &a, double &b, double &c) {
+  const double s2 = 2.0 * s;
+  double a1 = 0.0, a2 = 0.0, b1 = 0.0, b2 = 0.0, c1 = 0.0, c2 = 0.0;
+#pragma unroll
+  for (int k = TP_CHEB - 1; k >= 1; --k) {
+    const double an = fma(s2, a1, cf[k] - a2), bn = fma(s2, b1, cf[TP_CHEB + k] - b2),
+                 cn = fma(s2, c1, cf[2 * TP_CHEB + k] - c2);
+    a2 = a1; a1 = an; b2 = b1; b1 = bn; c2 = c1; c1 = cn;
+  }
+  a = fma(s, a1, fma(0.5, cf[0], -a2));
+  b = fma(s, b1, fma(0.5, cf[TP_CHEB], -b2));
+  c = fma(s, c1, fma(0.5, cf[2 * TP_CHEB], -c2));
+}
+
+// Planet j's state on its Kepler path at time t of the substep: the table for full-length
+// attempts, otherwise the Chebyshev series (or, where it is not exact, a Kepler solve).
 __device__ __forceinline__ void planet_at(const Sim &S, const TPSet &T, const DevParams &P, int j, bool table,
-                                          int k, int m, double t, double &px, double &py, double &pz) {
+                                          int k, int m, double t, double i2tau, double &px, double &py, double &pz) {
   if (table) {
     const double *o = T.ptab + ((size_t)j * TP_TAB + tab_index(k, m)) * 6;
     px = o[0]; py = o[1]; pz = o[2];
+    return;
+  }
+  if (T.pcok[j]) {
+    cheb3(T.pcheb + (size_t)j * 6 * TP_CHEB, fma(t, i2tau, -1.0), px, py, pz);
     return;
   }
   const int pp = S.npad;
@@ -211,18 +292,50 @@ __device__ __forceinline__ void planet_at(const Sim &S, const TPSet &T, const De
   px = x; py = y; pz = z;
 }
 
-// Acceleration of the TP at y (central + (1 - W_B) pull of the encountered planets at time t).
+// Planet j's position and velocity at time t (series or Kepler solve), for the contact test.
+__device__ __forceinline__ void planet_state_at(const Sim &S, const TPSet &T, const DevParams &P, int j, double t,
+                                                double i2tau, double *o) {
+  if (T.pcok[j]) {
+    const double s = fma(t, i2tau, -1.0);
+    const double *cf = T.pcheb + (size_t)j * 6 * TP_CHEB;
+    cheb3(cf, s, o[0], o[1], o[2]);
+    cheb3(cf + 3 * TP_CHEB, s, o[3], o[4], o[5]);
+    return;
+  }
+  const int pp = S.npad;
+  double x = S.x0[j], y = S.x0[pp + j], z = S.x0[2 * pp + j];
+  double vx = S.v0[j], vy = S.v0[pp + j], vz = S.v0[2 * pp + j];
+  if (dbits(t) != 0ULL) kepler_drift_dev(P.G * P.m0, P.mu2, x, y, z, vx, vy, vz, t, P.kepler_maxit, nullptr);
+  o[0] = x; o[1] = y; o[2] = z; o[3] = vx; o[4] = vy; o[5] = vz;
+}
+
+constexpr int TP_PRE = 2;  // encountered planets whose positions a BS attempt evaluates up front
+
+__constant__ double c_tp_facinv[BS_LEVELS + 1][BS_LEVELS];  // 1 / ((L / (L - j))^2 - 1)
+
+// Acceleration of the TP at y (central + (1 - W_B) pull of the encountered planets) at midpoint m of
+// level k: planet positions from the table (full-length attempt), from the warp's precomputed
+// positions (first TP_PRE planets of a shorter attempt) or evaluated here.
 __device__ __forceinline__ void tp_force(const Sim &S, const TPSet &T, const DevParams &P, int i, unsigned em, bool table,
-                                         int k, int m, double t, const double *y, double &ax, double &ay, double &az) {
+                                         int k, int m, double t0, double h, double H, double i2tau, const double *wpos,
+                                         const double *y, double &ax, double &ay, double &az) {
   const double r2 = fma(y[2], y[2], fma(y[1], y[1], y[0] * y[0]));
   const double f = -P.Gm0 * rcube_refined(r2);
   ax = f * y[0]; ay = f * y[1]; az = f * y[2];
   unsigned bits = em;
+  int p = 0;
   while (bits) {
     const int j = __ffs(bits) - 1;
     bits &= bits - 1;
     double px, py, pz;
-    planet_at(S, T, P, j, table, k, m, t, px, py, pz);
+    if (!table && p < TP_PRE) {
+      const double *q = wpos + (p * TP_TAB + tab_index(k, m)) * 3;
+      px = q[0]; py = q[1]; pz = q[2];
+    } else {
+      const double t = (m == 2 * k) ? t0 + H : t0 + m * h;
+      planet_at(S, T, P, j, table, k, m, t, i2tau, px, py, pz);
+    }
+    ++p;
     const double dx = px - y[0], dy = py - y[1], dz = pz - y[2];
     const double pr2 = fma(dz, dz, fma(dy, dy, dx * dx));
     if (dbits(pr2) >= umax64(T.rcsq[i], S.rcsq[j])) continue;
@@ -235,12 +348,20 @@ __device__ __forceinline__ void tp_force(const Sim &S, const TPSet &T, const Dev
 }
 
 // BS of one listed TP per warp; lane L-1 runs level L (n_L = 2L midpoint substeps).
-__global__ void __launch_bounds__(128) k_tp_bs(Sim S, TPSet T, DevParams P, double tau) {
+// Launched with 3 blocks per SM (the register budget of one block allows three).
+__global__ void __launch_bounds__(128, 3) k_tp_bs(Sim S, TPSet T, DevParams P, double tau) {
+  __shared__ double s_pos[4][TP_PRE * TP_TAB * 3];
   const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarp = (gridDim.x * blockDim.x) >> 5;
+  double *wpos = s_pos[threadIdx.x >> 5];
   const int nlist = *T.nbs;
   const int np = T.npad;
-  for (int w = warp; w < nlist; w += nwarp) {
+  const double i2tau = 2.0 / tau;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *T.npairs = 0u;  // consumed by the encounter test
+  for (;;) {  // each warp takes the next listed TP: long encounters do not hold up the rest
+    int w = 0;
+    if (lane == 0) w = (int)atomicAdd(T.bsnext, 1u);
+    w = __shfl_sync(0xffffffffu, w, 0);
+    if (w >= nlist) break;
     const int i = T.bslist[w];
     const unsigned em = T.emask[i];
     const int L = lane < BS_LEVELS ? lane + 1 : 1, nk = 2 * L;
@@ -253,14 +374,31 @@ __global__ void __launch_bounds__(128) k_tp_bs(Sim S, TPSet T, DevParams P, doub
       if (absbits(H) > absbits(rem)) H = rem;
       const bool table = dbits(t0) == 0ULL && dbits(H) == dbits(tau);
       const double h = __ddiv_rn(H, (double)nk), h2 = 2.0 * h;
+      if (!table && em) {  // positions of the first TP_PRE planets at all midpoint times, lane-parallel
+        __syncwarp();
+        unsigned bits = em;
+        for (int p = 0; p < TP_PRE && bits; ++p) {
+          const int j = __ffs(bits) - 1;
+          bits &= bits - 1;
+          for (int e = lane; e < TP_TAB; e += 32) {
+            int k = 1;
+            while (tab_index(k + 1, 0) <= e) k++;
+            const int m = e - tab_index(k, 0);
+            const double hk = __ddiv_rn(H, (double)(2 * k));
+            const double t = (m == 2 * k) ? t0 + H : t0 + m * hk;
+            double *q = wpos + (p * TP_TAB + e) * 3;
+            planet_at(S, T, P, j, false, k, m, t, i2tau, q[0], q[1], q[2]);
+          }
+        }
+        __syncwarp();
+      }
       double za[6], zb[6], out[6], ax, ay, az;
       for (int c = 0; c < 6; ++c) za[c] = y[c];
-      tp_force(S, T, P, i, em, table, L, 0, t0, y, ax, ay, az);
+      tp_force(S, T, P, i, em, table, L, 0, t0, h, H, i2tau, wpos, y, ax, ay, az);
       zb[0] = fma(h, y[3], y[0]); zb[1] = fma(h, y[4], y[1]); zb[2] = fma(h, y[5], y[2]);
       zb[3] = fma(h, ax, y[3]); zb[4] = fma(h, ay, y[4]); zb[5] = fma(h, az, y[5]);
       for (int m = 1; m <= nk; ++m) {
-        const double t = (m == nk) ? t0 + H : t0 + m * h;
-        tp_force(S, T, P, i, em, table, L, m, t, zb, ax, ay, az);
+        tp_force(S, T, P, i, em, table, L, m, t0, h, H, i2tau, wpos, zb, ax, ay, az);
         if (m < nk) {
           double zn[6];
           zn[0] = fma(h2, zb[3], za[0]); zn[1] = fma(h2, zb[4], za[1]); zn[2] = fma(h2, zb[5], za[2]);
@@ -279,8 +417,7 @@ __global__ void __launch_bounds__(128) k_tp_bs(Sim S, TPSet T, DevParams P, doub
         double up[6];
         for (int c = 0; c < 6; ++c) up[c] = __shfl_up_sync(0xffffffffu, Tk[c], 1);
         if (lane < BS_LEVELS && L > j) {
-          const double ratio = (double)L / (double)(L - j);
-          const double fi = rcp_refined(ratio * ratio - 1.0);
+          const double fi = c_tp_facinv[L][j];
           if (j == L - 1) for (int c = 0; c < 6; ++c) Tm1[c] = Tk[c];
           for (int c = 0; c < 6; ++c) Tk[c] = fma(Tk[c] - up[c], fi, Tk[c]);
         }
@@ -308,16 +445,14 @@ __global__ void __launch_bounds__(128) k_tp_bs(Sim S, TPSet T, DevParams P, doub
         while (bits && !hit) {
           const int j = __ffs(bits) - 1;
           bits &= bits - 1;
-          const int pp = S.npad;
-          double xa = S.x0[j], ya = S.x0[pp + j], zaa = S.x0[2 * pp + j], ua = S.v0[j], va = S.v0[pp + j], wa = S.v0[2 * pp + j];
-          double xb = xa, yb = ya, zbb = zaa, ub = ua, vb = va, wb = wa;
-          if (dbits(t0) != 0ULL) kepler_drift_dev(P.G * P.m0, P.mu2, xa, ya, zaa, ua, va, wa, t0, P.kepler_maxit, nullptr);
-          kepler_drift_dev(P.G * P.m0, P.mu2, xb, yb, zbb, ub, vb, wb, t0 + H, P.kepler_maxit, nullptr);
+          double pa[6], pb[6];
+          planet_state_at(S, T, P, j, t0, i2tau, pa);
+          planet_state_at(S, T, P, j, t0 + H, i2tau, pb);
           const double dmin = hermite_min_exact(
-              __dsub_rn(xa, y[0]), __dsub_rn(ya, y[1]), __dsub_rn(zaa, y[2]),
-              __dsub_rn(ua, y[3]), __dsub_rn(va, y[4]), __dsub_rn(wa, y[5]),
-              __dsub_rn(xb, yn[0]), __dsub_rn(yb, yn[1]), __dsub_rn(zbb, yn[2]),
-              __dsub_rn(ub, yn[3]), __dsub_rn(vb, yn[4]), __dsub_rn(wb, yn[5]), H);
+              __dsub_rn(pa[0], y[0]), __dsub_rn(pa[1], y[1]), __dsub_rn(pa[2], y[2]),
+              __dsub_rn(pa[3], y[3]), __dsub_rn(pa[4], y[4]), __dsub_rn(pa[5], y[5]),
+              __dsub_rn(pb[0], yn[0]), __dsub_rn(pb[1], yn[1]), __dsub_rn(pb[2], yn[2]),
+              __dsub_rn(pb[3], yn[3]), __dsub_rn(pb[4], yn[4]), __dsub_rn(pb[5], yn[5]), H);
           const double rr = T.R[i] + S.R[j];
           hit = dmin < rr * rr;
         }
@@ -408,6 +543,16 @@ __global__ void k_tp_to_helio(Sim S, TPSet T, DevParams P, double *xh, double *v
 // ---------------------------------------------------------------------------------------------
 static int grid_of(int n, int b) { return (n + b - 1) / b; }
 
+int tp_init_constants() {
+  double f[BS_LEVELS + 1][BS_LEVELS] = {};
+  for (int L = 2; L <= BS_LEVELS; ++L)
+    for (int j = 1; j < L; ++j) {
+      const double ratio = (double)L / (double)(L - j);
+      f[L][j] = 1.0 / (ratio * ratio - 1.0);
+    }
+  return cudaMemcpyToSymbol(c_tp_facinv, f, sizeof(f)) == cudaSuccess ? 0 : -1;
+}
+
 void launch_tp_from_helio(const TPSet &T, int nmass, const double *mh, const double *vmh, const double *xh,
                           const double *vh, const double *Rh, int keep, cudaStream_t st) {
   k_tp_from_helio<<<grid_of(T.npad, 256), 256, 0, st>>>(T, nmass, mh, vmh, xh, vh, Rh, keep);
@@ -430,10 +575,10 @@ void launch_tp_drift(const Sim &S, const TPSet &T, const DevParams &P, double ta
   k_tp_drift<<<grid_of(T.n, 128), 128, 0, st>>>(S, T, P, tau, hcm1, hcm2);
 }
 void launch_planet_table(const Sim &S, const TPSet &T, const DevParams &P, double tau, cudaStream_t st) {
-  k_planet_table<<<grid_of(S.n * TP_TAB, 32), 32, 0, st>>>(S, T, P, tau);
+  k_planet_table<<<S.n, 128, 0, st>>>(S, T, P, tau);
 }
-void launch_tp_encounter(const Sim &S, const TPSet &T, double tau, cudaStream_t st) {
-  k_tp_encounter<<<grid_of(T.n, 128), 128, 0, st>>>(S, T, tau);
+void launch_tp_encounter(const Sim &S, const TPSet &T, double tau, int blocks, cudaStream_t st) {
+  k_tp_encounter<<<blocks, 256, 0, st>>>(S, T, tau);
 }
 void launch_tp_bs(const Sim &S, const TPSet &T, const DevParams &P, double tau, int blocks, cudaStream_t st) {
   k_tp_bs<<<blocks, 128, 0, st>>>(S, T, P, tau);
