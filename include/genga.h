@@ -47,6 +47,7 @@ extern "C" {
 #define GENGA_ST_REUSE_FULLKICK 4    /* rcrit grew past pc*rcrit_old: the opening kick was recomputed */
 #define GENGA_ST_GROUP_TOO_LARGE 8   /* an encounter group exceeded the in-kernel size cap */
 #define GENGA_ST_UNION_ROUNDS 16     /* grouping did not reach its fixpoint within its round cap */
+#define GENGA_ST_RECORD_OVERFLOW 32  /* adjoint engine: a recording buffer was too small (gradient invalid) */
 
 /* modes of genga_init (Sect. 3): main mode with up to 2048 massive bodies */
 #define GENGA_MODE_MASSIVE 0
@@ -252,6 +253,55 @@ int genga_phase_energy(int n, double G, double m0, const double *m, const int *a
 int genga_kick_noalloc(int n, double G, double pc, int kmode, int precise_div, const double *m,
                        const int *alive, const double *x, const double *rc, double *a, int *cand,
                        int cap, int *ncand, void *stream);
+
+/* ------------------------------------------------------------------------------------------ */
+/* Differentiable engine and its adjoint (reverse-mode derivative of the hybrid step)            */
+/* ------------------------------------------------------------------------------------------ */
+/* The paper has no adjoint; this is its hybrid step (Sect. 2.2-2.3: kicks weighted by K, Sun drifts,
+ * universal-variable Kepler drifts, the Hermite encounter test, groups, Bulirsch-Stoer of H_A, the
+ * Yoshida compositions) differentiated by hand, with perfect merging switched off (a merger changes
+ * the number of bodies; the engine integrates through close passes instead). Every discrete
+ * decision is frozen from the forward pass: the branch of K, the candidate and encounter pairs, the
+ * groups, each group's accepted BS substeps and levels, and the Kepler solves (differentiated
+ * implicitly at the converged universal anomaly). The critical radii depend on the state at the
+ * start of each step, and that dependence is differentiated too.
+ *
+ * The engine advances n_sys independent systems of n bodies each (n <= 1024), central mass m0[b]
+ * for system b, G, time step dt, order 2, 4 or 6, all with the default parameters of
+ * genga_default_params (kmode 0) and collisions off.
+ *
+ * Memory: a checkpoint (state and critical radii) every ckpt_every steps, kept by
+ * genga_adj_forward; genga_adj_backward recomputes one segment of ckpt_every steps at a time from
+ * its checkpoint, recording every intermediate state and decision, then runs the vector-Jacobian
+ * products backwards through it. The recording holds about 16 doubles per body per substep of a
+ * segment, so ckpt_every trades device memory against nothing but that memory: the recomputation
+ * is one forward pass in any case. */
+typedef struct genga_adj genga_adj;
+
+/* m0: host [n_sys]. Allocates all device memory of the engine (checkpoints grow on demand). */
+int genga_adj_init(genga_adj **ctx, int n_sys, int n, const double *m0, double G, double dt, int order,
+                   int ckpt_every);
+
+/* Work is enqueued on this stream (cudaStream_t as void*; NULL = the CUDA default stream, which is
+ * also the stream until this is called). The engine captures no graphs. */
+int genga_adj_set_stream(genga_adj *ctx, void *stream);
+
+/* n_steps hybrid steps from (x, v, m). DEVICE pointers, AoS: x, v, x_out, v_out [n_sys][n][3]
+ * heliocentric, m [n_sys][n]. The inputs are copied; the engine keeps what the backward pass needs.
+ * Asynchronous on the stream; status bits through genga_adj_status. */
+int genga_adj_forward(genga_adj *ctx, int n_steps, const double *x, const double *v, const double *m,
+                      double *x_out, double *v_out);
+
+/* Gradients of <xbar, x_out> + <vbar, v_out> of the last genga_adj_forward with respect to its
+ * inputs: gx, gv [n_sys][n][3], gm [n_sys][n]. DEVICE pointers, asynchronous on the stream. Must
+ * follow the forward call it differentiates (the engine's state is that call's final state). */
+int genga_adj_backward(genga_adj *ctx, const double *xbar, const double *vbar, double *gx, double *gv,
+                       double *gm);
+
+/* Waits for the stream, then returns the status bits (GENGA_ST_*) raised since the last forward. */
+int genga_adj_status(genga_adj *ctx, int *code);
+int genga_adj_sync(genga_adj *ctx);
+void genga_adj_free(genga_adj *ctx);
 
 /* Self-test of the device arithmetic helpers: out[i] = f(in[i]) for which = 0: x^(-1/2),
  * 1: x^(-3/2), 2: 1/x (the refined estimates used by the kernels). Device arrays. */

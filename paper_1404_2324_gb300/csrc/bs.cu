@@ -25,6 +25,9 @@ struct BsShared {
   unsigned char cont[BS_GMAX * (BS_GMAX - 1) / 2];
   double H, rem, U;
   int accept;
+  int nseq, seq_base;          // recorded accepted substeps (adjoint engine only)
+  double seqH[BS_SEQCAP];
+  unsigned char seqk[BS_SEQCAP];
 };
 
 // Acceleration terms of member q assigned to this thread: term p == q is the central mass, any
@@ -88,7 +91,7 @@ __global__ void __launch_bounds__(BS_THREADS) k_bs(Sim S, DevParams P, double ta
       sh.rcsq[tid] = S.rcsq[i];
       for (int c = 0; c < 3; ++c) { sh.y[tid][c] = S.x0[c * np + i]; sh.y[tid][3 + c] = S.v0[c * np + i]; }
     }
-    if (tid == 0) { sh.H = tau; sh.rem = tau; sh.U = 0.0; }
+    if (tid == 0) { sh.H = tau; sh.rem = tau; sh.U = 0.0; sh.nseq = 0; }
     __syncthreads();
     int halvings = 0, attempts = 0, steps = 0;
     while (true) {
@@ -230,7 +233,11 @@ __global__ void __launch_bounds__(BS_THREADS) k_bs(Sim S, DevParams P, double ta
           __syncthreads();
         }
         if (tid < g) for (int c = 0; c < 6; ++c) sh.y[tid][c] = sh.yn[tid][c];
-        if (tid == 0) { sh.rem = rem - H; sh.H = 2.0 * H; }
+        if (tid == 0) {
+          sh.rem = rem - H; sh.H = 2.0 * H;
+          if (sh.nseq < BS_SEQCAP) { sh.seqH[sh.nseq] = H; sh.seqk[sh.nseq] = (unsigned char)acc; }
+          sh.nseq++;
+        }
         halvings = 0;
         steps++;
       } else {
@@ -256,7 +263,22 @@ __global__ void __launch_bounds__(BS_THREADS) k_bs(Sim S, DevParams P, double ta
     if (tid == 0) {
       atomicAdd((unsigned long long *)&S.counters[C_BSSTEPS], (unsigned long long)steps);
       if (dbits(sh.U) != 0ULL) atomicAdd(S.U, sh.U);
+      if (S.seq_len) {  // the adjoint engine records the accepted sequence
+        int n = sh.nseq, base = -1;
+        if (n <= BS_SEQCAP) {
+          base = atomicAdd(S.seq_count, n);
+          if (base + n > S.seq_cap) base = -1;
+        }
+        if (base < 0) { atomicOr(S.status, ST_RECORD_OVERFLOW); n = 0; base = 0; }
+        S.seq_off[gidx] = base;
+        S.seq_len[gidx] = n;
+        sh.seq_base = base;
+        sh.nseq = n;
+      }
     }
+    __syncthreads();
+    if (S.seq_len)
+      for (int k = tid; k < sh.nseq; k += BS_THREADS) S.seq_pool[sh.seq_base + k] = make_double2(sh.seqH[k], (double)sh.seqk[k]);
     __syncthreads();
   }
 }

@@ -18,6 +18,7 @@ constexpr int NMAX = 2048;        // main mode: up to 2048 massive bodies (Sect.
 constexpr int BS_LEVELS = 8;      // Bulirsch-Stoer levels, substep sequence n_k = 2k
 constexpr int BS_GMAX = 32;       // largest encounter group integrated in one CTA
 constexpr int BS_THREADS = 256;
+constexpr int BS_SEQCAP = 256;   // accepted BS substeps one group may record per substep
 constexpr int NCOUNTERS = 8;
 constexpr int CCAP = 32;          // candidate-list slots per body (more: the bitmap row is scanned)
 constexpr double PARK = 1.0e8;    // ghosts are parked this far out (AU) so no pair ever sees them
@@ -28,6 +29,7 @@ constexpr int ST_BS_FAILED = 2;
 constexpr int ST_REUSE_FULLKICK = 4;
 constexpr int ST_GROUP_TOO_LARGE = 8;
 constexpr int ST_UNION_ROUNDS = 16;
+constexpr int ST_RECORD_OVERFLOW = 32;  // a recording buffer of the adjoint engine was too small
 
 // counters (mirrors genga_status detail[])
 enum { C_STEPS = 0, C_CAND, C_ENC, C_GROUPS, C_BSSTEPS, C_KFALL, C_MERGE, C_FULLKICK };
@@ -66,6 +68,11 @@ struct Sim {
   u64 *bmask, *emask;            // per body: candidate / encounter partners (bit = index in system)
   int *gsize;                    // batched groups: member count per group (gstart = first member)
   int *gtotal;                   // batched groups: members placed so far
+  // recording of the BS decisions for the adjoint engine (null otherwise): the accepted
+  // (H, level) of every substep of group g go to seq_pool[seq_off[g] .. + seq_len[g]]
+  double2 *seq_pool;
+  int *seq_count, seq_cap;
+  int *seq_off, *seq_len;
   int *flags;                    // [0] full opening kick needed
   int *status;                   // status bits
   long long *counters;           // [NCOUNTERS]
@@ -296,7 +303,8 @@ __device__ __forceinline__ void stumpff_d(double z, double &c0, double &c1, doub
 // precision with one Halley step and Newton steps until |ds| <= 4 ulp |s| or a tiny step stops
 // shrinking (rounding floor). Returns 0 on success, 1 when no convergence (state untouched).
 static __device__ int kepler_drift_dev(double mu, double mu2, double &x, double &y, double &z, double &vx,
-                                double &vy, double &vz, double dt, int maxit, int *iters_out) {
+                                double &vy, double &vz, double dt, int maxit, int *iters_out,
+                                double *s_out = nullptr) {
   double r0sq = fma(z, z, fma(y, y, x * x));
   double ir0 = rsqrt_refined(r0sq);
   double r0 = r0sq * ir0;
@@ -350,6 +358,7 @@ static __device__ int kepler_drift_dev(double mu, double mu2, double &x, double 
   }
   if (iters_out) *iters_out = it;
   if (!ok) return 1;
+  if (s_out) *s_out = s_eval;
   // f, g and their derivatives at s_eval (the last point where the c_k were evaluated)
   double s2 = s_eval * s_eval;
   double mus2 = mu * s2;

@@ -27,6 +27,7 @@ ST_KEPLER_FALLBACK = 1
 ST_BS_FAILED = 2
 ST_REUSE_FULLKICK = 4
 ST_GROUP_TOO_LARGE = 8
+ST_RECORD_OVERFLOW = 32
 ST_UNION_ROUNDS = 16
 COUNTER_NAMES = ["steps", "candidates", "encounters", "groups", "bs_steps", "kepler_fallbacks",
                  "mergers", "full_kicks"]
@@ -75,6 +76,14 @@ _SIGS = {
                                  C.c_int, C.c_int, C.c_int, _V, _V, _V, _V, _V, _V, _V, _V, _D, _V]),
     "genga_phase_energy": (C.c_int, [C.c_int, C.c_double, C.c_double, _V, _V, _V, _V, _D, _V]),
     "genga_phase_mathcheck": (C.c_int, [C.c_int, C.c_int, _V, _V, _V]),
+    "genga_adj_init": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, _D, C.c_double, C.c_double, C.c_int,
+                                 C.c_int]),
+    "genga_adj_set_stream": (C.c_int, [_V, _V]),
+    "genga_adj_forward": (C.c_int, [_V, C.c_int, _V, _V, _V, _V, _V]),
+    "genga_adj_backward": (C.c_int, [_V, _V, _V, _V, _V, _V]),
+    "genga_adj_status": (C.c_int, [_V, _I]),
+    "genga_adj_sync": (C.c_int, [_V]),
+    "genga_adj_free": (None, [_V]),
     "genga_init_tp": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, _D, _D, _D, _D, C.c_double, C.c_double, C.c_int,
                                 C.c_int, _D, _D, _D]),
     "genga_get_state_tp": (C.c_int, [_V, _D, _D, _I]),

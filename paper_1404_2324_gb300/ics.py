@@ -15,6 +15,8 @@ stand in for them:
 * ``batch``      -- many independent systems, N_s ~ U{4..64} bodies including the star;
                     planets m log-uniform [1e-7, 1e-4], a U[0.1, 5], e ~ Rayleigh(0.02),
                     i ~ Rayleigh(0.01).
+* ``adj_disks``  -- many independent disks of equal size with the ``disk2048`` shapes, each with
+                    2 Earth masses x n/2048 (the differentiable engine's workload).
 
 Radii follow from a bulk density of 2 g/cm^3. Units: AU, day, Msun, G = k^2 (Gaussian).
 Orbital elements become heliocentric Cartesian states with mu = G (m0 + m_i); this conversion
@@ -132,3 +134,13 @@ def batch(seed=4, n_sys=8192, n_lo=4, n_hi=64):
     x, v = elements_to_cartesian(G_GAUSS * (1.0 + m), a, e, inc, *angs)
     return dict(m0=np.ones(n_sys), G=G_GAUSS, m=m, R=radius_from_mass(m), x=x, v=v,
                 offsets=offsets, dt=6.0, order=2, name="batch")
+
+
+def adj_disks(seed=5, n_sys=64, n=256, order=2):
+    """Config 'adj_disks': n_sys independent disks of n planetesimals with the 2048-disk shapes
+    (0.5-4 AU, e~Rayleigh(0.01), i~Rayleigh(0.005), masses log-uniform 1e-8..1e-6 Msun rescaled to
+    2 Earth masses x n/2048 per disk), for the differentiable engine. Arrays [n_sys, n(, 3)]."""
+    rng = np.random.default_rng(seed)
+    ds = [_disk(rng, n, 1e-8, 1e-6, 0.5, 4.0, 0.01, 0.005, total_mass=2.0 * M_EARTH * n / 2048) for _ in range(n_sys)]
+    return dict(m0=np.ones(n_sys), G=G_GAUSS, m=np.stack([d["m"] for d in ds]), x=np.stack([d["x"] for d in ds]),
+                v=np.stack([d["v"] for d in ds]), dt=6.0, order=order, name="adj_disks")

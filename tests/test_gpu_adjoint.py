@@ -1,0 +1,195 @@
+"""Differentiable engine (B systems of N bodies, merging off) and its hand-written adjoint.
+
+Forward: every system follows the CPU oracle run with collisions off (1e-12 after one step; after
+30 steps 1e-9, or a small multiple of the oracle's own sensitivity in chaotic close passes).
+Backward: the gradient J^T u equals the oracle tangent map (forward-mode derivatives with the same
+frozen decisions) applied to u, and agrees with central finite differences of the GPU forward;
+the checkpoint interval does not change it; torch.autograd sees the same numbers.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from oracle import tangent as TG
+from paper_1404_2324_gb300 import ics
+from paper_1404_2324_gb300.adjoint import AdjointEngine, hybrid_steps
+
+pytestmark = pytest.mark.gpu
+G = ics.G_GAUSS
+
+
+def _t(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _circular(x):
+    v = np.zeros_like(x)
+    for i in range(len(x)):
+        r = np.linalg.norm(x[i])
+        v[i] = np.sqrt(G / r) * np.array([-x[i, 1], x[i, 0], 0.0]) / r
+    return v
+
+
+def three_body_batch():
+    """System 0: a hyperbolic close pass integrated by BS; 1: three bodies far apart; 2: the pass
+    with other masses."""
+    xs, vs, ms = [], [], []
+    x = np.array([[1.0, 0.0, 0.0], [1.0, -0.02, 0.002], [-0.3, 1.5, 0.01]])
+    v = _circular(x)
+    v[1] += [0.0005, 0.0012, 0.0]
+    xs.append(x); vs.append(v); ms.append([3e-6, 1e-6, 2e-6])
+    x = np.array([[1.0, 0.0, 0.0], [0.0, 1.6, 0.01], [-2.4, 0.3, -0.02]])
+    v = _circular(x)
+    v[0] *= 1.01
+    xs.append(x); vs.append(v); ms.append([3e-6, 1e-5, 2e-6])
+    xs.append(xs[0].copy()); vs.append(vs[0].copy()); ms.append([1e-5, 4e-6, 1e-6])
+    return np.array(xs), np.array(vs), np.array(ms)
+
+
+def ring_batch(B=2, n=48, seed=11):
+    """Compact rings at 1 AU (0.95-1.05 AU): close encounters within a few steps."""
+    rng = np.random.default_rng(seed)
+    xs, vs, ms = [], [], []
+    for _ in range(B):
+        d = ics._disk(rng, n, 1e-7, 1e-6, 0.95, 1.05, 0.01, 0.005)
+        xs.append(d["x"]); vs.append(d["v"]); ms.append(d["m"])
+    return np.array(xs), np.array(vs), np.array(ms)
+
+
+def _oracle_run(x, v, m, order, steps, perturb=None):
+    out = []
+    for b in range(len(m)):
+        p = O.params(G=G, m0=1.0, dt=6.0, order=order, collisions=0)
+        xb = x[b] if perturb is None else x[b] * (1 + perturb[b])
+        s = O.Sim(p, m[b], np.zeros(len(m[b])), xb, v[b])
+        s.step(steps)
+        st = s.state()
+        out.append((st["x"], st["v"], s.stats()))
+        s.close()
+    return out
+
+
+def _rel(a, b):
+    return np.max(np.linalg.norm(a - b, axis=-1) / np.linalg.norm(b, axis=-1))
+
+
+@pytest.mark.parametrize("order", [2, 4])
+@pytest.mark.parametrize("batch", ["three", "ring"])
+def test_forward_matches_oracle(order, batch):
+    x, v, m = three_body_batch() if batch == "three" else ring_batch()
+    eng = AdjointEngine(np.ones(len(m)), G, 6.0, order, ckpt_every=10)
+    X, V, M = _t(x), _t(v), _t(m)
+    xo, vo = eng.forward(X, V, M, 1)
+    ref = _oracle_run(x, v, m, order, 1)
+    for b in range(len(m)):
+        assert _rel(xo[b].cpu().numpy(), ref[b][0]) <= 1e-12
+        assert _rel(vo[b].cpu().numpy(), ref[b][1]) <= 1e-12
+    xo, vo = eng.forward(X, V, M, 30)
+    assert eng.status() & 0x2A == 0  # no BS failure, group too large or recording overflow
+    ref = _oracle_run(x, v, m, order, 30)
+    assert sum(r[2]["bs_steps"] for r in ref) > 0
+    rng = np.random.default_rng(3)
+    for b in range(len(m)):
+        e = max(_rel(xo[b].cpu().numpy(), ref[b][0]), _rel(vo[b].cpu().numpy(), ref[b][1]))
+        if e > 1e-9:  # a chaotic close pass: compare with the oracle's own sensitivity
+            pert = [1e-15 * rng.standard_normal(x[k].shape) for k in range(len(m))]
+            alt = _oracle_run(x, v, m, order, 30, perturb=pert)
+            sens = max(_rel(alt[b][0], ref[b][0]), _rel(alt[b][1], ref[b][1]))
+            assert e <= 30 * sens, (b, e, sens)
+    eng.close()
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_gradient_equals_oracle_tangent_map(order):
+    x, v, m = three_body_batch()
+    B, n = m.shape
+    steps = 6
+    eng = AdjointEngine(np.ones(B), G, 6.0, order, ckpt_every=4)
+    X, V, M = _t(x), _t(v), _t(m)
+    eng.forward(X, V, M, steps)
+    rng = np.random.default_rng(5)
+    ux, uv = rng.standard_normal((B, n, 3)), rng.standard_normal((B, n, 3)) * 50.0
+    gx, gv, gm = eng.backward(_t(ux), _t(uv))
+    gx, gv, gm = gx.cpu().numpy(), gv.cpu().numpy(), gm.cpu().numpy()
+    bs_seen = 0
+    for b in range(B):
+        p = O.params(G=G, m0=1.0, dt=6.0, order=order, collisions=0)
+        T = TG.TangentSim(p, m[b], x[b], v[b])
+        T.step(steps)
+        bs_seen += sum(len(q[1]) for seqs in T.bs_sequences for q in seqs)
+        J = T.jacobian()  # (6n, 7n)
+        u = np.concatenate([ux[b].ravel(), uv[b].ravel()])
+        ref = J.T @ u
+        got = np.concatenate([gx[b].ravel(), gv[b].ravel(), gm[b]])
+        # x, v and m columns have different units: compare each block on its own scale
+        for sl in (slice(0, 3 * n), slice(3 * n, 6 * n), slice(6 * n, 7 * n)):
+            err = np.linalg.norm(got[sl] - ref[sl]) / np.linalg.norm(ref[sl])
+            assert err <= 1e-8, (b, sl, err)
+    assert bs_seen > 0
+    eng.close()
+
+
+def test_gradient_matches_central_differences():
+    x, v, m = ring_batch(B=2, n=32, seed=12)
+    B, n = m.shape
+    steps = 10
+    eng = AdjointEngine(np.ones(B), G, 6.0, 2, ckpt_every=4)
+    rng = np.random.default_rng(9)
+    ux, uv = rng.standard_normal((B, n, 3)), rng.standard_normal((B, n, 3)) * 50.0
+    dx = rng.standard_normal((B, n, 3)) * np.linalg.norm(x, axis=-1, keepdims=True)
+    dv = rng.standard_normal((B, n, 3)) * np.linalg.norm(v, axis=-1, keepdims=True)
+    dm = rng.standard_normal((B, n)) * m
+    X, V, M = _t(x), _t(v), _t(m)
+    eng.forward(X, V, M, steps)
+    gx, gv, gm = eng.backward(_t(ux), _t(uv))
+    pred = (gx.cpu().numpy() * dx).sum() + (gv.cpu().numpy() * dv).sum() + (gm.cpu().numpy() * dm).sum()
+
+    def loss(h):
+        xo, vo = eng.forward(_t(x + h * dx), _t(v + h * dv), _t(m + h * dm), steps)
+        return (xo.cpu().numpy() * ux).sum() + (vo.cpu().numpy() * uv).sum()
+
+    h = 1e-7
+    fd = (loss(h) - loss(-h)) / (2 * h)
+    assert abs(fd - pred) <= 1e-6 * abs(pred), (fd, pred)
+    eng.close()
+
+
+def test_checkpoint_interval_does_not_change_the_gradient():
+    x, v, m = ring_batch(B=2, n=40, seed=13)
+    B, n = m.shape
+    rng = np.random.default_rng(2)
+    ux, uv = _t(rng.standard_normal((B, n, 3))), _t(rng.standard_normal((B, n, 3)))
+    res = []
+    for k in (1, 3, 50):
+        eng = AdjointEngine(np.ones(B), G, 6.0, 4, ckpt_every=k)
+        eng.forward(_t(x), _t(v), _t(m), 12)
+        res.append([t.cpu().numpy() for t in eng.backward(ux, uv)])
+        eng.close()
+    for r in res[1:]:
+        for a, b in zip(res[0], r):
+            assert np.array_equal(a, b)
+
+
+def test_autograd_function_and_single_body():
+    # one body: the step is the Kepler drift (plus kicks of nothing); gradients flow to x, v and m
+    x = np.array([[[1.0, 0.1, 0.0]]])
+    v = np.array([[[0.0, 0.0172, 0.0005]]])
+    m = np.array([[1e-6]])
+    eng = AdjointEngine(np.ones(1), G, 6.0, 2, ckpt_every=5)
+    X = _t(x).requires_grad_(True)
+    V = _t(v).requires_grad_(True)
+    M = _t(m).requires_grad_(True)
+    xo, vo = hybrid_steps(X, V, M, eng, 7)
+    loss = (xo * xo).sum() + 3.0 * vo[..., 1].sum()
+    loss.backward()
+    p = O.params(G=G, m0=1.0, dt=6.0, order=2, collisions=0)
+    T = TG.TangentSim(p, m[0], x[0], v[0])
+    T.step(7)
+    J = T.jacobian()
+    xf, _ = T.state()
+    u = np.concatenate([2.0 * xf.ravel(), [0.0, 3.0, 0.0]])
+    ref = J.T @ u
+    got = np.concatenate([X.grad.cpu().numpy().ravel(), V.grad.cpu().numpy().ravel(), M.grad.cpu().numpy().ravel()])
+    np.testing.assert_allclose(got[:6], ref[:6], rtol=1e-9, atol=1e-12 * np.abs(ref[:6]).max())
+    eng.close()
