@@ -219,7 +219,7 @@ def run_batched(args):
                       f"a U[0.1,5], e~Rayleigh(0.02), i~Rayleigh(0.01), 2nd order, dt 6 d; L2 flushed per launch"}
 
 
-def batched_cpu_baseline(nsys=24, steps=20):
+def batched_cpu_baseline(nsys=512, steps=100):
     import oracle as O
     from paper_1404_2324_gb300 import ics
     b = ics.batch(BATCH_SEED, n_sys=BATCH_SYSTEMS)
@@ -246,8 +246,9 @@ TP_SOURCES = [os.path.join(ROOT, "paper_1404_2324_gb300", "csrc", f) for f in ("
 
 
 def tp_profile_counts():
-    """FP64 instructions and DRAM bytes per particle-step from the committed ncu summary of the
-    particle kernels, if it was taken from the current sources (else None)."""
+    """Per particle-step FP64 flops (thread level: DFMA = 2, DADD/DMUL = 1), FP64 warp instructions
+    and DRAM bytes of the particle kernels, from the committed ncu summary, if it was taken from
+    the current sources (else None)."""
     try:
         txt = open(TP_PROFILE).read()
     except OSError:
@@ -255,12 +256,15 @@ def tp_profile_counts():
     h = hashlib.sha256()
     for f in TP_SOURCES:
         h.update(open(f, "rb").read())
-    m = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
-    f = re.search(r"fp64_inst_per_tp_step:\s*([0-9.eE+-]+)", txt)
-    b = re.search(r"dram_bytes_per_tp_step:\s*([0-9.eE+-]+)", txt)
-    if not (m and f and b) or m.group(1) != h.hexdigest():
+    vals = {}
+    for key in ("source_sha256", "fp64_flop_per_tp_step", "fp64_warp_inst_per_tp_step", "dram_bytes_per_tp_step"):
+        m = re.search(key + r":\s*([0-9a-fA-F.eE+-]+)", txt)
+        if not m:
+            return None
+        vals[key] = m.group(1)
+    if vals.pop("source_sha256") != h.hexdigest():
         return None
-    return float(f.group(1)), float(b.group(1))
+    return {k: float(v) for k, v in vals.items()}
 
 
 def run_tp(args, peaks):
@@ -268,7 +272,8 @@ def run_tp(args, peaks):
     replay of the step graph (planets and particles). Each timed step follows an L2 flush."""
     import torch
     from paper_1404_2324_gb300 import genga, ics
-    d = ics.tp_disk(TP_SEED, n_tp=TP_COUNT)
+    n_tp = max(1, getattr(args, "tp_count", TP_COUNT))
+    d = ics.tp_disk(TP_SEED, n_tp=n_tp)
     m = np.concatenate([[d["m0"]], d["m"]])
     R = np.concatenate([[0.0], d["R"]])
     x = np.vstack([np.zeros(3), d["x"]])
@@ -295,25 +300,32 @@ def run_tp(args, peaks):
     code, _ = genga.genga_status(h)
     genga.genga_free(h)
     sec = tot * 1e-3 / steps
-    rate = TP_COUNT / sec
+    rate = n_tp / sec
     gbs = TP_BYTES_PER_TP_STEP * rate / 1e9
-    out = {"metric": "test-particle steps/s", "value": rate, "unit": "TP-steps/s", "n_tp": TP_COUNT,
+    out = {"metric": "test-particle steps/s", "value": rate, "unit": "TP-steps/s", "n_tp": n_tp,
            "n_planets": len(d["m"]), "steps": steps, "ms_per_step": tot / steps, "gpu_launches": kps * steps,
            "hbm": {"achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
                    "bytes_per_tp_step": TP_BYTES_PER_TP_STEP, "peak_source": peaks["hbm_source"]},
            "status": code, "counters": st,
            "config": f"tp_disk seed {TP_SEED}: 8 planets m log-U[1e-7,1e-3], a 0.4-30 AU; 2^20 particles "
                      f"a U[0.3,5], e U[0,0.3], i U[0,0.2]; 2nd order, dt 6 d; L2 flushed per step"}
+    if n_tp != TP_COUNT:
+        out["config"] = out["config"].replace("2^20 particles", f"{n_tp} particles")
     prof = tp_profile_counts()
     if prof is not None:
-        inst, dram = prof
-        fl = 2.0 * inst * rate / 1e12  # counting every FP64 pipe instruction as one FMA (upper bound)
-        out["fp64"] = {"pipe_inst_per_tp_step": inst, "achieved_tflops_upper": fl, "peak": peaks["fp64_tflops"],
-                       "frac_upper": fl / peaks["fp64_tflops"], "dram_bytes_per_tp_step": dram}
+        fl = prof["fp64_flop_per_tp_step"] * rate / 1e12
+        # a warp FP64 instruction holds its sub-partition 64 cycles whatever its active lanes
+        import torch
+        props = torch.cuda.get_device_properties(0)
+        warp_slots = props.multi_processor_count * 4 * peaks["sm_max_mhz"] * 1e6 / 64.0
+        out["fp64"] = {"achieved": fl, "peak": peaks["fp64_tflops"], "unit": "TFLOP/s", "frac": fl / peaks["fp64_tflops"],
+                       "pipe_busy_frac": prof["fp64_warp_inst_per_tp_step"] * rate / warp_slots,
+                       "dram_bytes_per_tp_step": prof["dram_bytes_per_tp_step"],
+                       "source": "per particle-step counts from profiles/tp_pass_ncu.md (ncu, 2^18 particles)"}
     return out
 
 
-def tp_cpu_baseline(n_tp=16384, steps=5):
+def tp_cpu_baseline(n_tp=1 << 20, steps=6):
     import oracle as O
     from paper_1404_2324_gb300 import ics
     d = ics.tp_disk(TP_SEED, n_tp=n_tp)
@@ -325,7 +337,75 @@ def tp_cpu_baseline(n_tp=16384, steps=5):
     dt = time.perf_counter() - t0
     sim.close()
     return {"value": n_tp * steps / dt, "unit": "TP-steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"8 planets + {n_tp} particles of the same recipe x {steps} steps ({dt:.1f} s)"}
+            "sample": f"8 planets + {n_tp} particles of the same recipe x {steps} steps after one ({dt:.1f} s)"}
+
+
+# ------------------------------------------------------------------------------------ adjoint
+ADJ_SYSTEMS, ADJ_N, ADJ_STEPS, ADJ_CKPT, ADJ_SEED = 64, 256, 2000, 50, 5
+
+
+def run_adjoint(args):
+    """Differentiable engine: 64 disks of 256 planetesimals (2048-disk shapes), 2nd order, 2000 steps,
+    a checkpoint every 50 steps. Forward = 2000 steps; backward = the gradient of a random linear
+    functional of the final state with respect to the initial x, v and masses (segment recompute
+    from the checkpoints + the VJPs). Reported: backward time / forward time, and the gradient's
+    agreement with central differences (h = 1e-7 relative along a random direction) on a bounded
+    sample (4 systems, 20 steps: over 2000 steps close passes make finite differences meaningless)."""
+    import torch
+    from paper_1404_2324_gb300 import ics
+    from paper_1404_2324_gb300.adjoint import AdjointEngine
+    d = ics.adj_disks(ADJ_SEED, n_sys=ADJ_SYSTEMS, n=ADJ_N)
+    steps = max(1, args.adj_steps)
+
+    def T(a):
+        return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    eng = AdjointEngine(d["m0"], d["G"], d["dt"], 2, ckpt_every=ADJ_CKPT)
+    X, V, M = T(d["x"]), T(d["v"]), T(d["m"])
+    rng = np.random.default_rng(1)
+    ux, uv = T(rng.standard_normal(d["x"].shape)), T(rng.standard_normal(d["v"].shape))
+    eng.forward(X, V, M, 20)  # warm-up
+    eng.backward(ux, uv)
+    torch.cuda.synchronize()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record(stream)
+    eng.forward(X, V, M, steps)
+    e1.record(stream)
+    eng.backward(ux, uv)
+    e2.record(stream)
+    e2.synchronize()
+    f_ms, b_ms = e0.elapsed_time(e1), e1.elapsed_time(e2)
+    status = eng.status()
+    eng.close()
+    # bounded central-difference check
+    S, K = 4, 20
+    e4 = AdjointEngine(d["m0"][:S], d["G"], d["dt"], 2, ckpt_every=ADJ_CKPT)
+    x4, v4, m4 = d["x"][:S], d["v"][:S], d["m"][:S]
+    u4x, u4v = rng.standard_normal(x4.shape), rng.standard_normal(v4.shape) * 50.0
+    dx = rng.standard_normal(x4.shape) * np.linalg.norm(x4, axis=-1, keepdims=True)
+    dv = rng.standard_normal(v4.shape) * np.linalg.norm(v4, axis=-1, keepdims=True)
+    dm = rng.standard_normal(m4.shape) * m4
+    e4.forward(T(x4), T(v4), T(m4), K)
+    gx, gv, gm = (t.cpu().numpy() for t in e4.backward(T(u4x), T(u4v)))
+    pred = (gx * dx).sum() + (gv * dv).sum() + (gm * dm).sum()
+
+    def loss(h):
+        xo, vo = e4.forward(T(x4 + h * dx), T(v4 + h * dv), T(m4 + h * dm), K)
+        return (xo.cpu().numpy() * u4x).sum() + (vo.cpu().numpy() * u4v).sum()
+
+    fd = (loss(1e-7) - loss(-1e-7)) / 2e-7
+    e4.close()
+    return {"metric": "adjoint/fwd", "value": b_ms / f_ms, "unit": "backward time / forward time",
+            "higher_is_better": False, "forward_ms": f_ms, "backward_ms": b_ms, "steps": steps,
+            "forward_system_steps_per_s": ADJ_SYSTEMS * steps / (f_ms * 1e-3),
+            "grad_vs_central_fd": {"rel_err": abs(fd - pred) / abs(pred), "h_rel": 1e-7,
+                                   "sample": f"{S} systems x {K} steps, one random direction"},
+            "status": status,
+            "config": f"adj_disks seed {ADJ_SEED}: {ADJ_SYSTEMS} disks x {ADJ_N} planetesimals (0.5-4 AU, "
+                      f"2 Earth masses x {ADJ_N}/2048 each), 2nd order, dt 6 d, checkpoint every {ADJ_CKPT} "
+                      f"steps, merging off; state resident in HBM (no L2 flush: each timed region is seconds long)"}
 
 
 # ------------------------------------------------------------------------------------ GPU arm
@@ -435,7 +515,8 @@ def measured_peaks(res):
             hbm, src = float(json.load(f)["hbm_gbs"]), "measured"
     except (OSError, ValueError, KeyError):
         hbm, src = 6800.0, "fallback"
-    return {"hbm_gbs": hbm, "hbm_source": src, "fp64_tflops": res["roofline"]["peak"]}
+    sm = (res.get("clocks") or {}).get("sm_max_mhz") or 2070.0
+    return {"hbm_gbs": hbm, "hbm_source": src, "fp64_tflops": res["roofline"]["peak"], "sm_max_mhz": sm}
 
 
 def main():
@@ -450,7 +531,10 @@ def main():
     ap.add_argument("--batch-launches", type=int, default=5, help="timed 100-step launches of the batched mode")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--tp-steps", type=int, default=TP_STEPS, help="timed steps of the test-particle mode")
+    ap.add_argument("--tp-count", type=int, default=TP_COUNT, help="particles of the test-particle leg (profiling: smaller)")
     ap.add_argument("--no-tp", action="store_true")
+    ap.add_argument("--adj-steps", type=int, default=ADJ_STEPS, help="steps of the differentiable-engine leg")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.warmup < 0 or args.steps < 1:
         ap.error("need --steps >= 1 and --warmup >= 0")
@@ -482,6 +566,8 @@ def main():
         res["batched"] = run_batched(args)
     if not args.no_tp:
         res["test_particles"] = run_tp(args, measured_peaks(res))
+    if not args.no_adjoint:
+        res["adjoint"] = run_adjoint(args)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             import oracle
