@@ -46,6 +46,7 @@ struct AdjDev {
 struct SubRec {
   double *x, *v1, *x1, *v2, *x3, *s;
   int *gstart, *gsize, *gmem, *ngroups, *seq_off, *seq_len;
+  long long *y_off;
 };
 
 __device__ __forceinline__ int sys_of_body(const AdjDev &D, int g) { return g / D.Np; }
@@ -268,15 +269,22 @@ __global__ void k_ad_kepler(Sim S, AdjDev D, DevParams P, double tau, double *re
 // Encounter search and grouping of one system per CTA: the Hermite test (Eqs. teqn, polydelta)
 // on the candidates of the last prechecker, union-find, then groups of >= 2 members (and every
 // body whose Kepler solve failed, alone) in ascending member order, appended to the group list.
+// Everything the serial parts touch is staged in shared memory first.
 __global__ void __launch_bounds__(256) k_ad_group(Sim S, AdjDev D, double tau) {
   __shared__ int par[AD_MAXN];
-  __shared__ int cnt[AD_MAXN];
+  __shared__ int root[AD_MAXN];
+  __shared__ unsigned char fl[AD_MAXN];
   __shared__ int edges[2 * 1024];
-  __shared__ int ne, gbase, mbase;
+  __shared__ int ne;
   const int b = blockIdx.x, tid = threadIdx.x, Np = D.Np, NB = D.NB, base = b * Np;
   const int nc = min(D.ccount[b], D.ccap);
   if (tid == 0) ne = 0;
-  for (int i = tid; i < Np; i += blockDim.x) { par[i] = i; cnt[i] = 0; }
+  int anyfail = 0;
+  for (int i = tid; i < Np; i += blockDim.x) {
+    par[i] = i;
+    fl[i] = (unsigned char)(i < D.N && D.fail[base + i]);
+    anyfail |= fl[i];
+  }
   __syncthreads();
   for (int k = tid; k < nc; k += blockDim.x) {
     const int pr = D.cand[(size_t)b * D.ccap + k];
@@ -292,9 +300,10 @@ __global__ void __launch_bounds__(256) k_ad_group(Sim S, AdjDev D, double tau) {
       if (e < 1024) { edges[2 * e] = i; edges[2 * e + 1] = j; }
     }
   }
-  __syncthreads();
+  anyfail = __syncthreads_or(anyfail);
+  if (tid == 0) D.ccount[b] = 0;  // consumed; the closing kick refills it
+  if (ne == 0 && !anyfail) return;  // uniform: nothing to integrate by BS in this system
   if (tid == 0) {
-    D.ccount[b] = 0;  // consumed; the closing kick refills it
     if (ne > 1024) { atomicOr(S.status, ST_RECORD_OVERFLOW); ne = 1024; }
     for (int e = 0; e < ne; ++e) {  // union by smaller root
       int a = edges[2 * e], c = edges[2 * e + 1];
@@ -307,27 +316,39 @@ __global__ void __launch_bounds__(256) k_ad_group(Sim S, AdjDev D, double tau) {
   for (int i = tid; i < Np; i += blockDim.x) {
     int r = i;
     while (par[r] != r) r = par[r];
-    cnt[i] = r;  // root (group id = smallest member)
+    root[i] = r;  // group id = smallest member
   }
   __syncthreads();
   for (int i = tid; i < Np; i += blockDim.x) par[i] = 0;
   __syncthreads();
-  for (int i = tid; i < Np; i += blockDim.x) atomicAdd(&par[cnt[i]], 1);  // sizes by root
+  for (int i = tid; i < D.N; i += blockDim.x) atomicAdd(&par[root[i]], 1);  // sizes by root
   __syncthreads();
-  if (tid == 0) {  // count groups (size >= 2, or a failed Kepler solve alone) and their members
+  if (tid == 0) {  // groups (size >= 2, or a failed Kepler solve alone), ascending root and member
     int g = 0, m = 0;
     for (int i = 0; i < D.N; ++i)
-      if (cnt[i] == i && (par[i] >= 2 || D.fail[base + i])) { g++; m += par[i]; }
-    gbase = g ? atomicAdd(S.ngroups, g) : 0;
-    mbase = m ? atomicAdd(S.gtotal, m) : 0;
+      if (root[i] == i && (par[i] >= 2 || fl[i])) { g++; m += par[i]; }
+    const int gbase = g ? atomicAdd(S.ngroups, g) : 0;
+    const int mbase = m ? atomicAdd(S.gtotal, m) : 0;
     int gk = gbase, pos = mbase;
-    for (int i = 0; i < D.N; ++i) {
-      if (cnt[i] != i || !(par[i] >= 2 || D.fail[base + i])) continue;
-      S.gstart[gk] = pos;
-      S.gsize[gk] = par[i];
-      for (int k = i; k < D.N; ++k)
-        if (cnt[k] == i) S.gmem[pos++] = base + k;
-      gk++;
+    for (int i = 0; i < D.N; ++i) {  // first pass: starts; par[] becomes the fill cursor
+      if (root[i] == i && (par[i] >= 2 || fl[i])) {
+        S.gstart[gk] = pos;
+        S.gsize[gk] = par[i];
+        gk++;
+        const int sz = par[i];
+        par[i] = -(pos + 1);  // negative: start position of this root's group
+        pos += sz;
+      } else if (root[i] == i) {
+        par[i] = 0;
+      }
+    }
+    for (int i = 0; i < D.N; ++i) {  // second pass: members in ascending order
+      const int r = root[i];
+      if (par[r] < 0) {
+        const int at = -par[r] - 1;
+        S.gmem[at] = base + i;
+        par[r] = -(at + 2);
+      }
     }
   }
 }
@@ -375,6 +396,10 @@ __device__ __forceinline__ void pair_vjp(double dx, double dy, double dz, double
 }
 
 // Kick VJP: ubar = h vbar at the kick positions x (recorded); adds to xbar, mbar, rcbar.
+// Outside the changeover zone (W = 1, W' = 0) the pair terms are regrouped exactly:
+//   xbar_i = -u_i sum_j Gm_j/r^3 + Gm_i sum_j u_j/r^3 + sum_j 3 (d.w)/r^5 d,
+//   mbar_i = -G sum_j (d.u_j)/r^3,   d.w = Gm_j (d.u_i) - Gm_i (d.u_j),
+// so a pair costs two dot products and a few accumulations; pairs inside rc take pair_vjp.
 __global__ void __launch_bounds__(128) k_ad_kick_vjp(Sim S, AdjDev D, double h, const double *xk) {
   extern __shared__ double sm[];
   const int b = blockIdx.y, Np = D.Np, NB = D.NB;
@@ -393,24 +418,44 @@ __global__ void __launch_bounds__(128) k_ad_kick_vjp(Sim S, AdjDev D, double h, 
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int i = blockIdx.x * 32 + lane;
-  double xb[3] = {0.0, 0.0, 0.0}, mb = 0.0, rcb = 0.0;
+  double xe[3] = {0.0, 0.0, 0.0}, me = 0.0, rcb = 0.0;   // changeover-zone pairs (general form)
+  double S1 = 0.0, V0 = 0.0, V1 = 0.0, V2 = 0.0, W0 = 0.0, W1 = 0.0, W2 = 0.0, Mb = 0.0;
+  const double gmi = sgm[i];
+  const double ui[3] = {su[i], su[Np + i], su[2 * Np + i]};
   if (sal[i]) {
     const double xi = sx[i], yi = sy[i], zi = sz[i];
-    const double ui[3] = {su[i], su[Np + i], su[2 * Np + i]};
     const int q = Np >> 2, j0 = w * q, j1 = j0 + q;
     for (int j = j0; j < j1; ++j) {
       if (j == i || !sal[j]) continue;
       const double dx = sx[j] - xi, dy = sy[j] - yi, dz = sz[j] - zi;
       const double r2 = r2_exact(dx, dy, dz);
-      const bool inside = dbits(r2) < umax64(sQ[i], sQ[j]);
-      const double uj[3] = {su[j], su[Np + j], su[2 * Np + j]};
-      const bool own = dbits(src[i]) > dbits(src[j]) || (dbits(src[i]) == dbits(src[j]) && i < j);
-      double rcb_pair = 0.0;
-      pair_vjp<1>(dx, dy, dz, sgm[i], sgm[j], D.G, ui, uj, pmin(sA[i], sA[j]), pmax(src[i], src[j]), inside, xb, mb,
-                  rcb_pair);
-      if (own) rcb += rcb_pair;
+      const double uj0 = su[j], uj1 = su[Np + j], uj2 = su[2 * Np + j];
+      if (dbits(r2) < umax64(sQ[i], sQ[j])) {
+        const double uj[3] = {uj0, uj1, uj2};
+        const bool own = dbits(src[i]) > dbits(src[j]) || (dbits(src[i]) == dbits(src[j]) && i < j);
+        double rcb_pair = 0.0;
+        pair_vjp<1>(dx, dy, dz, gmi, sgm[j], D.G, ui, uj, pmin(sA[i], sA[j]), pmax(src[i], src[j]), true, xe, me,
+                    rcb_pair);
+        if (own) rcb += rcb_pair;
+        continue;
+      }
+      const double yr = rsqrt_refined(r2), yr2 = yr * yr, yr3 = yr2 * yr;
+      const double dui = fma(dz, ui[2], fma(dy, ui[1], dx * ui[0]));
+      const double duj = fma(dz, uj2, fma(dy, uj1, dx * uj0));
+      const double gmj = sgm[j];
+      const double dw = fma(gmj, dui, -gmi * duj);
+      S1 = fma(gmj, yr3, S1);
+      V0 = fma(yr3, uj0, V0); V1 = fma(yr3, uj1, V1); V2 = fma(yr3, uj2, V2);
+      const double cc = 3.0 * yr3 * yr2 * dw;
+      W0 = fma(cc, dx, W0); W1 = fma(cc, dy, W1); W2 = fma(cc, dz, W2);
+      Mb = fma(yr3, duj, Mb);
     }
   }
+  double xb[3];
+  xb[0] = xe[0] + fma(-ui[0], S1, fma(gmi, V0, W0));
+  xb[1] = xe[1] + fma(-ui[1], S1, fma(gmi, V1, W1));
+  xb[2] = xe[2] + fma(-ui[2], S1, fma(gmi, V2, W2));
+  const double mb = fma(-D.G, Mb, me);
   part[w][0][lane] = xb[0]; part[w][1][lane] = xb[1]; part[w][2][lane] = xb[2];
   part[w][3][lane] = mb; part[w][4][lane] = rcb;
   __syncthreads();
@@ -457,18 +502,19 @@ __global__ void __launch_bounds__(256) k_ad_sundrift_vjp(Sim S, AdjDev D, double
   }
 }
 
-// Derivatives of the Stumpff functions, c_k'(z): series for |z| <= 1, identities beyond
-// (c0' = -c1/2, c_k' = (c_{k-1} - k c_k)/(2z)).
+// c_dst[k][m] = (m+1) / (2m+2+k)!: coefficients of c_k'(z) = -sum_m c_dst[k][m] (-z)^m
+constexpr int DST_TERMS = 14;
+__constant__ double c_dst[4][DST_TERMS];
+
+// Derivatives of the Stumpff functions, c_k'(z): series for |z| <= 1 (14 terms: the tail is below
+// 1e-22), identities beyond (c0' = -c1/2, c_k' = (c_{k-1} - k c_k)/(2z)).
 __device__ __forceinline__ void dstumpff(double z, const double c[4], double dc[4]) {
   if (fabs(z) <= 1.0) {
-    // c_k'(z) = -sum_m (m+1) (-z)^m / (2m+2+k)!, summed from the tail (m = 0..13)
+#pragma unroll
     for (int k = 0; k < 4; ++k) {
-      double acc = 0.0;
-      for (int m = 13; m >= 0; --m) {
-        double fact = 1.0;
-        for (int t = 2; t <= 2 * m + 2 + k; ++t) fact *= (double)t;
-        acc = fma(acc, -z, (double)(m + 1) / fact);
-      }
+      double acc = c_dst[k][DST_TERMS - 1];
+#pragma unroll
+      for (int m = DST_TERMS - 2; m >= 0; --m) acc = fma(acc, -z, c_dst[k][m]);
       dc[k] = -acc;
     }
   } else {
@@ -541,79 +587,51 @@ __global__ void k_ad_mark(AdjDev D, const int *gstart, const int *gsize, const i
     for (int q = threadIdx.x; q < gsize[gi]; q += blockDim.x) D.ingrp[gmem[gstart[gi] + q]] = 1;
 }
 
-// BS VJP: one warp per group. The accepted substeps are recomputed from the group's pre-drift state
+// BS VJP: one CTA per group, warp w = BS level w + 1 (the levels of a substep are independent
+// given its start state). The accepted substeps are recomputed from the group's pre-drift state
 // with the recorded (H, level) sequence, then differentiated backwards: Neville weights (linear),
-// then each level's modified-midpoint chain (Gragg), recomputed with its states kept in shared
+// then each level's modified-midpoint chain (Gragg), recomputed with its positions kept in shared
 // memory. Lane q is member q (at most 32).
-struct BsVjpShared {
-  double pos[2 * BS_LEVELS + 1][BS_GMAX][3];  // chain positions z_0..z_n
-  double fv[BS_GMAX][3];                      // adjoints of the members' accelerations
-  double cur[BS_GMAX][3];                     // positions for an acceleration evaluation
+struct GrpShared {  // per group
   double gm[BS_GMAX], A[BS_GMAX], rc[BS_GMAX];
   u64 rcsq[BS_GMAX];
 };
+struct LevShared {  // per level (warp)
+  double pos[2 * BS_LEVELS + 1][BS_GMAX][3];  // chain positions z_0..z_n
+  double cur[BS_GMAX][3];                     // positions for an acceleration evaluation
+  double fv[BS_GMAX][3];                      // adjoints of the members' accelerations
+  double out[BS_GMAX][6];                     // the level's result (forward) or z0 adjoint (reverse)
+  double mb[BS_GMAX], rcb[BS_GMAX];           // the level's mbar / rcbar contributions
+};
 
-__device__ void grp_accel(const BsVjpShared &sh, int g, int q, double Gm0, double *a) {
+__device__ void grp_accel(const GrpShared &G, const double (*cur)[3], int g, int q, double Gm0, double *a) {
   a[0] = a[1] = a[2] = 0.0;
   if (q >= g) return;
-  const double xq = sh.cur[q][0], yq = sh.cur[q][1], zq = sh.cur[q][2];
+  const double xq = cur[q][0], yq = cur[q][1], zq = cur[q][2];
   const double r2 = fma(zq, zq, fma(yq, yq, xq * xq));
   const double f = -Gm0 * rcube_refined(r2);
   a[0] = f * xq; a[1] = f * yq; a[2] = f * zq;
   for (int p = 0; p < g; ++p) {
     if (p == q) continue;
-    const double dx = sh.cur[p][0] - xq, dy = sh.cur[p][1] - yq, dz = sh.cur[p][2] - zq;
+    const double dx = cur[p][0] - xq, dy = cur[p][1] - yq, dz = cur[p][2] - zq;
     const double pr2 = fma(dz, dz, fma(dy, dy, dx * dx));
-    if (dbits(pr2) >= umax64(sh.rcsq[q], sh.rcsq[p])) continue;
+    if (dbits(pr2) >= umax64(G.rcsq[q], G.rcsq[p])) continue;
     const double yr = rsqrt_refined(pr2);
     double wB, wA;
-    changeover_w(pr2 * yr, pmin(sh.A[q], sh.A[p]), 0, wB, wA);
-    const double ff = sh.gm[p] * wA * (yr * yr * yr);
+    changeover_w(pr2 * yr, pmin(G.A[q], G.A[p]), 0, wB, wA);
+    const double ff = G.gm[p] * wA * (yr * yr * yr);
     a[0] = fma(ff, dx, a[0]); a[1] = fma(ff, dy, a[1]); a[2] = fma(ff, dz, a[2]);
   }
 }
 
-// One accepted BS substep (levels 1..k, Neville weights) from y (lane-held), into yo.
-__device__ void grp_bs_step(BsVjpShared &sh, int g, int q, double Gm0, double H, int k, const double *y, double *yo) {
-  for (int c = 0; c < 6; ++c) yo[c] = 0.0;
-  for (int l = 1; l <= k; ++l) {
-    const int n = 2 * l;
-    const double h = H / n, h2 = 2.0 * h;
-    double za[6], zb[6], a[3];
-    for (int c = 0; c < 6; ++c) za[c] = y[c];
-    if (q < g) for (int c = 0; c < 3; ++c) sh.cur[q][c] = za[c];
-    __syncwarp();
-    grp_accel(sh, g, q, Gm0, a);
-    __syncwarp();
-    for (int c = 0; c < 3; ++c) { zb[c] = fma(h, za[3 + c], za[c]); zb[3 + c] = fma(h, a[c], za[3 + c]); }
-    for (int m = 1; m <= n; ++m) {
-      if (q < g) for (int c = 0; c < 3; ++c) sh.cur[q][c] = zb[c];
-      __syncwarp();
-      grp_accel(sh, g, q, Gm0, a);
-      __syncwarp();
-      if (m < n) {
-        double zn[6];
-        for (int c = 0; c < 3; ++c) { zn[c] = fma(h2, zb[3 + c], za[c]); zn[3 + c] = fma(h2, a[c], za[3 + c]); }
-        for (int c = 0; c < 6; ++c) { za[c] = zb[c]; zb[c] = zn[c]; }
-      } else {
-        const double lam = c_lambda[k][l];
-        for (int c = 0; c < 3; ++c) {
-          yo[c] = fma(lam, 0.5 * fma(h, zb[3 + c], zb[c] + za[c]), yo[c]);
-          yo[3 + c] = fma(lam, 0.5 * fma(h, a[c], zb[3 + c] + za[3 + c]), yo[3 + c]);
-        }
-      }
-    }
-  }
-}
-
-// x-adjoint of the group acceleration field at the positions sh.cur, given sh.fv (adjoints of the
-// accelerations): central term and (1 - K) pair terms; also mbar, rcbar of member q.
-__device__ void grp_accel_vjp(const BsVjpShared &sh, int g, int q, double Gm0, double G, double *xb, double &mb,
-                              double &rcb) {
+// x-adjoint of the group acceleration field at cur, given fv (adjoints of the accelerations):
+// central term and (1 - K) pair terms; also mbar, rcbar of member q.
+__device__ void grp_accel_vjp(const GrpShared &G, const double (*cur)[3], const double (*fv)[3], int g, int q,
+                              double Gm0, double Gc, double *xb, double &mb, double &rcb) {
   xb[0] = xb[1] = xb[2] = 0.0;
   if (q >= g) return;
-  const double xq = sh.cur[q][0], yq = sh.cur[q][1], zq = sh.cur[q][2];
-  const double uq[3] = {sh.fv[q][0], sh.fv[q][1], sh.fv[q][2]};
+  const double xq = cur[q][0], yq = cur[q][1], zq = cur[q][2];
+  const double uq[3] = {fv[q][0], fv[q][1], fv[q][2]};
   {  // central: a = -G m0 x / |x|^3, J = -G m0 (I/r^3 - 3 x x^T / r^5)
     const double r2 = fma(zq, zq, fma(yq, yq, xq * xq));
     const double yr = rsqrt_refined(r2), yr3 = yr * yr * yr, yr5 = yr3 * yr * yr;
@@ -624,129 +642,141 @@ __device__ void grp_accel_vjp(const BsVjpShared &sh, int g, int q, double Gm0, d
   }
   for (int p = 0; p < g; ++p) {
     if (p == q) continue;
-    const double dx = sh.cur[p][0] - xq, dy = sh.cur[p][1] - yq, dz = sh.cur[p][2] - zq;
+    const double dx = cur[p][0] - xq, dy = cur[p][1] - yq, dz = cur[p][2] - zq;
     const double pr2 = fma(dz, dz, fma(dy, dy, dx * dx));
-    if (dbits(pr2) >= umax64(sh.rcsq[q], sh.rcsq[p])) continue;
-    const double up[3] = {sh.fv[p][0], sh.fv[p][1], sh.fv[p][2]};
+    if (dbits(pr2) >= umax64(G.rcsq[q], G.rcsq[p])) continue;
+    const double up[3] = {fv[p][0], fv[p][1], fv[p][2]};
     double rcb_pair = 0.0;
-    pair_vjp<-1>(dx, dy, dz, sh.gm[q], sh.gm[p], G, uq, up, pmin(sh.A[q], sh.A[p]), pmax(sh.rc[q], sh.rc[p]), true,
-                 xb, mb, rcb_pair);
-    const bool own = dbits(sh.rc[q]) > dbits(sh.rc[p]) || (dbits(sh.rc[q]) == dbits(sh.rc[p]) && q < p);
+    pair_vjp<-1>(dx, dy, dz, G.gm[q], G.gm[p], Gc, uq, up, pmin(G.A[q], G.A[p]), pmax(G.rc[q], G.rc[p]), true, xb,
+                 mb, rcb_pair);
+    const bool own = dbits(G.rc[q]) > dbits(G.rc[p]) || (dbits(G.rc[q]) == dbits(G.rc[p]) && q < p);
     if (own) rcb += rcb_pair;
   }
 }
 
-__global__ void __launch_bounds__(32) k_ad_bs_vjp(Sim S, AdjDev D, SubRec R, const double *x1, const double *v1,
-                                                  double *scratch) {
-  __shared__ BsVjpShared sh;
-  const int q = threadIdx.x, NB = D.NB;
+// The level-l chain of one BS substep of length H from y (lane-held): result into L.out, the chain
+// positions into L.pos (when keep).
+__device__ void grp_chain(const GrpShared &G, LevShared &L, int g, int q, double Gm0, double H, int l, const double *y,
+                          bool keep) {
+  const int n = 2 * l;
+  const double h = H / n, h2 = 2.0 * h;
+  double za[6], zb[6], a[3];
+  for (int c = 0; c < 6; ++c) za[c] = y[c];
+  if (q < g) for (int c = 0; c < 3; ++c) { L.cur[q][c] = za[c]; if (keep) L.pos[0][q][c] = za[c]; }
+  __syncwarp();
+  grp_accel(G, L.cur, g, q, Gm0, a);
+  __syncwarp();
+  for (int c = 0; c < 3; ++c) { zb[c] = fma(h, za[3 + c], za[c]); zb[3 + c] = fma(h, a[c], za[3 + c]); }
+  for (int m = 1; m <= n; ++m) {
+    if (q < g) for (int c = 0; c < 3; ++c) { L.cur[q][c] = zb[c]; if (keep) L.pos[m][q][c] = zb[c]; }
+    __syncwarp();
+    grp_accel(G, L.cur, g, q, Gm0, a);
+    __syncwarp();
+    if (m < n) {
+      double zn[6];
+      for (int c = 0; c < 3; ++c) { zn[c] = fma(h2, zb[3 + c], za[c]); zn[3 + c] = fma(h2, a[c], za[3 + c]); }
+      for (int c = 0; c < 6; ++c) { za[c] = zb[c]; zb[c] = zn[c]; }
+    } else if (q < g) {
+      for (int c = 0; c < 3; ++c) {
+        L.out[q][c] = 0.5 * fma(h, zb[3 + c], zb[c] + za[c]);
+        L.out[q][3 + c] = 0.5 * fma(h, a[c], zb[3 + c] + za[3 + c]);
+      }
+    }
+  }
+}
+
+constexpr int BSV_WARPS = BS_LEVELS;
+
+__global__ void __launch_bounds__(32 * BSV_WARPS) k_ad_bs_vjp(Sim S, AdjDev D, SubRec R, const double *x1,
+                                                              const double *v1) {
+  extern __shared__ double smraw[];
+  __shared__ GrpShared G;
+  LevShared *LS = (LevShared *)smraw;
+  const int q = threadIdx.x & 31, w = threadIdx.x >> 5, l = w + 1, NB = D.NB;
+  LevShared &L = LS[w];
   const int ng = *R.ngroups;
-  double *ys = scratch + (size_t)blockIdx.x * BS_SEQCAP * BS_GMAX * 6;
   for (int gi = blockIdx.x; gi < ng; gi += gridDim.x) {
     const int g = R.gsize[gi], g0 = R.gstart[gi];
-    if (g > BS_GMAX) continue;
+    if (g > BS_GMAX) continue;  // uniform
     const int body = q < g ? R.gmem[g0 + q] : 0;
-    const int b = sys_of_body(D, R.gmem[g0]);
-    const double Gm0 = D.G * D.m0[b];
-    double y[6], yb[6], mbq = 0.0, rcbq = 0.0;
-    if (q < g) {
-      sh.gm[q] = S.gm[body]; sh.A[q] = S.A[body]; sh.rc[q] = S.rc[body]; sh.rcsq[q] = S.rcsq[body];
-      for (int c = 0; c < 3; ++c) { y[c] = x1[c * NB + body]; y[3 + c] = v1[c * NB + body]; }
-    } else {
-      for (int c = 0; c < 6; ++c) y[c] = 0.0;
+    const double Gm0 = D.G * D.m0[sys_of_body(D, R.gmem[g0])];
+    if (w == 0 && q < g) {
+      G.gm[q] = S.gm[body]; G.A[q] = S.A[body]; G.rc[q] = S.rc[body]; G.rcsq[q] = S.rcsq[body];
     }
-    __syncwarp();
+    double y[6];
+    for (int c = 0; c < 3; ++c) {
+      y[c] = q < g ? x1[c * NB + body] : 0.0;
+      y[3 + c] = q < g ? v1[c * NB + body] : 0.0;
+    }
+    L.mb[q] = 0.0; L.rcb[q] = 0.0;
+    __syncthreads();
     const int nseq = R.seq_len[gi], soff = R.seq_off[gi];
-    // forward recompute of the accepted substeps, keeping their start states
-    for (int s = 0; s < nseq; ++s) {
-      for (int c = 0; c < 6; ++c) ys[(s * BS_GMAX + q) * 6 + c] = y[c];
-      const double2 hk = S.seq_pool[soff + s];
-      double yo[6];
-      grp_bs_step(sh, g, q, Gm0, hk.x, (int)hk.y, y, yo);
-      for (int c = 0; c < 6; ++c) y[c] = yo[c];
+    const long long yoff = R.y_off[gi];
+    double yb[6];
+    for (int c = 0; c < 3; ++c) {
+      yb[c] = q < g ? D.xb[c * NB + body] : 0.0;
+      yb[3 + c] = q < g ? D.vb[c * NB + body] : 0.0;
     }
-    if (q < g)
-      for (int c = 0; c < 3; ++c) { yb[c] = D.xb[c * NB + body]; yb[3 + c] = D.vb[c * NB + body]; }
-    else
-      for (int c = 0; c < 6; ++c) yb[c] = 0.0;
-    // backward over the substeps
+    // backward over the substeps; level l's chain on warp l - 1
     for (int s = nseq - 1; s >= 0; --s) {
       const double2 hk = S.seq_pool[soff + s];
       const double H = hk.x;
       const int k = (int)hk.y;
-      double y0[6], ybp[6];
-      for (int c = 0; c < 6; ++c) { y0[c] = ys[(s * BS_GMAX + q) * 6 + c]; ybp[c] = 0.0; }
-      for (int l = 1; l <= k; ++l) {
+      double y0[6];  // start state of accepted substep s: the pre-drift state, or recorded by k_bs
+      for (int c = 0; c < 6; ++c)
+        y0[c] = s == 0 ? y[c] : (q < g ? S.y_pool[yoff + ((long long)(s - 1) * g + q) * 6 + c] : 0.0);
+      if (l <= k) {
         const double lam = c_lambda[k][l];
         const int n = 2 * l;
         const double h = H / n, h2 = 2.0 * h;
-        // recompute the chain z_0..z_n, keeping positions; a at z_n kept for the output
-        double za[6], zb[6], a[3];
-        for (int c = 0; c < 6; ++c) za[c] = y0[c];
-        if (q < g) for (int c = 0; c < 3; ++c) { sh.cur[q][c] = za[c]; sh.pos[0][q][c] = za[c]; }
-        __syncwarp();
-        grp_accel(sh, g, q, Gm0, a);
-        __syncwarp();
-        for (int c = 0; c < 3; ++c) { zb[c] = fma(h, za[3 + c], za[c]); zb[3 + c] = fma(h, a[c], za[3 + c]); }
-        for (int m = 1; m < n; ++m) {
-          if (q < g) for (int c = 0; c < 3; ++c) { sh.cur[q][c] = zb[c]; sh.pos[m][q][c] = zb[c]; }
-          __syncwarp();
-          grp_accel(sh, g, q, Gm0, a);
-          __syncwarp();
-          double zn[6];
-          for (int c = 0; c < 3; ++c) { zn[c] = fma(h2, zb[3 + c], za[c]); zn[3 + c] = fma(h2, a[c], za[3 + c]); }
-          for (int c = 0; c < 6; ++c) { za[c] = zb[c]; zb[c] = zn[c]; }
-        }
-        if (q < g) for (int c = 0; c < 3; ++c) sh.pos[n][q][c] = zb[c];
-        // reverse: out = (z_n + z_{n-1} + h F(z_n)) / 2, scaled by lam
-        double zbn[6], zbn1[6], zbm[6];  // adjoints of z_n (then z_m), z_{n-1} (then z_{m-1}), running
+        grp_chain(G, L, g, q, Gm0, H, l, y0, true);
+        // reverse of out = (z_n + z_{n-1} + h F(z_n)) / 2, scaled by lam
+        double zbn[6], zbn1[6], xbq[3];
+        double mbq = L.mb[q], rcbq = L.rcb[q];
         for (int c = 0; c < 6; ++c) { zbn[c] = 0.5 * lam * yb[c]; zbn1[c] = 0.5 * lam * yb[c]; }
-        // F(z_n) = (v_n, a(x_n)): Fbar = (h/2) lam ybar
-        {
-          double xbq[3];
-          if (q < g) for (int c = 0; c < 3; ++c) { sh.cur[q][c] = sh.pos[n][q][c]; sh.fv[q][c] = 0.5 * h * lam * yb[3 + c]; }
-          __syncwarp();
-          grp_accel_vjp(sh, g, q, Gm0, D.G, xbq, mbq, rcbq);
-          __syncwarp();
-          for (int c = 0; c < 3; ++c) { zbn[c] += xbq[c]; zbn[3 + c] += 0.5 * h * lam * yb[c]; }
-        }
-        // z_{m+1} = z_{m-1} + 2h F(z_m), m = n-1 .. 1; zbn holds zbar_{m+1}, zbn1 zbar_m
+        if (q < g) for (int c = 0; c < 3; ++c) { L.cur[q][c] = L.pos[n][q][c]; L.fv[q][c] = 0.5 * h * lam * yb[3 + c]; }
+        __syncwarp();
+        grp_accel_vjp(G, L.cur, L.fv, g, q, Gm0, D.G, xbq, mbq, rcbq);
+        __syncwarp();
+        for (int c = 0; c < 3; ++c) { zbn[c] += xbq[c]; zbn[3 + c] += 0.5 * h * lam * yb[c]; }
+        // z_{m+1} = z_{m-1} + 2h F(z_m), m = n-1 .. 1; zbn holds zbar_{m+1}, zbn1 the partial zbar_m
         for (int m = n - 1; m >= 1; --m) {
-          // z_{m-1} gets zbar_{m+1} (carried into the next round as the partial zbar_{m-1})
-          for (int c = 0; c < 6; ++c) zbm[c] = zbn[c];
-          // z_m gets 2h J_F(z_m)^T zbar_{m+1}
-          double xbq[3];
-          if (q < g) for (int c = 0; c < 3; ++c) { sh.cur[q][c] = sh.pos[m][q][c]; sh.fv[q][c] = h2 * zbn[3 + c]; }
+          double carry[6];
+          for (int c = 0; c < 6; ++c) carry[c] = zbn[c];  // z_{m-1} gets zbar_{m+1}
+          if (q < g) for (int c = 0; c < 3; ++c) { L.cur[q][c] = L.pos[m][q][c]; L.fv[q][c] = h2 * zbn[3 + c]; }
           __syncwarp();
-          grp_accel_vjp(sh, g, q, Gm0, D.G, xbq, mbq, rcbq);
+          grp_accel_vjp(G, L.cur, L.fv, g, q, Gm0, D.G, xbq, mbq, rcbq);
           __syncwarp();
           for (int c = 0; c < 3; ++c) { zbn1[c] += xbq[c]; zbn1[3 + c] += h2 * zbn[c]; }
-          // shift: zbar_m becomes the "m+1" slot, zbar_{m-1} (accumulated) the "m" slot
-          double carry[6];
-          for (int c = 0; c < 6; ++c) carry[c] = zbm[c];
           for (int c = 0; c < 6; ++c) { zbn[c] = zbn1[c]; zbn1[c] = carry[c]; }
         }
-        // now zbn = zbar_1, zbn1 = contributions to zbar_0 so far; z_1 = z_0 + h F(z_0)
-        {
-          double xbq[3];
-          if (q < g) for (int c = 0; c < 3; ++c) { sh.cur[q][c] = sh.pos[0][q][c]; sh.fv[q][c] = h * zbn[3 + c]; }
-          __syncwarp();
-          grp_accel_vjp(sh, g, q, Gm0, D.G, xbq, mbq, rcbq);
-          __syncwarp();
-          for (int c = 0; c < 3; ++c) {
-            ybp[c] += zbn1[c] + zbn[c] + xbq[c];
-            ybp[3 + c] += zbn1[3 + c] + zbn[3 + c] + h * zbn[c];
-          }
+        // z_1 = z_0 + h F(z_0)
+        if (q < g) for (int c = 0; c < 3; ++c) { L.cur[q][c] = L.pos[0][q][c]; L.fv[q][c] = h * zbn[3 + c]; }
+        __syncwarp();
+        grp_accel_vjp(G, L.cur, L.fv, g, q, Gm0, D.G, xbq, mbq, rcbq);
+        __syncwarp();
+        for (int c = 0; c < 3; ++c) {
+          L.out[q][c] = zbn1[c] + zbn[c] + xbq[c];
+          L.out[q][3 + c] = zbn1[3 + c] + zbn[3 + c] + h * zbn[c];
         }
+        L.mb[q] = mbq; L.rcb[q] = rcbq;
       }
-      for (int c = 0; c < 6; ++c) yb[c] = ybp[c];
+      __syncthreads();
+      for (int c = 0; c < 6; ++c) {  // ybar of the substep's start: sum over levels in order
+        double acc = 0.0;
+        for (int ll = 1; ll <= k; ++ll) acc += LS[ll - 1].out[q][c];
+        yb[c] = acc;
+      }
+      __syncthreads();
     }
-    if (q < g) {
+    if (w == 0 && q < g) {
+      double mb = 0.0, rcb = 0.0;
+      for (int ll = 0; ll < BSV_WARPS; ++ll) { mb += LS[ll].mb[q]; rcb += LS[ll].rcb[q]; }
       for (int c = 0; c < 3; ++c) { D.xb[c * NB + body] = yb[c]; D.vb[c * NB + body] = yb[3 + c]; }
-      D.mb[body] += mbq;
-      D.rcb[body] += rcbq;
+      D.mb[body] += mb;
+      D.rcb[body] += rcb;
     }
-    __syncwarp();
+    __syncthreads();
   }
 }
 
@@ -861,6 +891,17 @@ int num_sms_adj() {
   return sms > 0 ? sms : 1;
 }
 
+void init_dstumpff() {
+  double t[4][DST_TERMS];
+  for (int k = 0; k < 4; ++k)
+    for (int m = 0; m < DST_TERMS; ++m) {
+      long double fact = 1.0L;
+      for (int q = 2; q <= 2 * m + 2 + k; ++q) fact *= (long double)q;
+      t[k][m] = (double)((long double)(m + 1) / fact);
+    }
+  cudaMemcpyToSymbol(c_dst, t, sizeof(t));
+}
+
 void init_lambda() {
   double lam[BS_LEVELS + 1][BS_LEVELS + 1] = {};
   for (int k = 1; k <= BS_LEVELS; ++k)
@@ -903,8 +944,9 @@ struct genga_adj {
   int *grec = nullptr;
   double2 *seq_pool = nullptr;
   int *seq_count = nullptr, seq_cap = 0;
-  double *bs_scratch = nullptr;
-  int bs_blocks = 0;
+  double *y_pool = nullptr, *y_scratch = nullptr;
+  long long *y_count = nullptr, *yoff_rec = nullptr;
+  int bs_blocks = 0, bs_fwd_grid = 0;
   size_t kick_smem = 0, vjp_smem = 0;
 };
 
@@ -926,6 +968,7 @@ SubRec subrec(genga_adj *c, int slot) {
   R.x = r; R.v1 = r + 3 * NB; R.x1 = r + 6 * NB; R.v2 = r + 9 * NB; R.x3 = r + 12 * NB; R.s = r + 15 * NB;
   R.gstart = gi; R.gsize = gi + NB; R.gmem = gi + 2 * NB; R.seq_off = gi + 3 * NB;
   R.ngroups = gi + 4 * NB; R.seq_len = nullptr;
+  R.y_off = c->yoff_rec + (size_t)slot * NB;
   return R;
 }
 
@@ -956,7 +999,7 @@ int run_step(genga_adj *c, int slot) {
       R = subrec(c, sl);
       R.seq_len = seq_len_of(c, sl);
       S.gstart = R.gstart; S.gsize = R.gsize; S.gmem = R.gmem; S.ngroups = R.ngroups;
-      S.seq_off = R.seq_off; S.seq_len = R.seq_len;
+      S.seq_off = R.seq_off; S.seq_len = R.seq_len; S.y_off = R.y_off;
     }
     if (cudaMemsetAsync(S.ngroups, 0, sizeof(int), st) != cudaSuccess) return GENGA_ECUDA;
     if (cudaMemsetAsync(S.gtotal, 0, sizeof(int), st) != cudaSuccess) return GENGA_ECUDA;
@@ -964,7 +1007,7 @@ int run_step(genga_adj *c, int slot) {
     k_ad_sundrift<<<c->B, 256, 0, st>>>(S, c->D, h, R.v1, R.x1);
     k_ad_kepler<<<(NB + 127) / 128, 128, 0, st>>>(S, c->D, c->P, tau, R.s);
     k_ad_group<<<c->B, 256, 0, st>>>(S, c->D, tau);
-    launch_bs(S, c->P, tau, 2 * c->B > 64 ? 2 * c->B : 64, st);
+    launch_bs(S, c->P, tau, c->bs_fwd_grid, st);
     k_ad_sundrift<<<c->B, 256, 0, st>>>(S, c->D, h, R.v2, R.x3);
     launch_kick(c, 1, h, nullptr);
   }
@@ -1071,10 +1114,15 @@ int genga_adj_init(genga_adj **out, int n_sys, int n, const double *m0, double G
   c->seq_cap = (int)std::min<size_t>(nslot * NB * 8 + 1024, (size_t)1 << 26);
   c->seq_pool = dalloc<double2>(c, c->seq_cap, err);
   c->seq_count = dalloc<int>(c, 1, err);
-  c->bs_blocks = 2 * num_sms_adj();
-  c->bs_scratch = dalloc<double>(c, (size_t)c->bs_blocks * BS_SEQCAP * BS_GMAX * 6, err);
+  c->bs_blocks = num_sms_adj();
+  c->bs_fwd_grid = 2 * c->B > 64 ? 2 * c->B : 64;
+  c->y_scratch = dalloc<double>(c, (size_t)c->bs_fwd_grid * BS_SEQCAP * BS_GMAX * 6, err);
+  c->y_pool = dalloc<double>(c, (size_t)1 << 24, err);
+  c->y_count = dalloc<long long>(c, 1, err);
+  c->yoff_rec = dalloc<long long>(c, nslot * NB, err);
   if (err != cudaSuccess) { genga_adj_free(c); return GENGA_ENOMEM; }
   S.seq_pool = c->seq_pool; S.seq_count = c->seq_count; S.seq_cap = c->seq_cap;
+  S.y_pool = c->y_pool; S.y_scratch = c->y_scratch; S.y_count = c->y_count; S.y_cap = (long long)1 << 24;
   std::vector<int> sys(NB);
   for (size_t g = 0; g < NB; ++g) sys[g] = (int)(g / c->Np);
   cudaMemcpy(S.sys_of, sys.data(), NB * sizeof(int), cudaMemcpyHostToDevice);
@@ -1085,8 +1133,10 @@ int genga_adj_init(genga_adj **out, int n_sys, int n, const double *m0, double G
   cudaFuncSetAttribute(k_ad_kick<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->kick_smem);
   cudaFuncSetAttribute(k_ad_kick<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->kick_smem);
   cudaFuncSetAttribute(k_ad_kick_vjp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->vjp_smem);
+  cudaFuncSetAttribute(k_ad_bs_vjp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(BSV_WARPS * sizeof(LevShared)));
   bs_init_constants();
   init_lambda();
+  init_dstumpff();
   if (cudaDeviceSynchronize() != cudaSuccess || cudaGetLastError() != cudaSuccess) { genga_adj_free(c); return GENGA_ECUDA; }
   *out = c;
   return GENGA_OK;
@@ -1144,6 +1194,7 @@ int genga_adj_backward(genga_adj *c, const double *xbar, const double *vbar, dou
     const int t0 = sgm * c->K, t1 = std::min(t0 + c->K, c->nsteps);
     restore(c, sgm);
     cudaMemsetAsync(c->seq_count, 0, sizeof(int), st);
+    cudaMemsetAsync(c->y_count, 0, sizeof(long long), st);
     for (int t = t0; t < t1; ++t) {
       const int rc = run_step(c, t - t0);
       if (rc != GENGA_OK) return rc;
@@ -1164,7 +1215,7 @@ int genga_adj_backward(genga_adj *c, const double *xbar, const double *vbar, dou
         cudaMemsetAsync(c->D.ingrp, 0, NB * sizeof(int), st);
         k_ad_mark<<<c->bs_blocks, 32, 0, st>>>(c->D, R.gstart, R.gsize, R.gmem, R.ngroups);
         k_ad_kepler_vjp<<<(NB + 127) / 128, 128, 0, st>>>(c->S, c->D, tau, R.x1, R.v1, R.s);
-        k_ad_bs_vjp<<<c->bs_blocks, 32, 0, st>>>(c->S, c->D, R, R.x1, R.v1, c->bs_scratch);
+        k_ad_bs_vjp<<<c->bs_blocks, 32 * BSV_WARPS, BSV_WARPS * sizeof(LevShared), st>>>(c->S, c->D, R, R.x1, R.v1);
         k_ad_sundrift_vjp<<<c->B, 256, 0, st>>>(c->S, c->D, h, R.v1);
         k_ad_kick_vjp<<<kgrid, 128, c->vjp_smem, st>>>(c->S, c->D, h, R.x);
       }

@@ -26,6 +26,7 @@ struct BsShared {
   double H, rem, U;
   int accept;
   int nseq, seq_base;          // recorded accepted substeps (adjoint engine only)
+  long long y_base;
   double seqH[BS_SEQCAP];
   unsigned char seqk[BS_SEQCAP];
 };
@@ -233,6 +234,9 @@ __global__ void __launch_bounds__(BS_THREADS) k_bs(Sim S, DevParams P, double ta
           __syncthreads();
         }
         if (tid < g) for (int c = 0; c < 6; ++c) sh.y[tid][c] = sh.yn[tid][c];
+        if (S.seq_len && tid < g && steps < BS_SEQCAP)  // adjoint engine: the state after this substep
+          for (int c = 0; c < 6; ++c)
+            S.y_scratch[(((size_t)blockIdx.x * BS_SEQCAP + steps) * BS_GMAX + tid) * 6 + c] = sh.yn[tid][c];
         if (tid == 0) {
           sh.rem = rem - H; sh.H = 2.0 * H;
           if (sh.nseq < BS_SEQCAP) { sh.seqH[sh.nseq] = H; sh.seqk[sh.nseq] = (unsigned char)acc; }
@@ -269,16 +273,29 @@ __global__ void __launch_bounds__(BS_THREADS) k_bs(Sim S, DevParams P, double ta
           base = atomicAdd(S.seq_count, n);
           if (base + n > S.seq_cap) base = -1;
         }
-        if (base < 0) { atomicOr(S.status, ST_RECORD_OVERFLOW); n = 0; base = 0; }
+        long long ybase = 0;
+        if (base >= 0 && n > 1) {  // states after substeps 1 .. n-1 (the last one is the result)
+          ybase = atomicAdd((unsigned long long *)S.y_count, (unsigned long long)((n - 1) * g * 6));
+          if (ybase + (long long)(n - 1) * g * 6 > S.y_cap) base = -1;
+        }
+        if (base < 0) { atomicOr(S.status, ST_RECORD_OVERFLOW); n = 0; base = 0; ybase = 0; }
         S.seq_off[gidx] = base;
         S.seq_len[gidx] = n;
+        S.y_off[gidx] = ybase;
         sh.seq_base = base;
+        sh.y_base = ybase;
         sh.nseq = n;
       }
     }
     __syncthreads();
-    if (S.seq_len)
+    if (S.seq_len) {
       for (int k = tid; k < sh.nseq; k += BS_THREADS) S.seq_pool[sh.seq_base + k] = make_double2(sh.seqH[k], (double)sh.seqk[k]);
+      const int ny = (sh.nseq > 1 ? sh.nseq - 1 : 0) * g * 6;
+      for (int k = tid; k < ny; k += BS_THREADS) {
+        const int s = k / (g * 6), r = k % (g * 6);
+        S.y_pool[sh.y_base + k] = S.y_scratch[(((size_t)blockIdx.x * BS_SEQCAP + s) * BS_GMAX + r / 6) * 6 + r % 6];
+      }
+    }
     __syncthreads();
   }
 }

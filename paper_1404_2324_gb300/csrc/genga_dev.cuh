@@ -73,6 +73,11 @@ struct Sim {
   double2 *seq_pool;
   int *seq_count, seq_cap;
   int *seq_off, *seq_len;
+  // ... and the state after each accepted substep but the last: members x 6 doubles per substep
+  // at y_pool[y_off[g] ..], staged in y_scratch [gridDim.x][BS_SEQCAP][BS_GMAX][6] meanwhile
+  double *y_pool, *y_scratch;
+  long long *y_count, y_cap;
+  long long *y_off;
   int *flags;                    // [0] full opening kick needed
   int *status;                   // status bits
   long long *counters;           // [NCOUNTERS]
