@@ -31,8 +31,25 @@ struct BsShared {
   unsigned char seqk[BS_SEQCAP];
 };
 
+// W_A = 1 - W_B of a pair at distance r, A = 1/(0.9 rc), without branches: y is clamped to [0, 1]
+// on the integer pipe, where the formula itself gives exactly 1 (y = 0) and 0 (y = 1), so the value
+// equals the branched changeover_w everywhere.
+__device__ __forceinline__ double changeover_wA_clamped(double r, double A, int kmode) {
+  double y = fma(r, A, -1.0 / 9.0);
+  y = is_neg_or_zero(y) ? 0.0 : (dbits(y) >= dbits(1.0) ? 1.0 : y);
+  const double omy = 1.0 - y, y2 = y * y, o2 = omy * omy;
+  const double iD = rcp_refined(y2 + o2);  // 1/(2y^2 - 2y + 1)
+  double wA = o2 * iD;
+  if (kmode == 1) wA += (y + 1.0 / 9.0) * (2.0 * y * omy) * (iD * iD);
+  return wA;
+}
+
 // Acceleration terms of member q assigned to this thread: term p == q is the central mass, any
 // other p the (1 - K)-weighted pull of partner p (H_A, Eq. Ha). Summed over the slot's threads.
+// Every lane runs the same straight-line code (the central mass is a partner at the origin with
+// G m0 and weight 1; a partner outside rc gets weight 0): lanes of one warp that took different
+// branches would each pay for both, and an FP64 warp instruction costs its sub-partition 64
+// cycles whatever its active lanes.
 __device__ __forceinline__ void bs_terms(const BsShared &sh, const DevParams &P, double Gm0, int g, int q, int sub,
                                          int tps, const double (*pos)[3], bool q_alive, double &ax, double &ay,
                                          double &az) {
@@ -40,21 +57,16 @@ __device__ __forceinline__ void bs_terms(const BsShared &sh, const DevParams &P,
   const double xq = pos[q][0], yq = pos[q][1], zq = pos[q][2];
   if (q_alive) {
     for (int p = sub; p < g; p += tps) {
-      if (p == q) {
-        const double r2 = fma(zq, zq, fma(yq, yq, xq * xq));
-        const double f = -Gm0 * rcube_refined(r2);
-        ax = fma(f, xq, ax); ay = fma(f, yq, ay); az = fma(f, zq, az);
-      } else if (sh.alive[p]) {
-        const double dx = pos[p][0] - xq, dy = pos[p][1] - yq, dz = pos[p][2] - zq;
-        const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
-        if (dbits(r2) < umax64(sh.rcsq[q], sh.rcsq[p])) {
-          const double yr = rsqrt_refined(r2);
-          double wB, wA;
-          changeover_w(r2 * yr, pmin(sh.A[q], sh.A[p]), P.kmode, wB, wA);
-          const double f = sh.gm[p] * wA * (yr * yr * yr);
-          ax = fma(f, dx, ax); ay = fma(f, dy, ay); az = fma(f, dz, az);
-        }
-      }
+      const bool cen = p == q;
+      const double dx = (cen ? 0.0 : pos[p][0]) - xq, dy = (cen ? 0.0 : pos[p][1]) - yq,
+                   dz = (cen ? 0.0 : pos[p][2]) - zq;
+      const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+      const double yr = rsqrt_refined(r2);
+      const bool inside = sh.alive[p] && dbits(r2) < umax64(sh.rcsq[q], sh.rcsq[p]);
+      const double wA = changeover_wA_clamped(r2 * yr, pmin(sh.A[q], sh.A[p]), P.kmode);
+      const double w = cen ? 1.0 : (inside ? wA : 0.0);
+      const double f = (cen ? Gm0 : sh.gm[p]) * w * (yr * yr * yr);
+      ax = fma(f, dx, ax); ay = fma(f, dy, ay); az = fma(f, dz, az);
     }
   }
   for (int o = tps >> 1; o > 0; o >>= 1) {
