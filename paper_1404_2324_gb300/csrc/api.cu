@@ -139,6 +139,11 @@ struct genga_ctx {
   cudaGraphExec_t gexec = nullptr;
   int bs_grid = 1;
   int tp_grid = 1;  // blocks of the test-particle encounter and BS kernels
+  // main mode: groups of gsplit or more members go to the cluster BS kernel, on a side branch of
+  // the step graph that runs beside the one-CTA BS kernel
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int gsplit = BS_GMAX + 1, cl_grid = 0;
   bool profiling = false;
   // batched mode
   bool batched = false;
@@ -250,7 +255,16 @@ void enqueue_step(genga_ctx *c, cudaStream_t st) {
     if (tp) launch_planet_table(S, T, P, tau, st);
     launch_encounter(S, tau, S.ebm + (size_t)j * S.npad * S.W, st);
     launch_group(S, st);
-    launch_bs(S, P, tau, c->bs_grid, st);
+    if (c->side) {  // fork: cluster kernel for the larger groups, one-CTA kernel for the rest; join
+      cudaEventRecord(c->ev_fork, st);
+      cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+      launch_bs_cluster(S, P, tau, c->gsplit, c->cl_grid, c->side);
+      launch_bs(S, P, tau, c->bs_grid, st, c->gsplit);
+      cudaEventRecord(c->ev_join, c->side);
+      cudaStreamWaitEvent(st, c->ev_join, 0);
+    } else {
+      launch_bs(S, P, tau, c->bs_grid, st);
+    }
     if (tp) {
       launch_tp_encounter(S, T, tau, c->tp_grid, st);
       launch_tp_bs(S, T, P, tau, 3 * num_sms(), st);
@@ -350,6 +364,15 @@ int genga_init(genga_ctx **out, int n, const double *masses, const double *radii
   c->bs_grid = 2 * num_sms();
   if (c->bs_grid > c->S.npad) c->bs_grid = c->S.npad;
   bs_init_constants();
+  bs_cluster_init_constants();
+  if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    genga_free(c);
+    return GENGA_ECUDA;
+  }
+  c->gsplit = 5;  // measured: from 5 members on, a cluster per group beats one CTA per group
+  c->cl_grid = bs_cluster_grid();
   cudaStream_t st = c->stream;
   if (cudaMemcpyAsync(c->sx, x, 3 * nn * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync(c->sv, v, 3 * nn * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
@@ -773,6 +796,9 @@ void genga_free(genga_ctx *c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   drop_graph(c);
   for (int k = 0; k < c->nkev; ++k) cudaEventDestroy(c->kev[k]);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->side) cudaStreamDestroy(c->side);
   c->mem.release();
   if (c->own) cudaStreamDestroy(c->own);
   delete c;

@@ -31,19 +31,6 @@ struct BsShared {
   unsigned char seqk[BS_SEQCAP];
 };
 
-// W_A = 1 - W_B of a pair at distance r, A = 1/(0.9 rc), without branches: y is clamped to [0, 1]
-// on the integer pipe, where the formula itself gives exactly 1 (y = 0) and 0 (y = 1), so the value
-// equals the branched changeover_w everywhere.
-__device__ __forceinline__ double changeover_wA_clamped(double r, double A, int kmode) {
-  double y = fma(r, A, -1.0 / 9.0);
-  y = is_neg_or_zero(y) ? 0.0 : (dbits(y) >= dbits(1.0) ? 1.0 : y);
-  const double omy = 1.0 - y, y2 = y * y, o2 = omy * omy;
-  const double iD = rcp_refined(y2 + o2);  // 1/(2y^2 - 2y + 1)
-  double wA = o2 * iD;
-  if (kmode == 1) wA += (y + 1.0 / 9.0) * (2.0 * y * omy) * (iD * iD);
-  return wA;
-}
-
 // Acceleration terms of member q assigned to this thread: term p == q is the central mass, any
 // other p the (1 - K)-weighted pull of partner p (H_A, Eq. Ha). Summed over the slot's threads.
 // Every lane runs the same straight-line code (the central mass is a partner at the origin with
@@ -76,7 +63,7 @@ __device__ __forceinline__ void bs_terms(const BsShared &sh, const DevParams &P,
   }
 }
 
-__global__ void __launch_bounds__(BS_THREADS) k_bs(Sim S, DevParams P, double tau) {
+__global__ void __launch_bounds__(BS_THREADS) k_bs(Sim S, DevParams P, double tau, int gsplit) {
   __shared__ BsShared sh;
   const int tid = threadIdx.x;
   const int np = S.npad;
@@ -86,6 +73,7 @@ __global__ void __launch_bounds__(BS_THREADS) k_bs(Sim S, DevParams P, double ta
     // central mass of the group's system (batched mode) or of the single system
     const double m0 = S.sys_of ? S.sys_m0[S.sys_of[S.gmem[g0]]] : P.m0;
     const double Gm0 = P.G * m0;
+    if (g >= gsplit && g <= BS_GMAX) continue;  // uniform: integrated by the cluster kernel
     if (g > BS_GMAX) {
       if (tid == 0) atomicOr(S.status, ST_GROUP_TOO_LARGE);
       continue;  // uniform across the CTA
@@ -322,9 +310,9 @@ void bs_init_constants() {
   cudaMemcpyToSymbol(c_facinv, h, sizeof(h));
 }
 
-void launch_bs(const Sim &S, const DevParams &P, double tau, int max_groups, cudaStream_t st) {
+void launch_bs(const Sim &S, const DevParams &P, double tau, int max_groups, cudaStream_t st, int gsplit) {
   const int grid = max_groups < 1 ? 1 : max_groups;
-  k_bs<<<grid, BS_THREADS, 0, st>>>(S, P, tau);
+  k_bs<<<grid, BS_THREADS, 0, st>>>(S, P, tau, gsplit);
 }
 
 }  // namespace genga

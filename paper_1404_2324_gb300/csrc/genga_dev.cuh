@@ -193,6 +193,19 @@ __device__ __forceinline__ void changeover_w(double r, double A, int kmode, doub
   }
 }
 
+// W_A = 1 - W_B of a pair at distance r, A = 1/(0.9 rc), without branches: y is clamped to [0, 1]
+// on the integer pipe, where the formula itself gives exactly 1 (y = 0) and 0 (y = 1), so the value
+// equals the branched changeover_w everywhere.
+__device__ __forceinline__ double changeover_wA_clamped(double r, double A, int kmode) {
+  double y = fma(r, A, -1.0 / 9.0);
+  y = is_neg_or_zero(y) ? 0.0 : (dbits(y) >= dbits(1.0) ? 1.0 : y);
+  const double omy = 1.0 - y, y2 = y * y, o2 = omy * omy;
+  const double iD = rcp_refined(y2 + o2);  // 1/(2y^2 - 2y + 1)
+  double wA = o2 * iD;
+  if (kmode == 1) wA += (y + 1.0 / 9.0) * (2.0 * y * omy) * (iD * iD);
+  return wA;
+}
+
 // ---------------------------------------------------------------------------------------------
 // Canonical decision quantities, evaluated exactly as the CPU oracle does (no contraction):
 // |d|^2 = fma(dz, dz, fma(dy, dy, dx*dx)), a.b likewise.

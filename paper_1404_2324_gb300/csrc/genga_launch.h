@@ -30,7 +30,13 @@ void launch_copy_edges(const Sim &S, const int *pairs, int npairs, cudaStream_t 
 
 // bs.cu
 void bs_init_constants();  // once per device, before any capture
-void launch_bs(const Sim &S, const DevParams &P, double tau, int max_groups, cudaStream_t st);
+// Groups of at least gsplit members are skipped (left to the cluster kernel); BS_GMAX + 1: none.
+void launch_bs(const Sim &S, const DevParams &P, double tau, int max_groups, cudaStream_t st,
+               int gsplit = BS_GMAX + 1);
+// bs_cluster.cu: groups of gmin .. BS_GMAX members, one cluster of 8 CTAs (one per level) each
+void bs_cluster_init_constants();  // once per device, before any capture
+int bs_cluster_grid();
+void launch_bs_cluster(const Sim &S, const DevParams &P, double tau, int gmin, int grid, cudaStream_t st);
 
 // batch.cu
 void launch_b_rcrit(const Sim &S, const DevParams &P, double tau_abs, int check, cudaStream_t st);
