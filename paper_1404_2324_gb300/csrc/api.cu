@@ -79,7 +79,9 @@ bool alloc_sim(Sim &S, DevMem &mem, int n, int nsub) {
   }
   S.nitems = (int)items.size();
   S.items = mem.get<int>(items.size());
-  const int target = 4 * num_sms();  // one warp per sub-partition
+  // two warps per sub-partition: the second hides the first's FP64 dependency waits (measured at
+  // N = 2048: one warp 102.6 us, two 88.3 us, three 89.8 us, four 90.2 us per kick)
+  const int target = 8 * num_sms();
   S.nwarps = S.nitems < target ? S.nitems : target;
   S.flags = mem.get<int>(4); S.status = mem.get<int>(1);
   S.counters = mem.get<long long>(NCOUNTERS); S.U = mem.get<double>(1);
