@@ -63,7 +63,7 @@ __device__ __forceinline__ void bs_terms(const BsShared &sh, const DevParams &P,
   }
 }
 
-__global__ void __launch_bounds__(BS_THREADS) k_bs(Sim S, DevParams P, double tau, int gsplit) {
+__global__ void __launch_bounds__(BS_THREADS, 2) k_bs(Sim S, DevParams P, double tau, int gsplit) {
   __shared__ BsShared sh;
   const int tid = threadIdx.x;
   const int np = S.npad;
@@ -102,19 +102,24 @@ __global__ void __launch_bounds__(BS_THREADS) k_bs(Sim S, DevParams P, double ta
       if (absbits(H) > absbits(rem)) H = rem;
       if (++attempts > 200000) { if (tid == 0) atomicOr(S.status, ST_BS_FAILED); break; }
       // ---- one attempt of length H: all levels' modified-midpoint integrations at once ----
+      // Level L finishes its chain at evaluation 2L; its tableau row and error are then computed
+      // right away (thread (qc, cc) holds member qc's component cc of the previous row), and the
+      // attempt stops at the first converged level: the same decision as building the whole
+      // tableau first, but attempts that converge at level 4-6 (almost all) skip the deeper chains.
       const double h = __ddiv_rn(H, (double)nk), h2 = 2.0 * h;
       const bool qa = act && sh.alive[q];
       double zA[6], zB[6], out[6];
       for (int c = 0; c < 6; ++c) zA[c] = sh.y[q][c];
       if (act && sub == 0) for (int c = 0; c < 3; ++c) sh.pos[0][lev][q][c] = zA[c];
-      // error scales 1/|x|, 1/|v| at the start of the attempt
-      double isx, isv;
-      {
-        const double sx2 = fma(zA[2], zA[2], fma(zA[1], zA[1], zA[0] * zA[0]));
-        const double sv2 = fma(zA[5], zA[5], fma(zA[4], zA[4], zA[3] * zA[3]));
-        isx = dbits(sx2) == 0ULL ? 4.49423283715579e307 : rsqrt_refined(sx2);
-        isv = dbits(sv2) == 0ULL ? 4.49423283715579e307 : rsqrt_refined(sv2);
+      const int qc = tid / 6, cc = tid % 6;
+      const bool rowth = qc < g;
+      double scale = 0.0;  // error scale of (qc, cc): 1/|x| or 1/|v| at the start of the attempt
+      if (rowth) {
+        const double *yq = sh.y[qc] + (cc < 3 ? 0 : 3);
+        const double s2 = fma(yq[2], yq[2], fma(yq[1], yq[1], yq[0] * yq[0]));
+        scale = dbits(s2) == 0ULL ? 4.49423283715579e307 : rsqrt_refined(s2);
       }
+      if (tid < BS_LEVELS) sh.err[tid] = 0ULL;
       __syncthreads();
       double ax = 0.0, ay = 0.0, az = 0.0;
       // every lane of a warp that holds any active slot takes part (the term sums shuffle across
@@ -126,8 +131,12 @@ __global__ void __launch_bounds__(BS_THREADS) k_bs(Sim S, DevParams P, double ta
       } else {
         for (int c = 0; c < 6; ++c) zB[c] = zA[c];
       }
+      const int lmax = P.bs_kmax < BS_LEVELS ? P.bs_kmax : BS_LEVELS;
+      const u64 eps = dbits(P.bs_eps);
+      double prev[BS_LEVELS], cur[BS_LEVELS];
+      int acc = 0;
       int b = 1;
-      for (int e = 1; e <= 2 * BS_LEVELS; ++e) {
+      for (int e = 1; e <= 2 * lmax; ++e) {
         const bool lv = act && e <= nk;
         if (lv && sub == 0) for (int c = 0; c < 3; ++c) sh.pos[b][lev][q][c] = zB[c];
         __syncthreads();
@@ -150,41 +159,24 @@ __global__ void __launch_bounds__(BS_THREADS) k_bs(Sim S, DevParams P, double ta
           } else if (e == nk) {
             for (int c = 0; c < 6; ++c) out[c] = zA[c];
           }
+          if (e == nk && sub == 0) for (int c = 0; c < 6; ++c) sh.tab[lev][q][c] = out[c];  // T_{L,1}
         }
         b ^= 1;
-      }
-      // ---- polynomial extrapolation in h^2 (Neville), as a wavefront across levels ----
-      double T[6], Tm1[6];
-      for (int c = 0; c < 6; ++c) { T[c] = out[c]; Tm1[c] = out[c]; }
-      if (tid < BS_LEVELS) sh.err[tid] = 0ULL;
-      for (int j = 1; j < BS_LEVELS; ++j) {
+        if (e & 1) continue;
+        // level Lc = e/2 is complete: its tableau row (polynomial extrapolation in h^2, Neville)
+        const int Lc = e >> 1;
         __syncthreads();
-        if (act && sub == 0) for (int c = 0; c < 6; ++c) sh.tab[lev][q][c] = T[c];
-        __syncthreads();
-        if (act && L > j) {
-          const double fi = c_facinv[L][j];
-          if (j == L - 1) for (int c = 0; c < 6; ++c) Tm1[c] = T[c];
-          for (int c = 0; c < 6; ++c) T[c] = fma(T[c] - sh.tab[lev - 1][q][c], fi, T[c]);
+        if (rowth) {
+          cur[0] = sh.tab[Lc - 1][qc][cc];
+          for (int j = 1; j < Lc; ++j) cur[j] = fma(cur[j - 1] - prev[j - 1], c_facinv[Lc][j], cur[j - 1]);
+          if (Lc >= 2 && sh.alive[qc]) atomicMax(&sh.err[Lc - 1], absbits((cur[Lc - 1] - cur[Lc - 2]) * scale));
+          for (int j = 0; j < Lc; ++j) prev[j] = cur[j];
         }
+        __syncthreads();
+        if (Lc >= 2 && sh.err[Lc - 1] <= eps) { acc = Lc; break; }  // uniform: every thread reads the same error
       }
-      // level error: max over live members and components of |T[L][L] - T[L][L-1]| / scale
-      if (act && sub == 0 && L >= 2 && L <= P.bs_kmax && qa) {
-        u64 em = 0ULL;
-        for (int c = 0; c < 6; ++c) em = umax64(em, absbits((T[c] - Tm1[c]) * (c < 3 ? isx : isv)));
-        atomicMax(&sh.err[lev], em);
-      }
-      __syncthreads();
-      if (tid == 0) {
-        int acc = 0;
-        const u64 eps = dbits(P.bs_eps);
-        for (int l = 1; l < P.bs_kmax && l < BS_LEVELS; ++l)
-          if (sh.err[l] <= eps) { acc = l + 1; break; }
-        sh.accept = acc;
-      }
-      __syncthreads();
-      const int acc = sh.accept;
+      if (acc && rowth) sh.yn[qc][cc] = cur[acc - 1];
       if (acc) {
-        if (act && sub == 0 && L == acc) for (int c = 0; c < 6; ++c) sh.yn[q][c] = T[c];
         __syncthreads();
         if (P.collisions) {  // contact test over the accepted substep (Hermite, threshold (R_a + R_b)^2)
           const int npair = g * (g - 1) / 2;

@@ -112,10 +112,17 @@ __global__ void __cluster_dims__(CL_SIZE, 1, 1) __launch_bounds__(CL_THREADS)
         sh.isc[tid][0] = dbits(sx2) == 0ULL ? 4.49423283715579e307 : rsqrt_refined(sx2);
         sh.isc[tid][1] = dbits(sv2) == 0ULL ? 4.49423283715579e307 : rsqrt_refined(sv2);
       }
-      // ---- this level's modified-midpoint integration ----
+      // ---- this level's modified-midpoint integration; levels checked as they complete ----
+      // Level Lc finishes at evaluation 2 Lc. At every even evaluation all CTAs meet at a cluster
+      // barrier, read T_{Lc,1} from its CTA, extend their tableau rows (thread (qc, cc): member
+      // qc, component cc) and test level Lc; the first converged level ends the attempt in every
+      // CTA at once (the same data, the same arithmetic, so the same decision).
       double zA[6], zB[6], out[6];
       for (int c = 0; c < 6; ++c) zA[c] = act ? sh.y[q][c] : 0.0;
       if (act && sub == 0) for (int c = 0; c < 3; ++c) sh.pos[0][q][c] = zA[c];
+      const int qc = tid / 6, cc = tid % 6;
+      const bool rowth = qc < g;
+      if (tid < BS_LEVELS) sh.err[tid] = 0ULL;
       __syncthreads();
       double ax = 0.0, ay = 0.0, az = 0.0;
       if (__any_sync(0xffffffffu, act)) cl_terms(sh, P, Gm0, g, act ? q : 0, sub, sh.pos[0], qa, ax, ay, az);
@@ -125,63 +132,54 @@ __global__ void __cluster_dims__(CL_SIZE, 1, 1) __launch_bounds__(CL_THREADS)
       } else {
         for (int c = 0; c < 6; ++c) zB[c] = zA[c];
       }
+      const int lmax = P.bs_kmax < BS_LEVELS ? P.bs_kmax : BS_LEVELS;
+      const u64 eps = dbits(P.bs_eps);
+      const double scale = rowth ? sh.isc[qc][cc < 3 ? 0 : 1] : 0.0;
+      double prev[BS_LEVELS], cur[BS_LEVELS];
+      int acc = 0;
       int b = 1;
-      for (int e = 1; e <= nk; ++e) {
-        if (act && sub == 0) for (int c = 0; c < 3; ++c) sh.pos[b][q][c] = zB[c];
-        __syncthreads();
-        if (__any_sync(0xffffffffu, act)) cl_terms(sh, P, Gm0, g, act ? q : 0, sub, sh.pos[b], qa, ax, ay, az);
-        if (qa) {
-          if (e < nk) {
-            double zn[6];
-            zn[0] = fma(h2, zB[3], zA[0]); zn[1] = fma(h2, zB[4], zA[1]); zn[2] = fma(h2, zB[5], zA[2]);
-            zn[3] = fma(h2, ax, zA[3]); zn[4] = fma(h2, ay, zA[4]); zn[5] = fma(h2, az, zA[5]);
-            for (int c = 0; c < 6; ++c) { zA[c] = zB[c]; zB[c] = zn[c]; }
-          } else {
-            out[0] = 0.5 * fma(h, zB[3], zB[0] + zA[0]);
-            out[1] = 0.5 * fma(h, zB[4], zB[1] + zA[1]);
-            out[2] = 0.5 * fma(h, zB[5], zB[2] + zA[2]);
-            out[3] = 0.5 * fma(h, ax, zB[3] + zA[3]);
-            out[4] = 0.5 * fma(h, ay, zB[4] + zA[4]);
-            out[5] = 0.5 * fma(h, az, zB[5] + zA[5]);
+      for (int e = 1; e <= 2 * lmax; ++e) {
+        const bool lv = e <= nk;  // this CTA's level is still integrating
+        if (lv) {
+          if (act && sub == 0) for (int c = 0; c < 3; ++c) sh.pos[b][q][c] = zB[c];
+          __syncthreads();
+          if (__any_sync(0xffffffffu, act)) cl_terms(sh, P, Gm0, g, act ? q : 0, sub, sh.pos[b], qa, ax, ay, az);
+          if (qa) {
+            if (e < nk) {
+              double zn[6];
+              zn[0] = fma(h2, zB[3], zA[0]); zn[1] = fma(h2, zB[4], zA[1]); zn[2] = fma(h2, zB[5], zA[2]);
+              zn[3] = fma(h2, ax, zA[3]); zn[4] = fma(h2, ay, zA[4]); zn[5] = fma(h2, az, zA[5]);
+              for (int c = 0; c < 6; ++c) { zA[c] = zB[c]; zB[c] = zn[c]; }
+            } else {
+              out[0] = 0.5 * fma(h, zB[3], zB[0] + zA[0]);
+              out[1] = 0.5 * fma(h, zB[4], zB[1] + zA[1]);
+              out[2] = 0.5 * fma(h, zB[5], zB[2] + zA[2]);
+              out[3] = 0.5 * fma(h, ax, zB[3] + zA[3]);
+              out[4] = 0.5 * fma(h, ay, zB[4] + zA[4]);
+              out[5] = 0.5 * fma(h, az, zB[5] + zA[5]);
+            }
+          } else if (act && e == nk) {
+            for (int c = 0; c < 6; ++c) out[c] = zA[c];
           }
-        } else if (e == nk) {
-          for (int c = 0; c < 6; ++c) out[c] = zA[c];
+          if (e == nk && act && sub == 0) for (int c = 0; c < 6; ++c) sh.T1[buf][q][c] = out[c];
+          b ^= 1;
         }
-        b ^= 1;
-      }
-      if (act && sub == 0) for (int c = 0; c < 6; ++c) sh.T1[buf][q][c] = out[c];
-      if (tid < BS_LEVELS) sh.err[tid] = 0ULL;
-      cluster.sync();  // every level's result is in place
-      // ---- Neville tableau of all levels, per (member, component), from the gathered results ----
-      double diag[BS_LEVELS];
-      const int qc = tid / 6, cc = tid % 6;
-      if (qc < g) {
-        double prev[BS_LEVELS], cur[BS_LEVELS];
-        const bool live = sh.alive[qc];
-        const double scale = sh.isc[qc][cc < 3 ? 0 : 1];
-        for (int l = 1; l <= BS_LEVELS; ++l) {
-          const double *rt = cluster.map_shared_rank(&sh.T1[buf][0][0], (unsigned)(l - 1));
+        if (e & 1) continue;
+        const int Lc = e >> 1;
+        cluster.sync();  // T_{Lc,1} is complete in CTA Lc - 1
+        if (rowth) {
+          const double *rt = cluster.map_shared_rank(&sh.T1[buf][0][0], (unsigned)(Lc - 1));
           cur[0] = rt[qc * 6 + cc];
-          for (int j = 1; j < l; ++j) cur[j] = fma(cur[j - 1] - prev[j - 1], c_facinv_cl[l][j], cur[j - 1]);
-          diag[l - 1] = cur[l - 1];
-          if (l >= 2 && l <= P.bs_kmax && live)
-            atomicMax(&sh.err[l - 1], absbits((cur[l - 1] - cur[l - 2]) * scale));
-          for (int j = 0; j < l; ++j) prev[j] = cur[j];
+          for (int j = 1; j < Lc; ++j) cur[j] = fma(cur[j - 1] - prev[j - 1], c_facinv_cl[Lc][j], cur[j - 1]);
+          if (Lc >= 2 && sh.alive[qc]) atomicMax(&sh.err[Lc - 1], absbits((cur[Lc - 1] - cur[Lc - 2]) * scale));
+          for (int j = 0; j < Lc; ++j) prev[j] = cur[j];
         }
+        __syncthreads();
+        if (Lc >= 2 && sh.err[Lc - 1] <= eps) { acc = Lc; break; }
       }
-      __syncthreads();
-      if (tid == 0) {
-        int acc = 0;
-        const u64 eps = dbits(P.bs_eps);
-        for (int l = 1; l < P.bs_kmax && l < BS_LEVELS; ++l)
-          if (sh.err[l] <= eps) { acc = l + 1; break; }
-        sh.accept = acc;
-      }
-      __syncthreads();
-      const int acc = sh.accept;
+      if (acc && rowth) sh.yn[qc][cc] = cur[acc - 1];
       buf ^= 1;
       if (acc) {
-        if (qc < g) sh.yn[qc][cc] = diag[acc - 1];
         __syncthreads();
         if (P.collisions) {  // contact test and mergers, redundantly in every CTA; globals by rank 0
           const int npair = g * (g - 1) / 2;
