@@ -395,78 +395,171 @@ __device__ __forceinline__ void pair_vjp(double dx, double dy, double dz, double
   rcb += Wrc * yr3 * dw;
 }
 
-// Kick VJP: ubar = h vbar at the kick positions x (recorded); adds to xbar, mbar, rcbar.
-// Outside the changeover zone (W = 1, W' = 0) the pair terms are regrouped exactly:
-//   xbar_i = -u_i sum_j Gm_j/r^3 + Gm_i sum_j u_j/r^3 + sum_j 3 (d.w)/r^5 d,
-//   mbar_i = -G sum_j (d.u_j)/r^3,   d.w = Gm_j (d.u_i) - Gm_i (d.u_j),
-// so a pair costs two dot products and a few accumulations; pairs inside rc take pair_vjp.
-__global__ void __launch_bounds__(128) k_ad_kick_vjp(Sim S, AdjDev D, double h, const double *xk) {
-  extern __shared__ double sm[];
-  const int b = blockIdx.y, Np = D.Np, NB = D.NB;
-  double *sx = sm, *sy = sx + Np, *sz = sy + Np, *sgm = sz + Np, *sA = sgm + Np, *src = sA + Np;
-  double *su = src + Np;  // [3 Np]
-  u64 *sQ = (u64 *)(su + 3 * Np);
-  int *sal = (int *)(sQ + Np);
-  __shared__ double part[4][5][32];
-  const int base = b * Np;
-  for (int j = threadIdx.x; j < Np; j += blockDim.x) {
-    const int g = base + j;
-    sx[j] = xk[g]; sy[j] = xk[NB + g]; sz[j] = xk[2 * NB + g];
-    sgm[j] = S.gm[g]; sA[j] = S.A[g]; src[j] = S.rc[g]; sQ[j] = S.rcsq[g]; sal[j] = S.alive[g];
-    for (int c = 0; c < 3; ++c) su[c * Np + j] = h * D.vb[c * NB + g];
+// Both sides of one changeover-zone pair of the kick (weight W = K): Jw (xbar_i -= Jw, xbar_j += Jw),
+// the mbar contributions of i (from a_j) and of j (from a_i), and the pair's rcbar.
+__device__ __forceinline__ void pair_vjp_zone(double dx, double dy, double dz, double gmi, double gmj, double G,
+                                              const double *ui, const double *uj, double Apair, double rcpair,
+                                              double *Jw, double &mbi, double &mbj, double &rcbp) {
+  const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+  const double yr = rsqrt_refined(r2), yr2 = yr * yr, yr3 = yr2 * yr;
+  const double r = r2 * yr;
+  double K, dK;
+  k_and_dk(r, Apair, K, dK);
+  const double W = K, Wr = dK * Apair, Wrc = -dK * (r * Apair) / rcpair;
+  const double w0 = gmj * ui[0] - gmi * uj[0], w1 = gmj * ui[1] - gmi * uj[1], w2 = gmj * ui[2] - gmi * uj[2];
+  const double dw = fma(dz, w2, fma(dy, w1, dx * w0));
+  const double c1 = W * yr3, c2 = dw * (Wr * yr2 * yr2 - 3.0 * W * yr3 * yr2);
+  Jw[0] = fma(c1, w0, c2 * dx); Jw[1] = fma(c1, w1, c2 * dy); Jw[2] = fma(c1, w2, c2 * dz);
+  mbi = -G * c1 * fma(dz, uj[2], fma(dy, uj[1], dx * uj[0]));
+  mbj = G * c1 * fma(dz, ui[2], fma(dy, ui[1], dx * ui[0]));
+  rcbp = Wrc * yr3 * dw;
+}
+
+// Kick VJP, Newton's third law: every unordered pair once, on 32x32 tile pairs of one system with a
+// warp-shuffle ring (lane l holds body i = I*32 + l, the j data and j-side sums rotate), as in the
+// forward kick. Outside the changeover zone a body's sums are S1 = sum Gm_p/r^3, V = sum u_p/r^3,
+// Wd = sum 3 (d.w)/r^5 d (d pointing from the body to its partner) and Mb = sum (d.u_p)/r^3, and
+// xbar = -u S1 + Gm V + Wd, mbar = -G Mb: the exact regrouping of sum_p -J w, w = Gm_p u - Gm u_p,
+// J = (I - 3 d d^T / r^2)/r^3, d.w = Gm_p (d.u) - Gm (d.u_p). Work item k of system
+// b is the tile pair (I, J), I <= J; its sums for tile I go to part[b][I][J], those for tile J to
+// part[b][J][I] (5 values x 32 lanes each), reduced per body in a fixed order afterwards.
+struct VjpBody {
+  double x, y, z, gm, u0, u1, u2, rc, A;
+  u64 Q;
+  int al;
+};
+
+__device__ __forceinline__ void vjp_shfl(VjpBody &B, int src) {
+  B.x = __shfl_sync(0xffffffffu, B.x, src); B.y = __shfl_sync(0xffffffffu, B.y, src);
+  B.z = __shfl_sync(0xffffffffu, B.z, src); B.gm = __shfl_sync(0xffffffffu, B.gm, src);
+  B.u0 = __shfl_sync(0xffffffffu, B.u0, src); B.u1 = __shfl_sync(0xffffffffu, B.u1, src);
+  B.u2 = __shfl_sync(0xffffffffu, B.u2, src); B.rc = __shfl_sync(0xffffffffu, B.rc, src);
+  B.A = __shfl_sync(0xffffffffu, B.A, src); B.Q = __shfl_sync(0xffffffffu, B.Q, src);
+  B.al = __shfl_sync(0xffffffffu, B.al, src);
+}
+
+struct VjpAcc {
+  double S1, V0, V1, V2, W0, W1, W2, Mb, e0, e1, e2, me, rcb;
+};
+
+__device__ __forceinline__ void vjp_acc_zero(VjpAcc &a) {
+  a.S1 = a.V0 = a.V1 = a.V2 = a.W0 = a.W1 = a.W2 = a.Mb = a.e0 = a.e1 = a.e2 = a.me = a.rcb = 0.0;
+}
+
+__device__ __forceinline__ void vjp_acc_shfl(VjpAcc &a, int src) {
+  a.S1 = __shfl_sync(0xffffffffu, a.S1, src); a.V0 = __shfl_sync(0xffffffffu, a.V0, src);
+  a.V1 = __shfl_sync(0xffffffffu, a.V1, src); a.V2 = __shfl_sync(0xffffffffu, a.V2, src);
+  a.W0 = __shfl_sync(0xffffffffu, a.W0, src); a.W1 = __shfl_sync(0xffffffffu, a.W1, src);
+  a.W2 = __shfl_sync(0xffffffffu, a.W2, src); a.Mb = __shfl_sync(0xffffffffu, a.Mb, src);
+  a.e0 = __shfl_sync(0xffffffffu, a.e0, src); a.e1 = __shfl_sync(0xffffffffu, a.e1, src);
+  a.e2 = __shfl_sync(0xffffffffu, a.e2, src); a.me = __shfl_sync(0xffffffffu, a.me, src);
+  a.rcb = __shfl_sync(0xffffffffu, a.rcb, src);
+}
+
+// The pair (a, b) with d = x_b - x_a, both sides.
+__device__ __forceinline__ void vjp_pair(const VjpBody &Pa, const VjpBody &Pb, int ia, int ib, double G, bool act,
+                                         VjpAcc &aa, VjpAcc &ab) {
+  if (!act || !Pa.al || !Pb.al) return;
+  const double dx = Pb.x - Pa.x, dy = Pb.y - Pa.y, dz = Pb.z - Pa.z;
+  const double r2 = r2_exact(dx, dy, dz);
+  const double ua[3] = {Pa.u0, Pa.u1, Pa.u2}, ub[3] = {Pb.u0, Pb.u1, Pb.u2};
+  if (dbits(r2) < umax64(Pa.Q, Pb.Q)) {  // changeover zone (rare): general form
+    double Jw[3], mba, mbb, rcbp;
+    pair_vjp_zone(dx, dy, dz, Pa.gm, Pb.gm, G, ua, ub, pmin(Pa.A, Pb.A), pmax(Pa.rc, Pb.rc), Jw, mba, mbb, rcbp);
+    aa.e0 -= Jw[0]; aa.e1 -= Jw[1]; aa.e2 -= Jw[2]; aa.me += mba;
+    ab.e0 += Jw[0]; ab.e1 += Jw[1]; ab.e2 += Jw[2]; ab.me += mbb;
+    const bool own_a = dbits(Pa.rc) > dbits(Pb.rc) || (dbits(Pa.rc) == dbits(Pb.rc) && ia < ib);
+    if (own_a) aa.rcb += rcbp; else ab.rcb += rcbp;
+    return;
   }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int i = blockIdx.x * 32 + lane;
-  double xe[3] = {0.0, 0.0, 0.0}, me = 0.0, rcb = 0.0;   // changeover-zone pairs (general form)
-  double S1 = 0.0, V0 = 0.0, V1 = 0.0, V2 = 0.0, W0 = 0.0, W1 = 0.0, W2 = 0.0, Mb = 0.0;
-  const double gmi = sgm[i];
-  const double ui[3] = {su[i], su[Np + i], su[2 * Np + i]};
-  if (sal[i]) {
-    const double xi = sx[i], yi = sy[i], zi = sz[i];
-    const int q = Np >> 2, j0 = w * q, j1 = j0 + q;
-    for (int j = j0; j < j1; ++j) {
-      if (j == i || !sal[j]) continue;
-      const double dx = sx[j] - xi, dy = sy[j] - yi, dz = sz[j] - zi;
-      const double r2 = r2_exact(dx, dy, dz);
-      const double uj0 = su[j], uj1 = su[Np + j], uj2 = su[2 * Np + j];
-      if (dbits(r2) < umax64(sQ[i], sQ[j])) {
-        const double uj[3] = {uj0, uj1, uj2};
-        const bool own = dbits(src[i]) > dbits(src[j]) || (dbits(src[i]) == dbits(src[j]) && i < j);
-        double rcb_pair = 0.0;
-        pair_vjp<1>(dx, dy, dz, gmi, sgm[j], D.G, ui, uj, pmin(sA[i], sA[j]), pmax(src[i], src[j]), true, xe, me,
-                    rcb_pair);
-        if (own) rcb += rcb_pair;
-        continue;
-      }
-      const double yr = rsqrt_refined(r2), yr2 = yr * yr, yr3 = yr2 * yr;
-      const double dui = fma(dz, ui[2], fma(dy, ui[1], dx * ui[0]));
-      const double duj = fma(dz, uj2, fma(dy, uj1, dx * uj0));
-      const double gmj = sgm[j];
-      const double dw = fma(gmj, dui, -gmi * duj);
-      S1 = fma(gmj, yr3, S1);
-      V0 = fma(yr3, uj0, V0); V1 = fma(yr3, uj1, V1); V2 = fma(yr3, uj2, V2);
-      const double cc = 3.0 * yr3 * yr2 * dw;
-      W0 = fma(cc, dx, W0); W1 = fma(cc, dy, W1); W2 = fma(cc, dz, W2);
-      Mb = fma(yr3, duj, Mb);
+  const double yr = rsqrt_refined(r2), yr2 = yr * yr, yr3 = yr2 * yr;
+  const double dua = fma(dz, ua[2], fma(dy, ua[1], dx * ua[0]));
+  const double dub = fma(dz, ub[2], fma(dy, ub[1], dx * ub[0]));
+  const double dw = fma(Pb.gm, dua, -Pa.gm * dub);  // d.w with w = Gm_b u_a - Gm_a u_b
+  const double cc = 3.0 * yr3 * yr2 * dw;
+  aa.S1 = fma(Pb.gm, yr3, aa.S1);
+  aa.V0 = fma(yr3, ub[0], aa.V0); aa.V1 = fma(yr3, ub[1], aa.V1); aa.V2 = fma(yr3, ub[2], aa.V2);
+  aa.W0 = fma(cc, dx, aa.W0); aa.W1 = fma(cc, dy, aa.W1); aa.W2 = fma(cc, dz, aa.W2);
+  aa.Mb = fma(yr3, dub, aa.Mb);
+  ab.S1 = fma(Pa.gm, yr3, ab.S1);
+  ab.V0 = fma(yr3, ua[0], ab.V0); ab.V1 = fma(yr3, ua[1], ab.V1); ab.V2 = fma(yr3, ua[2], ab.V2);
+  ab.W0 = fma(-cc, dx, ab.W0); ab.W1 = fma(-cc, dy, ab.W1); ab.W2 = fma(-cc, dz, ab.W2);
+  ab.Mb = fma(-yr3, dua, ab.Mb);
+}
+
+// The five per-body outputs of a set of sums.
+__device__ __forceinline__ void vjp_store(double *p, const VjpAcc &a, const VjpBody &B, double G) {
+  p[0] = a.e0 + fma(-B.u0, a.S1, fma(B.gm, a.V0, a.W0));
+  p[32] = a.e1 + fma(-B.u1, a.S1, fma(B.gm, a.V1, a.W1));
+  p[64] = a.e2 + fma(-B.u2, a.S1, fma(B.gm, a.V2, a.W2));
+  p[96] = fma(-G, a.Mb, a.me);
+  p[128] = a.rcb;
+}
+
+__global__ void __launch_bounds__(128) k_ad_kick_vjp_sym(Sim S, AdjDev D, double h, const double *xk, double *part) {
+  const int T = D.Np >> 5, npair = T * (T + 1) / 2, NB = D.NB;
+  const int lane = threadIdx.x & 31;
+  const int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (item >= D.B * npair) return;
+  const int b = item / npair;
+  int k = item % npair, I = 0;
+  while (k >= T - I) { k -= T - I; ++I; }
+  const int J = I + k;
+  const int base = b * D.Np;
+  auto load = [&](int g, VjpBody &B) {
+    B.x = xk[g]; B.y = xk[NB + g]; B.z = xk[2 * NB + g];
+    B.gm = S.gm[g]; B.rc = S.rc[g]; B.A = S.A[g]; B.Q = S.rcsq[g]; B.al = S.alive[g];
+    B.u0 = h * D.vb[g]; B.u1 = h * D.vb[NB + g]; B.u2 = h * D.vb[2 * NB + g];
+  };
+  VjpBody Pi, Pj;
+  load(base + I * 32 + lane, Pi);
+  VjpAcc ai, aj;
+  vjp_acc_zero(ai);
+  vjp_acc_zero(aj);
+  const int src = (lane + 1) & 31;
+  double *pbase = part + (size_t)b * T * T * 160;
+  if (I == J) {  // diagonal tile: lane l pairs with l + s + 1, s = 0..15 (the last step for half the lanes)
+    Pj = Pi;
+    for (int s = 0; s < 16; ++s) {
+      vjp_shfl(Pj, src);
+      vjp_acc_shfl(aj, src);
+      const int jl = (lane + s + 1) & 31;
+      vjp_pair(Pi, Pj, I * 32 + lane, I * 32 + jl, D.G, s < 15 || lane < 16, ai, aj);
     }
+    const int home = (lane + 16) & 31;  // the j sums return to the lane that owns body I*32 + lane
+    vjp_acc_shfl(aj, home);
+    Pj = Pi;
+    VjpAcc t = ai;
+    t.S1 += aj.S1; t.V0 += aj.V0; t.V1 += aj.V1; t.V2 += aj.V2; t.W0 += aj.W0; t.W1 += aj.W1; t.W2 += aj.W2;
+    t.Mb += aj.Mb; t.e0 += aj.e0; t.e1 += aj.e1; t.e2 += aj.e2; t.me += aj.me; t.rcb += aj.rcb;
+    vjp_store(pbase + ((size_t)I * T + I) * 160 + lane, t, Pi, D.G);
+  } else {  // off-diagonal: lane l meets body J*32 + (l + s) mod 32 at step s
+    load(base + J * 32 + lane, Pj);
+    for (int s = 0; s < 32; ++s) {
+      const int jl = (lane + s) & 31;
+      vjp_pair(Pi, Pj, I * 32 + lane, J * 32 + jl, D.G, true, ai, aj);
+      vjp_shfl(Pj, src);
+      vjp_acc_shfl(aj, src);
+    }
+    // after 32 rotations every j value and j sum is back on its owning lane
+    vjp_store(pbase + ((size_t)I * T + J) * 160 + lane, ai, Pi, D.G);
+    vjp_store(pbase + ((size_t)J * T + I) * 160 + lane, aj, Pj, D.G);
   }
-  double xb[3];
-  xb[0] = xe[0] + fma(-ui[0], S1, fma(gmi, V0, W0));
-  xb[1] = xe[1] + fma(-ui[1], S1, fma(gmi, V1, W1));
-  xb[2] = xe[2] + fma(-ui[2], S1, fma(gmi, V2, W2));
-  const double mb = fma(-D.G, Mb, me);
-  part[w][0][lane] = xb[0]; part[w][1][lane] = xb[1]; part[w][2][lane] = xb[2];
-  part[w][3][lane] = mb; part[w][4][lane] = rcb;
-  __syncthreads();
-  if (w == 0 && sal[i]) {
-    const int g = base + i;
-    double t[5];
-    for (int c = 0; c < 5; ++c) t[c] = ((part[0][c][lane] + part[1][c][lane]) + part[2][c][lane]) + part[3][c][lane];
-    for (int c = 0; c < 3; ++c) D.xb[c * NB + g] += t[c];
-    D.mb[g] += t[3];
-    D.rcb[g] += t[4];
-  }
+}
+
+// Sum of the tile partials of each body, in a fixed order, into xbar, mbar, rcbar.
+__global__ void k_ad_kick_vjp_reduce(Sim S, AdjDev D, const double *part) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= D.NB || !S.alive[g]) return;
+  const int T = D.Np >> 5, b = g / D.Np, i = g % D.Np, I = i >> 5, lane = i & 31;
+  const double *p = part + ((size_t)b * T * T + (size_t)I * T) * 160 + lane;
+  double t[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int J = 0; J < T; ++J)
+    for (int c = 0; c < 5; ++c) t[c] += p[(size_t)J * 160 + 32 * c];
+  const int NB = D.NB;
+  for (int c = 0; c < 3; ++c) D.xb[c * NB + g] += t[c];
+  D.mb[g] += t[3];
+  D.rcb[g] += t[4];
 }
 
 // Sun-drift VJP: x' = x + (h/m0) sum_k m_k v_k -> vbar_i += (h/m0) m_i Xs, mbar_i += (h/m0) v_i . Xs,
@@ -947,7 +1040,8 @@ struct genga_adj {
   double *y_pool = nullptr, *y_scratch = nullptr;
   long long *y_count = nullptr, *yoff_rec = nullptr;
   int bs_blocks = 0, bs_fwd_grid = 0;
-  size_t kick_smem = 0, vjp_smem = 0;
+  size_t kick_smem = 0;
+  double *kv_part = nullptr;  // kick-VJP tile partials [B][T][T][5][32]
 };
 
 namespace {
@@ -980,6 +1074,12 @@ void launch_kick(genga_adj *c, int mode, double h, double *rec_x) {
   if (mode == 0) k_ad_kick<0><<<grid, 128, c->kick_smem, c->stream>>>(c->S, c->D, c->P, h, rec_x);
   else if (mode == 1) k_ad_kick<1><<<grid, 128, c->kick_smem, c->stream>>>(c->S, c->D, c->P, h, rec_x);
   else k_ad_kick<2><<<grid, 128, c->kick_smem, c->stream>>>(c->S, c->D, c->P, h, rec_x);
+}
+
+void launch_kick_vjp(genga_adj *c, double h, const double *xk) {
+  const int T = c->Np / 32, items = c->B * T * (T + 1) / 2;
+  k_ad_kick_vjp_sym<<<(items * 32 + 127) / 128, 128, 0, c->stream>>>(c->S, c->D, h, xk, c->kv_part);
+  k_ad_kick_vjp_reduce<<<(c->NB + 127) / 128, 128, 0, c->stream>>>(c->S, c->D, c->kv_part);
 }
 
 // One full step t. With slot >= 0 the step is recorded into segment slot `slot`.
@@ -1114,6 +1214,7 @@ int genga_adj_init(genga_adj **out, int n_sys, int n, const double *m0, double G
   c->seq_cap = (int)std::min<size_t>(nslot * NB * 8 + 1024, (size_t)1 << 26);
   c->seq_pool = dalloc<double2>(c, c->seq_cap, err);
   c->seq_count = dalloc<int>(c, 1, err);
+  c->kv_part = dalloc<double>(c, (size_t)c->B * (c->Np / 32) * (c->Np / 32) * 160, err);
   c->bs_blocks = num_sms_adj();
   c->bs_fwd_grid = 2 * c->B > 64 ? 2 * c->B : 64;
   c->y_scratch = dalloc<double>(c, (size_t)c->bs_fwd_grid * BS_SEQCAP * BS_GMAX * 6, err);
@@ -1128,11 +1229,9 @@ int genga_adj_init(genga_adj **out, int n_sys, int n, const double *m0, double G
   cudaMemcpy(S.sys_of, sys.data(), NB * sizeof(int), cudaMemcpyHostToDevice);
   cudaMemcpy(S.sys_m0, m0, c->B * sizeof(double), cudaMemcpyHostToDevice);
   c->kick_smem = (size_t)c->Np * (5 * sizeof(double) + 2 * sizeof(u64) + sizeof(int));
-  c->vjp_smem = (size_t)c->Np * (9 * sizeof(double) + sizeof(u64) + sizeof(int));
   cudaFuncSetAttribute(k_ad_kick<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->kick_smem);
   cudaFuncSetAttribute(k_ad_kick<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->kick_smem);
   cudaFuncSetAttribute(k_ad_kick<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->kick_smem);
-  cudaFuncSetAttribute(k_ad_kick_vjp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->vjp_smem);
   cudaFuncSetAttribute(k_ad_bs_vjp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(BSV_WARPS * sizeof(LevShared)));
   bs_init_constants();
   init_lambda();
@@ -1189,7 +1288,6 @@ int genga_adj_backward(genga_adj *c, const double *xbar, const double *vbar, dou
   // the state still holds the forward's final state: output conversion VJP
   k_ad_out_vjp<<<c->B, 128, 0, st>>>(c->S, c->D, xbar, vbar);
   const int nseg = (c->nsteps + c->K - 1) / c->K;
-  dim3 kgrid(c->Np / 32, c->B);
   for (int sgm = nseg - 1; sgm >= 0; --sgm) {
     const int t0 = sgm * c->K, t1 = std::min(t0 + c->K, c->nsteps);
     restore(c, sgm);
@@ -1210,14 +1308,14 @@ int genga_adj_backward(genga_adj *c, const double *xbar, const double *vbar, dou
         if (j == c->nsub - 1)
           k_ad_rcrit<<<(NB + 127) / 128, 128, 0, st>>>(c->S, c->D, c->P, tau_abs, c->rec_step + (size_t)slot * 4 * NB,
                                                         nullptr, nullptr);
-        k_ad_kick_vjp<<<kgrid, 128, c->vjp_smem, st>>>(c->S, c->D, h, R.x3);
+        launch_kick_vjp(c, h, R.x3);
         k_ad_sundrift_vjp<<<c->B, 256, 0, st>>>(c->S, c->D, h, R.v2);
         cudaMemsetAsync(c->D.ingrp, 0, NB * sizeof(int), st);
         k_ad_mark<<<c->bs_blocks, 32, 0, st>>>(c->D, R.gstart, R.gsize, R.gmem, R.ngroups);
         k_ad_kepler_vjp<<<(NB + 127) / 128, 128, 0, st>>>(c->S, c->D, tau, R.x1, R.v1, R.s);
         k_ad_bs_vjp<<<c->bs_blocks, 32 * BSV_WARPS, BSV_WARPS * sizeof(LevShared), st>>>(c->S, c->D, R, R.x1, R.v1);
         k_ad_sundrift_vjp<<<c->B, 256, 0, st>>>(c->S, c->D, h, R.v1);
-        k_ad_kick_vjp<<<kgrid, 128, c->vjp_smem, st>>>(c->S, c->D, h, R.x);
+        launch_kick_vjp(c, h, R.x);
       }
       const double *rstep = c->rec_step + (size_t)slot * 4 * NB;
       const SubRec R0 = subrec(c, slot * c->nsub);
