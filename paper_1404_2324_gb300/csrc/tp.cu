@@ -392,51 +392,67 @@ __global__ void __launch_bounds__(128, 3) k_tp_bs(Sim S, TPSet T, DevParams P, d
         }
         __syncwarp();
       }
-      double za[6], zb[6], out[6], ax, ay, az;
+      double za[6], zb[6], ax, ay, az;
       for (int c = 0; c < 6; ++c) za[c] = y[c];
       tp_force(S, T, P, i, em, table, L, 0, t0, h, H, i2tau, wpos, y, ax, ay, az);
       zb[0] = fma(h, y[3], y[0]); zb[1] = fma(h, y[4], y[1]); zb[2] = fma(h, y[5], y[2]);
       zb[3] = fma(h, ax, y[3]); zb[4] = fma(h, ay, y[4]); zb[5] = fma(h, az, y[5]);
-      for (int m = 1; m <= nk; ++m) {
-        tp_force(S, T, P, i, em, table, L, m, t0, h, H, i2tau, wpos, zb, ax, ay, az);
-        if (m < nk) {
-          double zn[6];
-          zn[0] = fma(h2, zb[3], za[0]); zn[1] = fma(h2, zb[4], za[1]); zn[2] = fma(h2, zb[5], za[2]);
-          zn[3] = fma(h2, ax, za[3]); zn[4] = fma(h2, ay, za[4]); zn[5] = fma(h2, az, za[5]);
-          for (int c = 0; c < 6; ++c) { za[c] = zb[c]; zb[c] = zn[c]; }
-        } else {
+      // Level L (lane L - 1) finishes at evaluation 2L; lanes 8..13 then extend the tableau by its
+      // row, component c on lane 8 + c (polynomial extrapolation in h^2, Neville), and the first
+      // converged level ends the attempt: the same decision as building the whole tableau first.
+      const int cc = lane - BS_LEVELS;           // component of the tableau lanes
+      const bool tabl = cc >= 0 && cc < 6;
+      double sc = 0.0;                           // 1/|x| or 1/|v| at the start of the attempt
+      if (tabl) {
+        const double *yy = y + (cc < 3 ? 0 : 3);
+        const double s2 = fma(yy[2], yy[2], fma(yy[1], yy[1], yy[0] * yy[0]));
+        sc = dbits(s2) == 0ULL ? 4.49423283715579e307 : rsqrt_refined(s2);
+      }
+      const int lmax = P.bs_kmax < BS_LEVELS ? P.bs_kmax : BS_LEVELS;
+      double prev[BS_LEVELS], cur[BS_LEVELS];
+      int acc = 0;
+      for (int m = 1; m <= 2 * lmax; ++m) {
+        double out[6];
+        if (m <= nk) {
+          tp_force(S, T, P, i, em, table, L, m, t0, h, H, i2tau, wpos, zb, ax, ay, az);
+          if (m < nk) {
+            double zn[6];
+            zn[0] = fma(h2, zb[3], za[0]); zn[1] = fma(h2, zb[4], za[1]); zn[2] = fma(h2, zb[5], za[2]);
+            zn[3] = fma(h2, ax, za[3]); zn[4] = fma(h2, ay, za[4]); zn[5] = fma(h2, az, za[5]);
+            for (int c = 0; c < 6; ++c) { za[c] = zb[c]; zb[c] = zn[c]; }
+          }
+        }
+        if (m & 1) continue;
+        const int Lc = m >> 1;
+        if (lane == Lc - 1) {  // this lane's level is complete: T_{Lc,1}
           out[0] = 0.5 * fma(h, zb[3], zb[0] + za[0]); out[1] = 0.5 * fma(h, zb[4], zb[1] + za[1]);
           out[2] = 0.5 * fma(h, zb[5], zb[2] + za[2]); out[3] = 0.5 * fma(h, ax, zb[3] + za[3]);
           out[4] = 0.5 * fma(h, ay, zb[4] + za[4]); out[5] = 0.5 * fma(h, az, zb[5] + za[5]);
+        } else {
+          for (int c = 0; c < 6; ++c) out[c] = 0.0;
         }
-      }
-      // Neville wavefront across lanes: lane L holds row L
-      double Tk[6], Tm1[6];
-      for (int c = 0; c < 6; ++c) { Tk[c] = out[c]; Tm1[c] = out[c]; }
-      for (int j = 1; j < BS_LEVELS; ++j) {
-        double up[6];
-        for (int c = 0; c < 6; ++c) up[c] = __shfl_up_sync(0xffffffffu, Tk[c], 1);
-        if (lane < BS_LEVELS && L > j) {
-          const double fi = c_tp_facinv[L][j];
-          if (j == L - 1) for (int c = 0; c < 6; ++c) Tm1[c] = Tk[c];
-          for (int c = 0; c < 6; ++c) Tk[c] = fma(Tk[c] - up[c], fi, Tk[c]);
+        double t1 = 0.0;
+        for (int c = 0; c < 6; ++c) {
+          const double v = __shfl_sync(0xffffffffu, out[c], Lc - 1);
+          if (c == cc) t1 = v;
         }
+        bool ok = false;
+        if (tabl) {
+          cur[0] = t1;
+          for (int j = 1; j < Lc; ++j) cur[j] = fma(cur[j - 1] - prev[j - 1], c_tp_facinv[Lc][j], cur[j - 1]);
+          ok = Lc >= 2 && absbits((cur[Lc - 1] - cur[Lc - 2]) * sc) <= dbits(P.bs_eps);
+          for (int j = 0; j < Lc; ++j) prev[j] = cur[j];
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, ok);
+        if (((bal >> BS_LEVELS) & 0x3fu) == 0x3fu) { acc = Lc; break; }  // all six components converged
       }
-      const double sx2 = fma(y[2], y[2], fma(y[1], y[1], y[0] * y[0]));
-      const double sv2 = fma(y[5], y[5], fma(y[4], y[4], y[3] * y[3]));
-      const double isx = rsqrt_refined(sx2), isv = dbits(sv2) == 0ULL ? 4.49423283715579e307 : rsqrt_refined(sv2);
-      u64 em_ = 0ULL;
-      for (int c = 0; c < 6; ++c) em_ = umax64(em_, absbits((Tk[c] - Tm1[c]) * (c < 3 ? isx : isv)));
-      const bool conv = lane < BS_LEVELS && L >= 2 && L <= P.bs_kmax && em_ <= dbits(P.bs_eps);
-      const unsigned bal = __ballot_sync(0xffffffffu, conv);
-      if (!bal) {
+      if (!acc) {
         H *= 0.5;
         if (++halvings > P.bs_max_halvings) { failed = true; break; }
         continue;
       }
-      const int src = __ffs(bal) - 1;
       double yn[6];
-      for (int c = 0; c < 6; ++c) yn[c] = __shfl_sync(0xffffffffu, Tk[c], src);
+      for (int c = 0; c < 6; ++c) yn[c] = __shfl_sync(0xffffffffu, tabl ? cur[acc - 1] : 0.0, BS_LEVELS + c);
       halvings = 0;
       steps++;
       if (P.collisions) {  // contact with an encountered planet during the substep removes the TP
