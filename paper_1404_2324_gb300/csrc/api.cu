@@ -145,7 +145,7 @@ struct genga_ctx {
   // the step graph that runs beside the one-CTA BS kernel
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-  int gsplit = BS_GMAX + 1, cl_grid = 0;
+  int gsplit = BS_GMAX + 1, cl_grid = 0, pair_grid = 0;
   bool profiling = false;
   // batched mode
   bool batched = false;
@@ -228,7 +228,16 @@ void enqueue_step_batch(genga_ctx *c, cudaStream_t st) {
     launch_b_drift(S, P, tau, 0.5 * tau, j > 0 ? 0.5 * c->w[j - 1] * dt : 0.0, j == 0, st);
     launch_b_encounter(S, tau, st);
     launch_b_group(S, st);
-    launch_bs(S, P, tau, c->bs_grid, st);
+    if (c->side) {  // fork: pairs one warp each on a side branch, larger groups one CTA each; join
+      cudaEventRecord(c->ev_fork, st);
+      cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+      launch_bs_pair(S, P, tau, c->pair_grid, c->side);
+      launch_bs(S, P, tau, c->bs_grid, st, BS_GMAX + 1, 3);
+      cudaEventRecord(c->ev_join, c->side);
+      cudaStreamWaitEvent(st, c->ev_join, 0);
+    } else {
+      launch_bs(S, P, tau, c->bs_grid, st);
+    }
     launch_b_momentum(S, S.sys_ppre, st);
     const double h2 = (j + 1 < c->nsub) ? 0.5 * c->w[j + 1] * dt : 0.0;
     launch_b_kick(S, P, FIN_CLOSE, 0.5 * tau, h2, c->b_split, c->b_block, st);
@@ -538,6 +547,13 @@ int genga_init_batch(genga_ctx **out, int n_sys, const int *offsets, const doubl
   c->sm = mem.get<double>(n); c->sR = mem.get<double>(n); c->salive = mem.get<int>(n);
   if (mem.err != cudaSuccess) { genga_free(c); return GENGA_ENOMEM; }
   c->bs_grid = 2 * num_sms();
+  c->pair_grid = 2 * num_sms();  // 8 warps (groups) per CTA, 2 CTAs per SM
+  if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    genga_free(c);
+    return GENGA_ECUDA;
+  }
   sys_of.resize(np, 0);  // padding bodies: never alive
   cudaStream_t st = c->stream;
   if (cudaMemcpy(S.sys_of, sys_of.data(), np * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||

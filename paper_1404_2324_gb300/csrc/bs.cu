@@ -63,7 +63,7 @@ __device__ __forceinline__ void bs_terms(const BsShared &sh, const DevParams &P,
   }
 }
 
-__global__ void __launch_bounds__(BS_THREADS, 2) k_bs(Sim S, DevParams P, double tau, int gsplit) {
+__global__ void __launch_bounds__(BS_THREADS, 2) k_bs(Sim S, DevParams P, double tau, int gmin, int gsplit) {
   __shared__ BsShared sh;
   const int tid = threadIdx.x;
   const int np = S.npad;
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(BS_THREADS, 2) k_bs(Sim S, DevParams P, double
     // central mass of the group's system (batched mode) or of the single system
     const double m0 = S.sys_of ? S.sys_m0[S.sys_of[S.gmem[g0]]] : P.m0;
     const double Gm0 = P.G * m0;
-    if (g >= gsplit && g <= BS_GMAX) continue;  // uniform: integrated by the cluster kernel
+    if (g < gmin || (g >= gsplit && g <= BS_GMAX)) continue;  // uniform: the pair or the cluster kernel
     if (g > BS_GMAX) {
       if (tid == 0) atomicOr(S.status, ST_GROUP_TOO_LARGE);
       continue;  // uniform across the CTA
@@ -302,9 +302,213 @@ void bs_init_constants() {
   cudaMemcpyToSymbol(c_facinv, h, sizeof(h));
 }
 
-void launch_bs(const Sim &S, const DevParams &P, double tau, int max_groups, cudaStream_t st, int gsplit) {
+void launch_bs(const Sim &S, const DevParams &P, double tau, int max_groups, cudaStream_t st, int gsplit, int gmin) {
   const int grid = max_groups < 1 ? 1 : max_groups;
-  k_bs<<<grid, BS_THREADS, 0, st>>>(S, P, tau, gsplit);
+  k_bs<<<grid, BS_THREADS, 0, st>>>(S, P, tau, gmin, gsplit);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Groups of one or two members (the common case in systems with many bodies): one warp per group,
+// eight groups per CTA. Lane l: level l/4 + 1, member (l/2) % 2, term l % 2 (the central mass or
+// the partner); the same arithmetic and decisions as k_bs. A CTA-wide kernel spends most of its
+// threads idle on such a group and is latency-bound; with a group per warp every SM works on many
+// groups at once.
+// ---------------------------------------------------------------------------------------------
+constexpr int BSP_WARPS = 8;
+
+struct BsPairShared {
+  int idx[2], alive[2];
+  double gm[2], m[2], R[2], A[2];
+  u64 rcsq[2];
+  double y[2][6], yn[2][6];
+  double pos[2][BS_LEVELS][2][3];
+  double tab[BS_LEVELS][2][6];
+  u64 err[BS_LEVELS];
+  double U;
+};
+
+__device__ __forceinline__ void pair_terms(const BsPairShared &sh, const DevParams &P, double Gm0, int g, int q, int sub,
+                                           const double (*pos)[3], bool q_alive, double &ax, double &ay, double &az) {
+  ax = ay = az = 0.0;
+  const int p = sub;
+  if (q_alive && p < g) {
+    const double xq = pos[q][0], yq = pos[q][1], zq = pos[q][2];
+    const bool cen = p == q;
+    const double dx = (cen ? 0.0 : pos[p][0]) - xq, dy = (cen ? 0.0 : pos[p][1]) - yq, dz = (cen ? 0.0 : pos[p][2]) - zq;
+    const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+    const double yr = rsqrt_refined(r2);
+    const bool inside = sh.alive[p] && dbits(r2) < umax64(sh.rcsq[q], sh.rcsq[p]);
+    const double wA = changeover_wA_clamped(r2 * yr, pmin(sh.A[q], sh.A[p]), P.kmode);
+    const double w = cen ? 1.0 : (inside ? wA : 0.0);
+    const double f = (cen ? Gm0 : sh.gm[p]) * w * (yr * yr * yr);
+    ax = f * dx; ay = f * dy; az = f * dz;
+  }
+  ax += __shfl_xor_sync(0xffffffffu, ax, 1);
+  ay += __shfl_xor_sync(0xffffffffu, ay, 1);
+  az += __shfl_xor_sync(0xffffffffu, az, 1);
+}
+
+__global__ void __launch_bounds__(32 * BSP_WARPS, 2) k_bs_pair(Sim S, DevParams P, double tau) {
+  __shared__ BsPairShared shw[BSP_WARPS];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  BsPairShared &sh = shw[wid];
+  const int np = S.npad;
+  const int ngroups = *S.ngroups;
+  const int slot = lane >> 1, sub = lane & 1;
+  const int lev = slot >> 1, q = slot & 1, L = lev + 1, nk = 2 * L;
+  const int nwarp = gridDim.x * BSP_WARPS;
+  for (int gidx = blockIdx.x * BSP_WARPS + wid; gidx < ngroups; gidx += nwarp) {
+    const int g0 = S.gstart[gidx], g = S.gsize ? S.gsize[gidx] : S.gstart[gidx + 1] - g0;
+    if (g > 2) continue;  // uniform within the warp
+    const double m0 = S.sys_of ? S.sys_m0[S.sys_of[S.gmem[g0]]] : P.m0;
+    const double Gm0 = P.G * m0;
+    const bool act = q < g;
+    if (lane < g) {
+      const int i = S.gmem[g0 + lane];
+      sh.idx[lane] = i;
+      sh.alive[lane] = S.alive[i];
+      sh.gm[lane] = S.gm[i]; sh.m[lane] = S.m[i]; sh.R[lane] = S.R[i]; sh.A[lane] = S.A[i];
+      sh.rcsq[lane] = S.rcsq[i];
+      for (int c = 0; c < 3; ++c) { sh.y[lane][c] = S.x0[c * np + i]; sh.y[lane][3 + c] = S.v0[c * np + i]; }
+    }
+    if (lane == 0) sh.U = 0.0;
+    __syncwarp();
+    double H = tau, rem = tau;
+    int halvings = 0, attempts = 0, steps = 0;
+    bool failed = false;
+    while (absbits(rem) != 0ULL) {
+      if (absbits(H) > absbits(rem)) H = rem;
+      if (++attempts > 200000) { failed = true; break; }
+      const double h = __ddiv_rn(H, (double)nk), h2 = 2.0 * h;
+      const bool qa = act && sh.alive[q];
+      double zA[6], zB[6];
+      for (int c = 0; c < 6; ++c) zA[c] = act ? sh.y[q][c] : 0.0;
+      if (act && sub == 0) for (int c = 0; c < 3; ++c) sh.pos[0][lev][q][c] = zA[c];
+      const int qc = lane / 6, cc = lane % 6;
+      const bool rowth = qc < g;
+      double scale = 0.0;
+      if (rowth) {
+        const double *yq = sh.y[qc] + (cc < 3 ? 0 : 3);
+        const double s2 = fma(yq[2], yq[2], fma(yq[1], yq[1], yq[0] * yq[0]));
+        scale = dbits(s2) == 0ULL ? 4.49423283715579e307 : rsqrt_refined(s2);
+      }
+      if (lane < BS_LEVELS) sh.err[lane] = 0ULL;
+      __syncwarp();
+      double ax, ay, az;
+      pair_terms(sh, P, Gm0, g, act ? q : 0, sub, sh.pos[0][lev], qa, ax, ay, az);
+      if (qa) {
+        zB[0] = fma(h, zA[3], zA[0]); zB[1] = fma(h, zA[4], zA[1]); zB[2] = fma(h, zA[5], zA[2]);
+        zB[3] = fma(h, ax, zA[3]); zB[4] = fma(h, ay, zA[4]); zB[5] = fma(h, az, zA[5]);
+      } else {
+        for (int c = 0; c < 6; ++c) zB[c] = zA[c];
+      }
+      const int lmax = P.bs_kmax < BS_LEVELS ? P.bs_kmax : BS_LEVELS;
+      const u64 eps = dbits(P.bs_eps);
+      double prev[BS_LEVELS], cur[BS_LEVELS];
+      int acc = 0, b = 1;
+      for (int e = 1; e <= 2 * lmax; ++e) {
+        const bool lv = act && e <= nk;
+        if (lv && sub == 0) for (int c = 0; c < 3; ++c) sh.pos[b][lev][q][c] = zB[c];
+        __syncwarp();
+        pair_terms(sh, P, Gm0, g, act ? q : 0, sub, sh.pos[b][lev], qa && e <= nk, ax, ay, az);
+        if (lv) {
+          double out[6];
+          if (qa) {
+            if (e < nk) {
+              double zn[6];
+              zn[0] = fma(h2, zB[3], zA[0]); zn[1] = fma(h2, zB[4], zA[1]); zn[2] = fma(h2, zB[5], zA[2]);
+              zn[3] = fma(h2, ax, zA[3]); zn[4] = fma(h2, ay, zA[4]); zn[5] = fma(h2, az, zA[5]);
+              for (int c = 0; c < 6; ++c) { zA[c] = zB[c]; zB[c] = zn[c]; }
+            } else {
+              out[0] = 0.5 * fma(h, zB[3], zB[0] + zA[0]);
+              out[1] = 0.5 * fma(h, zB[4], zB[1] + zA[1]);
+              out[2] = 0.5 * fma(h, zB[5], zB[2] + zA[2]);
+              out[3] = 0.5 * fma(h, ax, zB[3] + zA[3]);
+              out[4] = 0.5 * fma(h, ay, zB[4] + zA[4]);
+              out[5] = 0.5 * fma(h, az, zB[5] + zA[5]);
+            }
+          } else {
+            for (int c = 0; c < 6; ++c) out[c] = zA[c];
+          }
+          if (e == nk && sub == 0) for (int c = 0; c < 6; ++c) sh.tab[lev][q][c] = out[c];
+        }
+        b ^= 1;
+        if (e & 1) continue;
+        const int Lc = e >> 1;  // level Lc is complete: its tableau row (Neville, in h^2)
+        __syncwarp();
+        if (rowth) {
+          cur[0] = sh.tab[Lc - 1][qc][cc];
+          for (int j = 1; j < Lc; ++j) cur[j] = fma(cur[j - 1] - prev[j - 1], c_facinv[Lc][j], cur[j - 1]);
+          if (Lc >= 2 && sh.alive[qc]) atomicMax(&sh.err[Lc - 1], absbits((cur[Lc - 1] - cur[Lc - 2]) * scale));
+          for (int j = 0; j < Lc; ++j) prev[j] = cur[j];
+        }
+        __syncwarp();
+        if (Lc >= 2 && sh.err[Lc - 1] <= eps) { acc = Lc; break; }
+      }
+      if (!acc) {
+        H *= 0.5;
+        if (++halvings > P.bs_max_halvings) { failed = true; break; }
+        continue;
+      }
+      if (rowth) sh.yn[qc][cc] = cur[acc - 1];
+      __syncwarp();
+      if (P.collisions && g == 2 && lane == 0 && sh.alive[0] && sh.alive[1]) {  // contact over the substep
+        const double dmin = hermite_min_exact(
+            __dsub_rn(sh.y[1][0], sh.y[0][0]), __dsub_rn(sh.y[1][1], sh.y[0][1]), __dsub_rn(sh.y[1][2], sh.y[0][2]),
+            __dsub_rn(sh.y[1][3], sh.y[0][3]), __dsub_rn(sh.y[1][4], sh.y[0][4]), __dsub_rn(sh.y[1][5], sh.y[0][5]),
+            __dsub_rn(sh.yn[1][0], sh.yn[0][0]), __dsub_rn(sh.yn[1][1], sh.yn[0][1]), __dsub_rn(sh.yn[1][2], sh.yn[0][2]),
+            __dsub_rn(sh.yn[1][3], sh.yn[0][3]), __dsub_rn(sh.yn[1][4], sh.yn[0][4]), __dsub_rn(sh.yn[1][5], sh.yn[0][5]), H);
+        const double rr = sh.R[0] + sh.R[1];
+        if (dmin < rr * rr) {  // perfect merger (Sect. 3.2, Collisions), as in k_bs
+          const int ia = sh.idx[0], ib = sh.idx[1];
+          const double ma = sh.m[0], mb = sh.m[1], M = ma + mb;
+          const double dx = sh.yn[1][0] - sh.yn[0][0], dy = sh.yn[1][1] - sh.yn[0][1], dz = sh.yn[1][2] - sh.yn[0][2];
+          const double dvx = sh.yn[1][3] - sh.yn[0][3], dvy = sh.yn[1][4] - sh.yn[0][4], dvz = sh.yn[1][5] - sh.yn[0][5];
+          const double r = sqrt(dx * dx + dy * dy + dz * dz);
+          const double v2 = dvx * dvx + dvy * dvy + dvz * dvz;
+          sh.U += 0.5 * ma * mb / M * v2 - P.G * ma * mb / r;
+          const bool keep_a = ma > mb || (ma == mb && ia < ib);
+          const int sv = keep_a ? 0 : 1, d = keep_a ? 1 : 0;
+          for (int c = 0; c < 6; ++c) sh.yn[sv][c] = (ma * sh.yn[0][c] + mb * sh.yn[1][c]) / M;
+          const double Ra = sh.R[0], Rb = sh.R[1];
+          sh.R[sv] = cbrt(Ra * Ra * Ra + Rb * Rb * Rb);
+          sh.m[sv] = M; sh.gm[sv] = P.G * M;
+          sh.m[d] = 0.0; sh.gm[d] = 0.0; sh.R[d] = 0.0; sh.alive[d] = 0;
+          const int is = sh.idx[sv], idd = sh.idx[d];
+          S.m[is] = M; S.gm[is] = P.G * M; S.R[is] = sh.R[sv]; S.hill[is] = cbrt(M / (3.0 * m0));
+          S.m[idd] = 0.0; S.gm[idd] = 0.0; S.R[idd] = 0.0; S.hill[idd] = 0.0; S.alive[idd] = 0;
+          S.T[idd] = 0ULL; S.rcsq[idd] = 0ULL;
+          atomicAdd((unsigned long long *)&S.counters[C_MERGE], 1ULL);
+        }
+      }
+      __syncwarp();
+      if (lane < g) for (int c = 0; c < 6; ++c) sh.y[lane][c] = sh.yn[lane][c];
+      __syncwarp();
+      rem -= H;
+      H *= 2.0;
+      halvings = 0;
+      steps++;
+    }
+    if (lane < g) {
+      const int i = sh.idx[lane];
+      if (sh.alive[lane]) {
+        for (int c = 0; c < 3; ++c) { S.x[c * np + i] = sh.y[lane][c]; S.v[c * np + i] = sh.y[lane][3 + c]; }
+      } else {
+        S.x[i] = PARK + 1.0e4 * i; S.x[np + i] = 0.0; S.x[2 * np + i] = 0.0;
+        for (int c = 0; c < 3; ++c) S.v[c * np + i] = 0.0;
+      }
+    }
+    if (lane == 0) {
+      if (failed) atomicOr(S.status, ST_BS_FAILED);
+      atomicAdd((unsigned long long *)&S.counters[C_BSSTEPS], (unsigned long long)steps);
+      if (dbits(sh.U) != 0ULL) atomicAdd(S.U, sh.U);
+    }
+    __syncwarp();
+  }
+}
+
+void launch_bs_pair(const Sim &S, const DevParams &P, double tau, int blocks, cudaStream_t st) {
+  k_bs_pair<<<blocks, 32 * BSP_WARPS, 0, st>>>(S, P, tau);
 }
 
 }  // namespace genga

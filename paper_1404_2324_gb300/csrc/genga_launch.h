@@ -32,7 +32,9 @@ void launch_copy_edges(const Sim &S, const int *pairs, int npairs, cudaStream_t 
 void bs_init_constants();  // once per device, before any capture
 // Groups of at least gsplit members are skipped (left to the cluster kernel); BS_GMAX + 1: none.
 void launch_bs(const Sim &S, const DevParams &P, double tau, int max_groups, cudaStream_t st,
-               int gsplit = BS_GMAX + 1);
+               int gsplit = BS_GMAX + 1, int gmin = 1);
+// groups of one or two members, one warp each (no adjoint recording)
+void launch_bs_pair(const Sim &S, const DevParams &P, double tau, int blocks, cudaStream_t st);
 // bs_cluster.cu: groups of gmin .. BS_GMAX members, one cluster of 8 CTAs (one per level) each
 void bs_cluster_init_constants();  // once per device, before any capture
 int bs_cluster_grid();
