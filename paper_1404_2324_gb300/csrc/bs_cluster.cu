@@ -70,7 +70,7 @@ __device__ __forceinline__ void cl_terms(const BsClShared &sh, const DevParams &
   }
 }
 
-__global__ void __cluster_dims__(CL_SIZE, 1, 1) __launch_bounds__(CL_THREADS)
+__global__ void __cluster_dims__(CL_SIZE, 1, 1) __launch_bounds__(CL_THREADS, 2)
     k_bs_cluster(Sim S, DevParams P, double tau, int gmin) {
   __shared__ BsClShared sh;
   cg::cluster_group cluster = cg::this_cluster();
