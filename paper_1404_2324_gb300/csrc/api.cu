@@ -68,6 +68,7 @@ bool alloc_sim(Sim &S, DevMem &mem, int n, int nsub) {
   S.edges = mem.get<int>(2 * ecap); S.nedges = mem.get<int>(1);
   S.fail = mem.get<int>(np); S.nfail = mem.get<int>(1);
   S.gstart = mem.get<int>(np + 1); S.gmem = mem.get<int>(np); S.ngroups = mem.get<int>(1);
+  S.big = mem.get<int>(np); S.nbig = mem.get<int>(1);
   // kick work list: for each tile I, the diagonal tile, then both halves of every J > I
   std::vector<int> items;
   for (int I = 0; I < S.nt; ++I) {
@@ -265,7 +266,7 @@ void enqueue_step(genga_ctx *c, cudaStream_t st) {
     launch_drift(S, P, tau, 0.5 * tau * inv_m0, hcm2, j == 0, st);        // clears the reuse flag
     if (tp) launch_planet_table(S, T, P, tau, st);
     launch_encounter(S, tau, S.ebm + (size_t)j * S.npad * S.W, st);
-    launch_group(S, st);
+    launch_group(S, st, c->side ? c->gsplit : BS_GMAX + 1);
     if (c->side) {  // fork: cluster kernel for the larger groups, one-CTA kernel for the rest; join
       cudaEventRecord(c->ev_fork, st);
       cudaStreamWaitEvent(c->side, c->ev_fork, 0);
@@ -534,7 +535,7 @@ int genga_init_batch(genga_ctx **out, int n_sys, const int *offsets, const doubl
   S.afar = mem.get<double>(3 * np);
   S.fail = mem.get<int>(np); S.nfail = mem.get<int>(1);
   S.gstart = mem.get<int>(np + 1); S.gmem = mem.get<int>(np); S.ngroups = mem.get<int>(1);
-  S.gsize = mem.get<int>(np + 1); S.gtotal = mem.get<int>(1);
+  S.gsize = mem.get<int>(np + 1); S.gtotal = mem.get<int>(1); S.bsq = mem.get<unsigned>(2);
   S.flags = mem.get<int>(4); S.status = mem.get<int>(1);
   S.counters = mem.get<long long>(NCOUNTERS); S.U = mem.get<double>(1);
   S.nsys = n_sys;

@@ -150,7 +150,7 @@ __global__ void k_b_momentum(Sim S, double *out) {
 // substep's second with the momentum before its closing kick), then the Kepler drift.
 __global__ void k_b_drift(Sim S, DevParams P, double tau, double h1, double h2, int first) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0) { *S.ngroups = 0; *S.gtotal = 0; }
+  if (i == 0) { *S.ngroups = 0; *S.gtotal = 0; S.bsq[0] = 0u; S.bsq[1] = 0u; }
   if (i >= S.npad) return;
   const int np = S.npad;
   const int s = S.sys_of[i];

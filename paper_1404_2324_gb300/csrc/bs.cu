@@ -24,7 +24,7 @@ struct BsShared {
   u64 err[BS_LEVELS];
   unsigned char cont[BS_GMAX * (BS_GMAX - 1) / 2];
   double H, rem, U;
-  int accept;
+  int accept, next;
   int nseq, seq_base;          // recorded accepted substeps (adjoint engine only)
   long long y_base;
   double seqH[BS_SEQCAP];
@@ -68,7 +68,13 @@ __global__ void __launch_bounds__(BS_THREADS, 2) k_bs(Sim S, DevParams P, double
   const int tid = threadIdx.x;
   const int np = S.npad;
   const int ngroups = *S.ngroups;
-  for (int gidx = blockIdx.x; gidx < ngroups; gidx += gridDim.x) {
+  for (int it = 0;; ++it) {
+    // next group: from the queue when there is one (batched mode), else a fixed stride
+    if (tid == 0) sh.next = S.bsq ? (int)atomicAdd(&S.bsq[1], 1u) : blockIdx.x + it * gridDim.x;
+    __syncthreads();
+    const int gidx = sh.next;
+    __syncthreads();
+    if (gidx >= ngroups) break;  // uniform
     const int g0 = S.gstart[gidx], g = S.gsize ? S.gsize[gidx] : S.gstart[gidx + 1] - g0;
     // central mass of the group's system (batched mode) or of the single system
     const double m0 = S.sys_of ? S.sys_m0[S.sys_of[S.gmem[g0]]] : P.m0;
@@ -308,24 +314,34 @@ void launch_bs(const Sim &S, const DevParams &P, double tau, int max_groups, cud
 }
 
 // ---------------------------------------------------------------------------------------------
-// Groups of one or two members (the common case in systems with many bodies): one warp per group,
-// eight groups per CTA. Lane l: level l/4 + 1, member (l/2) % 2, term l % 2 (the central mass or
-// the partner); the same arithmetic and decisions as k_bs. A CTA-wide kernel spends most of its
-// threads idle on such a group and is latency-bound; with a group per warp every SM works on many
-// groups at once.
+// Groups of one or two members (the common case in systems with many bodies): one unit of two warps
+// per group, four groups per CTA. Lane l of a warp: level l/4 + 1, member (l/2) % 2, term l % 2 (the
+// central mass or the partner); the same arithmetic and decisions as k_bs.
+//
+// Speculation. The step control halves H on failure and doubles it on acceptance, so a long
+// integration alternates a failed attempt at 2H with an accepted one at H. The unit's first warp
+// attempts H while the second attempts H/2 from the same state; the second result is used exactly
+// when the serial algorithm's next attempt would be that one (the first failed), so every result
+// and decision equals the serial algorithm's, and a fail/accept pair costs one attempt's time.
 // ---------------------------------------------------------------------------------------------
-constexpr int BSP_WARPS = 8;
+constexpr int BSP_UNITS = 4;
 
 struct BsPairShared {
   int idx[2], alive[2];
   double gm[2], m[2], R[2], A[2];
   u64 rcsq[2];
-  double y[2][6], yn[2][6];
-  double pos[2][BS_LEVELS][2][3];
-  double tab[BS_LEVELS][2][6];
-  u64 err[BS_LEVELS];
+  double y[2][6];                     // state at the start of the round
+  double yn[2][2][6];                 // [warp] result of the warp's attempt
+  double pos[2][2][BS_LEVELS][2][3];  // [warp][buffer][level][member]
+  double tab[2][BS_LEVELS][2][6];     // [warp] T_{L,1} per level
+  u64 err[2][BS_LEVELS];              // [warp]
+  int acc[2];
+  int gidx;
   double U;
 };
+
+// the two warps of a unit (named barrier 1 + unit, 64 threads)
+__device__ __forceinline__ void unit_sync(int bar) { asm volatile("bar.sync %0, 64;" ::"r"(bar) : "memory"); }
 
 __device__ __forceinline__ void pair_terms(const BsPairShared &sh, const DevParams &P, double Gm0, int g, int q, int sub,
                                            const double (*pos)[3], bool q_alive, double &ax, double &ay, double &az) {
@@ -348,128 +364,157 @@ __device__ __forceinline__ void pair_terms(const BsPairShared &sh, const DevPara
   az += __shfl_xor_sync(0xffffffffu, az, 1);
 }
 
-__global__ void __launch_bounds__(32 * BSP_WARPS, 2) k_bs_pair(Sim S, DevParams P, double tau) {
-  __shared__ BsPairShared shw[BSP_WARPS];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  BsPairShared &sh = shw[wid];
-  const int np = S.npad;
-  const int ngroups = *S.ngroups;
+// One attempt of length H from sh.y by one warp, with the warp's own buffers (index w). Returns the
+// accepted level (0: no level converged) and leaves the extrapolated state in sh.yn[w].
+__device__ int pair_attempt(BsPairShared &sh, int w, const DevParams &P, double Gm0, int g, double H, int lane) {
   const int slot = lane >> 1, sub = lane & 1;
   const int lev = slot >> 1, q = slot & 1, L = lev + 1, nk = 2 * L;
-  const int nwarp = gridDim.x * BSP_WARPS;
-  for (int gidx = blockIdx.x * BSP_WARPS + wid; gidx < ngroups; gidx += nwarp) {
+  const bool act = q < g;
+  const double h = __ddiv_rn(H, (double)nk), h2 = 2.0 * h;
+  const bool qa = act && sh.alive[q];
+  double zA[6], zB[6];
+  for (int c = 0; c < 6; ++c) zA[c] = act ? sh.y[q][c] : 0.0;
+  if (act && sub == 0) for (int c = 0; c < 3; ++c) sh.pos[w][0][lev][q][c] = zA[c];
+  const int qc = lane / 6, cc = lane % 6;
+  const bool rowth = qc < g;
+  double scale = 0.0;
+  if (rowth) {
+    const double *yq = sh.y[qc] + (cc < 3 ? 0 : 3);
+    const double s2 = fma(yq[2], yq[2], fma(yq[1], yq[1], yq[0] * yq[0]));
+    scale = dbits(s2) == 0ULL ? 4.49423283715579e307 : rsqrt_refined(s2);
+  }
+  if (lane < BS_LEVELS) sh.err[w][lane] = 0ULL;
+  __syncwarp();
+  double ax, ay, az;
+  pair_terms(sh, P, Gm0, g, act ? q : 0, sub, sh.pos[w][0][lev], qa, ax, ay, az);
+  if (qa) {
+    zB[0] = fma(h, zA[3], zA[0]); zB[1] = fma(h, zA[4], zA[1]); zB[2] = fma(h, zA[5], zA[2]);
+    zB[3] = fma(h, ax, zA[3]); zB[4] = fma(h, ay, zA[4]); zB[5] = fma(h, az, zA[5]);
+  } else {
+    for (int c = 0; c < 6; ++c) zB[c] = zA[c];
+  }
+  const int lmax = P.bs_kmax < BS_LEVELS ? P.bs_kmax : BS_LEVELS;
+  const u64 eps = dbits(P.bs_eps);
+  double prev[BS_LEVELS], cur[BS_LEVELS];
+  int acc = 0, b = 1;
+  for (int e = 1; e <= 2 * lmax; ++e) {
+    const bool lv = act && e <= nk;
+    if (lv && sub == 0) for (int c = 0; c < 3; ++c) sh.pos[w][b][lev][q][c] = zB[c];
+    __syncwarp();
+    pair_terms(sh, P, Gm0, g, act ? q : 0, sub, sh.pos[w][b][lev], qa && e <= nk, ax, ay, az);
+    if (lv) {
+      double out[6];
+      if (qa) {
+        if (e < nk) {
+          double zn[6];
+          zn[0] = fma(h2, zB[3], zA[0]); zn[1] = fma(h2, zB[4], zA[1]); zn[2] = fma(h2, zB[5], zA[2]);
+          zn[3] = fma(h2, ax, zA[3]); zn[4] = fma(h2, ay, zA[4]); zn[5] = fma(h2, az, zA[5]);
+          for (int c = 0; c < 6; ++c) { zA[c] = zB[c]; zB[c] = zn[c]; }
+        } else {
+          out[0] = 0.5 * fma(h, zB[3], zB[0] + zA[0]);
+          out[1] = 0.5 * fma(h, zB[4], zB[1] + zA[1]);
+          out[2] = 0.5 * fma(h, zB[5], zB[2] + zA[2]);
+          out[3] = 0.5 * fma(h, ax, zB[3] + zA[3]);
+          out[4] = 0.5 * fma(h, ay, zB[4] + zA[4]);
+          out[5] = 0.5 * fma(h, az, zB[5] + zA[5]);
+        }
+      } else {
+        for (int c = 0; c < 6; ++c) out[c] = zA[c];
+      }
+      if (e == nk && sub == 0) for (int c = 0; c < 6; ++c) sh.tab[w][lev][q][c] = out[c];
+    }
+    b ^= 1;
+    if (e & 1) continue;
+    const int Lc = e >> 1;  // level Lc is complete: its tableau row (Neville, in h^2)
+    __syncwarp();
+    if (rowth) {
+      cur[0] = sh.tab[w][Lc - 1][qc][cc];
+      for (int j = 1; j < Lc; ++j) cur[j] = fma(cur[j - 1] - prev[j - 1], c_facinv[Lc][j], cur[j - 1]);
+      if (Lc >= 2 && sh.alive[qc]) atomicMax(&sh.err[w][Lc - 1], absbits((cur[Lc - 1] - cur[Lc - 2]) * scale));
+      for (int j = 0; j < Lc; ++j) prev[j] = cur[j];
+    }
+    __syncwarp();
+    if (Lc >= 2 && sh.err[w][Lc - 1] <= eps) { acc = Lc; break; }
+  }
+  if (acc && rowth) sh.yn[w][qc][cc] = cur[acc - 1];
+  __syncwarp();
+  return acc;
+}
+
+__global__ void __launch_bounds__(64 * BSP_UNITS, 2) k_bs_pair(Sim S, DevParams P, double tau) {
+  __shared__ BsPairShared shu[BSP_UNITS];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, unit = wid >> 1, spec = wid & 1;
+  const int bar = 1 + unit;
+  BsPairShared &sh = shu[unit];
+  const int np = S.npad;
+  const int ngroups = *S.ngroups;
+  for (int it = 0;; ++it) {
+    // next group: from the queue when there is one, else a fixed stride
+    if (spec == 0 && lane == 0)
+      sh.gidx = S.bsq ? (int)atomicAdd(&S.bsq[0], 1u) : (blockIdx.x + it * gridDim.x) * BSP_UNITS + unit;
+    unit_sync(bar);
+    const int gidx = sh.gidx;
+    if (gidx >= ngroups) break;  // uniform within the unit
     const int g0 = S.gstart[gidx], g = S.gsize ? S.gsize[gidx] : S.gstart[gidx + 1] - g0;
-    if (g > 2) continue;  // uniform within the warp
+    if (g > 2) { unit_sync(bar); continue; }  // uniform within the unit
     const double m0 = S.sys_of ? S.sys_m0[S.sys_of[S.gmem[g0]]] : P.m0;
     const double Gm0 = P.G * m0;
-    const bool act = q < g;
-    if (lane < g) {
-      const int i = S.gmem[g0 + lane];
-      sh.idx[lane] = i;
-      sh.alive[lane] = S.alive[i];
-      sh.gm[lane] = S.gm[i]; sh.m[lane] = S.m[i]; sh.R[lane] = S.R[i]; sh.A[lane] = S.A[i];
-      sh.rcsq[lane] = S.rcsq[i];
-      for (int c = 0; c < 3; ++c) { sh.y[lane][c] = S.x0[c * np + i]; sh.y[lane][3 + c] = S.v0[c * np + i]; }
+    if (spec == 0) {
+      if (lane < g) {
+        const int i = S.gmem[g0 + lane];
+        sh.idx[lane] = i;
+        sh.alive[lane] = S.alive[i];
+        sh.gm[lane] = S.gm[i]; sh.m[lane] = S.m[i]; sh.R[lane] = S.R[i]; sh.A[lane] = S.A[i];
+        sh.rcsq[lane] = S.rcsq[i];
+        for (int c = 0; c < 3; ++c) { sh.y[lane][c] = S.x0[c * np + i]; sh.y[lane][3 + c] = S.v0[c * np + i]; }
+      }
+      if (lane == 0) sh.U = 0.0;
     }
-    if (lane == 0) sh.U = 0.0;
-    __syncwarp();
+    unit_sync(bar);
+    // both warps keep identical copies of the step control
     double H = tau, rem = tau;
     int halvings = 0, attempts = 0, steps = 0;
     bool failed = false;
     while (absbits(rem) != 0ULL) {
       if (absbits(H) > absbits(rem)) H = rem;
       if (++attempts > 200000) { failed = true; break; }
-      const double h = __ddiv_rn(H, (double)nk), h2 = 2.0 * h;
-      const bool qa = act && sh.alive[q];
-      double zA[6], zB[6];
-      for (int c = 0; c < 6; ++c) zA[c] = act ? sh.y[q][c] : 0.0;
-      if (act && sub == 0) for (int c = 0; c < 3; ++c) sh.pos[0][lev][q][c] = zA[c];
-      const int qc = lane / 6, cc = lane % 6;
-      const bool rowth = qc < g;
-      double scale = 0.0;
-      if (rowth) {
-        const double *yq = sh.y[qc] + (cc < 3 ? 0 : 3);
-        const double s2 = fma(yq[2], yq[2], fma(yq[1], yq[1], yq[0] * yq[0]));
-        scale = dbits(s2) == 0ULL ? 4.49423283715579e307 : rsqrt_refined(s2);
-      }
-      if (lane < BS_LEVELS) sh.err[lane] = 0ULL;
-      __syncwarp();
-      double ax, ay, az;
-      pair_terms(sh, P, Gm0, g, act ? q : 0, sub, sh.pos[0][lev], qa, ax, ay, az);
-      if (qa) {
-        zB[0] = fma(h, zA[3], zA[0]); zB[1] = fma(h, zA[4], zA[1]); zB[2] = fma(h, zA[5], zA[2]);
-        zB[3] = fma(h, ax, zA[3]); zB[4] = fma(h, ay, zA[4]); zB[5] = fma(h, az, zA[5]);
-      } else {
-        for (int c = 0; c < 6; ++c) zB[c] = zA[c];
-      }
-      const int lmax = P.bs_kmax < BS_LEVELS ? P.bs_kmax : BS_LEVELS;
-      const u64 eps = dbits(P.bs_eps);
-      double prev[BS_LEVELS], cur[BS_LEVELS];
-      int acc = 0, b = 1;
-      for (int e = 1; e <= 2 * lmax; ++e) {
-        const bool lv = act && e <= nk;
-        if (lv && sub == 0) for (int c = 0; c < 3; ++c) sh.pos[b][lev][q][c] = zB[c];
-        __syncwarp();
-        pair_terms(sh, P, Gm0, g, act ? q : 0, sub, sh.pos[b][lev], qa && e <= nk, ax, ay, az);
-        if (lv) {
-          double out[6];
-          if (qa) {
-            if (e < nk) {
-              double zn[6];
-              zn[0] = fma(h2, zB[3], zA[0]); zn[1] = fma(h2, zB[4], zA[1]); zn[2] = fma(h2, zB[5], zA[2]);
-              zn[3] = fma(h2, ax, zA[3]); zn[4] = fma(h2, ay, zA[4]); zn[5] = fma(h2, az, zA[5]);
-              for (int c = 0; c < 6; ++c) { zA[c] = zB[c]; zB[c] = zn[c]; }
-            } else {
-              out[0] = 0.5 * fma(h, zB[3], zB[0] + zA[0]);
-              out[1] = 0.5 * fma(h, zB[4], zB[1] + zA[1]);
-              out[2] = 0.5 * fma(h, zB[5], zB[2] + zA[2]);
-              out[3] = 0.5 * fma(h, ax, zB[3] + zA[3]);
-              out[4] = 0.5 * fma(h, ay, zB[4] + zA[4]);
-              out[5] = 0.5 * fma(h, az, zB[5] + zA[5]);
-            }
-          } else {
-            for (int c = 0; c < 6; ++c) out[c] = zA[c];
-          }
-          if (e == nk && sub == 0) for (int c = 0; c < 6; ++c) sh.tab[lev][q][c] = out[c];
-        }
-        b ^= 1;
-        if (e & 1) continue;
-        const int Lc = e >> 1;  // level Lc is complete: its tableau row (Neville, in h^2)
-        __syncwarp();
-        if (rowth) {
-          cur[0] = sh.tab[Lc - 1][qc][cc];
-          for (int j = 1; j < Lc; ++j) cur[j] = fma(cur[j - 1] - prev[j - 1], c_facinv[Lc][j], cur[j - 1]);
-          if (Lc >= 2 && sh.alive[qc]) atomicMax(&sh.err[Lc - 1], absbits((cur[Lc - 1] - cur[Lc - 2]) * scale));
-          for (int j = 0; j < Lc; ++j) prev[j] = cur[j];
-        }
-        __syncwarp();
-        if (Lc >= 2 && sh.err[Lc - 1] <= eps) { acc = Lc; break; }
-      }
-      if (!acc) {
+      const int a = pair_attempt(sh, spec, P, Gm0, g, spec ? 0.5 * H : H, lane);
+      if (lane == 0) sh.acc[spec] = a;
+      unit_sync(bar);
+      const int a0 = sh.acc[0], a1 = sh.acc[1];
+      int use = 0;
+      if (!a0) {  // the serial algorithm halves H and tries again: the second warp's attempt
         H *= 0.5;
         if (++halvings > P.bs_max_halvings) { failed = true; break; }
-        continue;
+        if (++attempts > 200000) { failed = true; break; }
+        if (!a1) {
+          H *= 0.5;
+          if (++halvings > P.bs_max_halvings) { failed = true; break; }
+          unit_sync(bar);  // both warps have read acc[] before the next round writes it
+          continue;
+        }
+        use = 1;
       }
-      if (rowth) sh.yn[qc][cc] = cur[acc - 1];
-      __syncwarp();
-      if (P.collisions && g == 2 && lane == 0 && sh.alive[0] && sh.alive[1]) {  // contact over the substep
+      // accepted: substep H from sh.y to sh.yn[use]
+      if (spec == 0 && P.collisions && g == 2 && lane == 0 && sh.alive[0] && sh.alive[1]) {  // contact over the substep
+        double (*yn)[6] = sh.yn[use];
         const double dmin = hermite_min_exact(
             __dsub_rn(sh.y[1][0], sh.y[0][0]), __dsub_rn(sh.y[1][1], sh.y[0][1]), __dsub_rn(sh.y[1][2], sh.y[0][2]),
             __dsub_rn(sh.y[1][3], sh.y[0][3]), __dsub_rn(sh.y[1][4], sh.y[0][4]), __dsub_rn(sh.y[1][5], sh.y[0][5]),
-            __dsub_rn(sh.yn[1][0], sh.yn[0][0]), __dsub_rn(sh.yn[1][1], sh.yn[0][1]), __dsub_rn(sh.yn[1][2], sh.yn[0][2]),
-            __dsub_rn(sh.yn[1][3], sh.yn[0][3]), __dsub_rn(sh.yn[1][4], sh.yn[0][4]), __dsub_rn(sh.yn[1][5], sh.yn[0][5]), H);
+            __dsub_rn(yn[1][0], yn[0][0]), __dsub_rn(yn[1][1], yn[0][1]), __dsub_rn(yn[1][2], yn[0][2]),
+            __dsub_rn(yn[1][3], yn[0][3]), __dsub_rn(yn[1][4], yn[0][4]), __dsub_rn(yn[1][5], yn[0][5]), H);
         const double rr = sh.R[0] + sh.R[1];
         if (dmin < rr * rr) {  // perfect merger (Sect. 3.2, Collisions), as in k_bs
           const int ia = sh.idx[0], ib = sh.idx[1];
           const double ma = sh.m[0], mb = sh.m[1], M = ma + mb;
-          const double dx = sh.yn[1][0] - sh.yn[0][0], dy = sh.yn[1][1] - sh.yn[0][1], dz = sh.yn[1][2] - sh.yn[0][2];
-          const double dvx = sh.yn[1][3] - sh.yn[0][3], dvy = sh.yn[1][4] - sh.yn[0][4], dvz = sh.yn[1][5] - sh.yn[0][5];
+          const double dx = yn[1][0] - yn[0][0], dy = yn[1][1] - yn[0][1], dz = yn[1][2] - yn[0][2];
+          const double dvx = yn[1][3] - yn[0][3], dvy = yn[1][4] - yn[0][4], dvz = yn[1][5] - yn[0][5];
           const double r = sqrt(dx * dx + dy * dy + dz * dz);
           const double v2 = dvx * dvx + dvy * dvy + dvz * dvz;
           sh.U += 0.5 * ma * mb / M * v2 - P.G * ma * mb / r;
           const bool keep_a = ma > mb || (ma == mb && ia < ib);
           const int sv = keep_a ? 0 : 1, d = keep_a ? 1 : 0;
-          for (int c = 0; c < 6; ++c) sh.yn[sv][c] = (ma * sh.yn[0][c] + mb * sh.yn[1][c]) / M;
+          for (int c = 0; c < 6; ++c) yn[sv][c] = (ma * yn[0][c] + mb * yn[1][c]) / M;
           const double Ra = sh.R[0], Rb = sh.R[1];
           sh.R[sv] = cbrt(Ra * Ra * Ra + Rb * Rb * Rb);
           sh.m[sv] = M; sh.gm[sv] = P.G * M;
@@ -482,33 +527,35 @@ __global__ void __launch_bounds__(32 * BSP_WARPS, 2) k_bs_pair(Sim S, DevParams 
         }
       }
       __syncwarp();
-      if (lane < g) for (int c = 0; c < 6; ++c) sh.y[lane][c] = sh.yn[lane][c];
-      __syncwarp();
+      if (spec == 0 && lane < g) for (int c = 0; c < 6; ++c) sh.y[lane][c] = sh.yn[use][lane][c];
+      unit_sync(bar);
       rem -= H;
       H *= 2.0;
       halvings = 0;
       steps++;
     }
-    if (lane < g) {
-      const int i = sh.idx[lane];
-      if (sh.alive[lane]) {
-        for (int c = 0; c < 3; ++c) { S.x[c * np + i] = sh.y[lane][c]; S.v[c * np + i] = sh.y[lane][3 + c]; }
-      } else {
-        S.x[i] = PARK + 1.0e4 * i; S.x[np + i] = 0.0; S.x[2 * np + i] = 0.0;
-        for (int c = 0; c < 3; ++c) S.v[c * np + i] = 0.0;
+    if (spec == 0) {
+      if (lane < g) {
+        const int i = sh.idx[lane];
+        if (sh.alive[lane]) {
+          for (int c = 0; c < 3; ++c) { S.x[c * np + i] = sh.y[lane][c]; S.v[c * np + i] = sh.y[lane][3 + c]; }
+        } else {
+          S.x[i] = PARK + 1.0e4 * i; S.x[np + i] = 0.0; S.x[2 * np + i] = 0.0;
+          for (int c = 0; c < 3; ++c) S.v[c * np + i] = 0.0;
+        }
+      }
+      if (lane == 0) {
+        if (failed) atomicOr(S.status, ST_BS_FAILED);
+        atomicAdd((unsigned long long *)&S.counters[C_BSSTEPS], (unsigned long long)steps);
+        if (dbits(sh.U) != 0ULL) atomicAdd(S.U, sh.U);
       }
     }
-    if (lane == 0) {
-      if (failed) atomicOr(S.status, ST_BS_FAILED);
-      atomicAdd((unsigned long long *)&S.counters[C_BSSTEPS], (unsigned long long)steps);
-      if (dbits(sh.U) != 0ULL) atomicAdd(S.U, sh.U);
-    }
-    __syncwarp();
+    unit_sync(bar);  // the group's shared state is free for the next one
   }
 }
 
 void launch_bs_pair(const Sim &S, const DevParams &P, double tau, int blocks, cudaStream_t st) {
-  k_bs_pair<<<blocks, 32 * BSP_WARPS, 0, st>>>(S, P, tau);
+  k_bs_pair<<<blocks, 64 * BSP_UNITS, 0, st>>>(S, P, tau);
 }
 
 }  // namespace genga

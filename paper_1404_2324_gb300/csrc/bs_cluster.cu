@@ -80,7 +80,10 @@ __global__ void __cluster_dims__(CL_SIZE, 1, 1) __launch_bounds__(CL_THREADS, 2)
   const int np = S.npad;
   const int ngroups = *S.ngroups;
   const int ncl = gridDim.x / CL_SIZE, cid = blockIdx.x / CL_SIZE;
-  for (int gidx = cid; gidx < ngroups; gidx += ncl) {
+  // the groups listed by size (one per cluster while there are no more than clusters), else all
+  const int nwork = S.big ? *S.nbig : ngroups;
+  for (int k = cid; k < nwork; k += ncl) {
+    const int gidx = S.big ? S.big[k] : k;
     const int g0 = S.gstart[gidx], g = S.gsize ? S.gsize[gidx] : S.gstart[gidx + 1] - g0;
     if (g < gmin || g > BS_GMAX) continue;  // the same for all CTAs of the cluster (g < gmin: one-CTA kernel)
     const double m0 = S.sys_of ? S.sys_m0[S.sys_of[S.gmem[g0]]] : P.m0;

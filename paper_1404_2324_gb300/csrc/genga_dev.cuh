@@ -59,6 +59,7 @@ struct Sim {
   int *edges, *nedges;           // edge list [2 * cap] and its count
   int *fail, *nfail;             // Kepler-fallback bodies [npad] and count
   int *gstart, *gmem, *ngroups;  // groups
+  int *big, *nbig;               // groups with gbig or more members (the cluster kernel's work list)
   int *items, nitems, nwarps;    // kick work list
   // batched mode (independent systems; null in the single-system mode)
   int nsys;
@@ -68,6 +69,7 @@ struct Sim {
   u64 *bmask, *emask;            // per body: candidate / encounter partners (bit = index in system)
   int *gsize;                    // batched groups: member count per group (gstart = first member)
   int *gtotal;                   // batched groups: members placed so far
+  unsigned *bsq;                 // batched groups: next group taken by the pair kernel [0] and k_bs [1]
   // recording of the BS decisions for the adjoint engine (null otherwise): the accepted
   // (H, level) of every substep of group g go to seq_pool[seq_off[g] .. + seq_len[g]]
   double2 *seq_pool;

@@ -20,7 +20,7 @@ int kick_grid(const Sim &S);
 void launch_drift(const Sim &S, const DevParams &P, double tau, double hcm1, double hcm2,
                   int first_substep, cudaStream_t st);
 void launch_encounter(const Sim &S, double tau, unsigned *ebm, cudaStream_t st);
-void launch_group(const Sim &S, cudaStream_t st);
+void launch_group(const Sim &S, cudaStream_t st, int gbig = BS_GMAX + 1);  // gbig: size threshold of S.big
 void launch_kepler_phase(int n, double mu, double dt, int maxit, const int *alive, double *x, double *v,
                          int *fail, cudaStream_t st);
 void launch_pairs_to_bitmap(const Sim &S, const int *pairs, int npairs, cudaStream_t st);

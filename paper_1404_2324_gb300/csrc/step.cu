@@ -177,7 +177,7 @@ __device__ __forceinline__ int find_root(const int *link, int r) {
   return r;
 }
 
-__global__ void __launch_bounds__(GROUP_THREADS) k_group(Sim S) {
+__global__ void __launch_bounds__(GROUP_THREADS) k_group(Sim S, int gbig) {
   __shared__ int link[NMAX];
   __shared__ int key[NMAX];
   __shared__ unsigned char part[NMAX];
@@ -237,6 +237,12 @@ __global__ void __launch_bounds__(GROUP_THREADS) k_group(Sim S) {
     if (s_ng) atomicAdd((unsigned long long *)&S.counters[C_GROUPS], (unsigned long long)s_ng);
     *S.nedges = 0;
     *S.nfail = 0;
+  }
+  if (S.big) {  // the groups of gbig or more members, in group order
+    __syncthreads();
+    const int nb = block_compact(s_ng, [&](int g) { return S.gstart[g + 1] - S.gstart[g] >= gbig; },
+                                 [&](int g, int pos) { S.big[pos] = g; }, wtot, &s_base);
+    if (tid == 0) *S.nbig = nb;
   }
 }
 
@@ -337,7 +343,7 @@ void launch_drift(const Sim &S, const DevParams &P, double tau, double hcm1, dou
 void launch_encounter(const Sim &S, double tau, unsigned *ebm, cudaStream_t st) {
   k_encounter<<<(S.npad * 32 + 127) / 128, 128, 0, st>>>(S, tau, ebm);
 }
-void launch_group(const Sim &S, cudaStream_t st) { k_group<<<1, GROUP_THREADS, 0, st>>>(S); }
+void launch_group(const Sim &S, cudaStream_t st, int gbig) { k_group<<<1, GROUP_THREADS, 0, st>>>(S, gbig); }
 void launch_kepler_phase(int n, double mu, double dt, int maxit, const int *alive, double *x, double *v,
                          int *fail, cudaStream_t st) {
   k_kepler_phase<<<(n + 31) / 32, 32, 0, st>>>(n, mu, dt, maxit, alive, x, v, fail);
