@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(BS_THREADS, 2) k_bs(Sim S, DevParams P, double
       }
       const int lmax = P.bs_kmax < BS_LEVELS ? P.bs_kmax : BS_LEVELS;
       const u64 eps = dbits(P.bs_eps);
-      double prev[BS_LEVELS], cur[BS_LEVELS];
+      double prev[BS_LEVELS], tlast = 0.0;  // previous tableau row; T_{Lc,Lc} of the current one
       int acc = 0;
       int b = 1;
       for (int e = 1; e <= 2 * lmax; ++e) {
@@ -173,15 +173,14 @@ __global__ void __launch_bounds__(BS_THREADS, 2) k_bs(Sim S, DevParams P, double
         const int Lc = e >> 1;
         __syncthreads();
         if (rowth) {
-          cur[0] = sh.tab[Lc - 1][qc][cc];
-          for (int j = 1; j < Lc; ++j) cur[j] = fma(cur[j - 1] - prev[j - 1], c_facinv[Lc][j], cur[j - 1]);
-          if (Lc >= 2 && sh.alive[qc]) atomicMax(&sh.err[Lc - 1], absbits((cur[Lc - 1] - cur[Lc - 2]) * scale));
-          for (int j = 0; j < Lc; ++j) prev[j] = cur[j];
+          double before;
+          tlast = neville_row(sh.tab[Lc - 1][qc][cc], Lc, [&](int j) { return c_facinv[Lc][j]; }, prev, before);
+          if (Lc >= 2 && sh.alive[qc]) atomicMax(&sh.err[Lc - 1], absbits((tlast - before) * scale));
         }
         __syncthreads();
         if (Lc >= 2 && sh.err[Lc - 1] <= eps) { acc = Lc; break; }  // uniform: every thread reads the same error
       }
-      if (acc && rowth) sh.yn[qc][cc] = cur[acc - 1];
+      if (acc && rowth) sh.yn[qc][cc] = tlast;  // the accepted row is the last one built
       if (acc) {
         __syncthreads();
         if (P.collisions) {  // contact test over the accepted substep (Hermite, threshold (R_a + R_b)^2)
@@ -343,20 +342,40 @@ struct BsPairShared {
 // the two warps of a unit (named barrier 1 + unit, 64 threads)
 __device__ __forceinline__ void unit_sync(int bar) { asm volatile("bar.sync %0, 64;" ::"r"(bar) : "memory"); }
 
-__device__ __forceinline__ void pair_terms(const BsPairShared &sh, const DevParams &P, double Gm0, int g, int q, int sub,
-                                           const double (*pos)[3], bool q_alive, double &ax, double &ay, double &az) {
+// One lane's term (the central mass if p == q, else partner p) with what stays fixed over an
+// attempt: the source's G m, the smaller A = 1/(0.9 rc), the larger rc^2 (bits) and the partner's
+// live flag; only the positions change between evaluations.
+struct PairTerm {
+  double pref, Amin;
+  u64 thr;
+  bool cen, palive, has;
+};
+
+__device__ __forceinline__ PairTerm pair_term(const BsPairShared &sh, double Gm0, int g, int q, int p) {
+  PairTerm t;
+  t.has = p < g;
+  const int pp = t.has ? p : q;
+  t.cen = p == q;
+  t.pref = t.cen ? Gm0 : sh.gm[pp];
+  t.Amin = pmin(sh.A[q], sh.A[pp]);
+  t.thr = umax64(sh.rcsq[q], sh.rcsq[pp]);
+  t.palive = sh.alive[pp] != 0;
+  return t;
+}
+
+__device__ __forceinline__ void pair_terms(const PairTerm &t, const DevParams &P, int q, int p, const double (*pos)[3],
+                                           bool q_alive, double &ax, double &ay, double &az) {
   ax = ay = az = 0.0;
-  const int p = sub;
-  if (q_alive && p < g) {
+  if (q_alive && t.has) {
     const double xq = pos[q][0], yq = pos[q][1], zq = pos[q][2];
-    const bool cen = p == q;
+    const bool cen = t.cen;
     const double dx = (cen ? 0.0 : pos[p][0]) - xq, dy = (cen ? 0.0 : pos[p][1]) - yq, dz = (cen ? 0.0 : pos[p][2]) - zq;
     const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
     const double yr = rsqrt_refined(r2);
-    const bool inside = sh.alive[p] && dbits(r2) < umax64(sh.rcsq[q], sh.rcsq[p]);
-    const double wA = changeover_wA_clamped(r2 * yr, pmin(sh.A[q], sh.A[p]), P.kmode);
+    const bool inside = t.palive && dbits(r2) < t.thr;
+    const double wA = changeover_wA_clamped(r2 * yr, t.Amin, P.kmode);
     const double w = cen ? 1.0 : (inside ? wA : 0.0);
-    const double f = (cen ? Gm0 : sh.gm[p]) * w * (yr * yr * yr);
+    const double f = t.pref * w * (yr * yr * yr);
     ax = f * dx; ay = f * dy; az = f * dz;
   }
   ax += __shfl_xor_sync(0xffffffffu, ax, 1);
@@ -385,8 +404,10 @@ __device__ int pair_attempt(BsPairShared &sh, int w, const DevParams &P, double 
   }
   if (lane < BS_LEVELS) sh.err[w][lane] = 0ULL;
   __syncwarp();
+  const int qq = act ? q : 0;
+  const PairTerm term = pair_term(sh, Gm0, g, qq, sub);
   double ax, ay, az;
-  pair_terms(sh, P, Gm0, g, act ? q : 0, sub, sh.pos[w][0][lev], qa, ax, ay, az);
+  pair_terms(term, P, qq, sub, sh.pos[w][0][lev], qa, ax, ay, az);
   if (qa) {
     zB[0] = fma(h, zA[3], zA[0]); zB[1] = fma(h, zA[4], zA[1]); zB[2] = fma(h, zA[5], zA[2]);
     zB[3] = fma(h, ax, zA[3]); zB[4] = fma(h, ay, zA[4]); zB[5] = fma(h, az, zA[5]);
@@ -395,13 +416,13 @@ __device__ int pair_attempt(BsPairShared &sh, int w, const DevParams &P, double 
   }
   const int lmax = P.bs_kmax < BS_LEVELS ? P.bs_kmax : BS_LEVELS;
   const u64 eps = dbits(P.bs_eps);
-  double prev[BS_LEVELS], cur[BS_LEVELS];
+  double prev[BS_LEVELS], tlast = 0.0;  // previous tableau row; T_{Lc,Lc} of the current one
   int acc = 0, b = 1;
   for (int e = 1; e <= 2 * lmax; ++e) {
     const bool lv = act && e <= nk;
     if (lv && sub == 0) for (int c = 0; c < 3; ++c) sh.pos[w][b][lev][q][c] = zB[c];
     __syncwarp();
-    pair_terms(sh, P, Gm0, g, act ? q : 0, sub, sh.pos[w][b][lev], qa && e <= nk, ax, ay, az);
+    pair_terms(term, P, qq, sub, sh.pos[w][b][lev], qa && e <= nk, ax, ay, az);
     if (lv) {
       double out[6];
       if (qa) {
@@ -428,15 +449,14 @@ __device__ int pair_attempt(BsPairShared &sh, int w, const DevParams &P, double 
     const int Lc = e >> 1;  // level Lc is complete: its tableau row (Neville, in h^2)
     __syncwarp();
     if (rowth) {
-      cur[0] = sh.tab[w][Lc - 1][qc][cc];
-      for (int j = 1; j < Lc; ++j) cur[j] = fma(cur[j - 1] - prev[j - 1], c_facinv[Lc][j], cur[j - 1]);
-      if (Lc >= 2 && sh.alive[qc]) atomicMax(&sh.err[w][Lc - 1], absbits((cur[Lc - 1] - cur[Lc - 2]) * scale));
-      for (int j = 0; j < Lc; ++j) prev[j] = cur[j];
+      double before;
+      tlast = neville_row(sh.tab[w][Lc - 1][qc][cc], Lc, [&](int j) { return c_facinv[Lc][j]; }, prev, before);
+      if (Lc >= 2 && sh.alive[qc]) atomicMax(&sh.err[w][Lc - 1], absbits((tlast - before) * scale));
     }
     __syncwarp();
     if (Lc >= 2 && sh.err[w][Lc - 1] <= eps) { acc = Lc; break; }
   }
-  if (acc && rowth) sh.yn[w][qc][cc] = cur[acc - 1];
+  if (acc && rowth) sh.yn[w][qc][cc] = tlast;  // the accepted row is the last one built
   __syncwarp();
   return acc;
 }
@@ -446,17 +466,18 @@ __global__ void __launch_bounds__(64 * BSP_UNITS, 2) k_bs_pair(Sim S, DevParams 
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, unit = wid >> 1, spec = wid & 1;
   const int bar = 1 + unit;
   BsPairShared &sh = shu[unit];
+  auto usync = [&]() { unit_sync(bar); };
   const int np = S.npad;
   const int ngroups = *S.ngroups;
   for (int it = 0;; ++it) {
     // next group: from the queue when there is one, else a fixed stride
     if (spec == 0 && lane == 0)
       sh.gidx = S.bsq ? (int)atomicAdd(&S.bsq[0], 1u) : (blockIdx.x + it * gridDim.x) * BSP_UNITS + unit;
-    unit_sync(bar);
+    usync();
     const int gidx = sh.gidx;
     if (gidx >= ngroups) break;  // uniform within the unit
     const int g0 = S.gstart[gidx], g = S.gsize ? S.gsize[gidx] : S.gstart[gidx + 1] - g0;
-    if (g > 2) { unit_sync(bar); continue; }  // uniform within the unit
+    if (g > 2) { usync(); continue; }  // uniform within the unit
     const double m0 = S.sys_of ? S.sys_m0[S.sys_of[S.gmem[g0]]] : P.m0;
     const double Gm0 = P.G * m0;
     if (spec == 0) {
@@ -470,7 +491,7 @@ __global__ void __launch_bounds__(64 * BSP_UNITS, 2) k_bs_pair(Sim S, DevParams 
       }
       if (lane == 0) sh.U = 0.0;
     }
-    unit_sync(bar);
+    usync();
     // both warps keep identical copies of the step control
     double H = tau, rem = tau;
     int halvings = 0, attempts = 0, steps = 0;
@@ -480,7 +501,7 @@ __global__ void __launch_bounds__(64 * BSP_UNITS, 2) k_bs_pair(Sim S, DevParams 
       if (++attempts > 200000) { failed = true; break; }
       const int a = pair_attempt(sh, spec, P, Gm0, g, spec ? 0.5 * H : H, lane);
       if (lane == 0) sh.acc[spec] = a;
-      unit_sync(bar);
+      usync();
       const int a0 = sh.acc[0], a1 = sh.acc[1];
       int use = 0;
       if (!a0) {  // the serial algorithm halves H and tries again: the second warp's attempt
@@ -490,7 +511,7 @@ __global__ void __launch_bounds__(64 * BSP_UNITS, 2) k_bs_pair(Sim S, DevParams 
         if (!a1) {
           H *= 0.5;
           if (++halvings > P.bs_max_halvings) { failed = true; break; }
-          unit_sync(bar);  // both warps have read acc[] before the next round writes it
+          usync();  // both warps have read acc[] before the next round writes it
           continue;
         }
         use = 1;
@@ -528,7 +549,7 @@ __global__ void __launch_bounds__(64 * BSP_UNITS, 2) k_bs_pair(Sim S, DevParams 
       }
       __syncwarp();
       if (spec == 0 && lane < g) for (int c = 0; c < 6; ++c) sh.y[lane][c] = sh.yn[use][lane][c];
-      unit_sync(bar);
+      usync();
       rem -= H;
       H *= 2.0;
       halvings = 0;
@@ -550,7 +571,7 @@ __global__ void __launch_bounds__(64 * BSP_UNITS, 2) k_bs_pair(Sim S, DevParams 
         if (dbits(sh.U) != 0ULL) atomicAdd(S.U, sh.U);
       }
     }
-    unit_sync(bar);  // the group's shared state is free for the next one
+    usync();  // the group's shared state is free for the next one
   }
 }
 

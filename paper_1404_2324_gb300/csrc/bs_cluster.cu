@@ -138,7 +138,7 @@ __global__ void __cluster_dims__(CL_SIZE, 1, 1) __launch_bounds__(CL_THREADS, 2)
       const int lmax = P.bs_kmax < BS_LEVELS ? P.bs_kmax : BS_LEVELS;
       const u64 eps = dbits(P.bs_eps);
       const double scale = rowth ? sh.isc[qc][cc < 3 ? 0 : 1] : 0.0;
-      double prev[BS_LEVELS], cur[BS_LEVELS];
+      double prev[BS_LEVELS], tlast = 0.0;  // previous tableau row; T_{Lc,Lc} of the current one
       int acc = 0;
       int b = 1;
       for (int e = 1; e <= 2 * lmax; ++e) {
@@ -172,15 +172,14 @@ __global__ void __cluster_dims__(CL_SIZE, 1, 1) __launch_bounds__(CL_THREADS, 2)
         cluster.sync();  // T_{Lc,1} is complete in CTA Lc - 1
         if (rowth) {
           const double *rt = cluster.map_shared_rank(&sh.T1[buf][0][0], (unsigned)(Lc - 1));
-          cur[0] = rt[qc * 6 + cc];
-          for (int j = 1; j < Lc; ++j) cur[j] = fma(cur[j - 1] - prev[j - 1], c_facinv_cl[Lc][j], cur[j - 1]);
-          if (Lc >= 2 && sh.alive[qc]) atomicMax(&sh.err[Lc - 1], absbits((cur[Lc - 1] - cur[Lc - 2]) * scale));
-          for (int j = 0; j < Lc; ++j) prev[j] = cur[j];
+          double before;
+          tlast = neville_row(rt[qc * 6 + cc], Lc, [&](int j) { return c_facinv_cl[Lc][j]; }, prev, before);
+          if (Lc >= 2 && sh.alive[qc]) atomicMax(&sh.err[Lc - 1], absbits((tlast - before) * scale));
         }
         __syncthreads();
         if (Lc >= 2 && sh.err[Lc - 1] <= eps) { acc = Lc; break; }
       }
-      if (acc && rowth) sh.yn[qc][cc] = cur[acc - 1];
+      if (acc && rowth) sh.yn[qc][cc] = tlast;  // the accepted row is the last one built
       buf ^= 1;
       if (acc) {
         __syncthreads();

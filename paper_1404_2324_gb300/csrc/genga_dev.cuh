@@ -152,15 +152,27 @@ __device__ __forceinline__ double f2d_exact(float f) {
 // Taylor series of (1 - e)^p in the residual e of a single-precision seed). The seed has a
 // relative error below 2^-21, so the truncated series leaves ~1e-19 and the result is within
 // about one ulp. Valid for positive normal arguments inside the float exponent range.
+// The seeds are the single-instruction approximations of the PTX ISA (rsqrt.approx.ftz.f32,
+// rcp.approx.ftz.f32: relative error about 2^-23); the refinement supplies the accuracy.
 // ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ float rsqrt_seed(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_seed(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 __device__ __forceinline__ double rsqrt_refined(double x) {  // x^(-1/2): 5 FP64 operations
-  double y = f2d_exact(rsqrtf(d2f_trunc(x)));
+  double y = f2d_exact(rsqrt_seed(d2f_trunc(x)));
   double e = fma(-x, y * y, 1.0);   // y*y is exact (24-bit significand squared)
   double p = fma(e, 0.375, 0.5);
   return fma(y * e, p, y);
 }
 __device__ __forceinline__ double rcube_refined(double x) {  // x^(-3/2): 6 FP64 operations
-  double y = f2d_exact(rsqrtf(d2f_trunc(x)));
+  double y = f2d_exact(rsqrt_seed(d2f_trunc(x)));
   double y2 = y * y;
   double e = fma(-x, y2, 1.0);
   double y3 = y2 * y;
@@ -168,10 +180,37 @@ __device__ __forceinline__ double rcube_refined(double x) {  // x^(-3/2): 6 FP64
   return fma(y3, e * p, y3);
 }
 __device__ __forceinline__ double rcp_refined(double x) {  // 1/x, either sign: 3 FP64 operations
-  double y = f2d_exact(__frcp_rn(d2f_trunc(x)));
+  double y = f2d_exact(rcp_seed(d2f_trunc(x)));
   double e = fma(-x, y, 1.0);
   double t = fma(e, e, e);
   return fma(y, t, y);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Row Lc of the Neville tableau of the Bulirsch-Stoer extrapolation (polynomial in h^2, Sect. 3.2):
+// T_{Lc,1} = t1, T_{Lc,j+1} = T_{Lc,j} + (T_{Lc,j} - T_{Lc-1,j}) fac(j), with the previous row in
+// prev[] (overwritten by this one). The loops are unrolled with a uniform exit, so both rows stay
+// in registers. Returns T_{Lc,Lc}; *before receives T_{Lc,Lc-1} (Lc >= 2).
+// ---------------------------------------------------------------------------------------------
+template <class Fac>
+__device__ __forceinline__ double neville_row(double t1, int Lc, Fac fac, double (&prev)[BS_LEVELS], double &before) {
+  double cur[BS_LEVELS];
+  cur[0] = t1;
+  double last = t1;
+  before = 0.0;
+#pragma unroll
+  for (int j = 1; j < BS_LEVELS; ++j) {
+    if (j >= Lc) break;
+    cur[j] = fma(cur[j - 1] - prev[j - 1], fac(j), cur[j - 1]);
+    before = last;
+    last = cur[j];
+  }
+#pragma unroll
+  for (int j = 0; j < BS_LEVELS; ++j) {
+    if (j >= Lc) break;
+    prev[j] = cur[j];
+  }
+  return last;
 }
 
 // ---------------------------------------------------------------------------------------------

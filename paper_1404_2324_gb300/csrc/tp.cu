@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(128, 3) k_tp_bs(Sim S, TPSet T, DevParams P, d
         sc = dbits(s2) == 0ULL ? 4.49423283715579e307 : rsqrt_refined(s2);
       }
       const int lmax = P.bs_kmax < BS_LEVELS ? P.bs_kmax : BS_LEVELS;
-      double prev[BS_LEVELS], cur[BS_LEVELS];
+      double prev[BS_LEVELS], tlast = 0.0;  // previous tableau row; T_{Lc,Lc} of the current one
       int acc = 0;
       for (int m = 1; m <= 2 * lmax; ++m) {
         double out[6];
@@ -438,10 +438,9 @@ __global__ void __launch_bounds__(128, 3) k_tp_bs(Sim S, TPSet T, DevParams P, d
         }
         bool ok = false;
         if (tabl) {
-          cur[0] = t1;
-          for (int j = 1; j < Lc; ++j) cur[j] = fma(cur[j - 1] - prev[j - 1], c_tp_facinv[Lc][j], cur[j - 1]);
-          ok = Lc >= 2 && absbits((cur[Lc - 1] - cur[Lc - 2]) * sc) <= dbits(P.bs_eps);
-          for (int j = 0; j < Lc; ++j) prev[j] = cur[j];
+          double before;
+          tlast = neville_row(t1, Lc, [&](int j) { return c_tp_facinv[Lc][j]; }, prev, before);
+          ok = Lc >= 2 && absbits((tlast - before) * sc) <= dbits(P.bs_eps);
         }
         const unsigned bal = __ballot_sync(0xffffffffu, ok);
         if (((bal >> BS_LEVELS) & 0x3fu) == 0x3fu) { acc = Lc; break; }  // all six components converged
@@ -452,7 +451,7 @@ __global__ void __launch_bounds__(128, 3) k_tp_bs(Sim S, TPSet T, DevParams P, d
         continue;
       }
       double yn[6];
-      for (int c = 0; c < 6; ++c) yn[c] = __shfl_sync(0xffffffffu, tabl ? cur[acc - 1] : 0.0, BS_LEVELS + c);
+      for (int c = 0; c < 6; ++c) yn[c] = __shfl_sync(0xffffffffu, tabl ? tlast : 0.0, BS_LEVELS + c);
       halvings = 0;
       steps++;
       if (P.collisions) {  // contact with an encountered planet during the substep removes the TP
