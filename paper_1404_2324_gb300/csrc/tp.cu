@@ -347,12 +347,20 @@ __device__ __forceinline__ void tp_force(const Sim &S, const TPSet &T, const Dev
   }
 }
 
-// BS of one listed TP per warp; lane L-1 runs level L (n_L = 2L midpoint substeps).
-// Launched with 3 blocks per SM (the register budget of one block allows three).
+// BS of one listed TP per warp; lane L-1 runs level L (n_L = 2L midpoint substeps) and lanes
+// 8..13 hold the tableau rows. Launched with 3 blocks per SM (the register budget of one block
+// allows three).
+//
+// Speculation. After a failed full-length attempt the step control alternates a failed attempt at
+// 2H with an accepted one at H. From the second attempt on, lanes 16..29 mirror lanes 0..13 with
+// H/2 from the same state; their result is used exactly when the serial algorithm's next attempt
+// would be that one (the H attempt failed), so results and decisions are the serial algorithm's.
+// The mirror lanes cost no FP64 issue: a warp instruction costs the same whatever its active lanes.
 __global__ void __launch_bounds__(128, 3) k_tp_bs(Sim S, TPSet T, DevParams P, double tau) {
-  __shared__ double s_pos[4][TP_PRE * TP_TAB * 3];
-  const int lane = threadIdx.x & 31;
-  double *wpos = s_pos[threadIdx.x >> 5];
+  constexpr int WPOS = TP_PRE * TP_TAB * 3;
+  __shared__ double s_pos[4][2 * WPOS];
+  const int lane = threadIdx.x & 31, half = lane >> 4, l16 = lane & 15;
+  double *wpos0 = s_pos[threadIdx.x >> 5];
   const int nlist = *T.nbs;
   const int np = T.npad;
   const double i2tau = 2.0 / tau;
@@ -364,7 +372,7 @@ __global__ void __launch_bounds__(128, 3) k_tp_bs(Sim S, TPSet T, DevParams P, d
     if (w >= nlist) break;
     const int i = T.bslist[w];
     const unsigned em = T.emask[i];
-    const int L = lane < BS_LEVELS ? lane + 1 : 1, nk = 2 * L;
+    const int L = l16 < BS_LEVELS ? l16 + 1 : 1, nk = 2 * L;
     double y[6];
     for (int c = 0; c < 3; ++c) { y[c] = T.x0[c * np + i]; y[3 + c] = T.v0[c * np + i]; }
     double t0 = 0.0, rem = tau, H = tau;
@@ -373,20 +381,25 @@ __global__ void __launch_bounds__(128, 3) k_tp_bs(Sim S, TPSet T, DevParams P, d
     while (absbits(rem) != 0ULL && ++attempts < 100000) {
       if (absbits(H) > absbits(rem)) H = rem;
       const bool table = dbits(t0) == 0ULL && dbits(H) == dbits(tau);
-      const double h = __ddiv_rn(H, (double)nk), h2 = 2.0 * h;
-      if (!table && em) {  // positions of the first TP_PRE planets at all midpoint times, lane-parallel
+      const bool spec = !table;  // the mirror lanes attempt H/2
+      const double Hl = (spec && half) ? 0.5 * H : H;  // this lane's attempt length
+      const double h = __ddiv_rn(Hl, (double)nk), h2 = 2.0 * h;
+      double *wpos = wpos0 + (spec ? half * WPOS : 0);
+      if (!table && em) {  // positions of the first TP_PRE planets at all midpoint times of both attempts
         __syncwarp();
         unsigned bits = em;
         for (int p = 0; p < TP_PRE && bits; ++p) {
           const int j = __ffs(bits) - 1;
           bits &= bits - 1;
-          for (int e = lane; e < TP_TAB; e += 32) {
+          for (int e2 = lane; e2 < 2 * TP_TAB; e2 += 32) {
+            const int hf = e2 >= TP_TAB ? 1 : 0, e = e2 - hf * TP_TAB;
+            const double He = hf ? 0.5 * H : H;
             int k = 1;
             while (tab_index(k + 1, 0) <= e) k++;
             const int m = e - tab_index(k, 0);
-            const double hk = __ddiv_rn(H, (double)(2 * k));
-            const double t = (m == 2 * k) ? t0 + H : t0 + m * hk;
-            double *q = wpos + (p * TP_TAB + e) * 3;
+            const double hk = __ddiv_rn(He, (double)(2 * k));
+            const double t = (m == 2 * k) ? t0 + He : t0 + m * hk;
+            double *q = wpos0 + hf * WPOS + (p * TP_TAB + e) * 3;
             planet_at(S, T, P, j, false, k, m, t, i2tau, q[0], q[1], q[2]);
           }
         }
@@ -394,13 +407,14 @@ __global__ void __launch_bounds__(128, 3) k_tp_bs(Sim S, TPSet T, DevParams P, d
       }
       double za[6], zb[6], ax, ay, az;
       for (int c = 0; c < 6; ++c) za[c] = y[c];
-      tp_force(S, T, P, i, em, table, L, 0, t0, h, H, i2tau, wpos, y, ax, ay, az);
+      tp_force(S, T, P, i, em, table, L, 0, t0, h, Hl, i2tau, wpos, y, ax, ay, az);
       zb[0] = fma(h, y[3], y[0]); zb[1] = fma(h, y[4], y[1]); zb[2] = fma(h, y[5], y[2]);
       zb[3] = fma(h, ax, y[3]); zb[4] = fma(h, ay, y[4]); zb[5] = fma(h, az, y[5]);
-      // Level L (lane L - 1) finishes at evaluation 2L; lanes 8..13 then extend the tableau by its
-      // row, component c on lane 8 + c (polynomial extrapolation in h^2, Neville), and the first
-      // converged level ends the attempt: the same decision as building the whole tableau first.
-      const int cc = lane - BS_LEVELS;           // component of the tableau lanes
+      // Level L (lane L - 1 of each half) finishes at evaluation 2L; the half's lanes 8..13 then
+      // extend its tableau by that row, component c on lane 8 + c (polynomial extrapolation in h^2,
+      // Neville), and the first converged level ends that half's attempt: the same decision as
+      // building the whole tableau first.
+      const int cc = l16 - BS_LEVELS;            // component of the tableau lanes
       const bool tabl = cc >= 0 && cc < 6;
       double sc = 0.0;                           // 1/|x| or 1/|v| at the start of the attempt
       if (tabl) {
@@ -410,11 +424,12 @@ __global__ void __launch_bounds__(128, 3) k_tp_bs(Sim S, TPSet T, DevParams P, d
       }
       const int lmax = P.bs_kmax < BS_LEVELS ? P.bs_kmax : BS_LEVELS;
       double prev[BS_LEVELS], tlast = 0.0;  // previous tableau row; T_{Lc,Lc} of the current one
-      int acc = 0;
+      double tfix = 0.0;                    // the mirror half's accepted value (its tableau lanes)
+      int acc = 0, accB = 0;
       for (int m = 1; m <= 2 * lmax; ++m) {
         double out[6];
         if (m <= nk) {
-          tp_force(S, T, P, i, em, table, L, m, t0, h, H, i2tau, wpos, zb, ax, ay, az);
+          tp_force(S, T, P, i, em, table, L, m, t0, h, Hl, i2tau, wpos, zb, ax, ay, az);
           if (m < nk) {
             double zn[6];
             zn[0] = fma(h2, zb[3], za[0]); zn[1] = fma(h2, zb[4], za[1]); zn[2] = fma(h2, zb[5], za[2]);
@@ -424,7 +439,7 @@ __global__ void __launch_bounds__(128, 3) k_tp_bs(Sim S, TPSet T, DevParams P, d
         }
         if (m & 1) continue;
         const int Lc = m >> 1;
-        if (lane == Lc - 1) {  // this lane's level is complete: T_{Lc,1}
+        if (l16 == Lc - 1) {  // this lane's level is complete: T_{Lc,1}
           out[0] = 0.5 * fma(h, zb[3], zb[0] + za[0]); out[1] = 0.5 * fma(h, zb[4], zb[1] + za[1]);
           out[2] = 0.5 * fma(h, zb[5], zb[2] + za[2]); out[3] = 0.5 * fma(h, ax, zb[3] + za[3]);
           out[4] = 0.5 * fma(h, ay, zb[4] + za[4]); out[5] = 0.5 * fma(h, az, zb[5] + za[5]);
@@ -433,7 +448,7 @@ __global__ void __launch_bounds__(128, 3) k_tp_bs(Sim S, TPSet T, DevParams P, d
         }
         double t1 = 0.0;
         for (int c = 0; c < 6; ++c) {
-          const double v = __shfl_sync(0xffffffffu, out[c], Lc - 1);
+          const double v = __shfl_sync(0xffffffffu, out[c], (lane & 16) + Lc - 1);
           if (c == cc) t1 = v;
         }
         bool ok = false;
@@ -443,15 +458,28 @@ __global__ void __launch_bounds__(128, 3) k_tp_bs(Sim S, TPSet T, DevParams P, d
           ok = Lc >= 2 && absbits((tlast - before) * sc) <= dbits(P.bs_eps);
         }
         const unsigned bal = __ballot_sync(0xffffffffu, ok);
+        if (spec && !accB && ((bal >> (16 + BS_LEVELS)) & 0x3fu) == 0x3fu) {  // the H/2 attempt converged
+          accB = Lc;
+          tfix = tlast;
+        }
         if (((bal >> BS_LEVELS) & 0x3fu) == 0x3fu) { acc = Lc; break; }  // all six components converged
       }
-      if (!acc) {
+      int use = 0;
+      if (!acc) {  // the serial algorithm halves H and tries again: the mirror lanes' attempt
         H *= 0.5;
         if (++halvings > P.bs_max_halvings) { failed = true; break; }
-        continue;
+        if (!spec) continue;
+        ++attempts;
+        if (!accB) {
+          H *= 0.5;
+          if (++halvings > P.bs_max_halvings) { failed = true; break; }
+          continue;
+        }
+        use = 1;
       }
       double yn[6];
-      for (int c = 0; c < 6; ++c) yn[c] = __shfl_sync(0xffffffffu, tabl ? tlast : 0.0, BS_LEVELS + c);
+      const double mine = half ? tfix : tlast;
+      for (int c = 0; c < 6; ++c) yn[c] = __shfl_sync(0xffffffffu, tabl ? mine : 0.0, 16 * use + BS_LEVELS + c);
       halvings = 0;
       steps++;
       if (P.collisions) {  // contact with an encountered planet during the substep removes the TP
