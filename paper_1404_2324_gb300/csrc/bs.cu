@@ -332,7 +332,7 @@ struct BsPairShared {
   double y[2][6];                     // state at the start of the round
   double yn[2][2][6];                 // [warp] result of the warp's attempt
   double pos[2][2][BS_LEVELS][2][3];  // [warp][buffer][level][member]
-  double tab[2][BS_LEVELS][2][6];     // [warp] T_{L,1} per level
+  double zt[2][BS_LEVELS][2][16];     // [warp] a level's last midpoint state: z_{n-1}, z_n, a(z_n), h
   u64 err[2][BS_LEVELS];              // [warp]
   int acc[2];
   int gidx;
@@ -424,33 +424,30 @@ __device__ int pair_attempt(BsPairShared &sh, int w, const DevParams &P, double 
     __syncwarp();
     pair_terms(term, P, qq, sub, sh.pos[w][b][lev], qa && e <= nk, ax, ay, az);
     if (lv) {
-      double out[6];
-      if (qa) {
-        if (e < nk) {
-          double zn[6];
-          zn[0] = fma(h2, zB[3], zA[0]); zn[1] = fma(h2, zB[4], zA[1]); zn[2] = fma(h2, zB[5], zA[2]);
-          zn[3] = fma(h2, ax, zA[3]); zn[4] = fma(h2, ay, zA[4]); zn[5] = fma(h2, az, zA[5]);
-          for (int c = 0; c < 6; ++c) { zA[c] = zB[c]; zB[c] = zn[c]; }
-        } else {
-          out[0] = 0.5 * fma(h, zB[3], zB[0] + zA[0]);
-          out[1] = 0.5 * fma(h, zB[4], zB[1] + zA[1]);
-          out[2] = 0.5 * fma(h, zB[5], zB[2] + zA[2]);
-          out[3] = 0.5 * fma(h, ax, zB[3] + zA[3]);
-          out[4] = 0.5 * fma(h, ay, zB[4] + zA[4]);
-          out[5] = 0.5 * fma(h, az, zB[5] + zA[5]);
-        }
-      } else {
-        for (int c = 0; c < 6; ++c) out[c] = zA[c];
+      if (qa && e < nk) {
+        double zn[6];
+        zn[0] = fma(h2, zB[3], zA[0]); zn[1] = fma(h2, zB[4], zA[1]); zn[2] = fma(h2, zB[5], zA[2]);
+        zn[3] = fma(h2, ax, zA[3]); zn[4] = fma(h2, ay, zA[4]); zn[5] = fma(h2, az, zA[5]);
+        for (int c = 0; c < 6; ++c) { zA[c] = zB[c]; zB[c] = zn[c]; }
       }
-      if (e == nk && sub == 0) for (int c = 0; c < 6; ++c) sh.tab[w][lev][q][c] = out[c];
+      // the level's chain is done: its tableau lanes form T_{L,1} = (z_{n-1} + z_n + h z'_n) / 2,
+      // one component each, so the warp issues that arithmetic once instead of per level lane
+      if (e == nk && sub == 0) {
+        double *z = sh.zt[w][lev][q];
+        for (int c = 0; c < 6; ++c) { z[c] = zA[c]; z[6 + c] = zB[c]; }
+        z[12] = ax; z[13] = ay; z[14] = az; z[15] = h;
+      }
     }
     b ^= 1;
     if (e & 1) continue;
     const int Lc = e >> 1;  // level Lc is complete: its tableau row (Neville, in h^2)
     __syncwarp();
     if (rowth) {
+      const double *z = sh.zt[w][Lc - 1][qc];
+      const double dz = cc < 3 ? z[9 + cc] : z[12 + cc - 3];  // derivative of component cc at z_n
+      const double t1 = sh.alive[qc] ? 0.5 * fma(z[15], dz, z[6 + cc] + z[cc]) : z[cc];
       double before;
-      tlast = neville_row(sh.tab[w][Lc - 1][qc][cc], Lc, [&](int j) { return c_facinv[Lc][j]; }, prev, before);
+      tlast = neville_row(t1, Lc, [&](int j) { return c_facinv[Lc][j]; }, prev, before);
       if (Lc >= 2 && sh.alive[qc]) atomicMax(&sh.err[w][Lc - 1], absbits((tlast - before) * scale));
     }
     __syncwarp();

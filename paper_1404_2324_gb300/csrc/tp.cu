@@ -359,6 +359,7 @@ __device__ __forceinline__ void tp_force(const Sim &S, const TPSet &T, const Dev
 __global__ void __launch_bounds__(128, 3) k_tp_bs(Sim S, TPSet T, DevParams P, double tau) {
   constexpr int WPOS = TP_PRE * TP_TAB * 3;
   __shared__ double s_pos[4][2 * WPOS];
+  __shared__ double s_zt[4][2][16];  // per warp and half: a completed level's z_{n-1}, z_n, z'_n, h
   const int lane = threadIdx.x & 31, half = lane >> 4, l16 = lane & 15;
   double *wpos0 = s_pos[threadIdx.x >> 5];
   const int nlist = *T.nbs;
@@ -427,7 +428,6 @@ __global__ void __launch_bounds__(128, 3) k_tp_bs(Sim S, TPSet T, DevParams P, d
       double tfix = 0.0;                    // the mirror half's accepted value (its tableau lanes)
       int acc = 0, accB = 0;
       for (int m = 1; m <= 2 * lmax; ++m) {
-        double out[6];
         if (m <= nk) {
           tp_force(S, T, P, i, em, table, L, m, t0, h, Hl, i2tau, wpos, zb, ax, ay, az);
           if (m < nk) {
@@ -439,18 +439,20 @@ __global__ void __launch_bounds__(128, 3) k_tp_bs(Sim S, TPSet T, DevParams P, d
         }
         if (m & 1) continue;
         const int Lc = m >> 1;
-        if (l16 == Lc - 1) {  // this lane's level is complete: T_{Lc,1}
-          out[0] = 0.5 * fma(h, zb[3], zb[0] + za[0]); out[1] = 0.5 * fma(h, zb[4], zb[1] + za[1]);
-          out[2] = 0.5 * fma(h, zb[5], zb[2] + za[2]); out[3] = 0.5 * fma(h, ax, zb[3] + za[3]);
-          out[4] = 0.5 * fma(h, ay, zb[4] + za[4]); out[5] = 0.5 * fma(h, az, zb[5] + za[5]);
-        } else {
-          for (int c = 0; c < 6; ++c) out[c] = 0.0;
+        // level Lc's lane hands its last midpoint state to the tableau lanes, which form
+        // T_{Lc,1} = (z_{n-1} + z_n + h z'_n) / 2 one component each
+        double *zt = s_zt[threadIdx.x >> 5][half];
+        if (l16 == Lc - 1) {
+          for (int c = 0; c < 6; ++c) { zt[c] = za[c]; zt[6 + c] = zb[c]; }
+          zt[12] = ax; zt[13] = ay; zt[14] = az; zt[15] = h;
         }
+        __syncwarp();
         double t1 = 0.0;
-        for (int c = 0; c < 6; ++c) {
-          const double v = __shfl_sync(0xffffffffu, out[c], (lane & 16) + Lc - 1);
-          if (c == cc) t1 = v;
+        if (tabl) {
+          const double dz = cc < 3 ? zt[9 + cc] : zt[12 + cc - 3];
+          t1 = 0.5 * fma(zt[15], dz, zt[6 + cc] + zt[cc]);
         }
+        __syncwarp();
         bool ok = false;
         if (tabl) {
           double before;
