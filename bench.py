@@ -14,7 +14,8 @@ metric through the public API with host buffers: each step uploads the state fro
 memory (genga_set_state), steps, and reads it back (genga_get_state). roofline: the pairwise
 kick kernel (dominant), FP64-ALU bound. cpu_baseline: the CPU oracle on a bounded sample.
 With --gpus N > 1 (torchrun) every rank runs an independent replica (the method does not shard
-at this N); value counts the steps of all ranks over the slowest rank's time.
+at this N); value counts the steps of all ranks over the slowest rank's time, and only the main
+line runs (the batched, test-particle and adjoint legs are single-GPU measurements).
 """
 from __future__ import annotations
 
@@ -408,6 +409,23 @@ def run_adjoint(args):
                       f"steps, merging off; state resident in HBM (no L2 flush: each timed region is seconds long)"}
 
 
+# ------------------------------------------------------------------------------------ ranks
+def rank_max(x, world, device=None):
+    """The largest x over all ranks (the slowest replica sets the job's time); x itself at N = 1."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput of `world` replicas that each processed `units_per_rank` units, timed by
+    the slowest one."""
+    return world * units_per_rank / seconds
+
+
 # ------------------------------------------------------------------------------------ GPU arm
 def run_gpu(args, rank, world):
     import torch
@@ -449,12 +467,8 @@ def run_gpu(args, rank, world):
         torch.distributed.barrier()
     clocks = sampler.stop()
     code, counters = genga.genga_status(ctx)
-    t_max = total_ms
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * args.steps / (t_max * 1e-3)
+    t_max = rank_max(total_ms, world, "cuda")
+    value = job_rate(args.steps, world, t_max * 1e-3)
 
     # end to end through the public API with host buffers (pinned)
     genga.genga_set_profiling(ctx, False)
@@ -474,12 +488,8 @@ def run_gpu(args, rank, world):
         genga.genga_set_state(ctx, hx, hv)
         genga.genga_step(ctx, 1)
         genga.lib().genga_get_state(ctx, hx.ctypes.data_as(genga._D), hv.ctypes.data_as(genga._D), None, None, None)
-    t_e2e = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e = {"value": world * e2e_steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(hx.nbytes + hv.nbytes),
+    t_e2e = rank_max(time.perf_counter() - t0, world, "cuda")
+    e2e = {"value": job_rate(e2e_steps, world, t_e2e), "unit": UNIT, "h2d_bytes_per_step": int(hx.nbytes + hv.nbytes),
            "d2h_bytes_per_step": int(hx.nbytes + hv.nbytes), "steps": e2e_steps,
            "note": "genga_set_state + genga_step + genga_get_state per step; set_state recomputes the first kick"}
     genga.genga_free(ctx)
@@ -562,12 +572,13 @@ def main():
         import torch
         torch.distributed.init_process_group("nccl")
     res = run_gpu(args, rank, world)
-    if not args.no_batched:
-        res["batched"] = run_batched(args)
-    if not args.no_tp:
-        res["test_particles"] = run_tp(args, measured_peaks(res))
-    if not args.no_adjoint:
-        res["adjoint"] = run_adjoint(args)
+    if world == 1:  # the other modes are single-GPU measurements: with replicas only the main line runs
+        if not args.no_batched:
+            res["batched"] = run_batched(args)
+        if not args.no_tp:
+            res["test_particles"] = run_tp(args, measured_peaks(res))
+        if not args.no_adjoint:
+            res["adjoint"] = run_adjoint(args)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             import oracle
