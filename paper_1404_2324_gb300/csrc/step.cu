@@ -56,74 +56,90 @@ __global__ void k_kepler_phase(int n, double mu, double dt, int maxit, const int
 }
 
 // ---------------------------------------------------------------------------------------------
-// Encounter search: one warp per body i scans its row of the candidate bitmap (clearing it for
-// the next kick), tests the pairs j > i with the Hermite minimum over the drift and writes the
-// confirmed pairs into the row of this substep's encounter bitmap and into the edge list.
+// Encounter search: one CTA per 32 bodies. Its warps gather the candidate pairs (i, j > i) of those
+// bodies from the candidate lists (or the bitmap row when a list overflowed) into shared memory,
+// clearing the candidate rows for the next kick; then every thread tests one pair with the
+// Hermite minimum over the drift, and confirmed pairs go into this substep's encounter bitmap and
+// the edge list. One pair per lane: a warp per body would issue the whole FP64 test for one or two
+// active lanes, and an FP64 warp instruction costs its sub-partition the same whatever its lanes.
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_encounter(Sim S, double tau, unsigned *ebm) {
-  const int lane = threadIdx.x & 31;
-  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (i >= S.npad) return;
+constexpr int ENC_BODIES = 32;   // bodies per CTA (one word of the row-nonempty bits)
+constexpr int ENC_THREADS = 256;
+constexpr int ENC_CAP = 1024;    // gathered pairs per CTA; further pairs are tested where found
+
+__device__ __forceinline__ bool encounter_test(const Sim &S, double tau, int i, int j) {
+  const int np = S.npad;
+  if (!S.alive[i] || !S.alive[j]) return false;
+  const double dmin = hermite_min_exact(
+      __dsub_rn(S.x0[j], S.x0[i]), __dsub_rn(S.x0[np + j], S.x0[np + i]), __dsub_rn(S.x0[2 * np + j], S.x0[2 * np + i]),
+      __dsub_rn(S.v0[j], S.v0[i]), __dsub_rn(S.v0[np + j], S.v0[np + i]), __dsub_rn(S.v0[2 * np + j], S.v0[2 * np + i]),
+      __dsub_rn(S.x[j], S.x[i]), __dsub_rn(S.x[np + j], S.x[np + i]), __dsub_rn(S.x[2 * np + j], S.x[2 * np + i]),
+      __dsub_rn(S.v[j], S.v[i]), __dsub_rn(S.v[np + j], S.v[np + i]), __dsub_rn(S.v[2 * np + j], S.v[2 * np + i]), tau);
+  const double rcij = pmax(S.rc[i], S.rc[j]);
+  return dmin < __dmul_rn(rcij, rcij);
+}
+
+__global__ void __launch_bounds__(ENC_THREADS) k_encounter(Sim S, double tau, unsigned *ebm) {
+  __shared__ int s_i[ENC_CAP], s_j[ENC_CAP];
+  __shared__ int s_n, s_found;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int np = S.npad, W = S.W;
-  unsigned *erow = ebm + (size_t)i * W;
-  unsigned *crow = S.cbm + (size_t)i * W;
-  if (!((S.rowany[i >> 5] >> (i & 31)) & 1u)) {
-    for (int w = lane; w < W; w += 32) erow[w] = 0u;
-    return;
+  const int i0 = blockIdx.x * ENC_BODIES;
+  if (tid == 0) { s_n = 0; s_found = 0; }
+  for (int k = tid; k < ENC_BODIES * W; k += ENC_THREADS) {  // this substep's rows start empty
+    const int i = i0 + k / W;
+    if (i < np) ebm[(size_t)i * W + k % W] = 0u;
   }
-  const double x0i = S.x0[i], y0i = S.x0[np + i], z0i = S.x0[2 * np + i];
-  const double u0i = S.v0[i], v0i = S.v0[np + i], w0i = S.v0[2 * np + i];
-  const double x1i = S.x[i], y1i = S.x[np + i], z1i = S.x[2 * np + i];
-  const double u1i = S.v[i], v1i = S.v[np + i], w1i = S.v[2 * np + i];
-  const double rci = S.rc[i];
-  const bool ai = S.alive[i] != 0;
+  __syncthreads();
   int found = 0;
-  // Hermite test of candidate (i, j), j > i; sets the pair's bit in this row and lists the edge
-  auto test = [&](int j) {
-    if (!ai || !S.alive[j]) return;
-    const double dmin = hermite_min_exact(
-        __dsub_rn(S.x0[j], x0i), __dsub_rn(S.x0[np + j], y0i), __dsub_rn(S.x0[2 * np + j], z0i),
-        __dsub_rn(S.v0[j], u0i), __dsub_rn(S.v0[np + j], v0i), __dsub_rn(S.v0[2 * np + j], w0i),
-        __dsub_rn(S.x[j], x1i), __dsub_rn(S.x[np + j], y1i), __dsub_rn(S.x[2 * np + j], z1i),
-        __dsub_rn(S.v[j], u1i), __dsub_rn(S.v[np + j], v1i), __dsub_rn(S.v[2 * np + j], w1i), tau);
-    const double rcij = pmax(rci, S.rc[j]);
-    if (dmin < __dmul_rn(rcij, rcij)) {
-      atomicOr(&erow[j >> 5], 1u << (j & 31));
-      const int e = atomicAdd(S.nedges, 1);
-      S.edges[2 * e] = i;
-      S.edges[2 * e + 1] = j;
-      found++;
-    }
+  auto hit = [&](int i, int j) {
+    atomicOr(&ebm[(size_t)i * W + (j >> 5)], 1u << (j & 31));
+    const int e = atomicAdd(S.nedges, 1);
+    S.edges[2 * e] = i;
+    S.edges[2 * e + 1] = j;
+    found++;
   };
-  for (int w = lane; w < W; w += 32) erow[w] = 0u;
-  __syncwarp();
-  const int cnt = S.ccnt[i];
-  if (cnt <= CCAP) {  // partners from the list, one per lane
-    for (int k = lane; k < cnt; k += 32) {
-      const int j = S.clist[i * CCAP + k];
-      if (j > i) test(j);
-    }
-    for (int w = lane; w < W; w += 32) crow[w] = 0u;
-  } else {  // list overflowed: scan the bitmap row
-    for (int w = lane; w < W; w += 32) {
-      unsigned bits = crow[w];
-      crow[w] = 0u;
-      const int lo = w * 32;
-      if (lo + 31 <= i) bits = 0u;
-      else if (lo <= i) bits &= (i - lo + 1 >= 32) ? 0u : (0xffffffffu << (i - lo + 1));
-      while (bits) {
-        const int b = __ffs(bits) - 1;
-        bits &= bits - 1;
-        test(lo + b);
+  auto add = [&](int i, int j) {  // gather, or test at once if the shared list is full
+    const int p = atomicAdd(&s_n, 1);
+    if (p < ENC_CAP) { s_i[p] = i; s_j[p] = j; }
+    else if (encounter_test(S, tau, i, j)) hit(i, j);
+  };
+  const unsigned rows = i0 < np ? S.rowany[i0 >> 5] : 0u;
+  for (int b = wid; b < ENC_BODIES; b += ENC_THREADS / 32) {
+    const int i = i0 + b;
+    if (i >= np || !((rows >> b) & 1u)) continue;  // uniform within the warp
+    unsigned *crow = S.cbm + (size_t)i * W;
+    const int cnt = S.ccnt[i];
+    if (cnt <= CCAP) {  // partners from the list
+      for (int k = lane; k < cnt; k += 32) {
+        const int j = S.clist[i * CCAP + k];
+        if (j > i) add(i, j);
+      }
+      for (int w = lane; w < W; w += 32) crow[w] = 0u;
+    } else {  // list overflowed: scan the bitmap row
+      for (int w = lane; w < W; w += 32) {
+        unsigned bits = crow[w];
+        crow[w] = 0u;
+        const int lo = w * 32;
+        if (lo + 31 <= i) bits = 0u;
+        else if (lo <= i) bits &= (i - lo + 1 >= 32) ? 0u : (0xffffffffu << (i - lo + 1));
+        while (bits) {
+          const int bb = __ffs(bits) - 1;
+          bits &= bits - 1;
+          add(i, lo + bb);
+        }
       }
     }
+    if (lane == 0) S.ccnt[i] = 0;
   }
-  __syncwarp();
-  if (found) atomicAdd((unsigned long long *)&S.counters[C_ENC], (unsigned long long)found);
-  if (lane == 0) {
-    S.ccnt[i] = 0;
-    atomicAnd(&S.rowany[i >> 5], ~(1u << (i & 31)));
-  }
+  __syncthreads();
+  if (tid == 0 && i0 < np) S.rowany[i0 >> 5] = 0u;  // the CTA's 32 rows are clear
+  const int n = s_n < ENC_CAP ? s_n : ENC_CAP;
+  for (int p = tid; p < n; p += ENC_THREADS)
+    if (encounter_test(S, tau, s_i[p], s_j[p])) hit(s_i[p], s_j[p]);
+  if (found) atomicAdd(&s_found, found);
+  __syncthreads();
+  if (tid == 0 && s_found) atomicAdd((unsigned long long *)&S.counters[C_ENC], (unsigned long long)s_found);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -341,7 +357,7 @@ void launch_drift(const Sim &S, const DevParams &P, double tau, double hcm1, dou
   k_drift<<<S.npad / 32, 32, 0, st>>>(S, P, tau, hcm1, hcm2, first_substep);
 }
 void launch_encounter(const Sim &S, double tau, unsigned *ebm, cudaStream_t st) {
-  k_encounter<<<(S.npad * 32 + 127) / 128, 128, 0, st>>>(S, tau, ebm);
+  k_encounter<<<(S.npad + ENC_BODIES - 1) / ENC_BODIES, ENC_THREADS, 0, st>>>(S, tau, ebm);
 }
 void launch_group(const Sim &S, cudaStream_t st, int gbig) { k_group<<<1, GROUP_THREADS, 0, st>>>(S, gbig); }
 void launch_kepler_phase(int n, double mu, double dt, int maxit, const int *alive, double *x, double *v,
