@@ -208,7 +208,8 @@ __device__ __forceinline__ double near_term(const Sim &S, const DevParams &P, in
 //   OPEN : first kick of a full step with the new critical radii: a = stored far field + near
 //          pairs recomputed (KickA; KickB when there are none), or the full recompute's partials.
 //   INIT : the very first kick: store the far field (and a = far + near into aout if given).
-// The near pairs of the tile's 32 bodies are gathered from the candidate lists, sorted per body,
+// The near pairs of the tile's 32 bodies are gathered from the candidate lists (one coalesced pass
+// into shared memory), put in ascending partner order per body (each entry goes to its rank),
 // evaluated one per thread across the CTA and summed per body in partner order.
 // Also writes the per-tile momentum of the new velocities for the next Sun drift.
 // ---------------------------------------------------------------------------------------------
@@ -217,9 +218,9 @@ __global__ void __launch_bounds__(128) k_fin(Sim S, DevParams P, double h1, doub
   const int B = blockIdx.x, c = blockIdx.y, wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int np = S.npad, nt = S.nt, i = B * 32 + lane;
   __shared__ double red[4][32];
-  __shared__ int ent[32 * CCAP];
+  __shared__ int ent[32 * CCAP], raw[32 * CCAP];
   __shared__ double contrib[32 * CCAP];
-  __shared__ int off[33];
+  __shared__ int off[33], s_cnt[32];
   const bool use_part = (MODE != FIN_OPEN) || (S.flags[0] != 0);
   const bool full_open = (MODE == FIN_OPEN) && (S.flags[0] != 0);
   if (use_part) {
@@ -229,12 +230,11 @@ __global__ void __launch_bounds__(128) k_fin(Sim S, DevParams P, double h1, doub
     for (int s = s0; s < s1; ++s) acc += base[(size_t)s * 96];
     red[wi][lane] = acc;
   }
-  // gather this tile's candidate partners (warp 0), each body's list sorted ascending
-  int cnt = 0;
+  // this tile's candidate partners: counts and offsets (warp 0), then the lists (all threads)
   bool overflow = false;
   if (wi == 0) {
     const bool any = !full_open && ((S.rowany[i >> 5] >> (i & 31)) & 1u);
-    cnt = any ? S.ccnt[i] : 0;
+    int cnt = any ? S.ccnt[i] : 0;
     overflow = cnt > CCAP;
     if (overflow) cnt = 0;
     int incl = cnt;
@@ -243,24 +243,32 @@ __global__ void __launch_bounds__(128) k_fin(Sim S, DevParams P, double h1, doub
       const int t = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= o) incl += t;
     }
-    const int o0 = incl - cnt;
     off[lane + 1] = incl;
+    s_cnt[lane] = cnt;
     if (lane == 0) off[0] = 0;
-    for (int k = 0; k < cnt; ++k) {  // insertion into place: ascending partner index
-      const int j = S.clist[i * CCAP + k];
-      int q = o0 + k;
-      while (q > o0 && ent[q - 1] > j) { ent[q] = ent[q - 1]; q--; }
-      ent[q] = j;
-    }
   }
   __syncthreads();
   const int M = off[32];
-  for (int k = threadIdx.x; k < M; k += 128) {
-    int b = 0;  // owner: the last body whose offset is <= k
+  for (int e = threadIdx.x; e < 32 * CCAP; e += 128) {
+    const int b = e / CCAP, k = e % CCAP;
+    if (k < s_cnt[b]) raw[off[b] + k] = S.clist[(B * 32 + b) * CCAP + k];
+  }
+  __syncthreads();
+  auto owner = [&](int k) {  // the last body whose offset is <= k
+    int b = 0;
     for (int s = 16; s > 0; s >>= 1)
       if (b + s <= 32 && off[b + s] <= k) b += s;
-    contrib[k] = near_term(S, P, B * 32 + b, ent[k], c);
+    return b;
+  };
+  for (int k = threadIdx.x; k < M; k += 128) {  // ascending partner order: each entry to its rank
+    const int b = owner(k), o = off[b], n = off[b + 1] - o;
+    const int j = raw[k];
+    int r = 0;
+    for (int q = 0; q < n; ++q) r += raw[o + q] < j;
+    ent[o + r] = j;
   }
+  __syncthreads();
+  for (int k = threadIdx.x; k < M; k += 128) contrib[k] = near_term(S, P, B * 32 + owner(k), ent[k], c);
   __syncthreads();
   if (wi != 0) return;
   double a = use_part ? (red[0][lane] + red[1][lane]) + (red[2][lane] + red[3][lane]) : S.afar[c * np + i];
