@@ -424,7 +424,7 @@ int genga_init_tp(genga_ctx **out, int n, const double *masses, const double *ra
   T.T = mem.get<u64>(np); T.rcsq = mem.get<u64>(np);
   T.alive = mem.get<int>(np); T.full = mem.get<int>(np); T.fail = mem.get<int>(np);
   T.cmask = mem.get<unsigned>(np); T.emask = mem.get<unsigned>(np);
-  T.bslist = mem.get<int>(np); T.nbs = mem.get<int>(1); T.bsnext = mem.get<unsigned>(1);
+  T.bslist = mem.get<int>(np); T.nbs = mem.get<int>(2); T.bsnext = mem.get<unsigned>(1);
   T.pairs = mem.get<unsigned>(np * (size_t)(n - 1)); T.npairs = mem.get<unsigned>(1);
   T.ptab = mem.get<double>(TP_MAXPL * TP_TAB * 6);
   T.pcheb = mem.get<double>(TP_MAXPL * 6 * TP_CHEB); T.pcok = mem.get<int>(TP_MAXPL);

@@ -95,7 +95,8 @@ struct TPSet {
   u64 *T, *rcsq;                 // [npad]
   int *alive, *full, *fail;      // [npad]
   unsigned *cmask, *emask;       // candidate / encountered planets per TP
-  int *bslist, *nbs;             // TPs that need Bulirsch-Stoer this substep
+  int *bslist, *nbs;             // TPs that need Bulirsch-Stoer this substep: nbs[0] from the front of
+                                 // bslist (deep encounters), nbs[1] from its back (the rest)
   unsigned *bsnext;              // next list entry a BS warp takes
   unsigned *pairs, *npairs;      // candidate (TP, planet) pairs of the last closing kick: i * 32 + j
   double *ptab;                  // planets' Kepler paths at the BS midpoint times [TP_MAXPL * TP_TAB * 6]

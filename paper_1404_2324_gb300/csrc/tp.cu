@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(128) k_tp_kick(Sim S, TPSet T, DevParams P, do
   __shared__ PlanetSm ps;
   load_planets(S, ps);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0) *T.nbs = 0;
+  if (i == 0) { T.nbs[0] = 0; T.nbs[1] = 0; }
   const bool act = i < T.n && T.alive[i];
   unsigned cm = 0u;
   if (act) {
@@ -169,7 +169,7 @@ __global__ void k_tp_drift(Sim S, TPSet T, DevParams P, double tau, double hcm1,
   if (kepler_drift_dev(P.G * P.m0, P.mu2, x, y, z, vx, vy, vz, tau, P.kepler_maxit, &it)) {
     T.fail[i] = 1;
     atomicOr(S.status, ST_KEPLER_FALLBACK);
-    T.bslist[atomicAdd(T.nbs, 1)] = i;  // integrated by BS in the field of m0 alone (unless it meets a planet)
+    T.bslist[T.npad - 1 - atomicAdd(&T.nbs[1], 1)] = i;  // BS in the field of m0 alone (unless it meets a planet)
   }
   T.x[i] = x; T.x[np + i] = y; T.x[2 * np + i] = z;
   T.v[i] = vx; T.v[np + i] = vy; T.v[2 * np + i] = vz;
@@ -252,7 +252,12 @@ __global__ void __launch_bounds__(256) k_tp_encounter(Sim S, TPSet T, double tau
     if (dmin < __dmul_rn(rcij, rcij)) {
       const unsigned old = atomicOr(&T.emask[i], 1u << j);
       atomicAdd((unsigned long long *)&T.counters[1], 1ULL);
-      if (old == 0u && !T.fail[i]) T.bslist[atomicAdd(T.nbs, 1)] = i;
+      // a pass inside a tenth of the critical radius (the planet's pull entirely in BS) needs the
+      // most substeps: such particles go to the front of the list, so they start first
+      if (old == 0u && !T.fail[i]) {
+        if (dmin < 0.01 * __dmul_rn(rcij, rcij)) T.bslist[atomicAdd(&T.nbs[0], 1)] = i;
+        else T.bslist[T.npad - 1 - atomicAdd(&T.nbs[1], 1)] = i;
+      }
     }
   }
 }
@@ -362,7 +367,7 @@ __global__ void __launch_bounds__(128, 3) k_tp_bs(Sim S, TPSet T, DevParams P, d
   __shared__ double s_zt[4][2][16];  // per warp and half: a completed level's z_{n-1}, z_n, z'_n, h
   const int lane = threadIdx.x & 31, half = lane >> 4, l16 = lane & 15;
   double *wpos0 = s_pos[threadIdx.x >> 5];
-  const int nlist = *T.nbs;
+  const int nfront = T.nbs[0], nlist = nfront + T.nbs[1];
   const int np = T.npad;
   const double i2tau = 2.0 / tau;
   if (blockIdx.x == 0 && threadIdx.x == 0) *T.npairs = 0u;  // consumed by the encounter test
@@ -371,7 +376,7 @@ __global__ void __launch_bounds__(128, 3) k_tp_bs(Sim S, TPSet T, DevParams P, d
     if (lane == 0) w = (int)atomicAdd(T.bsnext, 1u);
     w = __shfl_sync(0xffffffffu, w, 0);
     if (w >= nlist) break;
-    const int i = T.bslist[w];
+    const int i = T.bslist[w < nfront ? w : T.npad - 1 - (w - nfront)];
     const unsigned em = T.emask[i];
     const int L = l16 < BS_LEVELS ? l16 + 1 : 1, nk = 2 * L;
     double y[6];
