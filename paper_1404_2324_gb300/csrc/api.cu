@@ -536,6 +536,7 @@ int genga_init_batch(genga_ctx **out, int n_sys, const int *offsets, const doubl
   S.fail = mem.get<int>(np); S.nfail = mem.get<int>(1);
   S.gstart = mem.get<int>(np + 1); S.gmem = mem.get<int>(np); S.ngroups = mem.get<int>(1);
   S.gsize = mem.get<int>(np + 1); S.gtotal = mem.get<int>(1); S.bsq = mem.get<unsigned>(2);
+  S.gorder = mem.get<int>(np); S.norder = mem.get<int>(2); S.bsn = mem.get<unsigned char>(np);
   S.flags = mem.get<int>(4); S.status = mem.get<int>(1);
   S.counters = mem.get<long long>(NCOUNTERS); S.U = mem.get<double>(1);
   S.nsys = n_sys;

@@ -150,7 +150,8 @@ __global__ void k_b_momentum(Sim S, double *out) {
 // substep's second with the momentum before its closing kick), then the Kepler drift.
 __global__ void k_b_drift(Sim S, DevParams P, double tau, double h1, double h2, int first) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0) { *S.ngroups = 0; *S.gtotal = 0; S.bsq[0] = 0u; S.bsq[1] = 0u; }
+  if (i == 0) { *S.ngroups = 0; *S.gtotal = 0; S.bsq[0] = 0u; S.bsq[1] = 0u; S.norder[0] = 0; S.norder[1] = 0; }
+  if (i < S.npad) S.bsn[i] >>= 1;  // the substep history fades
   if (i >= S.npad) return;
   const int np = S.npad;
   const int s = S.sys_of[i];
@@ -217,13 +218,15 @@ __global__ void __launch_bounds__(32 * BG_WARPS) k_b_group(Sim S) {
   __shared__ int cnt_s[BG_WARPS][64];
   __shared__ int pos_s[BG_WARPS][64];
   __shared__ unsigned char part_s[BG_WARPS][64];
+  __shared__ int hist_s[BG_WARPS][64];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int s = blockIdx.x * BG_WARPS + w;
   if (s >= S.nsys) return;  // warp-uniform
   int *link = link_s[w], *cnt = cnt_s[w], *pos = pos_s[w];
   unsigned char *part = part_s[w];
   const int st = S.sys_start[s], n = S.sys_start[s + 1] - st;
-  for (int k = lane; k < 64; k += 32) { link[k] = k; cnt[k] = 0; part[k] = 0; }
+  int *hist = hist_s[w];
+  for (int k = lane; k < 64; k += 32) { link[k] = k; cnt[k] = 0; part[k] = 0; hist[k] = 0; }
   __syncwarp();
   for (int k = lane; k < n; k += 32) {
     const u64 em = S.emask[st + k];
@@ -258,7 +261,10 @@ __global__ void __launch_bounds__(32 * BG_WARPS) k_b_group(Sim S) {
     if (!__any_sync(0xffffffffu, ch)) break;
   }
   for (int k = lane; k < n; k += 32)
-    if (part[k]) atomicAdd(&cnt[link[k]], 1);
+    if (part[k]) {
+      atomicAdd(&cnt[link[k]], 1);
+      atomicMax(&hist[link[k]], (int)S.bsn[st + k]);
+    }
   __syncwarp();
   if (lane == 0) {
     int ng = 0;
@@ -268,6 +274,9 @@ __global__ void __launch_bounds__(32 * BG_WARPS) k_b_group(Sim S) {
         const int p = atomicAdd(S.gtotal, cnt[r]);
         S.gstart[g] = p;
         S.gsize[g] = cnt[r];
+        // groups whose members needed many substeps last time start first (they set the BS time)
+        if (hist[r] >= BS_HEAVY) S.gorder[atomicAdd(&S.norder[0], 1)] = g;
+        else S.gorder[S.npad - 1 - atomicAdd(&S.norder[1], 1)] = g;
         pos[r] = p;
         ng++;
       }

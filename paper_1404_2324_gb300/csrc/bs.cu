@@ -14,6 +14,13 @@ namespace genga {
 // 1/((L/(L-j))^2 - 1) for the Neville extrapolation in h^2 with n_k = 2k
 __constant__ double c_facinv[BS_LEVELS + 1][BS_LEVELS];
 
+// Batched mode: the q-th group of the BS queues (the expected long ones first); q >= ngroups: done.
+__device__ __forceinline__ int batch_group(const Sim &S, int q) {
+  const int nfront = S.norder[0], n = nfront + S.norder[1];
+  if (q >= n) return 0x7fffffff;
+  return S.gorder[q < nfront ? q : S.npad - 1 - (q - nfront)];
+}
+
 struct BsShared {
   int idx[BS_GMAX], alive[BS_GMAX];
   double gm[BS_GMAX], m[BS_GMAX], R[BS_GMAX], A[BS_GMAX];
@@ -70,7 +77,7 @@ __global__ void __launch_bounds__(BS_THREADS, 2) k_bs(Sim S, DevParams P, double
   const int ngroups = *S.ngroups;
   for (int it = 0;; ++it) {
     // next group: from the queue when there is one (batched mode), else a fixed stride
-    if (tid == 0) sh.next = S.bsq ? (int)atomicAdd(&S.bsq[1], 1u) : blockIdx.x + it * gridDim.x;
+    if (tid == 0) sh.next = S.bsq ? batch_group(S, (int)atomicAdd(&S.bsq[1], 1u)) : blockIdx.x + it * gridDim.x;
     __syncthreads();
     const int gidx = sh.next;
     __syncthreads();
@@ -252,6 +259,7 @@ __global__ void __launch_bounds__(BS_THREADS, 2) k_bs(Sim S, DevParams P, double
       __syncthreads();
     }
     // write back: live members take the integrated state, ghosts are parked far out
+    if (tid < g && S.bsn) S.bsn[sh.idx[tid]] = (unsigned char)(steps < 255 ? steps : 255);
     if (tid < g) {
       const int i = sh.idx[tid];
       if (sh.alive[tid]) {
@@ -469,7 +477,7 @@ __global__ void __launch_bounds__(64 * BSP_UNITS, 2) k_bs_pair(Sim S, DevParams 
   for (int it = 0;; ++it) {
     // next group: from the queue when there is one, else a fixed stride
     if (spec == 0 && lane == 0)
-      sh.gidx = S.bsq ? (int)atomicAdd(&S.bsq[0], 1u) : (blockIdx.x + it * gridDim.x) * BSP_UNITS + unit;
+      sh.gidx = S.bsq ? batch_group(S, (int)atomicAdd(&S.bsq[0], 1u)) : (blockIdx.x + it * gridDim.x) * BSP_UNITS + unit;
     usync();
     const int gidx = sh.gidx;
     if (gidx >= ngroups) break;  // uniform within the unit
@@ -553,6 +561,7 @@ __global__ void __launch_bounds__(64 * BSP_UNITS, 2) k_bs_pair(Sim S, DevParams 
       steps++;
     }
     if (spec == 0) {
+      if (lane < g && S.bsn) S.bsn[sh.idx[lane]] = (unsigned char)(steps < 255 ? steps : 255);
       if (lane < g) {
         const int i = sh.idx[lane];
         if (sh.alive[lane]) {

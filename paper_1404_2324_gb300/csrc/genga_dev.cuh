@@ -18,6 +18,7 @@ constexpr int NMAX = 2048;        // main mode: up to 2048 massive bodies (Sect.
 constexpr int BS_LEVELS = 8;      // Bulirsch-Stoer levels, substep sequence n_k = 2k
 constexpr int BS_GMAX = 32;       // largest encounter group integrated in one CTA
 constexpr int BS_THREADS = 256;
+constexpr int BS_HEAVY = 2;      // batched: groups with a member that needed >= 2 BS_HEAVY substeps last time go first
 constexpr int BS_SEQCAP = 256;   // accepted BS substeps one group may record per substep
 constexpr int NCOUNTERS = 8;
 constexpr int CCAP = 32;          // candidate-list slots per body (more: the bitmap row is scanned)
@@ -70,6 +71,9 @@ struct Sim {
   int *gsize;                    // batched groups: member count per group (gstart = first member)
   int *gtotal;                   // batched groups: members placed so far
   unsigned *bsq;                 // batched groups: next group taken by the pair kernel [0] and k_bs [1]
+  int *gorder, *norder;          // batched groups: the order the BS queues take them in: norder[0] groups
+                                 // expected to need many substeps from the front of gorder, norder[1] from its back
+  unsigned char *bsn;            // batched bodies: substeps of the body's last BS group, halved every substep
   // recording of the BS decisions for the adjoint engine (null otherwise): the accepted
   // (H, level) of every substep of group g go to seq_pool[seq_off[g] .. + seq_len[g]]
   double2 *seq_pool;
