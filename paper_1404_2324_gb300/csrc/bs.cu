@@ -1,12 +1,14 @@
 // bs.cu -- Bulirsch-Stoer integration of the encounter groups (Sect. 3.2) with perfect merging
 // on contact (Sect. 3.2, Collisions).
 //
-// One CTA per group. The modified-midpoint integrations of all extrapolation levels
+// k_bs: one CTA per group. The modified-midpoint integrations of all extrapolation levels
 // (n_k = 2k, k = 1..8) run at once: thread (level, member, term) evaluates one term of the
-// member's acceleration (the central mass or one partner), so a step costs the critical path of
-// the deepest level (16 evaluations) instead of the 72 evaluations of the serial scheme. The
-// tableau is then built as a wavefront across levels and the first converged level is accepted,
-// which is exactly the decision of the serial algorithm.
+// member's acceleration (the central mass or one partner). Level L completes after 2L force
+// evaluations; its tableau row is built and tested right away, and the attempt stops at the first
+// converged level -- exactly the decision of the serial algorithm, at 2L + 1 evaluations instead
+// of the serial scheme's 72. Batched groups come from work queues ordered by expected cost.
+// k_bs_pair: groups of one or two members, one warp per attempt, the attempt at H/2 run beside the
+// attempt at H (see there).
 #include "genga_launch.h"
 
 namespace genga {

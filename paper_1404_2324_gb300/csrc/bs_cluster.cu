@@ -3,12 +3,13 @@
 //
 // A group of g members costs 8 levels x g members x g terms per force evaluation; on one SM (the
 // one-CTA kernel in bs.cu) that saturates the FP64 pipes once g reaches a handful. Here each level
-// has an SM of its own. After each attempt every CTA gathers the 8 level results from the others'
-// shared memory (distributed shared memory) and evaluates the whole Neville tableau and the
-// acceptance test itself, with the same arithmetic and order as the one-CTA kernel, so all CTAs take
-// the same decision and follow the same control flow: every cluster barrier is reached by all 8
-// CTAs the same number of times. Results are double-buffered by attempt parity, so one cluster
-// barrier per attempt suffices.
+// has an SM of its own. After every second evaluation the CTAs meet at a cluster barrier; level Lc
+// is then complete in CTA Lc - 1, every CTA reads its T_{Lc,1} from that CTA's shared memory
+// (distributed shared memory), extends its own copy of the Neville tableau and tests level Lc, with
+// the same arithmetic and order as the one-CTA kernel. All CTAs therefore take the same decision
+// and follow the same control flow: every cluster barrier is reached by all 8 CTAs the same number
+// of times. Level results are double-buffered by attempt parity. Cluster k takes the k-th entry of
+// the large-group list that the grouping kernel writes.
 #include <cooperative_groups.h>
 
 #include "genga_launch.h"

@@ -2,14 +2,16 @@
 // single-system kernels) plus massless test particles (TPs) that they perturb.
 //
 // One thread per TP for the kick (K-weighted, prechecker against every planet, planets staged in
-// shared memory), the Sun drift with the massive momentum, the Kepler drift and the Hermite test.
-// A TP with a confirmed planet encounter (or a failed Kepler solve) is integrated alone by
-// Bulirsch-Stoer on one warp, lanes = extrapolation levels, in the field of m0 and the (1 - K)
-// pull of the encountered planets, which move on their Kepler paths from the pre-drift state
-// (Sect. 3.3: only the test particle is updated). The planets' positions at every midpoint time of
-// a full-length BS attempt come from a table computed once per substep; shorter attempts (after a
-// halving) solve Kepler's equation on the fly. A TP whose BS substep reaches a planet's surface is
-// removed.
+// shared memory), the Sun drift with the massive momentum and the Kepler drift; one lane per
+// candidate (TP, planet) pair for the Hermite test. A TP with a confirmed planet encounter (or a
+// failed Kepler solve) is integrated alone by Bulirsch-Stoer on one warp (levels on lanes 0..7,
+// the tableau on lanes 8..13) in the field of m0 and the (1 - K) pull of the encountered planets,
+// which move on their Kepler paths from the pre-drift state (Sect. 3.3: only the test particle is
+// updated). The planets' positions at every midpoint time of a full-length BS attempt come from a
+// table computed once per substep; shorter attempts evaluate a 16-node Chebyshev series of each
+// planet's path (or solve Kepler's equation where the series is not exact to rounding) and attempt
+// H/2 on lanes 16..29 beside H. Particles in the deepest encounters are integrated first. A TP
+// whose BS substep reaches a planet's surface is removed.
 #include "genga_launch.h"
 
 namespace genga {
