@@ -780,6 +780,135 @@ __device__ void grp_chain(const GrpShared &G, LevShared &L, int g, int q, double
 
 constexpr int BSV_WARPS = BS_LEVELS;
 
+// Groups of at most four members (nearly all of them): the whole group on one warp, lane = (level
+// (lane >> 2) + 1, member lane & 3), so one warp instruction serves all levels; an FP64 warp
+// instruction costs the same whatever its active lanes. Every level's lanes run the same arithmetic
+// as in the level-per-warp kernel below, stepping through the evaluations in lock step (a level
+// takes part while the index lies within its chain), so the results are that kernel's.
+constexpr int BSV4_GROUPS = 4;  // groups (warps) per CTA
+struct LevShared4 {
+  double pos[2 * BS_LEVELS + 1][4][3];
+  double cur[4][3], fv[4][3], out[4][6];
+  double mb[4], rcb[4];
+};
+struct GrpVjp4 {
+  GrpShared G;
+  LevShared4 L[BS_LEVELS];
+};
+
+__global__ void __launch_bounds__(32 * BSV4_GROUPS) k_ad_bs_vjp4(Sim S, AdjDev D, SubRec R, const double *x1,
+                                                                 const double *v1) {
+  extern __shared__ double smraw4[];
+  GrpVjp4 &W = ((GrpVjp4 *)smraw4)[threadIdx.x >> 5];
+  GrpShared &G = W.G;
+  const int lane = threadIdx.x & 31, l = (lane >> 2) + 1, q = lane & 3, NB = D.NB;
+  LevShared4 &L = W.L[l - 1];
+  const int ng = *R.ngroups;
+  for (int gi = blockIdx.x * BSV4_GROUPS + (threadIdx.x >> 5); gi < ng; gi += gridDim.x * BSV4_GROUPS) {
+    const int g = R.gsize[gi], g0 = R.gstart[gi];
+    if (g > 4) continue;  // uniform within the warp: the level-per-warp kernel takes it
+    const int body = q < g ? R.gmem[g0 + q] : 0;
+    const double Gm0 = D.G * D.m0[sys_of_body(D, R.gmem[g0])];
+    if (l == 1 && q < g) {
+      G.gm[q] = S.gm[body]; G.A[q] = S.A[body]; G.rc[q] = S.rc[body]; G.rcsq[q] = S.rcsq[body];
+    }
+    double y[6], yb[6];
+    for (int c = 0; c < 3; ++c) {
+      y[c] = q < g ? x1[c * NB + body] : 0.0;
+      y[3 + c] = q < g ? v1[c * NB + body] : 0.0;
+      yb[c] = q < g ? D.xb[c * NB + body] : 0.0;
+      yb[3 + c] = q < g ? D.vb[c * NB + body] : 0.0;
+    }
+    L.mb[q] = 0.0; L.rcb[q] = 0.0;
+    __syncwarp();
+    const int nseq = R.seq_len[gi], soff = R.seq_off[gi];
+    const long long yoff = R.y_off[gi];
+    for (int s = nseq - 1; s >= 0; --s) {
+      const double2 hk = S.seq_pool[soff + s];
+      const double H = hk.x;
+      const int k = (int)hk.y;
+      const bool lvl = l <= k;  // this lane's level enters the accepted extrapolation
+      const int n = 2 * l;
+      const double h = H / n, h2 = 2.0 * h;
+      const double lam = lvl ? c_lambda[k][l] : 0.0;
+      double y0[6];  // start state of accepted substep s: the pre-drift state, or recorded by k_bs
+      for (int c = 0; c < 6; ++c)
+        y0[c] = s == 0 ? y[c] : (q < g ? S.y_pool[yoff + ((long long)(s - 1) * g + q) * 6 + c] : 0.0);
+      // the level's modified-midpoint chain again, positions kept
+      double za[6], zb[6], a[3] = {0.0, 0.0, 0.0};
+      for (int c = 0; c < 6; ++c) za[c] = y0[c];
+      if (lvl && q < g) for (int c = 0; c < 3; ++c) { L.cur[q][c] = za[c]; L.pos[0][q][c] = za[c]; }
+      __syncwarp();
+      if (lvl) grp_accel(G, L.cur, g, q, Gm0, a);
+      __syncwarp();
+      for (int c = 0; c < 3; ++c) { zb[c] = fma(h, za[3 + c], za[c]); zb[3 + c] = fma(h, a[c], za[3 + c]); }
+      for (int m = 1; m <= 2 * k; ++m) {
+        const bool on = lvl && m <= n;
+        if (on && q < g) for (int c = 0; c < 3; ++c) { L.cur[q][c] = zb[c]; L.pos[m][q][c] = zb[c]; }
+        __syncwarp();
+        if (on) grp_accel(G, L.cur, g, q, Gm0, a);
+        __syncwarp();
+        if (on && m < n) {
+          double zn[6];
+          for (int c = 0; c < 3; ++c) { zn[c] = fma(h2, zb[3 + c], za[c]); zn[3 + c] = fma(h2, a[c], za[3 + c]); }
+          for (int c = 0; c < 6; ++c) { za[c] = zb[c]; zb[c] = zn[c]; }
+        }
+      }
+      // backwards through the chain, scaled by the Neville weight lam: t = n is the reverse of
+      // out = (z_n + z_{n-1} + h F(z_n)) / 2, t = n-1 .. 1 of z_{t+1} = z_{t-1} + 2h F(z_t), t = 0 of
+      // z_1 = z_0 + h F(z_0); zbn holds zbar_{t+1}, zbn1 the partial zbar_t
+      double zbn[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, zbn1[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, carry[6], xbq[3];
+      double mbq = L.mb[q], rcbq = L.rcb[q];
+      for (int t = 2 * k; t >= 0; --t) {
+        const bool on = lvl && t <= n;
+        if (on) {
+          if (t == n) {
+            for (int c = 0; c < 6; ++c) { zbn[c] = 0.5 * lam * yb[c]; zbn1[c] = 0.5 * lam * yb[c]; }
+            if (q < g) for (int c = 0; c < 3; ++c) { L.cur[q][c] = L.pos[n][q][c]; L.fv[q][c] = 0.5 * h * lam * yb[3 + c]; }
+          } else if (t >= 1) {
+            for (int c = 0; c < 6; ++c) carry[c] = zbn[c];  // z_{t-1} gets zbar_{t+1}
+            if (q < g) for (int c = 0; c < 3; ++c) { L.cur[q][c] = L.pos[t][q][c]; L.fv[q][c] = h2 * zbn[3 + c]; }
+          } else {
+            if (q < g) for (int c = 0; c < 3; ++c) { L.cur[q][c] = L.pos[0][q][c]; L.fv[q][c] = h * zbn[3 + c]; }
+          }
+        }
+        __syncwarp();
+        if (on) grp_accel_vjp(G, L.cur, L.fv, g, q, Gm0, D.G, xbq, mbq, rcbq);
+        __syncwarp();
+        if (on) {
+          if (t == n) {
+            for (int c = 0; c < 3; ++c) { zbn[c] += xbq[c]; zbn[3 + c] += 0.5 * h * lam * yb[c]; }
+          } else if (t >= 1) {
+            for (int c = 0; c < 3; ++c) { zbn1[c] += xbq[c]; zbn1[3 + c] += h2 * zbn[c]; }
+            for (int c = 0; c < 6; ++c) { zbn[c] = zbn1[c]; zbn1[c] = carry[c]; }
+          } else {
+            for (int c = 0; c < 3; ++c) {
+              L.out[q][c] = zbn1[c] + zbn[c] + xbq[c];
+              L.out[q][3 + c] = zbn1[3 + c] + zbn[3 + c] + h * zbn[c];
+            }
+          }
+        }
+      }
+      if (lvl) { L.mb[q] = mbq; L.rcb[q] = rcbq; }
+      __syncwarp();
+      for (int c = 0; c < 6; ++c) {  // ybar of the substep's start: sum over levels in order
+        double acc = 0.0;
+        for (int ll = 1; ll <= k; ++ll) acc += W.L[ll - 1].out[q][c];
+        yb[c] = acc;
+      }
+      __syncwarp();
+    }
+    if (l == 1 && q < g) {
+      double mb = 0.0, rcb = 0.0;
+      for (int ll = 0; ll < BS_LEVELS; ++ll) { mb += W.L[ll].mb[q]; rcb += W.L[ll].rcb[q]; }
+      for (int c = 0; c < 3; ++c) { D.xb[c * NB + body] = yb[c]; D.vb[c * NB + body] = yb[3 + c]; }
+      D.mb[body] += mb;
+      D.rcb[body] += rcb;
+    }
+    __syncwarp();
+  }
+}
+
 __global__ void __launch_bounds__(32 * BSV_WARPS) k_ad_bs_vjp(Sim S, AdjDev D, SubRec R, const double *x1,
                                                               const double *v1) {
   extern __shared__ double smraw[];
@@ -790,7 +919,7 @@ __global__ void __launch_bounds__(32 * BSV_WARPS) k_ad_bs_vjp(Sim S, AdjDev D, S
   const int ng = *R.ngroups;
   for (int gi = blockIdx.x; gi < ng; gi += gridDim.x) {
     const int g = R.gsize[gi], g0 = R.gstart[gi];
-    if (g > BS_GMAX) continue;  // uniform
+    if (g <= 4 || g > BS_GMAX) continue;  // uniform: groups of up to four members go to k_ad_bs_vjp4
     const int body = q < g ? R.gmem[g0 + q] : 0;
     const double Gm0 = D.G * D.m0[sys_of_body(D, R.gmem[g0])];
     if (w == 0 && q < g) {
@@ -1233,6 +1362,7 @@ int genga_adj_init(genga_adj **out, int n_sys, int n, const double *m0, double G
   cudaFuncSetAttribute(k_ad_kick<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->kick_smem);
   cudaFuncSetAttribute(k_ad_kick<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->kick_smem);
   cudaFuncSetAttribute(k_ad_bs_vjp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(BSV_WARPS * sizeof(LevShared)));
+  cudaFuncSetAttribute(k_ad_bs_vjp4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(BSV4_GROUPS * sizeof(GrpVjp4)));
   bs_init_constants();
   init_lambda();
   init_dstumpff();
@@ -1313,6 +1443,8 @@ int genga_adj_backward(genga_adj *c, const double *xbar, const double *vbar, dou
         cudaMemsetAsync(c->D.ingrp, 0, NB * sizeof(int), st);
         k_ad_mark<<<c->bs_blocks, 32, 0, st>>>(c->D, R.gstart, R.gsize, R.gmem, R.ngroups);
         k_ad_kepler_vjp<<<(NB + 127) / 128, 128, 0, st>>>(c->S, c->D, tau, R.x1, R.v1, R.s);
+        k_ad_bs_vjp4<<<2 * c->bs_blocks, 32 * BSV4_GROUPS, BSV4_GROUPS * sizeof(GrpVjp4), st>>>(c->S, c->D, R, R.x1,
+                                                                                               R.v1);
         k_ad_bs_vjp<<<c->bs_blocks, 32 * BSV_WARPS, BSV_WARPS * sizeof(LevShared), st>>>(c->S, c->D, R, R.x1, R.v1);
         k_ad_sundrift_vjp<<<c->B, 256, 0, st>>>(c->S, c->D, h, R.v1);
         launch_kick_vjp(c, h, R.x);
