@@ -180,34 +180,54 @@ __global__ void k_b_drift(Sim S, DevParams P, double tau, double h1, double h2, 
 }
 
 // Encounter search over each body's candidates with a larger index (Hermite, bit-exact).
-__global__ void k_b_encounter(Sim S, double tau) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= S.npad) return;
-  const int np = S.npad;
-  u64 em = 0ULL;
-  if (S.alive[i]) {
-    const int s = S.sys_of[i], st = S.sys_start[s], li = i - st;
+// Encounter test of the candidate pairs (i, j > i within a system): each CTA gathers the pairs of
+// its 128 bodies in shared memory and tests one per thread (a thread per body would issue the FP64
+// Hermite test for the few lanes that have a candidate); the same arithmetic, so the same masks.
+constexpr int BENC_THREADS = 128;
+constexpr int BENC_CAP = 1024;  // gathered pairs per CTA; further pairs are tested where found
+__global__ void __launch_bounds__(BENC_THREADS) k_b_encounter(Sim S, double tau) {
+  __shared__ u64 s_em[BENC_THREADS];
+  __shared__ int s_i[BENC_CAP];
+  __shared__ unsigned char s_b[BENC_CAP];
+  __shared__ int s_n, s_cnt;
+  const int tid = threadIdx.x, i0 = blockIdx.x * BENC_THREADS, np = S.npad;
+  s_em[tid] = 0ULL;
+  if (tid == 0) { s_n = 0; s_cnt = 0; }
+  __syncthreads();
+  auto test = [&](int i, int b) {  // pair (i, system index b > i's): sets the bit in i's mask
+    const int j = S.sys_start[S.sys_of[i]] + b;
+    if (!S.alive[j]) return;
+    const double dmin = hermite_min_exact(
+        __dsub_rn(S.x0[j], S.x0[i]), __dsub_rn(S.x0[np + j], S.x0[np + i]), __dsub_rn(S.x0[2 * np + j], S.x0[2 * np + i]),
+        __dsub_rn(S.v0[j], S.v0[i]), __dsub_rn(S.v0[np + j], S.v0[np + i]), __dsub_rn(S.v0[2 * np + j], S.v0[2 * np + i]),
+        __dsub_rn(S.x[j], S.x[i]), __dsub_rn(S.x[np + j], S.x[np + i]), __dsub_rn(S.x[2 * np + j], S.x[2 * np + i]),
+        __dsub_rn(S.v[j], S.v[i]), __dsub_rn(S.v[np + j], S.v[np + i]), __dsub_rn(S.v[2 * np + j], S.v[2 * np + i]), tau);
+    const double rcij = pmax(S.rc[i], S.rc[j]);
+    if (dmin < __dmul_rn(rcij, rcij)) atomicOr(&s_em[i - i0], 1ULL << b);
+  };
+  const int i = i0 + tid;
+  if (i < np && S.alive[i]) {
+    const int li = i - S.sys_start[S.sys_of[i]];
     u64 bits = S.bmask[i] & (li >= 63 ? 0ULL : (~0ULL << (li + 1)));
-    const double x0i = S.x0[i], y0i = S.x0[np + i], z0i = S.x0[2 * np + i];
-    const double u0i = S.v0[i], v0i = S.v0[np + i], w0i = S.v0[2 * np + i];
-    const double x1i = S.x[i], y1i = S.x[np + i], z1i = S.x[2 * np + i];
-    const double u1i = S.v[i], v1i = S.v[np + i], w1i = S.v[2 * np + i];
     while (bits) {
       const int b = __ffsll((long long)bits) - 1;
       bits &= bits - 1;
-      const int j = st + b;
-      if (!S.alive[j]) continue;
-      const double dmin = hermite_min_exact(
-          __dsub_rn(S.x0[j], x0i), __dsub_rn(S.x0[np + j], y0i), __dsub_rn(S.x0[2 * np + j], z0i),
-          __dsub_rn(S.v0[j], u0i), __dsub_rn(S.v0[np + j], v0i), __dsub_rn(S.v0[2 * np + j], w0i),
-          __dsub_rn(S.x[j], x1i), __dsub_rn(S.x[np + j], y1i), __dsub_rn(S.x[2 * np + j], z1i),
-          __dsub_rn(S.v[j], u1i), __dsub_rn(S.v[np + j], v1i), __dsub_rn(S.v[2 * np + j], w1i), tau);
-      const double rcij = pmax(S.rc[i], S.rc[j]);
-      if (dmin < __dmul_rn(rcij, rcij)) em |= 1ULL << b;
+      const int p = atomicAdd(&s_n, 1);
+      if (p < BENC_CAP) { s_i[p] = i; s_b[p] = (unsigned char)b; }
+      else test(i, b);
     }
-    if (em) atomicAdd((unsigned long long *)&S.counters[C_ENC], (unsigned long long)__popcll(em));
   }
-  S.emask[i] = em;
+  __syncthreads();
+  const int n = s_n < BENC_CAP ? s_n : BENC_CAP;
+  for (int p = tid; p < n; p += BENC_THREADS) test(s_i[p], s_b[p]);
+  __syncthreads();
+  if (i < np) {
+    const u64 em = s_em[tid];
+    S.emask[i] = em;
+    if (em) atomicAdd(&s_cnt, __popcll(em));
+  }
+  __syncthreads();
+  if (tid == 0 && s_cnt) atomicAdd((unsigned long long *)&S.counters[C_ENC], (unsigned long long)s_cnt);
 }
 
 // Groups of one system per warp: union of encounter pairs by atomicMin on local links, then
@@ -411,7 +431,7 @@ void launch_b_drift(const Sim &S, const DevParams &P, double tau, double h1, dou
   k_b_drift<<<(S.npad + 127) / 128, 128, 0, st>>>(S, P, tau, h1, h2, first);
 }
 void launch_b_encounter(const Sim &S, double tau, cudaStream_t st) {
-  k_b_encounter<<<(S.npad + 127) / 128, 128, 0, st>>>(S, tau);
+  k_b_encounter<<<(S.npad + BENC_THREADS - 1) / BENC_THREADS, BENC_THREADS, 0, st>>>(S, tau);
 }
 void launch_b_group(const Sim &S, cudaStream_t st) {
   k_b_group<<<(S.nsys + BG_WARPS - 1) / BG_WARPS, 32 * BG_WARPS, 0, st>>>(S);
