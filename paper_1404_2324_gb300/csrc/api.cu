@@ -279,7 +279,7 @@ void enqueue_step(genga_ctx *c, cudaStream_t st) {
     }
     if (tp) {
       launch_tp_encounter(S, T, tau, c->tp_grid, st);
-      launch_tp_bs(S, T, P, tau, 3 * num_sms(), st);
+      launch_tp_bs(S, T, P, tau, num_sms(), st);
     }
     if (c->profiling) cudaEventRecordWithFlags(c->kev[2 * j], st, cudaEventRecordExternal);
     launch_kick(S, P, false, precise, st);

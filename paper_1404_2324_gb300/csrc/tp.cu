@@ -355,28 +355,45 @@ __device__ __forceinline__ void tp_force(const Sim &S, const TPSet &T, const Dev
 }
 
 // BS of one listed TP per warp; lane L-1 runs level L (n_L = 2L midpoint substeps) and lanes
-// 8..13 hold the tableau rows. Launched with 3 blocks per SM (the register budget of one block
-// allows three).
+// 8..13 hold the tableau rows. One block of TPB_WARPS warps per SM (the register budget allows
+// twelve warps per SM); warp w issues on sub-partition w % 4.
+//
+// Placement. The launch lasts as long as its slowest particle (one deep inside a planet's Hill
+// sphere takes 10-30 sequential attempts), and an FP64 warp instruction holds its sub-partition's
+// pipe whatever the other warps there do, so a particle sharing its sub-partition with two busy
+// warps advances at a third of its own rate. Warp 0 of block b < min(front entries, blocks) takes
+// front entry b (the front entries pass inside a tenth of the critical radius) and the other warps of its
+// sub-partition leave, so that particle has the pipe to itself; everything else is taken from a
+// shared counter, so long encounters do not hold up the rest.
 //
 // Speculation. After a failed full-length attempt the step control alternates a failed attempt at
 // 2H with an accepted one at H. From the second attempt on, lanes 16..29 mirror lanes 0..13 with
 // H/2 from the same state; their result is used exactly when the serial algorithm's next attempt
 // would be that one (the H attempt failed), so results and decisions are the serial algorithm's.
 // The mirror lanes cost no FP64 issue: a warp instruction costs the same whatever its active lanes.
-__global__ void __launch_bounds__(128, 3) k_tp_bs(Sim S, TPSet T, DevParams P, double tau) {
-  constexpr int WPOS = TP_PRE * TP_TAB * 3;
-  __shared__ double s_pos[4][2 * WPOS];
-  __shared__ double s_zt[4][2][16];  // per warp and half: a completed level's z_{n-1}, z_n, z'_n, h
-  const int lane = threadIdx.x & 31, half = lane >> 4, l16 = lane & 15;
-  double *wpos0 = s_pos[threadIdx.x >> 5];
+constexpr int TPB_WARPS = 12;
+constexpr int TPB_WPOS = TP_PRE * TP_TAB * 3;
+constexpr size_t TPB_SMEM = (size_t)TPB_WARPS * (2 * TPB_WPOS + 2 * 16) * sizeof(double);
+__global__ void __launch_bounds__(32 * TPB_WARPS, 1) k_tp_bs(Sim S, TPSet T, DevParams P, double tau) {
+  constexpr int WPOS = TPB_WPOS;
+  extern __shared__ double tpb_smem[];  // per warp: planet positions of both attempts, then s_zt
+  const int lane = threadIdx.x & 31, half = lane >> 4, l16 = lane & 15, warp = threadIdx.x >> 5;
+  double *wpos0 = tpb_smem + warp * 2 * WPOS;
+  double (*s_zt)[16] = reinterpret_cast<double (*)[16]>(tpb_smem + TPB_WARPS * 2 * WPOS + warp * 32);
   const int nfront = T.nbs[0], nlist = nfront + T.nbs[1];
   const int np = T.npad;
   const double i2tau = 2.0 / tau;
   if (blockIdx.x == 0 && threadIdx.x == 0) *T.npairs = 0u;  // consumed by the encounter test
-  for (;;) {  // each warp takes the next listed TP: long encounters do not hold up the rest
+  const int niso = nfront < (int)gridDim.x ? nfront : (int)gridDim.x;  // front entries placed alone
+  const bool iso = (int)blockIdx.x < niso;
+  if (iso && warp != 0 && (warp & 3) == 0) return;  // sub-partition 0 belongs to warp 0's entry
+  for (bool first = true;; first = false) {
     int w = 0;
-    if (lane == 0) w = (int)atomicAdd(T.bsnext, 1u);
-    w = __shfl_sync(0xffffffffu, w, 0);
+    if (iso && warp == 0 && first) w = blockIdx.x;
+    else {
+      if (lane == 0) w = niso + (int)atomicAdd(T.bsnext, 1u);
+      w = __shfl_sync(0xffffffffu, w, 0);
+    }
     if (w >= nlist) break;
     const int i = T.bslist[w < nfront ? w : T.npad - 1 - (w - nfront)];
     const unsigned em = T.emask[i];
@@ -448,7 +465,7 @@ __global__ void __launch_bounds__(128, 3) k_tp_bs(Sim S, TPSet T, DevParams P, d
         const int Lc = m >> 1;
         // level Lc's lane hands its last midpoint state to the tableau lanes, which form
         // T_{Lc,1} = (z_{n-1} + z_n + h z'_n) / 2 one component each
-        double *zt = s_zt[threadIdx.x >> 5][half];
+        double *zt = s_zt[half];
         if (l16 == Lc - 1) {
           for (int c = 0; c < 6; ++c) { zt[c] = za[c]; zt[6 + c] = zb[c]; }
           zt[12] = ax; zt[13] = ay; zt[14] = az; zt[15] = h;
@@ -602,6 +619,7 @@ int tp_init_constants() {
       const double ratio = (double)L / (double)(L - j);
       f[L][j] = 1.0 / (ratio * ratio - 1.0);
     }
+  if (cudaFuncSetAttribute(k_tp_bs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TPB_SMEM) != cudaSuccess) return -1;
   return cudaMemcpyToSymbol(c_tp_facinv, f, sizeof(f)) == cudaSuccess ? 0 : -1;
 }
 
@@ -633,7 +651,7 @@ void launch_tp_encounter(const Sim &S, const TPSet &T, double tau, int blocks, c
   k_tp_encounter<<<blocks, 256, 0, st>>>(S, T, tau);
 }
 void launch_tp_bs(const Sim &S, const TPSet &T, const DevParams &P, double tau, int blocks, cudaStream_t st) {
-  k_tp_bs<<<blocks, 128, 0, st>>>(S, T, P, tau);
+  k_tp_bs<<<blocks, 32 * TPB_WARPS, TPB_SMEM, st>>>(S, T, P, tau);
 }
 void launch_tp_hc(const Sim &S, const TPSet &T, double hcm, cudaStream_t st) {
   k_tp_hc<<<grid_of(T.n, 128), 128, 0, st>>>(S, T, hcm);
