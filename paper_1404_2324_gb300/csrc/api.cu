@@ -427,7 +427,7 @@ int genga_init_tp(genga_ctx **out, int n, const double *masses, const double *ra
   T.bslist = mem.get<int>(np); T.nbs = mem.get<int>(2); T.bsnext = mem.get<unsigned>(1);
   T.pairs = mem.get<unsigned>(np * (size_t)(n - 1)); T.npairs = mem.get<unsigned>(1);
   T.ptab = mem.get<double>(TP_MAXPL * TP_TAB * 6);
-  T.pcheb = mem.get<double>(TP_MAXPL * 6 * TP_CHEB); T.pcok = mem.get<int>(TP_MAXPL);
+  T.ppoly = mem.get<double>(TP_MAXPL * 6 * TP_CHEB); T.pcok = mem.get<int>(TP_MAXPL);
   T.counters = mem.get<long long>(8);
   c->stx = mem.get<double>(3 * (size_t)n_tp); c->stv = mem.get<double>(3 * (size_t)n_tp);
   c->stalive = mem.get<int>(n_tp);

@@ -104,7 +104,7 @@ struct TPSet {
   unsigned *bsnext;              // next list entry a BS warp takes
   unsigned *pairs, *npairs;      // candidate (TP, planet) pairs of the last closing kick: i * 32 + j
   double *ptab;                  // planets' Kepler paths at the BS midpoint times [TP_MAXPL * TP_TAB * 6]
-  double *pcheb;                 // Chebyshev series of the planets' paths over the substep [TP_MAXPL * 6 * TP_CHEB]
+  double *ppoly;                 // planets' paths over the substep, polynomials in s = 2t/tau - 1 [TP_MAXPL * 6 * TP_CHEB]
   int *pcok;                     // 1: planet j's series is exact to rounding; 0: solve Kepler instead
   long long *counters;           // candidates, encounters, BS steps, removed
 };

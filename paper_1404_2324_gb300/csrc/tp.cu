@@ -185,9 +185,15 @@ __global__ void k_tp_drift(Sim S, TPSet T, DevParams P, double tau, double hcm1,
 //    Kepler solve only when its last two coefficients are below 2^-60 of |x| (resp. |v|): the
 //    coefficients of a smooth path fall geometrically, so the truncation error is then far below
 //    one rounding of the position. Otherwise pcok = 0 and those times solve Kepler's equation.
+//    The same polynomial is stored in powers of s (Horner takes one FMA a term, Clenshaw two);
+//    pcok also asks that the power coefficients' magnitudes sum to at most 2|x| (2|v|), which
+//    bounds Horner's rounding error by that of a few roundings of the position.
+__constant__ double c_cheb_pow[TP_CHEB][TP_CHEB];  // [k][q]: coefficient of s^q in T_k(s)
+
 __global__ void __launch_bounds__(128) k_planet_table(Sim S, TPSet T, DevParams P, double tau) {
   __shared__ double node[TP_CHEB][6];
   __shared__ double coef[6][TP_CHEB];
+  __shared__ double mono[6][TP_CHEB];
   const int j = blockIdx.x, e = threadIdx.x;
   const int np = S.npad;
   const double x0 = S.x0[j], y0 = S.x0[np + j], z0 = S.x0[2 * np + j];
@@ -218,7 +224,14 @@ __global__ void __launch_bounds__(128) k_planet_table(Sim S, TPSet T, DevParams 
       acc = fma(node[q][c], cospi((double)(k * (2 * q + 1)) / (double)(2 * TP_CHEB)), acc);
     acc *= 2.0 / TP_CHEB;
     coef[c][k] = acc;
-    T.pcheb[((size_t)j * 6 + c) * TP_CHEB + k] = acc;
+  }
+  __syncthreads();
+  if (e < 6 * TP_CHEB) {  // c_0 / 2 + sum_k c_k T_k(s) in powers of s, the small terms summed first
+    const int c = e / TP_CHEB, q = e % TP_CHEB;
+    double a = 0.0;
+    for (int k = TP_CHEB - 1; k >= q; --k) a = fma(k == 0 ? 0.5 * coef[c][0] : coef[c][k], c_cheb_pow[k][q], a);
+    mono[c][q] = a;
+    T.ppoly[((size_t)j * 6 + c) * TP_CHEB + q] = a;
   }
   __syncthreads();
   if (e == 0) {
@@ -227,7 +240,10 @@ __global__ void __launch_bounds__(128) k_planet_table(Sim S, TPSet T, DevParams 
     bool ok = true;
     for (int c = 0; c < 6; ++c) {
       const double tail = fabs(coef[c][TP_CHEB - 1]) + fabs(coef[c][TP_CHEB - 2]);
-      if (!(tail <= lim * (c < 3 ? r : v))) ok = false;  // NaN (failed node) is not ok
+      double sum = 0.0;
+      for (int q = 0; q < TP_CHEB; ++q) sum += fabs(mono[c][q]);
+      const double scale = c < 3 ? r : v;
+      if (!(tail <= lim * scale) || !(sum <= 2.0 * scale)) ok = false;  // NaN (failed node) is not ok
     }
     T.pcok[j] = ok;
   }
@@ -264,19 +280,19 @@ __global__ void __launch_bounds__(256) k_tp_encounter(Sim S, TPSet T, double tau
   }
 }
 
-// Chebyshev series of planet j (components c0 .. c0 + 2) at s in [-1, 1] (Clenshaw).
-__device__ __forceinline__ void cheb3(const double *cf, double s, double &a, double &b, double &c) {
-  const double s2 = 2.0 * s;
-  double a1 = 0.0, a2 = 0.0, b1 = 0.0, b2 = 0.0, c1 = 0.0, c2 = 0.0;
+// A planet's path polynomial (components c0 .. c0 + 2, powers of s) at s in [-1, 1] (Horner).
+__device__ __forceinline__ void poly3(const double *cf, double s, double &a, double &b, double &c) {
+  a = cf[TP_CHEB - 1]; b = cf[2 * TP_CHEB - 1]; c = cf[3 * TP_CHEB - 1];
 #pragma unroll
-  for (int k = TP_CHEB - 1; k >= 1; --k) {
-    const double an = fma(s2, a1, cf[k] - a2), bn = fma(s2, b1, cf[TP_CHEB + k] - b2),
-                 cn = fma(s2, c1, cf[2 * TP_CHEB + k] - c2);
-    a2 = a1; a1 = an; b2 = b1; b1 = bn; c2 = c1; c1 = cn;
+  for (int k = TP_CHEB - 2; k >= 0; --k) {
+    a = fma(a, s, cf[k]); b = fma(b, s, cf[TP_CHEB + k]); c = fma(c, s, cf[2 * TP_CHEB + k]);
   }
-  a = fma(s, a1, fma(0.5, cf[0], -a2));
-  b = fma(s, b1, fma(0.5, cf[TP_CHEB], -b2));
-  c = fma(s, c1, fma(0.5, cf[2 * TP_CHEB], -c2));
+}
+__device__ __forceinline__ double poly1(const double *cf, double s) {
+  double a = cf[TP_CHEB - 1];
+#pragma unroll
+  for (int k = TP_CHEB - 2; k >= 0; --k) a = fma(a, s, cf[k]);
+  return a;
 }
 
 // Planet j's state on its Kepler path at time t of the substep: the table for full-length
@@ -289,7 +305,7 @@ __device__ __forceinline__ void planet_at(const Sim &S, const TPSet &T, const De
     return;
   }
   if (T.pcok[j]) {
-    cheb3(T.pcheb + (size_t)j * 6 * TP_CHEB, fma(t, i2tau, -1.0), px, py, pz);
+    poly3(T.ppoly + (size_t)j * 6 * TP_CHEB, fma(t, i2tau, -1.0), px, py, pz);
     return;
   }
   const int pp = S.npad;
@@ -304,9 +320,9 @@ __device__ __forceinline__ void planet_state_at(const Sim &S, const TPSet &T, co
                                                 double i2tau, double *o) {
   if (T.pcok[j]) {
     const double s = fma(t, i2tau, -1.0);
-    const double *cf = T.pcheb + (size_t)j * 6 * TP_CHEB;
-    cheb3(cf, s, o[0], o[1], o[2]);
-    cheb3(cf + 3 * TP_CHEB, s, o[3], o[4], o[5]);
+    const double *cf = T.ppoly + (size_t)j * 6 * TP_CHEB;
+    poly3(cf, s, o[0], o[1], o[2]);
+    poly3(cf + 3 * TP_CHEB, s, o[3], o[4], o[5]);
     return;
   }
   const int pp = S.npad;
@@ -422,7 +438,7 @@ __global__ void __launch_bounds__(32 * TPB_WARPS, 1) k_tp_bs(Sim S, TPSet T, Dev
             int k = 1;
             while (tab_index(k + 1, 0) <= e) k++;
             const int m = e - tab_index(k, 0);
-            const double hk = __ddiv_rn(He, (double)(2 * k));
+            const double hk = __shfl_sync(0xffffffffu, h, hf * 16 + k - 1);  // He / 2k: level k's lane of half hf
             const double t = (m == 2 * k) ? t0 + He : t0 + m * hk;
             double *q = wpos0 + hf * WPOS + (p * TP_TAB + e) * 3;
             planet_at(S, T, P, j, false, k, m, t, i2tau, q[0], q[1], q[2]);
@@ -515,8 +531,18 @@ __global__ void __launch_bounds__(32 * TPB_WARPS, 1) k_tp_bs(Sim S, TPSet T, Dev
           const int j = __ffs(bits) - 1;
           bits &= bits - 1;
           double pa[6], pb[6];
-          planet_state_at(S, T, P, j, t0, i2tau, pa);
-          planet_state_at(S, T, P, j, t0 + H, i2tau, pb);
+          if (T.pcok[j]) {  // lane q < 12 evaluates component q % 6 at t0 (q < 6) or t0 + H
+            double pv = 0.0;
+            if (lane < 12)
+              pv = poly1(T.ppoly + ((size_t)j * 6 + lane % 6) * TP_CHEB, fma(lane < 6 ? t0 : t0 + H, i2tau, -1.0));
+            for (int c = 0; c < 6; ++c) {
+              pa[c] = __shfl_sync(0xffffffffu, pv, c);
+              pb[c] = __shfl_sync(0xffffffffu, pv, 6 + c);
+            }
+          } else {
+            planet_state_at(S, T, P, j, t0, i2tau, pa);
+            planet_state_at(S, T, P, j, t0 + H, i2tau, pb);
+          }
           const double dmin = hermite_min_exact(
               __dsub_rn(pa[0], y[0]), __dsub_rn(pa[1], y[1]), __dsub_rn(pa[2], y[2]),
               __dsub_rn(pa[3], y[3]), __dsub_rn(pa[4], y[4]), __dsub_rn(pa[5], y[5]),
@@ -620,6 +646,12 @@ int tp_init_constants() {
       f[L][j] = 1.0 / (ratio * ratio - 1.0);
     }
   if (cudaFuncSetAttribute(k_tp_bs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TPB_SMEM) != cudaSuccess) return -1;
+  double tk[TP_CHEB][TP_CHEB] = {};  // T_0 = 1, T_1 = s, T_{k+1} = 2 s T_k - T_{k-1} (integers)
+  tk[0][0] = 1.0;
+  tk[1][1] = 1.0;
+  for (int k = 1; k + 1 < TP_CHEB; ++k)
+    for (int q = 0; q < TP_CHEB; ++q) tk[k + 1][q] = (q > 0 ? 2.0 * tk[k][q - 1] : 0.0) - tk[k - 1][q];
+  if (cudaMemcpyToSymbol(c_cheb_pow, tk, sizeof(tk)) != cudaSuccess) return -1;
   return cudaMemcpyToSymbol(c_tp_facinv, f, sizeof(f)) == cudaSuccess ? 0 : -1;
 }
 
