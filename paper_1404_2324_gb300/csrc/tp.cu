@@ -181,13 +181,16 @@ __global__ void k_tp_drift(Sim S, TPSet T, DevParams P, double tau, double hcm1,
 //  * the Kepler solution at every midpoint time of a full-length attempt (t = m tau/2k, and t = tau
 //    at m = 2k), also the drift result itself;
 //  * a Chebyshev series in s = 2t/tau - 1 of position and velocity through TP_CHEB Kepler solutions
-//    at the Chebyshev nodes, used for the times of shorter attempts. The series stands in for the
-//    Kepler solve only when its last two coefficients are below 2^-60 of |x| (resp. |v|): the
-//    coefficients of a smooth path fall geometrically, so the truncation error is then far below
-//    one rounding of the position. Otherwise pcok = 0 and those times solve Kepler's equation.
-//    The same polynomial is stored in powers of s (Horner takes one FMA a term, Clenshaw two);
-//    pcok also asks that the power coefficients' magnitudes sum to at most 2|x| (2|v|), which
-//    bounds Horner's rounding error by that of a few roundings of the position.
+//    at the Chebyshev nodes, used for the times of shorter attempts. Computed coefficients carry
+//    rounding noise of about 1e-16 |x| (16-term sums of values of size |x|), so no coefficient can
+//    be told from zero below that floor. The series stands in for the Kepler solve (pcok = 1) when
+//    coefficients 12 and 13 are within 2^-49 of |x| (resp. |v|) and the last two within 2^-48:
+//    a smooth path's coefficients fall geometrically, so the truncated ones are then far below a
+//    rounding, and the series reproduces the Kepler solutions to the nodes' own rounding (a few
+//    1e-15 of |x|). Otherwise those times solve Kepler's equation. The polynomial is stored in
+//    powers of s (Horner takes one FMA a term, Clenshaw two); pcok also asks that the power
+//    coefficients' magnitudes sum to at most 2|x| (2|v|), which bounds Horner's rounding error
+//    by a few roundings of the position.
 __constant__ double c_cheb_pow[TP_CHEB][TP_CHEB];  // [k][q]: coefficient of s^q in T_k(s)
 
 __global__ void __launch_bounds__(128) k_planet_table(Sim S, TPSet T, DevParams P, double tau) {
@@ -236,14 +239,16 @@ __global__ void __launch_bounds__(128) k_planet_table(Sim S, TPSet T, DevParams 
   __syncthreads();
   if (e == 0) {
     const double r = sqrt(fma(z0, z0, fma(y0, y0, x0 * x0))), v = sqrt(fma(w0, w0, fma(v0, v0, u0 * u0)));
-    const double lim = 8.673617379884035e-19;  // 2^-60
+    const double lim = 1.7763568394002505e-15;  // 2^-49
     bool ok = true;
     for (int c = 0; c < 6; ++c) {
+      const double decay = pmax(fabs(coef[c][TP_CHEB - 4]), fabs(coef[c][TP_CHEB - 3]));
       const double tail = fabs(coef[c][TP_CHEB - 1]) + fabs(coef[c][TP_CHEB - 2]);
       double sum = 0.0;
       for (int q = 0; q < TP_CHEB; ++q) sum += fabs(mono[c][q]);
       const double scale = c < 3 ? r : v;
-      if (!(tail <= lim * scale) || !(sum <= 2.0 * scale)) ok = false;  // NaN (failed node) is not ok
+      // NaN (a failed node) fails every comparison
+      if (!(decay <= lim * scale) || !(tail <= 2.0 * lim * scale) || !(sum <= 2.0 * scale)) ok = false;
     }
     T.pcok[j] = ok;
   }
