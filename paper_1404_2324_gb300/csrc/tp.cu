@@ -12,6 +12,8 @@
 // planet's path (or solve Kepler's equation where the series is not exact to rounding) and attempt
 // H/2 on lanes 16..29 beside H. Particles in the deepest encounters are integrated first. A TP
 // whose BS substep reaches a planet's surface is removed.
+#include <cstring>
+
 #include "genga_launch.h"
 
 namespace genga {
@@ -392,6 +394,19 @@ __device__ __forceinline__ void tp_force(const Sim &S, const TPSet &T, const Dev
 // H/2 from the same state; their result is used exactly when the serial algorithm's next attempt
 // would be that one (the H attempt failed), so results and decisions are the serial algorithm's.
 // The mirror lanes cost no FP64 issue: a warp instruction costs the same whatever its active lanes.
+// Distinct midpoint times of a shorter attempt pair. Entry (hf, k, m) of half hf (attempt length
+// He = H / 2^hf) is at t0 + m h_k with h_k = He / 2k rounded, or t0 + He at m = 2k. Write 2k = o 2^e
+// and m = mo 2^a (o, mo odd): h_k is round(H / o) 2^-(e + hf) exactly (a division by a power of
+// two only moves the exponent), so m h_k = round(mo round(H / o)) 2^(a - e - hf) depends on
+// (o, mo, a - e - hf) alone, and entries with equal keys have bit-identical times: the 160 entries
+// of the two attempts fall into 76 classes. The host builds the classes (and checks them on its
+// own arithmetic); each class is evaluated once and written to all its slots.
+constexpr int TP_PREP_MAX = 96;
+__device__ int d_prep_n;
+__device__ unsigned short d_prep_rep[TP_PREP_MAX];     // a member: hf << 12 | k << 8 | m
+__device__ unsigned char d_prep_first[TP_PREP_MAX + 1];  // class u owns slots [first[u], first[u + 1])
+__device__ unsigned char d_prep_slot[2 * TP_TAB];        // hf * TP_TAB + tab_index(k, m)
+
 constexpr int TPB_WARPS = 12;
 constexpr int TPB_WPOS = TP_PRE * TP_TAB * 3;
 constexpr size_t TPB_SMEM = (size_t)TPB_WARPS * (2 * TPB_WPOS + 2 * 16) * sizeof(double);
@@ -401,7 +416,7 @@ __global__ void __launch_bounds__(32 * TPB_WARPS, 1) k_tp_bs(Sim S, TPSet T, Dev
   const int lane = threadIdx.x & 31, half = lane >> 4, l16 = lane & 15, warp = threadIdx.x >> 5;
   double *wpos0 = tpb_smem + warp * 2 * WPOS;
   double (*s_zt)[16] = reinterpret_cast<double (*)[16]>(tpb_smem + TPB_WARPS * 2 * WPOS + warp * 32);
-  const int nfront = T.nbs[0], nlist = nfront + T.nbs[1];
+  const int nfront = T.nbs[0], nlist = nfront + T.nbs[1], nprep = d_prep_n;
   const int np = T.npad;
   const double i2tau = 2.0 / tau;
   if (blockIdx.x == 0 && threadIdx.x == 0) *T.npairs = 0u;  // consumed by the encounter test
@@ -437,16 +452,22 @@ __global__ void __launch_bounds__(32 * TPB_WARPS, 1) k_tp_bs(Sim S, TPSet T, Dev
         for (int p = 0; p < TP_PRE && bits; ++p) {
           const int j = __ffs(bits) - 1;
           bits &= bits - 1;
-          for (int e2 = lane; e2 < 2 * TP_TAB; e2 += 32) {
-            const int hf = e2 >= TP_TAB ? 1 : 0, e = e2 - hf * TP_TAB;
-            const double He = hf ? 0.5 * H : H;
-            int k = 1;
-            while (tab_index(k + 1, 0) <= e) k++;
-            const int m = e - tab_index(k, 0);
+          for (int u0 = 0; u0 < nprep; u0 += 32) {  // one time class per lane
+            const int u = u0 + lane;
+            const unsigned rp = d_prep_rep[u < nprep ? u : 0];
+            const int hf = rp >> 12, k = (rp >> 8) & 15, m = rp & 255;
             const double hk = __shfl_sync(0xffffffffu, h, hf * 16 + k - 1);  // He / 2k: level k's lane of half hf
-            const double t = (m == 2 * k) ? t0 + He : t0 + m * hk;
-            double *q = wpos0 + hf * WPOS + (p * TP_TAB + e) * 3;
-            planet_at(S, T, P, j, false, k, m, t, i2tau, q[0], q[1], q[2]);
+            if (u < nprep) {
+              const double He = hf ? 0.5 * H : H;
+              const double t = (m == 2 * k) ? t0 + He : t0 + m * hk;
+              double px, py, pz;
+              planet_at(S, T, P, j, false, k, m, t, i2tau, px, py, pz);
+              for (int q = d_prep_first[u]; q < d_prep_first[u + 1]; ++q) {
+                const int sl = d_prep_slot[q], sh = sl >= TP_TAB ? 1 : 0;
+                double *o = wpos0 + sh * WPOS + (p * TP_TAB + sl - sh * TP_TAB) * 3;
+                o[0] = px; o[1] = py; o[2] = pz;
+              }
+            }
           }
         }
         __syncwarp();
@@ -643,7 +664,70 @@ __global__ void k_tp_to_helio(Sim S, TPSet T, DevParams P, double *xh, double *v
 // ---------------------------------------------------------------------------------------------
 static int grid_of(int n, int b) { return (n + b - 1) / b; }
 
+// Classes of bit-identical midpoint times (see d_prep_rep), checked by evaluating every member's
+// time for several attempt lengths and start times: a class whose members differ is an error.
+static int build_prep_classes() {
+  struct Key { int o, mo, ex; };
+  Key keys[2 * TP_TAB];
+  int cls[2 * TP_TAB], nu = 0;
+  unsigned short rep[TP_PREP_MAX];
+  for (int hf = 0; hf < 2; ++hf)
+    for (int k = 1; k <= BS_LEVELS; ++k)
+      for (int m = 0; m <= 2 * k; ++m) {
+        Key key{0, 0, 0};  // m = 0: t0
+        if (m == 2 * k) key = Key{1, 1, -hf};  // t0 + He
+        else if (m > 0) {
+          int o = 2 * k, e = 0, mo = m, a = 0;
+          while (o % 2 == 0) { o /= 2; ++e; }
+          while (mo % 2 == 0) { mo /= 2; ++a; }
+          key = Key{o, mo, a - e - hf};
+        }
+        const int sl = hf * TP_TAB + k * k - 1 + m;
+        int c = 0;
+        while (c < nu && !(keys[c].o == key.o && keys[c].mo == key.mo && keys[c].ex == key.ex)) ++c;
+        if (c == nu) {
+          if (nu == TP_PREP_MAX) return -1;
+          keys[nu] = key;
+          rep[nu] = (unsigned short)(hf << 12 | k << 8 | m);
+          ++nu;
+        }
+        cls[sl] = c;
+      }
+  unsigned char first[TP_PREP_MAX + 1], slot[2 * TP_TAB];
+  int n = 0;
+  for (int c = 0; c < nu; ++c) {
+    first[c] = (unsigned char)n;
+    for (int sl = 0; sl < 2 * TP_TAB; ++sl)
+      if (cls[sl] == c) slot[n++] = (unsigned char)sl;
+  }
+  first[nu] = (unsigned char)n;
+  const double Hs[] = {6.0, 3.0, 0.75, 2.2206093, -6.0, -1.7320508075688772, 4.1e-3};
+  const double t0s[] = {0.0, 1.5, 2.9137, -3.3};
+  for (double H : Hs)
+    for (double t0 : t0s)
+      for (int c = 0; c < nu; ++c) {
+        double tc = 0.0;
+        for (int q = first[c]; q < first[c + 1]; ++q) {
+          const int sl = slot[q], hf = sl >= TP_TAB ? 1 : 0, e = sl - hf * TP_TAB;
+          int k = 1;
+          while ((k + 1) * (k + 1) - 1 <= e) ++k;
+          const int m = e - (k * k - 1);
+          const double He = hf ? 0.5 * H : H, hk = He / (double)(2 * k);
+          const double t = (m == 2 * k) ? t0 + He : t0 + m * hk;
+          if (q == first[c]) tc = t;
+          else if (memcmp(&t, &tc, sizeof(double)) != 0) return -1;
+        }
+      }
+  if (cudaMemcpyToSymbol(d_prep_n, &nu, sizeof(int)) != cudaSuccess ||
+      cudaMemcpyToSymbol(d_prep_rep, rep, sizeof(rep)) != cudaSuccess ||
+      cudaMemcpyToSymbol(d_prep_first, first, sizeof(first)) != cudaSuccess ||
+      cudaMemcpyToSymbol(d_prep_slot, slot, sizeof(slot)) != cudaSuccess)
+    return -1;
+  return 0;
+}
+
 int tp_init_constants() {
+  if (build_prep_classes() != 0) return -1;
   double f[BS_LEVELS + 1][BS_LEVELS] = {};
   for (int L = 2; L <= BS_LEVELS; ++L)
     for (int j = 1; j < L; ++j) {
