@@ -390,8 +390,8 @@ __device__ __forceinline__ void tp_force(const Sim &S, const TPSet &T, const Dev
 // shared counter, so long encounters do not hold up the rest.
 //
 // Speculation. After a failed full-length attempt the step control alternates a failed attempt at
-// 2H with an accepted one at H. From the second attempt on, lanes 16..29 mirror lanes 0..13 with
-// H/2 from the same state; their result is used exactly when the serial algorithm's next attempt
+// 2H with an accepted one at H. From the second attempt on (from the first for a front entry, whose
+// full-length attempt fails), lanes 16..29 mirror lanes 0..13 with H/2 from the same state; their result is used exactly when the serial algorithm's next attempt
 // would be that one (the H attempt failed), so results and decisions are the serial algorithm's.
 // The mirror lanes cost no FP64 issue: a warp instruction costs the same whatever its active lanes.
 // Distinct midpoint times of a shorter attempt pair. Entry (hf, k, m) of half hf (attempt length
@@ -442,11 +442,14 @@ __global__ void __launch_bounds__(32 * TPB_WARPS, 1) k_tp_bs(Sim S, TPSet T, Dev
     while (absbits(rem) != 0ULL && ++attempts < 100000) {
       if (absbits(H) > absbits(rem)) H = rem;
       const bool table = dbits(t0) == 0ULL && dbits(H) == dbits(tau);
-      const bool spec = !table;  // the mirror lanes attempt H/2
+      // the mirror lanes attempt H/2; on the full-length attempt only for a front entry, which
+      // fails it (a pass inside a tenth of rc needs shorter substeps)
+      const bool spec = !table || w < nfront;
+      const bool use_tab = table && !(spec && half);  // this lane's positions come from the table
       const double Hl = (spec && half) ? 0.5 * H : H;  // this lane's attempt length
       const double h = __ddiv_rn(Hl, (double)nk), h2 = 2.0 * h;
       double *wpos = wpos0 + (spec ? half * WPOS : 0);
-      if (!table && em) {  // positions of the first TP_PRE planets at all midpoint times of both attempts
+      if (spec && em) {  // positions of the first TP_PRE planets at all midpoint times of both attempts
         __syncwarp();
         unsigned bits = em;
         for (int p = 0; p < TP_PRE && bits; ++p) {
@@ -474,7 +477,7 @@ __global__ void __launch_bounds__(32 * TPB_WARPS, 1) k_tp_bs(Sim S, TPSet T, Dev
       }
       double za[6], zb[6], ax, ay, az;
       for (int c = 0; c < 6; ++c) za[c] = y[c];
-      tp_force(S, T, P, i, em, table, L, 0, t0, h, Hl, i2tau, wpos, y, ax, ay, az);
+      tp_force(S, T, P, i, em, use_tab, L, 0, t0, h, Hl, i2tau, wpos, y, ax, ay, az);
       zb[0] = fma(h, y[3], y[0]); zb[1] = fma(h, y[4], y[1]); zb[2] = fma(h, y[5], y[2]);
       zb[3] = fma(h, ax, y[3]); zb[4] = fma(h, ay, y[4]); zb[5] = fma(h, az, y[5]);
       // Level L (lane L - 1 of each half) finishes at evaluation 2L; the half's lanes 8..13 then
@@ -495,7 +498,7 @@ __global__ void __launch_bounds__(32 * TPB_WARPS, 1) k_tp_bs(Sim S, TPSet T, Dev
       int acc = 0, accB = 0;
       for (int m = 1; m <= 2 * lmax; ++m) {
         if (m <= nk) {
-          tp_force(S, T, P, i, em, table, L, m, t0, h, Hl, i2tau, wpos, zb, ax, ay, az);
+          tp_force(S, T, P, i, em, use_tab, L, m, t0, h, Hl, i2tau, wpos, zb, ax, ay, az);
           if (m < nk) {
             double zn[6];
             zn[0] = fma(h2, zb[3], za[0]); zn[1] = fma(h2, zb[4], za[1]); zn[2] = fma(h2, zb[5], za[2]);
