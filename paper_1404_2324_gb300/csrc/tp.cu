@@ -343,37 +343,57 @@ constexpr int TP_PRE = 2;  // encountered planets whose positions a BS attempt e
 
 __constant__ double c_tp_facinv[BS_LEVELS + 1][BS_LEVELS];  // 1 / ((L / (L - j))^2 - 1)
 
-// Acceleration of the TP at y (central + (1 - W_B) pull of the encountered planets) at midpoint m of
-// level k: planet positions from the table (full-length attempt), from the warp's precomputed
-// positions (first TP_PRE planets of a shorter attempt) or evaluated here.
+// Acceleration of a TP at state y (level k, midpoint m of an attempt of length H from t0): the
+// Sun, and each encountered planet weighted by 1 - W_B inside the pair's critical radius. Lanes
+// pair up: level lane l (l16 < 8) evaluates the Sun's pull at its own state while lane l + 8
+// evaluates the first planet's at the same state (passed over) with the same instructions, and
+// hands back g and the separation; further planets follow on the upper lane. The level lane
+// accumulates Sun, planet 1, planet 2, ... exactly as a serial evaluation would. `act` holds the
+// participating lanes (whole pairs); planet positions come from the prepared list (wpos) for the
+// first TP_PRE planets of a shorter attempt, otherwise from the table or the path polynomial.
 __device__ __forceinline__ void tp_force(const Sim &S, const TPSet &T, const DevParams &P, int i, unsigned em, bool table,
                                          int k, int m, double t0, double h, double H, double i2tau, const double *wpos,
-                                         const double *y, double &ax, double &ay, double &az) {
-  const double r2 = fma(y[2], y[2], fma(y[1], y[1], y[0] * y[0]));
-  const double f = -P.Gm0 * rcube_refined(r2);
-  ax = f * y[0]; ay = f * y[1]; az = f * y[2];
+                                         const double *y, double &ax, double &ay, double &az, unsigned act) {
+  const int lane = threadIdx.x & 31;
+  const bool up = (lane & 8) != 0;
+  const double sx = __shfl_sync(act, y[0], lane & ~8), sy = __shfl_sync(act, y[1], lane & ~8),
+               sz = __shfl_sync(act, y[2], lane & ~8);
   unsigned bits = em;
-  int p = 0;
-  while (bits) {
-    const int j = __ffs(bits) - 1;
-    bits &= bits - 1;
-    double px, py, pz;
-    if (!table && p < TP_PRE) {
-      const double *q = wpos + (p * TP_TAB + tab_index(k, m)) * 3;
-      px = q[0]; py = q[1]; pz = q[2];
-    } else {
-      const double t = (m == 2 * k) ? t0 + H : t0 + m * h;
-      planet_at(S, T, P, j, table, k, m, t, i2tau, px, py, pz);
+  for (int p = 0;; ++p) {
+    // this lane's body: the Sun (level lane, first round) or planet p (upper lane)
+    double bx = 0.0, by = 0.0, bz = 0.0, gm = P.Gm0, A = 0.0;
+    u64 cut = ~0ULL;
+    const bool body = up && bits;
+    if (body) {
+      const int j = __ffs(bits) - 1;
+      if (!table && p < TP_PRE) {
+        const double *q = wpos + (p * TP_TAB + tab_index(k, m)) * 3;
+        bx = q[0]; by = q[1]; bz = q[2];
+      } else {
+        const double t = (m == 2 * k) ? t0 + H : t0 + m * h;
+        planet_at(S, T, P, j, table, k, m, t, i2tau, bx, by, bz);
+      }
+      gm = S.gm[j];
+      A = pmin(T.A[i], S.A[j]);
+      cut = umax64(T.rcsq[i], S.rcsq[j]);
     }
-    ++p;
-    const double dx = px - y[0], dy = py - y[1], dz = pz - y[2];
-    const double pr2 = fma(dz, dz, fma(dy, dy, dx * dx));
-    if (dbits(pr2) >= umax64(T.rcsq[i], S.rcsq[j])) continue;
-    const double yr = rsqrt_refined(pr2);
-    double wB, wA;
-    changeover_w(pr2 * yr, pmin(T.A[i], S.A[j]), P.kmode, wB, wA);
-    const double g = S.gm[j] * wA * (yr * yr * yr);
-    ax = fma(g, dx, ax); ay = fma(g, dy, ay); az = fma(g, dz, az);
+    double g = 0.0, dx = 0.0, dy = 0.0, dz = 0.0;
+    if (body || (!up && p == 0)) {
+      dx = bx - sx; dy = by - sy; dz = bz - sz;
+      const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+      const double yr = rsqrt_refined(r2);
+      const double r3 = up ? yr * yr * yr : rcube_refined(r2);
+      double wB, wA;
+      changeover_w(r2 * yr, A, P.kmode, wB, wA);  // 1 for the Sun (A = 0)
+      g = dbits(r2) >= cut ? 0.0 : gm * wA * r3;
+    }
+    if (p == 0 && !up) { ax = g * dx; ay = g * dy; az = g * dz; }  // the Sun: -G m0 y / |y|^3
+    const double gp = __shfl_xor_sync(act, g, 8), px = __shfl_xor_sync(act, dx, 8),
+                 py = __shfl_xor_sync(act, dy, 8), pz = __shfl_xor_sync(act, dz, 8);
+    if (!bits) break;
+    if (!up) { ax = fma(gp, px, ax); ay = fma(gp, py, ay); az = fma(gp, pz, az); }
+    bits &= bits - 1;
+    if (!bits) break;
   }
 }
 
@@ -433,7 +453,8 @@ __global__ void __launch_bounds__(32 * TPB_WARPS, 1) k_tp_bs(Sim S, TPSet T, Dev
     if (w >= nlist) break;
     const int i = T.bslist[w < nfront ? w : T.npad - 1 - (w - nfront)];
     const unsigned em = T.emask[i];
-    const int L = l16 < BS_LEVELS ? l16 + 1 : 1, nk = 2 * L;
+    static_assert(BS_LEVELS == 8, "lanes l16 and l16 + 8 pair up on level (l16 & 7) + 1");
+    const int L = (l16 & 7) + 1, nk = 2 * L;
     double y[6];
     for (int c = 0; c < 3; ++c) { y[c] = T.x0[c * np + i]; y[3 + c] = T.v0[c * np + i]; }
     double t0 = 0.0, rem = tau, H = tau;
@@ -477,7 +498,7 @@ __global__ void __launch_bounds__(32 * TPB_WARPS, 1) k_tp_bs(Sim S, TPSet T, Dev
       }
       double za[6], zb[6], ax, ay, az;
       for (int c = 0; c < 6; ++c) za[c] = y[c];
-      tp_force(S, T, P, i, em, use_tab, L, 0, t0, h, Hl, i2tau, wpos, y, ax, ay, az);
+      tp_force(S, T, P, i, em, use_tab, L, 0, t0, h, Hl, i2tau, wpos, y, ax, ay, az, 0xffffffffu);
       zb[0] = fma(h, y[3], y[0]); zb[1] = fma(h, y[4], y[1]); zb[2] = fma(h, y[5], y[2]);
       zb[3] = fma(h, ax, y[3]); zb[4] = fma(h, ay, y[4]); zb[5] = fma(h, az, y[5]);
       // Level L (lane L - 1 of each half) finishes at evaluation 2L; the half's lanes 8..13 then
@@ -497,8 +518,9 @@ __global__ void __launch_bounds__(32 * TPB_WARPS, 1) k_tp_bs(Sim S, TPSet T, Dev
       double tfix = 0.0;                    // the mirror half's accepted value (its tableau lanes)
       int acc = 0, accB = 0;
       for (int m = 1; m <= 2 * lmax; ++m) {
+        const unsigned act = __ballot_sync(0xffffffffu, m <= nk);
         if (m <= nk) {
-          tp_force(S, T, P, i, em, use_tab, L, m, t0, h, Hl, i2tau, wpos, zb, ax, ay, az);
+          tp_force(S, T, P, i, em, use_tab, L, m, t0, h, Hl, i2tau, wpos, zb, ax, ay, az, act);
           if (m < nk) {
             double zn[6];
             zn[0] = fma(h2, zb[3], za[0]); zn[1] = fma(h2, zb[4], za[1]); zn[2] = fma(h2, zb[5], za[2]);
