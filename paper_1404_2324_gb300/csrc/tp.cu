@@ -12,6 +12,7 @@
 // planet's path (or solve Kepler's equation where the series is not exact to rounding) and attempt
 // H/2 on lanes 16..29 beside H. Particles in the deepest encounters are integrated first. A TP
 // whose BS substep reaches a planet's surface is removed.
+#include <cmath>
 #include <cstring>
 
 #include "genga_launch.h"
@@ -194,6 +195,7 @@ __global__ void k_tp_drift(Sim S, TPSet T, DevParams P, double tau, double hcm1,
 //    coefficients' magnitudes sum to at most 2|x| (2|v|), which bounds Horner's rounding error
 //    by a few roundings of the position.
 __constant__ double c_cheb_pow[TP_CHEB][TP_CHEB];  // [k][q]: coefficient of s^q in T_k(s)
+__device__ double d_cheb_cos[TP_CHEB][TP_CHEB];     // [k][q]: cos(pi k (2q + 1) / 2 TP_CHEB), T_k at node q
 
 __global__ void __launch_bounds__(128) k_planet_table(Sim S, TPSet T, DevParams P, double tau) {
   __shared__ double node[TP_CHEB][6];
@@ -225,8 +227,7 @@ __global__ void __launch_bounds__(128) k_planet_table(Sim S, TPSet T, DevParams 
   if (e < 6 * TP_CHEB) {
     const int c = e / TP_CHEB, k = e % TP_CHEB;
     double acc = 0.0;
-    for (int q = 0; q < TP_CHEB; ++q)
-      acc = fma(node[q][c], cospi((double)(k * (2 * q + 1)) / (double)(2 * TP_CHEB)), acc);
+    for (int q = 0; q < TP_CHEB; ++q) acc = fma(node[q][c], d_cheb_cos[k][q], acc);
     acc *= 2.0 / TP_CHEB;
     coef[c][k] = acc;
   }
@@ -239,21 +240,21 @@ __global__ void __launch_bounds__(128) k_planet_table(Sim S, TPSet T, DevParams 
     T.ppoly[((size_t)j * 6 + c) * TP_CHEB + q] = a;
   }
   __syncthreads();
-  if (e == 0) {
+  int ok = 1;
+  if (e < 6) {  // one component per thread
+    const int c = e;
     const double r = sqrt(fma(z0, z0, fma(y0, y0, x0 * x0))), v = sqrt(fma(w0, w0, fma(v0, v0, u0 * u0)));
     const double lim = 1.7763568394002505e-15;  // 2^-49
-    bool ok = true;
-    for (int c = 0; c < 6; ++c) {
-      const double decay = pmax(fabs(coef[c][TP_CHEB - 4]), fabs(coef[c][TP_CHEB - 3]));
-      const double tail = fabs(coef[c][TP_CHEB - 1]) + fabs(coef[c][TP_CHEB - 2]);
-      double sum = 0.0;
-      for (int q = 0; q < TP_CHEB; ++q) sum += fabs(mono[c][q]);
-      const double scale = c < 3 ? r : v;
-      // NaN (a failed node) fails every comparison
-      if (!(decay <= lim * scale) || !(tail <= 2.0 * lim * scale) || !(sum <= 2.0 * scale)) ok = false;
-    }
-    T.pcok[j] = ok;
+    const double decay = pmax(fabs(coef[c][TP_CHEB - 4]), fabs(coef[c][TP_CHEB - 3]));
+    const double tail = fabs(coef[c][TP_CHEB - 1]) + fabs(coef[c][TP_CHEB - 2]);
+    double sum = 0.0;
+    for (int q = 0; q < TP_CHEB; ++q) sum += fabs(mono[c][q]);
+    const double scale = c < 3 ? r : v;
+    // NaN (a failed node) fails every comparison
+    if (!(decay <= lim * scale) || !(tail <= 2.0 * lim * scale) || !(sum <= 2.0 * scale)) ok = 0;
   }
+  ok = __syncthreads_and(ok);
+  if (e == 0) T.pcok[j] = ok;
 }
 
 // Hermite test of each candidate (TP, planet) pair of the last closing kick over the drift,
@@ -766,6 +767,10 @@ int tp_init_constants() {
   for (int k = 1; k + 1 < TP_CHEB; ++k)
     for (int q = 0; q < TP_CHEB; ++q) tk[k + 1][q] = (q > 0 ? 2.0 * tk[k][q - 1] : 0.0) - tk[k - 1][q];
   if (cudaMemcpyToSymbol(c_cheb_pow, tk, sizeof(tk)) != cudaSuccess) return -1;
+  double cs[TP_CHEB][TP_CHEB];  // T_k at the Chebyshev nodes, from the host's cos
+  for (int k = 0; k < TP_CHEB; ++k)
+    for (int q = 0; q < TP_CHEB; ++q) cs[k][q] = cos(M_PI * (double)(k * (2 * q + 1)) / (double)(2 * TP_CHEB));
+  if (cudaMemcpyToSymbol(d_cheb_cos, cs, sizeof(cs)) != cudaSuccess) return -1;
   return cudaMemcpyToSymbol(c_tp_facinv, f, sizeof(f)) == cudaSuccess ? 0 : -1;
 }
 
