@@ -147,6 +147,10 @@ struct genga_ctx {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int gsplit = BS_GMAX + 1, cl_grid = 0, pair_grid = 0;
+  // batched mode: a third branch for the groups of more than BS_SMALL members
+  cudaStream_t side2 = nullptr;
+  cudaEvent_t ev_join2 = nullptr;
+  int small_grid = 0;
   bool profiling = false;
   // batched mode
   bool batched = false;
@@ -229,13 +233,18 @@ void enqueue_step_batch(genga_ctx *c, cudaStream_t st) {
     launch_b_drift(S, P, tau, 0.5 * tau, j > 0 ? 0.5 * c->w[j - 1] * dt : 0.0, j == 0, st);
     launch_b_encounter(S, tau, st);
     launch_b_group(S, st);
-    if (c->side) {  // fork: pairs one warp each on a side branch, larger groups one CTA each; join
+    if (c->side) {  // fork: pairs (two warps each), groups of 3..BS_SMALL (128-thread CTAs) and the
+                    // larger ones (256-thread CTAs) on three branches, each from its own queue; join
       cudaEventRecord(c->ev_fork, st);
       cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+      cudaStreamWaitEvent(c->side2, c->ev_fork, 0);
       launch_bs_pair(S, P, tau, c->pair_grid, c->side);
-      launch_bs(S, P, tau, c->bs_grid, st, BS_GMAX + 1, 3);
+      launch_bs(S, P, tau, c->bs_grid, c->side2, BS_GMAX + 1, BS_SMALL + 1);
+      launch_bs_small(S, P, tau, c->small_grid, st);
       cudaEventRecord(c->ev_join, c->side);
+      cudaEventRecord(c->ev_join2, c->side2);
       cudaStreamWaitEvent(st, c->ev_join, 0);
+      cudaStreamWaitEvent(st, c->ev_join2, 0);
     } else {
       launch_bs(S, P, tau, c->bs_grid, st);
     }
@@ -535,8 +544,8 @@ int genga_init_batch(genga_ctx **out, int n_sys, const int *offsets, const doubl
   S.afar = mem.get<double>(3 * np);
   S.fail = mem.get<int>(np); S.nfail = mem.get<int>(1);
   S.gstart = mem.get<int>(np + 1); S.gmem = mem.get<int>(np); S.ngroups = mem.get<int>(1);
-  S.gsize = mem.get<int>(np + 1); S.gtotal = mem.get<int>(1); S.bsq = mem.get<unsigned>(2);
-  S.gorder = mem.get<int>(np); S.norder = mem.get<int>(2); S.bsn = mem.get<unsigned char>(np);
+  S.gsize = mem.get<int>(np + 1); S.gtotal = mem.get<int>(1); S.bsq = mem.get<unsigned>(3);
+  S.gorder = mem.get<int>(3 * (size_t)np); S.norder = mem.get<int>(6); S.bsn = mem.get<unsigned char>(np);
   S.flags = mem.get<int>(4); S.status = mem.get<int>(1);
   S.counters = mem.get<long long>(NCOUNTERS); S.U = mem.get<double>(1);
   S.nsys = n_sys;
@@ -548,14 +557,19 @@ int genga_init_batch(genga_ctx **out, int n_sys, const int *offsets, const doubl
   c->sx = mem.get<double>(3 * (size_t)n); c->sv = mem.get<double>(3 * (size_t)n);
   c->sm = mem.get<double>(n); c->sR = mem.get<double>(n); c->salive = mem.get<int>(n);
   if (mem.err != cudaSuccess) { genga_free(c); return GENGA_ENOMEM; }
-  c->bs_grid = 2 * num_sms();
   // the pair kernel (4 groups per CTA) takes one CTA per SM, which leaves the other register half of
   // every SM to k_bs from the start: at two per SM it held the whole GPU and k_bs, the longer branch,
   // began 0.5 ms later (measured: 3.06M -> 3.15M system-steps/s)
   c->pair_grid = num_sms();
+  // groups of 3..BS_SMALL members (most of those above pairs) on 128-thread CTAs: two fit beside a
+  // pair CTA in the register file where one 256-thread CTA did; the few larger groups take a half grid
+  c->small_grid = 4 * num_sms();
+  c->bs_grid = num_sms() / 2;
   if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->side2, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming) != cudaSuccess) {
     genga_free(c);
     return GENGA_ECUDA;
   }
@@ -821,7 +835,9 @@ void genga_free(genga_ctx *c) {
   for (int k = 0; k < c->nkev; ++k) cudaEventDestroy(c->kev[k]);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->ev_join2) cudaEventDestroy(c->ev_join2);
   if (c->side) cudaStreamDestroy(c->side);
+  if (c->side2) cudaStreamDestroy(c->side2);
   c->mem.release();
   if (c->own) cudaStreamDestroy(c->own);
   delete c;

@@ -16,11 +16,12 @@ namespace genga {
 // 1/((L/(L-j))^2 - 1) for the Neville extrapolation in h^2 with n_k = 2k
 __constant__ double c_facinv[BS_LEVELS + 1][BS_LEVELS];
 
-// Batched mode: the q-th group of the BS queues (the expected long ones first); q >= ngroups: done.
-__device__ __forceinline__ int batch_group(const Sim &S, int q) {
-  const int nfront = S.norder[0], n = nfront + S.norder[1];
+// Batched mode: the q-th group of BS queue qi (the expected long ones first); past its end: done.
+__device__ __forceinline__ int batch_group(const Sim &S, int qi, int q) {
+  const int nfront = S.norder[2 * qi], n = nfront + S.norder[2 * qi + 1];
   if (q >= n) return 0x7fffffff;
-  return S.gorder[q < nfront ? q : S.npad - 1 - (q - nfront)];
+  const int *qo = S.gorder + (size_t)qi * S.npad;
+  return qo[q < nfront ? q : S.npad - 1 - (q - nfront)];
 }
 
 struct BsShared {
@@ -72,14 +73,18 @@ __device__ __forceinline__ void bs_terms(const BsShared &sh, const DevParams &P,
   }
 }
 
-__global__ void __launch_bounds__(BS_THREADS, 2) k_bs(Sim S, DevParams P, double tau, int gmin, int gsplit) {
+// NT threads: 256, or 128 for the batched queue of groups of 3 .. BS_SMALL members (BS_LEVELS x g
+// slots of four threads fill 128), so that two CTAs fit where one of 256 would. qi: the batched
+// queue the kernel takes its groups from.
+template <int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) k_bs(Sim S, DevParams P, double tau, int gmin, int gsplit, int qi) {
   __shared__ BsShared sh;
   const int tid = threadIdx.x;
   const int np = S.npad;
   const int ngroups = *S.ngroups;
   for (int it = 0;; ++it) {
     // next group: from the queue when there is one (batched mode), else a fixed stride
-    if (tid == 0) sh.next = S.bsq ? batch_group(S, (int)atomicAdd(&S.bsq[1], 1u)) : blockIdx.x + it * gridDim.x;
+    if (tid == 0) sh.next = S.bsq ? batch_group(S, qi, (int)atomicAdd(&S.bsq[qi], 1u)) : blockIdx.x + it * gridDim.x;
     __syncthreads();
     const int gidx = sh.next;
     __syncthreads();
@@ -94,6 +99,10 @@ __global__ void __launch_bounds__(BS_THREADS, 2) k_bs(Sim S, DevParams P, double
       continue;  // uniform across the CTA
     }
     const int tps = g <= 8 ? 4 : (g <= 16 ? 2 : 1);  // threads per (level, member) slot
+    if (BS_LEVELS * g * tps > NT) {  // uniform; the queues route larger groups elsewhere
+      if (tid == 0) atomicOr(S.status, ST_GROUP_TOO_LARGE);
+      continue;
+    }
     const int slot = tid / tps, sub = tid % tps;
     const bool act = slot < BS_LEVELS * g;
     const int lev = act ? slot / g : 0;  // level k = lev + 1, n_k = 2k substeps
@@ -194,7 +203,7 @@ __global__ void __launch_bounds__(BS_THREADS, 2) k_bs(Sim S, DevParams P, double
         __syncthreads();
         if (P.collisions) {  // contact test over the accepted substep (Hermite, threshold (R_a + R_b)^2)
           const int npair = g * (g - 1) / 2;
-          for (int pi = tid; pi < npair; pi += BS_THREADS) {
+          for (int pi = tid; pi < npair; pi += NT) {
             int a = 0, rest = pi;
             while (rest >= g - 1 - a) { rest -= g - 1 - a; a++; }
             const int bq = a + 1 + rest;
@@ -296,9 +305,9 @@ __global__ void __launch_bounds__(BS_THREADS, 2) k_bs(Sim S, DevParams P, double
     }
     __syncthreads();
     if (S.seq_len) {
-      for (int k = tid; k < sh.nseq; k += BS_THREADS) S.seq_pool[sh.seq_base + k] = make_double2(sh.seqH[k], (double)sh.seqk[k]);
+      for (int k = tid; k < sh.nseq; k += NT) S.seq_pool[sh.seq_base + k] = make_double2(sh.seqH[k], (double)sh.seqk[k]);
       const int ny = (sh.nseq > 1 ? sh.nseq - 1 : 0) * g * 6;
-      for (int k = tid; k < ny; k += BS_THREADS) {
+      for (int k = tid; k < ny; k += NT) {
         const int s = k / (g * 6), r = k % (g * 6);
         S.y_pool[sh.y_base + k] = S.y_scratch[(((size_t)blockIdx.x * BS_SEQCAP + s) * BS_GMAX + r / 6) * 6 + r % 6];
       }
@@ -319,7 +328,10 @@ void bs_init_constants() {
 
 void launch_bs(const Sim &S, const DevParams &P, double tau, int max_groups, cudaStream_t st, int gsplit, int gmin) {
   const int grid = max_groups < 1 ? 1 : max_groups;
-  k_bs<<<grid, BS_THREADS, 0, st>>>(S, P, tau, gmin, gsplit);
+  k_bs<BS_THREADS><<<grid, BS_THREADS, 0, st>>>(S, P, tau, gmin, gsplit, 2);
+}
+void launch_bs_small(const Sim &S, const DevParams &P, double tau, int blocks, cudaStream_t st) {
+  k_bs<128><<<blocks < 1 ? 1 : blocks, 128, 0, st>>>(S, P, tau, 3, BS_SMALL + 1, 1);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -479,7 +491,7 @@ __global__ void __launch_bounds__(64 * BSP_UNITS, 2) k_bs_pair(Sim S, DevParams 
   for (int it = 0;; ++it) {
     // next group: from the queue when there is one, else a fixed stride
     if (spec == 0 && lane == 0)
-      sh.gidx = S.bsq ? batch_group(S, (int)atomicAdd(&S.bsq[0], 1u)) : (blockIdx.x + it * gridDim.x) * BSP_UNITS + unit;
+      sh.gidx = S.bsq ? batch_group(S, 0, (int)atomicAdd(&S.bsq[0], 1u)) : (blockIdx.x + it * gridDim.x) * BSP_UNITS + unit;
     usync();
     const int gidx = sh.gidx;
     if (gidx >= ngroups) break;  // uniform within the unit

@@ -19,6 +19,7 @@ constexpr int BS_LEVELS = 8;      // Bulirsch-Stoer levels, substep sequence n_k
 constexpr int BS_GMAX = 32;       // largest encounter group integrated in one CTA
 constexpr int BS_THREADS = 256;
 constexpr int BS_HEAVY = 2;      // batched: groups with a member that needed >= 2 BS_HEAVY substeps last time go first
+constexpr int BS_SMALL = 4;      // batched: groups of 3 .. BS_SMALL members run on 128-thread CTAs
 constexpr int BS_SEQCAP = 256;   // accepted BS substeps one group may record per substep
 constexpr int NCOUNTERS = 8;
 constexpr int CCAP = 32;          // candidate-list slots per body (more: the bitmap row is scanned)
@@ -70,9 +71,11 @@ struct Sim {
   u64 *bmask, *emask;            // per body: candidate / encounter partners (bit = index in system)
   int *gsize;                    // batched groups: member count per group (gstart = first member)
   int *gtotal;                   // batched groups: members placed so far
-  unsigned *bsq;                 // batched groups: next group taken by the pair kernel [0] and k_bs [1]
-  int *gorder, *norder;          // batched groups: the order the BS queues take them in: norder[0] groups
-                                 // expected to need many substeps from the front of gorder, norder[1] from its back
+  unsigned *bsq;                 // batched groups: next group of queue 0 (1-2 members, pair kernel), queue 1
+                                 // (3 .. BS_SMALL members) and queue 2 (larger)
+  int *gorder, *norder;          // batched groups: queue qi is region qi of gorder (npad entries): norder[2 qi]
+                                 // groups expected to need many substeps from its front, norder[2 qi + 1]
+                                 // from its back
   unsigned char *bsn;            // batched bodies: substeps of the body's last BS group, halved every substep
   // recording of the BS decisions for the adjoint engine (null otherwise): the accepted
   // (H, level) of every substep of group g go to seq_pool[seq_off[g] .. + seq_len[g]]

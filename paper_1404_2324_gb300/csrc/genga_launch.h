@@ -33,6 +33,9 @@ void bs_init_constants();  // once per device, before any capture
 // Groups of at least gsplit members are skipped (left to the cluster kernel); BS_GMAX + 1: none.
 void launch_bs(const Sim &S, const DevParams &P, double tau, int max_groups, cudaStream_t st,
                int gsplit = BS_GMAX + 1, int gmin = 1);
+// batched mode: groups of 3 .. BS_SMALL members from BS queue 1, 128-thread CTAs (launch_bs takes
+// queue 2 there)
+void launch_bs_small(const Sim &S, const DevParams &P, double tau, int blocks, cudaStream_t st);
 // groups of one or two members, one warp each (no adjoint recording)
 void launch_bs_pair(const Sim &S, const DevParams &P, double tau, int blocks, cudaStream_t st);
 // bs_cluster.cu: groups of gmin .. BS_GMAX members, one cluster of 8 CTAs (one per level) each
