@@ -6,7 +6,8 @@
 // member's acceleration (the central mass or one partner). Level L completes after 2L force
 // evaluations; its tableau row is built and tested right away, and the attempt stops at the first
 // converged level -- exactly the decision of the serial algorithm, at 2L + 1 evaluations instead
-// of the serial scheme's 72. Batched groups come from work queues ordered by expected cost.
+// of the serial scheme's 72. Batched groups come from work queues ordered by expected cost: groups
+// of 3..BS_SMALL members from queue 1 on 128-thread CTAs, larger ones from queue 2 on 256 threads.
 // k_bs_pair: groups of one or two members, one warp per attempt, the attempt at H/2 run beside the
 // attempt at H (see there).
 #include "genga_launch.h"

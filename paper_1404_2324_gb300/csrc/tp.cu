@@ -8,10 +8,11 @@
 // the tableau on lanes 8..13) in the field of m0 and the (1 - K) pull of the encountered planets,
 // which move on their Kepler paths from the pre-drift state (Sect. 3.3: only the test particle is
 // updated). The planets' positions at every midpoint time of a full-length BS attempt come from a
-// table computed once per substep; shorter attempts evaluate a 16-node Chebyshev series of each
-// planet's path (or solve Kepler's equation where the series is not exact to rounding) and attempt
-// H/2 on lanes 16..29 beside H. Particles in the deepest encounters are integrated first. A TP
-// whose BS substep reaches a planet's surface is removed.
+// table computed once per substep; shorter attempts evaluate the polynomial through 16 Kepler
+// solutions at the Chebyshev nodes of each planet's path (or solve Kepler's equation where that
+// polynomial is not admitted) and attempt H/2 on lanes 16..29 beside H. Particles in the deepest
+// encounters are integrated first, each alone on its SM sub-partition. A TP whose BS substep
+// reaches a planet's surface is removed.
 #include <cmath>
 #include <cstring>
 
@@ -304,7 +305,7 @@ __device__ __forceinline__ double poly1(const double *cf, double s) {
 }
 
 // Planet j's state on its Kepler path at time t of the substep: the table for full-length
-// attempts, otherwise the Chebyshev series (or, where it is not exact, a Kepler solve).
+// attempts, otherwise the path polynomial (or, where it was not admitted, a Kepler solve).
 __device__ __forceinline__ void planet_at(const Sim &S, const TPSet &T, const DevParams &P, int j, bool table,
                                           int k, int m, double t, double i2tau, double &px, double &py, double &pz) {
   if (table) {
