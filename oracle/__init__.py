@@ -31,7 +31,7 @@ ST_CAPACITY = 8
 
 STAT_NAMES = ["steps", "substeps", "candidates", "encounters", "groups", "bs_steps",
               "kepler_fallbacks", "collisions", "reuse_violations", "kepler_iterations",
-              "status_bits", "unused"]
+              "status_bits", "ejections"]
 
 
 def build(force: bool = False) -> str:
@@ -49,7 +49,7 @@ class Params(C.Structure):
     _fields_ = [("G", C.c_double), ("m0", C.c_double), ("dt", C.c_double), ("order", C.c_int),
                 ("kmode", C.c_int), ("n1", C.c_double), ("n2", C.c_double), ("pc", C.c_double),
                 ("bs_eps", C.c_double), ("bs_kmax", C.c_int), ("bs_max_halvings", C.c_int),
-                ("kepler_maxit", C.c_int), ("collisions", C.c_int)]
+                ("kepler_maxit", C.c_int), ("collisions", C.c_int), ("rcut", C.c_double), ("rcut_sun", C.c_double)]
 
 
 _D = C.POINTER(C.c_double)
@@ -92,6 +92,8 @@ def lib():
                 "orc_get_groups": (C.c_int, [C.c_void_p, C.c_int, _I, _I, C.c_int]),
                 "orc_get_stats": (None, [C.c_void_p, C.POINTER(C.c_longlong), C.c_int]),
                 "orc_get_collisions": (C.c_int, [C.c_void_p, _I, C.c_int]),
+                "orc_get_ejections": (C.c_int, [C.c_void_p, _D, C.c_int]),
+                "orc_tp_get_ejections": (C.c_int, [C.c_void_p, _D, C.c_int]),
                 "orc_tp_create": (C.c_void_p, [C.c_int, _P, _D, _D, _D, _D, C.c_int, _D, _D, _D]),
                 "orc_tp_free": (None, [C.c_void_p]),
                 "orc_tp_step": (C.c_int, [C.c_void_p, C.c_int]),
@@ -327,8 +329,19 @@ class Sim:
         lib().orc_get_collisions(self._h, po, cnt)
         return out[: 2 * cnt].reshape(-1, 2)
 
+    def ejections(self):
+        """Removed bodies (Sect. 3.2, Ejections): rows of body index, step, heliocentric x[3], v[3]."""
+        return _ejections(lib().orc_get_ejections, self._h)
 
-TP_STAT_NAMES = ["tp_candidates", "tp_encounters", "tp_bs_steps", "tp_removed", "tp_bs_failed", "u5", "u6", "u7"]
+
+def _ejections(fn, h):
+    cnt = fn(h, None, 0)
+    out, po = _dout(8 * max(cnt, 1))
+    fn(h, po, cnt)
+    return out[: 8 * cnt].reshape(cnt, 8)
+
+
+TP_STAT_NAMES = ["tp_candidates", "tp_encounters", "tp_bs_steps", "tp_removed", "tp_bs_failed", "tp_ejected", "u6", "u7"]
 
 
 class TPSim:
@@ -367,6 +380,10 @@ class TPSim:
         arr = (C.c_longlong * 8)()
         lib().orc_tp_get_stats(self._h, arr, 8)
         return dict(zip(TP_STAT_NAMES, list(arr)))
+
+    def ejections(self):
+        """Removed planets, as Sim.ejections (removed particles: tp_alive and stats()["tp_ejected"])."""
+        return _ejections(lib().orc_tp_get_ejections, self._h)
 
     def encounters(self, substep=-1):
         cnt = lib().orc_tp_get_encounters(self._h, substep, None, 0)

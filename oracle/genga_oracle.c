@@ -52,6 +52,8 @@ void orc_default_params(orc_params *p) {
   p->bs_max_halvings = 30;
   p->kepler_maxit = 30;
   p->collisions = 1;
+  p->rcut = 0.0;     /* no ejections unless asked for */
+  p->rcut_sun = 0.0;
 }
 
 /* ------------------------------------------------------------------------------------------ */
@@ -647,6 +649,8 @@ struct orc_sim {
   int *gstart[ORC_MAXSUB], *gmem[ORC_MAXSUB], ngroups[ORC_MAXSUB];
   int nsub_last;
   int *coll, ncoll, coll_cap;
+  double *ej;                    /* ejection records, 8 doubles each (orc_get_ejections) */
+  int nej, ej_cap;
   unsigned char *is_cand;
   double U;
   long long stats[ORC_NSTATS];
@@ -696,6 +700,8 @@ orc_sim *orc_create(int n, const orc_params *p, const double *m, const double *R
   }
   s->coll_cap = n;
   s->coll = (int *)xcalloc((size_t)2 * s->coll_cap, sizeof(int));
+  s->ej_cap = n + 1;
+  s->ej = (double *)xcalloc((size_t)8 * s->ej_cap, sizeof(double));
   /* heliocentric input -> democratic (heliocentric x, barycentric v): v_b = v_h - V_cm,
    * V_cm = sum m_i v_h,i / (m0 + sum m_i) (Sect. 2.1) */
   double M = p->m0, Pm[3] = {0, 0, 0};
@@ -721,7 +727,7 @@ orc_sim *orc_create(int n, const orc_params *p, const double *m, const double *R
 void orc_free(orc_sim *s) {
   if (!s) return;
   free(s->m); free(s->R); free(s->x); free(s->v); free(s->a); free(s->x0); free(s->v0);
-  free(s->rc); free(s->alive); free(s->fail); free(s->is_cand); free(s->cand); free(s->coll);
+  free(s->rc); free(s->alive); free(s->fail); free(s->is_cand); free(s->cand); free(s->coll); free(s->ej);
   for (int k = 0; k < ORC_MAXSUB; k++) { free(s->enc[k]); free(s->gstart[k]); free(s->gmem[k]); }
   free(s);
 }
@@ -789,6 +795,53 @@ static int substep(orc_sim *s, int js, double tau) {
   return st;
 }
 
+/* Ejections (Sect. 3.2): at the end of a step a body farther than rcut from the central mass, or
+ * closer than rcut_sun, is removed -- a ghost, as after a merger -- and its position and
+ * heliocentric velocity are recorded. The energy it takes away is booked into U (U += E before the
+ * removals - E after them), as for a merger, so that E + U does not jump. */
+static int eject(orc_sim *s) {
+  const orc_params *p = &s->p;
+  if (!(p->rcut > 0.0) && !(p->rcut_sun > 0.0)) return 0;
+  int n = s->n, nout = 0;
+  double E0 = 0.0, P[3] = {0.0, 0.0, 0.0};
+  for (int i = 0; i < n; i++) {
+    if (!s->alive[i]) continue;
+    const double *x = s->x + 3 * i;
+    double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+    int out = (p->rcut > 0.0 && r2 > p->rcut * p->rcut) || (p->rcut_sun > 0.0 && r2 < p->rcut_sun * p->rcut_sun);
+    if (!out) continue;
+    if (nout == 0) {  /* the state before any removal */
+      E0 = orc_energy(n, p, s->m, s->alive, s->x, s->v);
+      orc_momentum(n, s->m, s->alive, s->v, P);
+    }
+    if (s->nej < s->ej_cap) {
+      double *rec = s->ej + 8 * s->nej;
+      rec[0] = (double)i;
+      rec[1] = (double)s->stats[0];
+      for (int k = 0; k < 3; k++) { rec[2 + k] = x[k]; rec[5 + k] = s->v[3 * i + k] + P[k] / p->m0; }
+    }
+    s->nej++;
+    nout++;
+  }
+  if (!nout) return 0;
+  /* remove after the scan: every test above saw the state at the end of the step */
+  for (int q = s->nej - nout; q < s->nej && q < s->ej_cap; q++) {
+    int i = (int)s->ej[8 * q];
+    s->alive[i] = 0;
+    s->m[i] = 0.0;
+    s->R[i] = 0.0;
+  }
+  s->U += E0 - orc_energy(n, p, s->m, s->alive, s->x, s->v);
+  s->stats[11] += nout;
+  return nout;
+}
+
+int orc_get_ejections(const orc_sim *s, double *rec, int cap) {
+  int k = s->nej < s->ej_cap ? s->nej : s->ej_cap;
+  if (rec) memcpy(rec, s->ej, sizeof(double) * 8 * (size_t)(k < cap ? k : cap));
+  return s->nej;
+}
+
 int orc_step(orc_sim *s, int nsteps) {
   int n = s->n, st = 0;
   double w[ORC_MAXSUB];
@@ -819,6 +872,7 @@ int orc_step(orc_sim *s, int nsteps) {
     for (int js = 0; js < nsub; js++) st |= substep(s, js, w[js] * s->p.dt);
     s->nsub_last = nsub;
     s->stats[0]++;
+    eject(s);
   }
   s->stats[10] |= st;
   return st;
@@ -916,7 +970,7 @@ struct orc_tpsim {
   unsigned *cmask;               /* per TP: planets flagged by the last closing kick's precheck */
   double *xp0, *vp0, *xpf, *vpf; /* planets: pre-drift state, Kepler-drift result */
   int *enc[ORC_MAXSUB], nenc[ORC_MAXSUB];
-  long long stats[ORC_TP_NSTATS]; /* candidates, encounters, BS steps, removed, BS failures */
+  long long stats[ORC_TP_NSTATS]; /* candidates, encounters, BS steps, removed, BS failures, ejected */
 };
 
 orc_tpsim *orc_tp_create(int n, const orc_params *p, const double *m, const double *R, const double *xh,
@@ -1236,6 +1290,20 @@ int orc_tp_step(orc_tpsim *T, int nsteps) {
     for (int js = 0; js < nsub; js++) st |= tp_substep(T, js, w[js] * s->p.dt);
     s->nsub_last = nsub;
     s->stats[0]++;
+    /* ejections at the end of the step: test particles by the same rule (they carry no energy),
+     * tested on the positions before any planet is removed, then the planets */
+    const orc_params *p = &s->p;
+    if (p->rcut > 0.0 || p->rcut_sun > 0.0)
+      for (int i = 0; i < T->nt; i++) {
+        if (!T->alive[i]) continue;
+        const double *x = T->x + 3 * i;
+        double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+        if ((p->rcut > 0.0 && r2 > p->rcut * p->rcut) || (p->rcut_sun > 0.0 && r2 < p->rcut_sun * p->rcut_sun)) {
+          T->alive[i] = 0;
+          T->stats[5]++;
+        }
+      }
+    eject(s);
   }
   return st;
 }
@@ -1258,6 +1326,8 @@ void orc_tp_get_state(const orc_tpsim *T, double *xh, double *vh, double *m, int
 void orc_tp_get_stats(const orc_tpsim *T, long long *stats, int nstats) {
   for (int k = 0; k < nstats && k < ORC_TP_NSTATS; k++) stats[k] = T->stats[k];
 }
+
+int orc_tp_get_ejections(const orc_tpsim *T, double *rec, int cap) { return orc_get_ejections(T->s, rec, cap); }
 
 int orc_tp_get_encounters(const orc_tpsim *T, int substep_idx, int *pairs, int cap) {
   if (substep_idx < 0) substep_idx = T->s->nsub_last - 1;

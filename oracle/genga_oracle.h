@@ -32,6 +32,8 @@ typedef struct orc_params {
   int bs_max_halvings; /* consecutive step halvings before a group is declared failed */
   int kepler_maxit;  /* Newton iteration cap of the universal Kepler solve */
   int collisions;    /* 1: perfect merging on contact (Sect. 3.2, Collisions) */
+  double rcut;       /* Sect. 3.2, Ejections: a body farther than rcut from m0 is removed (0: off) */
+  double rcut_sun;   /* ... and one closer than rcut_sun (0: off) */
 } orc_params;
 
 /* Status bits returned by orc_step and the phase routines. */
@@ -90,6 +92,9 @@ int orc_get_encounters(const orc_sim *s, int substep, int *pairs, int cap);
 int orc_get_groups(const orc_sim *s, int substep, int *group_start, int *members, int cap);
 void orc_get_stats(const orc_sim *s, long long *stats, int nstats);
 int orc_get_collisions(const orc_sim *s, int *pairs, int cap);
+/* Ejections so far (all of them; at most cap records written): record k = rec[8k .. 8k+7] =
+ * body index, step (1-based, the step at whose end it was removed), heliocentric x[3] and v[3]. */
+int orc_get_ejections(const orc_sim *s, double *rec, int cap);
 
 /* ---- test-particle mode (Sect. 3.3): massive bodies as above plus massless test particles ---- */
 typedef struct orc_tpsim orc_tpsim;
@@ -101,6 +106,7 @@ void orc_tp_get_state(const orc_tpsim *t, double *xh, double *vh, double *m, int
                       double *vt, int *tp_alive);
 void orc_tp_get_stats(const orc_tpsim *t, long long *stats, int nstats);
 int orc_tp_get_encounters(const orc_tpsim *t, int substep, int *pairs, int cap);
+int orc_tp_get_ejections(const orc_tpsim *t, double *rec, int cap);  /* the planets' (orc_get_ejections) */
 
 #ifdef __cplusplus
 }
