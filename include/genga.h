@@ -48,6 +48,8 @@ extern "C" {
 #define GENGA_ST_GROUP_TOO_LARGE 8   /* an encounter group exceeded the in-kernel size cap */
 #define GENGA_ST_UNION_ROUNDS 16     /* grouping did not reach its fixpoint within its round cap */
 #define GENGA_ST_RECORD_OVERFLOW 32  /* adjoint engine: a recording buffer was too small (gradient invalid) */
+#define GENGA_ST_EJECT_OVERFLOW 64   /* more than 4096 ejection records (later ones dropped), or more than
+                                        1024 bodies out of bounds in one step (the rest leave next step) */
 
 /* modes of genga_init (Sect. 3): main mode with up to 2048 massive bodies */
 #define GENGA_MODE_MASSIVE 0
@@ -66,6 +68,15 @@ typedef struct genga_params {
   int kmode;            /* 0: K multiplies the Newtonian pair force; 1: exact gradient of H_B */
   int collisions;       /* 1: perfect merging on contact (Sect. 3.2, Collisions) */
   int precise_div;      /* 1: kick uses IEEE sqrt and division; 0: refined reciprocal square root */
+  /* Ejections (Sect. 3.2): at the end of every step a body farther than rcut from its central mass
+   * or closer than rcut_sun is removed (a ghost, as after a merger), its heliocentric state
+   * recorded (genga_ejections) and the energy it takes away booked into U; test particles are
+   * removed by the same limits. 0 switches a limit off (the default); rcut > rcut_sun when both. */
+  double rcut;
+  double rcut_sun;
+  /* Batched mode (Sect. 3.4, Nmin): a system left with fewer than nmin live bodies at the end of a
+   * step is stopped, all its bodies removed (energy booked into U). 0: off (the default). */
+  int nmin;
 } genga_params;
 
 /* Fills *p with the paper's defaults (n1 = 3, n2 = 0.4, pc = 3) and the library's BS/Kepler caps. */
@@ -113,6 +124,13 @@ int genga_energy(genga_ctx *ctx, double *E, double *U);
  * returns GENGA_ECAP if cap < count (the first cap pairs are written). */
 int genga_encounters(genga_ctx *ctx, int substep, int *pairs, int cap, int *n_pairs);
 
+/* Ejections since the context was created (Sect. 3.2): *n receives their number; the first
+ * min(*n, cap, 4096) records are written to rec [8 cap], each: body index (the caller's: central
+ * mass at 0 in the single-system modes, the index into the concatenated bodies in the batched
+ * mode), the step (1-based) at whose end it left, heliocentric x[3] and v[3] at that moment, in
+ * ascending index within a step. Waits for the stream. */
+int genga_ejections(genga_ctx *ctx, double *rec, int cap, int *n);
+
 /* Device status word: bits GENGA_ST_*; *detail receives counters (may be NULL): detail[0] steps,
  * [1] candidates, [2] encounters, [3] groups, [4] BS steps, [5] Kepler fallbacks, [6] mergers,
  * [7] full-kick recomputes (8 entries). Waits for the stream. */
@@ -151,8 +169,9 @@ int genga_init_tp(genga_ctx **ctx, int n, const double *masses, const double *ra
 /* Test-particle state (heliocentric, host): xt, vt [3 n_tp], tp_alive [n_tp]; any may be NULL. */
 int genga_get_state_tp(genga_ctx *ctx, double *xt, double *vt, int *tp_alive);
 
-/* Test-particle counters since genga_init_tp: detail[0] (TP, planet) candidate pairs recorded by the
- * closing kicks, [1] confirmed encounter pairs, [2] accepted BS substeps, [3] particles removed. */
+/* Test-particle counters since genga_init_tp (5 entries): detail[0] (TP, planet) candidate pairs
+ * recorded by the closing kicks, [1] confirmed encounter pairs, [2] accepted BS substeps,
+ * [3] particles removed on contact, [4] particles ejected (rcut, rcut_sun). */
 int genga_tp_status(genga_ctx *ctx, long long *detail);
 
 /* ------------------------------------------------------------------------------------------ */

@@ -86,6 +86,7 @@ bool alloc_sim(Sim &S, DevMem &mem, int n, int nsub) {
   S.nwarps = S.nitems < target ? S.nitems : target;
   S.flags = mem.get<int>(4); S.status = mem.get<int>(1);
   S.counters = mem.get<long long>(NCOUNTERS); S.U = mem.get<double>(1);
+  S.ejrec = mem.get<double>(8 * (size_t)EJ_CAP); S.nej = mem.get<int>(1);
   if (mem.err != cudaSuccess) return false;
   cudaMemcpy(S.items, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice);
   return cudaGetLastError() == cudaSuccess;
@@ -99,6 +100,9 @@ DevParams make_params(double G, double m0, const genga_params &p) {
   P.n1 = p.n1; P.n2 = p.n2; P.pc = p.pc; P.bs_eps = p.bs_eps;
   P.bs_kmax = p.bs_kmax; P.bs_max_halvings = p.bs_max_halvings; P.kepler_maxit = p.kepler_maxit;
   P.kmode = p.kmode; P.collisions = p.collisions;
+  P.rcut2 = p.rcut > 0.0 ? p.rcut * p.rcut : 0.0;
+  P.rcut_sun2 = p.rcut_sun > 0.0 ? p.rcut_sun * p.rcut_sun : 0.0;
+  P.nmin = p.nmin;
   return P;
 }
 
@@ -156,6 +160,7 @@ struct genga_ctx {
   bool batched = false;
   int nsys = 0, b_split = 1, b_block = 128, steps_per_launch = 1;
   int *perm = nullptr, *sys_user = nullptr;  // device: internal body -> user body, internal system -> user system
+  std::vector<int> perm_h;                    // host copy of perm (ejection records)
   double *sysE = nullptr;
   // test-particle mode
   bool tpmode = false;
@@ -253,6 +258,7 @@ void enqueue_step_batch(genga_ctx *c, cudaStream_t st) {
     launch_b_kick(S, P, FIN_CLOSE, 0.5 * tau, h2, c->b_split, c->b_block, st);
   }
   launch_b_hc(S, 0.5 * c->w[c->nsub - 1] * dt, st);
+  if (P.rcut2 > 0.0 || P.rcut_sun2 > 0.0 || P.nmin > 0) launch_b_eject(S, P, st);
 }
 
 // One full step (Sect. 2.2 second list, composed per Sect. 2.3).
@@ -299,6 +305,10 @@ void enqueue_step(genga_ctx *c, cudaStream_t st) {
   }
   launch_hc(S, 0.5 * c->w[c->nsub - 1] * dt * inv_m0, st);
   if (tp) launch_tp_hc(S, T, 0.5 * c->w[c->nsub - 1] * dt * inv_m0, st);
+  if (P.rcut2 > 0.0 || P.rcut_sun2 > 0.0) {  // ejections at the end of the step (Sect. 3.2)
+    if (tp) launch_tp_eject(T, P, st);
+    launch_eject(S, P, st);
+  }
 }
 
 // Captured on the context's own stream (the caller's stream may be the legacy default stream,
@@ -349,6 +359,9 @@ int genga_default_params(genga_params *p) {
   p->kmode = 0;
   p->collisions = 1;
   p->precise_div = 0;
+  p->rcut = 0.0;
+  p->rcut_sun = 0.0;
+  p->nmin = 0;
   return GENGA_OK;
 }
 
@@ -477,7 +490,7 @@ int genga_get_state_tp(genga_ctx *c, double *xt, double *vt, int *tp_alive) {
 int genga_tp_status(genga_ctx *c, long long *detail) {
   if (!c || !c->tpmode || !detail) return GENGA_EINVAL;
   CK(cudaStreamSynchronize(c->stream));
-  CK(cudaMemcpy(detail, c->T.counters, 4 * sizeof(long long), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(detail, c->T.counters, 5 * sizeof(long long), cudaMemcpyDeviceToHost));
   return GENGA_OK;
 }
 
@@ -527,6 +540,7 @@ int genga_init_batch(genga_ctx **out, int n_sys, const int *offsets, const doubl
     sm0[k] = m0[s];
     for (int q = 0; q < ns; ++q) { perm.push_back(offsets[s] + q); sys_of.push_back(k); }
   }
+  c->perm_h = perm;
   Sim &S = c->S;
   DevMem &mem = c->mem;
   memset(&S, 0, sizeof(S));
@@ -548,6 +562,7 @@ int genga_init_batch(genga_ctx **out, int n_sys, const int *offsets, const doubl
   S.gorder = mem.get<int>(3 * (size_t)np); S.norder = mem.get<int>(6); S.bsn = mem.get<unsigned char>(np);
   S.flags = mem.get<int>(4); S.status = mem.get<int>(1);
   S.counters = mem.get<long long>(NCOUNTERS); S.U = mem.get<double>(1);
+  S.ejrec = mem.get<double>(8 * (size_t)EJ_CAP); S.nej = mem.get<int>(1);
   S.nsys = n_sys;
   S.sys_of = mem.get<int>(np); S.sys_start = mem.get<int>(n_sys + 1);
   S.sys_m0 = mem.get<double>(n_sys); S.sys_ppre = mem.get<double>(3 * (size_t)n_sys);
@@ -671,10 +686,30 @@ int genga_set_params(genga_ctx *c, const genga_params *p) {
   if (!(p->n1 >= 0.0) || !(p->n2 >= 0.0) || !(p->pc >= 1.0) || !(p->bs_eps > 0.0) || p->bs_kmax < 2 ||
       p->bs_kmax > BS_LEVELS || p->bs_max_halvings < 0 || p->kepler_maxit < 1 || (p->kmode != 0 && p->kmode != 1))
     return GENGA_EINVAL;
+  if (!(p->rcut >= 0.0) || !(p->rcut_sun >= 0.0) || p->nmin < 0 || (p->rcut > 0.0 && !(p->rcut > p->rcut_sun)))
+    return GENGA_EINVAL;
   c->prm = *p;
   c->P = make_params(c->G, c->m0, c->prm);
   drop_graph(c);
   return c->batched ? first_kick_batch(c) : first_kick(c);
+}
+
+int genga_ejections(genga_ctx *c, double *rec, int cap, int *n) {
+  if (!c || cap < 0 || (cap > 0 && !rec)) return GENGA_EINVAL;
+  CK(cudaStreamSynchronize(c->stream));
+  int cnt = 0;
+  CK(cudaMemcpy(&cnt, c->S.nej, sizeof(int), cudaMemcpyDeviceToHost));
+  if (n) *n = cnt;
+  int k = cnt < EJ_CAP ? cnt : EJ_CAP;
+  if (k > cap) k = cap;
+  if (k > 0) {
+    CK(cudaMemcpy(rec, c->S.ejrec, 8 * (size_t)k * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int q = 0; q < k; ++q) {  // internal index -> the caller's
+      const int i = (int)rec[8 * q];
+      rec[8 * q] = (double)(c->batched ? c->perm_h[i] : i + 1);
+    }
+  }
+  return GENGA_OK;
 }
 
 int genga_set_stream(genga_ctx *c, void *stream) {

@@ -32,6 +32,9 @@ constexpr int ST_REUSE_FULLKICK = 4;
 constexpr int ST_GROUP_TOO_LARGE = 8;
 constexpr int ST_UNION_ROUNDS = 16;
 constexpr int ST_RECORD_OVERFLOW = 32;  // a recording buffer of the adjoint engine was too small
+constexpr int ST_EJECT_OVERFLOW = 64;   // more ejections than EJ_CAP records, or than EJ_STEP in one step
+constexpr int EJ_CAP = 4096;            // ejection records kept (8 doubles each)
+constexpr int EJ_STEP = 1024;           // bodies one step can remove in the single-system modes
 
 // counters (mirrors genga_status detail[])
 enum { C_STEPS = 0, C_CAND, C_ENC, C_GROUPS, C_BSSTEPS, C_KFALL, C_MERGE, C_FULLKICK };
@@ -41,6 +44,8 @@ struct DevParams {
   double n1, n2, pc;
   double bs_eps;
   int bs_kmax, bs_max_halvings, kepler_maxit, kmode, collisions;
+  double rcut2, rcut_sun2;  // Sect. 3.2, Ejections: squared limits on |x|; 0: that test is off
+  int nmin;                 // batched: a system left with fewer live bodies is stopped; 0: off
 };
 
 // All per-body arrays are SoA with leading dimension npad (a multiple of 32); vectors are stored
@@ -90,7 +95,9 @@ struct Sim {
   int *flags;                    // [0] full opening kick needed
   int *status;                   // status bits
   long long *counters;           // [NCOUNTERS]
-  double *U;                     // internal energy of mergers
+  double *U;                     // internal energy of mergers and ejections
+  double *ejrec;                 // ejection records [EJ_CAP * 8]: index, step, heliocentric x, v
+  int *nej;                      // ejections so far (may exceed EJ_CAP: records past it are dropped)
 };
 
 // Test particles (massless, perturbed by the massive bodies of a Sim; Sect. 3.3). SoA with
@@ -109,7 +116,7 @@ struct TPSet {
   double *ptab;                  // planets' Kepler paths at the BS midpoint times [TP_MAXPL * TP_TAB * 6]
   double *ppoly;                 // planets' paths over the substep, polynomials in s = 2t/tau - 1 [TP_MAXPL * 6 * TP_CHEB]
   int *pcok;                     // 1: planet j's series is exact to rounding; 0: solve Kepler instead
-  long long *counters;           // candidates, encounters, BS steps, removed
+  long long *counters;           // candidates, encounters, BS steps, removed, ejected
 };
 constexpr int TP_MAXPL = 32;     // planets in test-particle mode
 constexpr int TP_TAB = 80;       // sum over BS levels k = 1..8 of the 2k + 1 midpoint times

@@ -28,6 +28,10 @@ void launch_bitmap_pairs(const unsigned *bm, int npad, int W, int *out, int cap,
 void launch_single_to_fail(const Sim &S, const int *single, cudaStream_t st);
 void launch_copy_edges(const Sim &S, const int *pairs, int npairs, cudaStream_t st);
 
+// eject.cu: ejections (and the batched stop below nmin) at the end of a step
+void launch_eject(const Sim &S, const DevParams &P, cudaStream_t st);
+void launch_b_eject(const Sim &S, const DevParams &P, cudaStream_t st);
+void launch_tp_eject(const TPSet &T, const DevParams &P, cudaStream_t st);
 // bs.cu
 void bs_init_constants();  // once per device, before any capture
 // Groups of at least gsplit members are skipped (left to the cluster kernel); BS_GMAX + 1: none.

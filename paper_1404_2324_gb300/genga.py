@@ -40,7 +40,8 @@ class GengaError(RuntimeError):
 class genga_params(C.Structure):
     _fields_ = [("n1", C.c_double), ("n2", C.c_double), ("pc", C.c_double), ("bs_eps", C.c_double),
                 ("bs_kmax", C.c_int), ("bs_max_halvings", C.c_int), ("kepler_maxit", C.c_int),
-                ("kmode", C.c_int), ("collisions", C.c_int), ("precise_div", C.c_int)]
+                ("kmode", C.c_int), ("collisions", C.c_int), ("precise_div", C.c_int),
+                ("rcut", C.c_double), ("rcut_sun", C.c_double), ("nmin", C.c_int)]
 
 
 _D = C.POINTER(C.c_double)
@@ -59,6 +60,7 @@ _SIGS = {
     "genga_get_state": (C.c_int, [_V, _D, _D, _D, _D, _I]),
     "genga_energy": (C.c_int, [_V, _D, _D]),
     "genga_encounters": (C.c_int, [_V, C.c_int, _I, C.c_int, _I]),
+    "genga_ejections": (C.c_int, [_V, _D, C.c_int, _I]),
     "genga_status": (C.c_int, [_V, _I, C.POINTER(C.c_longlong)]),
     "genga_free": (None, [_V]),
     "genga_set_profiling": (C.c_int, [_V, C.c_int]),
@@ -277,9 +279,18 @@ def genga_get_state_tp(ctx, n_tp):
 
 
 def genga_tp_status(ctx):
-    d = (C.c_longlong * 4)()
+    d = (C.c_longlong * 5)()
     _check(lib().genga_tp_status(ctx, d), "genga_tp_status")
-    return dict(zip(["tp_candidates", "tp_encounters", "tp_bs_steps", "tp_removed"], list(d)))
+    return dict(zip(["tp_candidates", "tp_encounters", "tp_bs_steps", "tp_removed", "tp_ejected"], list(d)))
+
+
+def genga_ejections(ctx):
+    """Ejection records (Sect. 3.2): rows of body index, step, heliocentric x[3], v[3]."""
+    n = C.c_int(0)
+    _check(lib().genga_ejections(ctx, None, 0, C.byref(n)), "genga_ejections")
+    out = np.zeros((max(n.value, 1), 8))
+    _check(lib().genga_ejections(ctx, out.ctypes.data_as(_D), n.value, C.byref(n)), "genga_ejections")
+    return out[: min(n.value, 4096)]
 
 
 # ------------------------------------------------------------------------------------ batched mode
