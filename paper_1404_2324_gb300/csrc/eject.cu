@@ -53,6 +53,7 @@ __device__ void write_record(const Sim &S, int slot, int i, double step, double 
 // ---------------------------------------------------------------------------------------------
 // Single system (N <= 2048, the massive bodies of the main and test-particle modes): one block.
 constexpr int EJ_THREADS = 1024;
+static_assert(NMAX <= 64 * 32, "the removal bitmap of k_eject covers NMAX bodies");
 
 __global__ void __launch_bounds__(EJ_THREADS) k_eject(Sim S, DevParams P) {
   __shared__ int s_n, s_base;
