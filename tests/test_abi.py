@@ -51,3 +51,32 @@ def test_invalid_arguments_are_rejected_on_the_host():
     assert not h.value
     p = genga.genga_default_params()
     assert (p.n1, p.n2, p.pc, p.bs_kmax) == (3.0, 0.4, 3.0, 8)
+
+
+def _c_layout(tmp_path, header, struct, fields):
+    """sizeof and field offsets of a C struct, from a small program compiled against the header."""
+    import subprocess
+    src = tmp_path / "layout.c"
+    body = "".join(f'  printf("%zu\\n", offsetof({struct}, {f}));\n' for f in fields)
+    src.write_text(f'#include <stddef.h>\n#include <stdio.h>\n#include "{header}"\nint main(void) {{\n'
+                   f'  printf("%zu\\n", sizeof({struct}));\n{body}  return 0;\n}}\n')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    return [int(v) for v in out]
+
+
+@pytest.mark.parametrize("which", ["genga", "oracle"])
+def test_params_struct_layout_matches_the_binding(tmp_path, which):
+    """The ctypes mirrors of genga_params (include/genga.h) and orc_params (the oracle's header)
+    have the C structs' size and field offsets: a field added on one side only shifts the rest."""
+    if which == "genga":
+        from paper_1404_2324_gb300 import genga as mod
+        cls, header, struct = mod.genga_params, os.path.join(ROOT, "include", "genga.h"), "genga_params"
+    else:
+        import oracle as mod
+        cls, header, struct = mod.Params, os.path.join(ROOT, "oracle", "genga_oracle.h"), "orc_params"
+    names = [f[0] for f in cls._fields_]
+    got = _c_layout(tmp_path, header, struct, names)
+    assert got[0] == ctypes.sizeof(cls)
+    assert got[1:] == [getattr(cls, n).offset for n in names]
