@@ -151,10 +151,11 @@ struct genga_ctx {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int gsplit = BS_GMAX + 1, cl_grid = 0, pair_grid = 0;
-  // batched mode: a third branch for the groups of more than BS_SMALL members
+  // a further branch: groups above BS_GMAX members (main mode; the larger batched groups too)
   cudaStream_t side2 = nullptr;
   cudaEvent_t ev_join2 = nullptr;
   int small_grid = 0;
+  int wide_grid = 8;  // CTAs of the wide BS kernel (groups of BS_GMAX + 1 .. BS_GWIDE members: rare)
   bool profiling = false;
   // batched mode
   bool batched = false;
@@ -245,6 +246,7 @@ void enqueue_step_batch(genga_ctx *c, cudaStream_t st) {
       cudaStreamWaitEvent(c->side2, c->ev_fork, 0);
       launch_bs_pair(S, P, tau, c->pair_grid, c->side);
       launch_bs(S, P, tau, c->bs_grid, c->side2, BS_GMAX + 1, BS_SMALL + 1);
+      launch_bs_wide(S, P, tau, c->wide_grid, c->side2);  // queue 3: groups above BS_GMAX members
       launch_bs_small(S, P, tau, c->small_grid, st);
       cudaEventRecord(c->ev_join, c->side);
       cudaEventRecord(c->ev_join2, c->side2);
@@ -282,13 +284,19 @@ void enqueue_step(genga_ctx *c, cudaStream_t st) {
     if (tp) launch_planet_table(S, T, P, tau, st);
     launch_encounter(S, tau, S.ebm + (size_t)j * S.npad * S.W, st);
     launch_group(S, st, c->side ? c->gsplit : BS_GMAX + 1);
-    if (c->side) {  // fork: cluster kernel for the larger groups, one-CTA kernel for the rest; join
+    if (c->side) {  // fork: cluster kernel for the larger groups, one-CTA kernel for the rest and
+                    // the wide kernel for groups above BS_GMAX members (its CTAs leave at once when
+                    // the large-group list holds none); join
       cudaEventRecord(c->ev_fork, st);
       cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+      cudaStreamWaitEvent(c->side2, c->ev_fork, 0);
       launch_bs_cluster(S, P, tau, c->gsplit, c->cl_grid, c->side);
+      launch_bs_wide(S, P, tau, c->wide_grid, c->side2);
       launch_bs(S, P, tau, c->bs_grid, st, c->gsplit);
       cudaEventRecord(c->ev_join, c->side);
+      cudaEventRecord(c->ev_join2, c->side2);
       cudaStreamWaitEvent(st, c->ev_join, 0);
+      cudaStreamWaitEvent(st, c->ev_join2, 0);
     } else {
       launch_bs(S, P, tau, c->bs_grid, st);
     }
@@ -400,8 +408,10 @@ int genga_init(genga_ctx **out, int n, const double *masses, const double *radii
   bs_init_constants();
   bs_cluster_init_constants();
   if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->side2, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming) != cudaSuccess) {
     genga_free(c);
     return GENGA_ECUDA;
   }
@@ -558,8 +568,8 @@ int genga_init_batch(genga_ctx **out, int n_sys, const int *offsets, const doubl
   S.afar = mem.get<double>(3 * np);
   S.fail = mem.get<int>(np); S.nfail = mem.get<int>(1);
   S.gstart = mem.get<int>(np + 1); S.gmem = mem.get<int>(np); S.ngroups = mem.get<int>(1);
-  S.gsize = mem.get<int>(np + 1); S.gtotal = mem.get<int>(1); S.bsq = mem.get<unsigned>(3);
-  S.gorder = mem.get<int>(3 * (size_t)np); S.norder = mem.get<int>(6); S.bsn = mem.get<unsigned char>(np);
+  S.gsize = mem.get<int>(np + 1); S.gtotal = mem.get<int>(1); S.bsq = mem.get<unsigned>(4);
+  S.gorder = mem.get<int>(4 * (size_t)np); S.norder = mem.get<int>(8); S.bsn = mem.get<unsigned char>(np);
   S.flags = mem.get<int>(4); S.status = mem.get<int>(1);
   S.counters = mem.get<long long>(NCOUNTERS); S.U = mem.get<double>(1);
   S.ejrec = mem.get<double>(8 * (size_t)EJ_CAP); S.nej = mem.get<int>(1);

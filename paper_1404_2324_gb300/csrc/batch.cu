@@ -151,8 +151,8 @@ __global__ void k_b_momentum(Sim S, double *out) {
 __global__ void k_b_drift(Sim S, DevParams P, double tau, double h1, double h2, int first) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) { *S.ngroups = 0; *S.gtotal = 0; }
-  if (i < 3) S.bsq[i] = 0u;
-  if (i < 6) S.norder[i] = 0;
+  if (i < 4) S.bsq[i] = 0u;
+  if (i < 8) S.norder[i] = 0;
   if (i < S.npad) S.bsn[i] >>= 1;  // the substep history fades
   if (i >= S.npad) return;
   const int np = S.npad;
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(32 * BG_WARPS) k_b_group(Sim S) {
         S.gsize[g] = cnt[r];
         // the queue of the kernel that integrates the group; groups whose members needed many
         // substeps last time start first (they set the BS time)
-        const int qi = cnt[r] <= 2 ? 0 : (cnt[r] <= BS_SMALL ? 1 : 2);
+        const int qi = cnt[r] <= 2 ? 0 : (cnt[r] <= BS_SMALL ? 1 : (cnt[r] <= BS_GMAX ? 2 : 3));
         int *qo = S.gorder + (size_t)qi * S.npad;
         if (hist[r] >= BS_HEAVY) qo[atomicAdd(&S.norder[2 * qi], 1)] = g;
         else qo[S.npad - 1 - atomicAdd(&S.norder[2 * qi + 1], 1)] = g;

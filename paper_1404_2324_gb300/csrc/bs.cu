@@ -25,15 +25,17 @@ __device__ __forceinline__ int batch_group(const Sim &S, int qi, int q) {
   return qo[q < nfront ? q : S.npad - 1 - (q - nfront)];
 }
 
-struct BsShared {
-  int idx[BS_GMAX], alive[BS_GMAX];
-  double gm[BS_GMAX], m[BS_GMAX], R[BS_GMAX], A[BS_GMAX];
-  u64 rcsq[BS_GMAX];
-  double y[BS_GMAX][6], yn[BS_GMAX][6];
-  double pos[2][BS_LEVELS][BS_GMAX][3];
-  double tab[BS_LEVELS][BS_GMAX][6];
+// A group's state in shared memory, for groups of up to GM members.
+template <int GM>
+struct BsSharedT {
+  int idx[GM], alive[GM];
+  double gm[GM], m[GM], R[GM], A[GM];
+  u64 rcsq[GM];
+  double y[GM][6], yn[GM][6];
+  double pos[2][BS_LEVELS][GM][3];
+  double tab[BS_LEVELS][GM][6];
   u64 err[BS_LEVELS];
-  unsigned char cont[BS_GMAX * (BS_GMAX - 1) / 2];
+  unsigned char cont[GM * (GM - 1) / 2];
   double H, rem, U;
   int accept, next;
   int nseq, seq_base;          // recorded accepted substeps (adjoint engine only)
@@ -41,6 +43,7 @@ struct BsShared {
   double seqH[BS_SEQCAP];
   unsigned char seqk[BS_SEQCAP];
 };
+using BsShared = BsSharedT<BS_GMAX>;
 
 // Acceleration terms of member q assigned to this thread: term p == q is the central mass, any
 // other p the (1 - K)-weighted pull of partner p (H_A, Eq. Ha). Summed over the slot's threads.
@@ -48,7 +51,8 @@ struct BsShared {
 // G m0 and weight 1; a partner outside rc gets weight 0): lanes of one warp that took different
 // branches would each pay for both, and an FP64 warp instruction costs its sub-partition 64
 // cycles whatever its active lanes.
-__device__ __forceinline__ void bs_terms(const BsShared &sh, const DevParams &P, double Gm0, int g, int q, int sub,
+template <class SH>
+__device__ __forceinline__ void bs_terms(const SH &sh, const DevParams &P, double Gm0, int g, int q, int sub,
                                          int tps, const double (*pos)[3], bool q_alive, double &ax, double &ay,
                                          double &az) {
   ax = ay = az = 0.0;
@@ -75,17 +79,28 @@ __device__ __forceinline__ void bs_terms(const BsShared &sh, const DevParams &P,
 }
 
 // NT threads: 256, or 128 for the batched queue of groups of 3 .. BS_SMALL members (BS_LEVELS x g
-// slots of four threads fill 128), so that two CTAs fit where one of 256 would. qi: the batched
-// queue the kernel takes its groups from.
-template <int NT>
-__global__ void __launch_bounds__(NT, 512 / NT) k_bs(Sim S, DevParams P, double tau, int gmin, int gsplit, int qi) {
-  __shared__ BsShared sh;
+// slots of four threads fill 128), so that two CTAs fit where one of 256 would, or 512 for groups
+// of BS_GMAX + 1 .. BS_GWIDE members (one thread a slot; the state, GM = BS_GWIDE, in dynamic
+// shared memory). The kernel integrates the groups of gmin .. gsplit - 1 members that it meets and
+// reports larger ones than GM; it takes its groups from batched queue qi, else from the
+// large-group list (from_big), else every group with a fixed stride.
+template <int NT, int GM>
+__global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 512 / NT)
+    k_bs(Sim S, DevParams P, double tau, int gmin, int gsplit, int qi, int from_big) {
+  __shared__ __align__(16) unsigned char bs_static[GM <= BS_GMAX ? sizeof(BsSharedT<GM>) : 16];
+  extern __shared__ __align__(16) unsigned char bs_dyn[];
+  BsSharedT<GM> &sh = *reinterpret_cast<BsSharedT<GM> *>(GM <= BS_GMAX ? bs_static : bs_dyn);
   const int tid = threadIdx.x;
   const int np = S.npad;
   const int ngroups = *S.ngroups;
   for (int it = 0;; ++it) {
     // next group: from the queue when there is one (batched mode), else a fixed stride
-    if (tid == 0) sh.next = S.bsq ? batch_group(S, qi, (int)atomicAdd(&S.bsq[qi], 1u)) : blockIdx.x + it * gridDim.x;
+    if (tid == 0) {
+      int nx = blockIdx.x + it * gridDim.x;
+      if (S.bsq) nx = batch_group(S, qi, (int)atomicAdd(&S.bsq[qi], 1u));
+      else if (from_big) nx = nx < *S.nbig ? S.big[nx] : 0x7fffffff;
+      sh.next = nx;
+    }
     __syncthreads();
     const int gidx = sh.next;
     __syncthreads();
@@ -94,8 +109,8 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_bs(Sim S, DevParams P, double 
     // central mass of the group's system (batched mode) or of the single system
     const double m0 = S.sys_of ? S.sys_m0[S.sys_of[S.gmem[g0]]] : P.m0;
     const double Gm0 = P.G * m0;
-    if (g < gmin || (g >= gsplit && g <= BS_GMAX)) continue;  // uniform: the pair or the cluster kernel
-    if (g > BS_GMAX) {
+    if (g < gmin || g >= gsplit) continue;  // uniform: the pair, cluster or wide kernel's
+    if (g > GM || (GM > BS_GMAX && S.seq_len)) {  // the adjoint's recording holds BS_GMAX members
       if (tid == 0) atomicOr(S.status, ST_GROUP_TOO_LARGE);
       continue;  // uniform across the CTA
     }
@@ -317,7 +332,11 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_bs(Sim S, DevParams P, double 
   }
 }
 
+static_assert(BS_WIDE_THREADS == BS_LEVELS * BS_GWIDE, "one thread per (level, member) slot");
+
 void bs_init_constants() {
+  cudaFuncSetAttribute(k_bs<BS_WIDE_THREADS, BS_GWIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sizeof(BsSharedT<BS_GWIDE>));
   double h[BS_LEVELS + 1][BS_LEVELS] = {};
   for (int L = 2; L <= BS_LEVELS; ++L)
     for (int j = 1; j < L; ++j) {
@@ -329,10 +348,14 @@ void bs_init_constants() {
 
 void launch_bs(const Sim &S, const DevParams &P, double tau, int max_groups, cudaStream_t st, int gsplit, int gmin) {
   const int grid = max_groups < 1 ? 1 : max_groups;
-  k_bs<BS_THREADS><<<grid, BS_THREADS, 0, st>>>(S, P, tau, gmin, gsplit, 2);
+  k_bs<BS_THREADS, BS_GMAX><<<grid, BS_THREADS, 0, st>>>(S, P, tau, gmin, gsplit, 2, 0);
 }
 void launch_bs_small(const Sim &S, const DevParams &P, double tau, int blocks, cudaStream_t st) {
-  k_bs<128><<<blocks < 1 ? 1 : blocks, 128, 0, st>>>(S, P, tau, 3, BS_SMALL + 1, 1);
+  k_bs<128, BS_GMAX><<<blocks < 1 ? 1 : blocks, 128, 0, st>>>(S, P, tau, 3, BS_SMALL + 1, 1, 0);
+}
+void launch_bs_wide(const Sim &S, const DevParams &P, double tau, int blocks, cudaStream_t st) {
+  k_bs<BS_WIDE_THREADS, BS_GWIDE><<<blocks < 1 ? 1 : blocks, BS_WIDE_THREADS, sizeof(BsSharedT<BS_GWIDE>), st>>>(
+      S, P, tau, BS_GMAX + 1, 0x7fffffff, 3, 1);
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -77,7 +77,7 @@ struct Sim {
   int *gsize;                    // batched groups: member count per group (gstart = first member)
   int *gtotal;                   // batched groups: members placed so far
   unsigned *bsq;                 // batched groups: next group of queue 0 (1-2 members, pair kernel), queue 1
-                                 // (3 .. BS_SMALL members) and queue 2 (larger)
+                                 // (3 .. BS_SMALL members), queue 2 (up to BS_GMAX) and queue 3 (larger)
   int *gorder, *norder;          // batched groups: queue qi is region qi of gorder (npad entries): norder[2 qi]
                                  // groups expected to need many substeps from its front, norder[2 qi + 1]
                                  // from its back

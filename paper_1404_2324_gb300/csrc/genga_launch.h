@@ -34,9 +34,15 @@ void launch_b_eject(const Sim &S, const DevParams &P, cudaStream_t st);
 void launch_tp_eject(const TPSet &T, const DevParams &P, cudaStream_t st);
 // bs.cu
 void bs_init_constants();  // once per device, before any capture
-// Groups of at least gsplit members are skipped (left to the cluster kernel); BS_GMAX + 1: none.
+// Groups of at least gsplit members are skipped (left to the cluster or the wide kernel); without
+// gsplit every group above BS_GMAX members is reported (GROUP_TOO_LARGE).
 void launch_bs(const Sim &S, const DevParams &P, double tau, int max_groups, cudaStream_t st,
-               int gsplit = BS_GMAX + 1, int gmin = 1);
+               int gsplit = 0x7fffffff, int gmin = 1);
+// groups of BS_GMAX + 1 .. BS_GWIDE members, one 512-thread CTA each (larger ones reported): batched
+// queue 3, else the large-group list of the grouping kernel
+constexpr int BS_GWIDE = 64;
+constexpr int BS_WIDE_THREADS = 512;
+void launch_bs_wide(const Sim &S, const DevParams &P, double tau, int blocks, cudaStream_t st);
 // batched mode: groups of 3 .. BS_SMALL members from BS queue 1, 128-thread CTAs (launch_bs takes
 // queue 2 there)
 void launch_bs_small(const Sim &S, const DevParams &P, double tau, int blocks, cudaStream_t st);

@@ -1,8 +1,8 @@
 """Large encounter groups on the GPU: groups of 5 or more members are integrated by the cluster BS
 kernel (one thread-block cluster per group, one CTA per extrapolation level), smaller ones by the
-one-CTA kernel. A compact swarm puts one large group through the cluster kernel; its result must
-follow the oracle like any other group (Sect. 3.2, Bulirsch-Stoer). A group above the in-kernel
-cap of 32 members is reported, not integrated.
+one-CTA kernel, groups of 33 to 64 members by the wide one-CTA kernel (512 threads). A compact
+swarm puts one large group through these kernels; its result must follow the oracle like any
+other group (Sect. 3.2, Bulirsch-Stoer). A group above 64 members is reported, not integrated.
 """
 import numpy as np
 import pytest
@@ -76,8 +76,54 @@ def test_group_of_thirty_two_members():
         o.close()
 
 
+@pytest.mark.parametrize("n_swarm", [40, 64])
+def test_groups_above_thirty_two_members(n_swarm):
+    d = swarm(n_swarm, n_far=4, seed=24 + n_swarm, spread=0.003)
+    g, o = _pair(d, 2)
+    try:
+        g.step(1)
+        o.step(1)
+        assert max(len(k) for k in o.groups(0)) == n_swarm
+        err, same = rel_state_error(g, o)
+        assert same and err <= 1e-12, err
+        code, cnt = g.status()
+        assert code & (genga.ST_BS_FAILED | genga.ST_GROUP_TOO_LARGE) == 0
+        assert cnt["bs_steps"] == o.stats()["bs_steps"]
+    finally:
+        g.close()
+        o.close()
+
+
+def test_large_group_in_a_batched_system():
+    """A batched system of 48 bodies, 40 of them in one swarm (queue 3, the wide kernel), next to
+    two ordinary systems."""
+    ds = [swarm(40, n_far=8, seed=30, spread=0.003), swarm(3, n_far=5, seed=31), swarm(2, n_far=10, seed=32)]
+    off = np.cumsum([0] + [len(d["m"]) for d in ds])
+    cat = {k: np.concatenate([d[k] for d in ds]) for k in ("m", "R", "x", "v")}
+    h = genga.genga_init_batch(off, np.ones(3), cat["m"], cat["R"], cat["x"], cat["v"], ds[0]["G"], ds[0]["dt"], 2, 1)
+    try:
+        genga.genga_step(h, 1)
+        gs = genga.genga_get_state_batch(h, off[-1])
+        code, _ = genga.genga_status(h)
+        assert code & (genga.ST_BS_FAILED | genga.ST_GROUP_TOO_LARGE) == 0
+        for s, d in enumerate(ds):
+            o = O.Sim(O.params(G=d["G"], m0=d["m0"], dt=d["dt"], order=2), d["m"], d["R"], d["x"], d["v"])
+            o.step(1)
+            if s == 0:
+                assert max(len(k) for k in o.groups(0)) == 40
+            st = o.state()
+            sl = slice(off[s], off[s + 1])
+            assert np.array_equal(gs["alive"][sl], st["alive"])
+            live = st["alive"] == 1
+            e = np.linalg.norm(gs["x"][sl][live] - st["x"][live], axis=1) / np.linalg.norm(st["x"][live], axis=1)
+            assert e.max() <= 1e-12, (s, e.max())
+            o.close()
+    finally:
+        genga.genga_free(h)
+
+
 def test_group_above_the_cap_is_reported():
-    d = swarm(40, n_far=4, seed=23, spread=0.003)
+    d = swarm(80, n_far=4, seed=23, spread=0.003)
     m, R, x, v = with_central(d)
     g = genga.Genga(m, R, x, v, d["G"], d["dt"], 2)
     try:
