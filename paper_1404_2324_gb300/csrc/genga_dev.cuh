@@ -16,7 +16,7 @@ typedef unsigned long long u64;
 constexpr int TILE = 32;          // bodies per kick tile (one per lane)
 constexpr int NMAX = 2048;        // main mode: up to 2048 massive bodies (Sect. 3)
 constexpr int BS_LEVELS = 8;      // Bulirsch-Stoer levels, substep sequence n_k = 2k
-constexpr int BS_GMAX = 32;       // largest encounter group integrated in one CTA
+constexpr int BS_GMAX = 32;       // largest group of the 256-thread BS kernel and the cluster kernel
 constexpr int BS_THREADS = 256;
 constexpr int BS_HEAVY = 2;      // batched: groups with a member that needed >= 2 BS_HEAVY substeps last time go first
 constexpr int BS_SMALL = 4;      // batched: groups of 3 .. BS_SMALL members run on 128-thread CTAs
