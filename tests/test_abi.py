@@ -51,6 +51,10 @@ def test_invalid_arguments_are_rejected_on_the_host():
     assert not h.value
     p = genga.genga_default_params()
     assert (p.n1, p.n2, p.pc, p.bs_kmax) == (3.0, 0.4, 3.0, 8)
+    assert (p.rcut, p.rcut_sun, p.nmin) == (0.0, 0.0, 0)  # ejections and the Nmin stop are off by default
+    n = ctypes.c_int(-1)
+    assert L.genga_ejections(None, None, 0, ctypes.byref(n)) == genga.GENGA_EINVAL
+    assert L.genga_set_params(None, ctypes.byref(p)) == genga.GENGA_EINVAL
 
 
 def _c_layout(tmp_path, header, struct, fields):
