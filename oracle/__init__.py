@@ -81,6 +81,7 @@ def lib():
                 "orc_energy": (C.c_double, [C.c_int, _P, _D, _I, _D, _D]),
                 "orc_bs_group": (C.c_int, [C.c_int, _P, C.c_int, _I, C.c_double, _D, _D, _I, _D,
                                            _D, _D, _D, _I, _I, C.c_int, _I]),
+                "orc_substep_weights": (C.c_int, [C.c_int, _D]),
                 "orc_create": (C.c_void_p, [C.c_int, _P, _D, _D, _D, _D]),
                 "orc_free": (None, [C.c_void_p]),
                 "orc_step": (C.c_int, [C.c_void_p, C.c_int]),
@@ -257,6 +258,13 @@ def bs_group(p: Params, idx, tau, m, R, alive, x, v, rc):
                             C.byref(steps))
     return dict(x=x, v=v, m=m, R=R, alive=alive, U=U.value, status=st,
                 collisions=coll[: 2 * nc.value].reshape(-1, 2), bs_steps=steps.value)
+
+
+def substep_weights(order):
+    """The oracle's composition weights (Sect. 2.3): substep j of a full step has length w[j] tau."""
+    w, pw = _dout(7)
+    k = lib().orc_substep_weights(int(order), pw)
+    return w[:k].copy()
 
 
 # ---------------------------------------------------------------- whole simulation

@@ -658,7 +658,7 @@ struct orc_sim {
 
 /* Substep weights: 2nd order is Eq. z1 itself; 4th order is S(w1 t) S(w0 t) S(w1 t) with
  * w1 = 1/(2 - 2^(1/3)), w0 = -2^(1/3)/(2 - 2^(1/3)); 6th order is Yoshida's (1990) solution A. */
-static int substep_weights(int order, double *w) {
+int orc_substep_weights(int order, double *w) {
   if (order == 4) {
     double c = cbrt(2.0);
     w[0] = w[2] = 1.0 / (2.0 - c);
@@ -845,7 +845,7 @@ int orc_get_ejections(const orc_sim *s, double *rec, int cap) {
 int orc_step(orc_sim *s, int nsteps) {
   int n = s->n, st = 0;
   double w[ORC_MAXSUB];
-  int nsub = substep_weights(s->p.order, w);
+  int nsub = orc_substep_weights(s->p.order, w);
   for (int it = 0; it < nsteps; it++) {
     /* critical radii once per full step, from the state at its start */
     orc_rcrit(n, &s->p, fabs(s->p.dt), s->m, s->alive, s->x, s->v, s->rc);
@@ -1277,7 +1277,7 @@ int orc_tp_step(orc_tpsim *T, int nsteps) {
   orc_sim *s = T->s;
   int n = s->n, st = 0;
   double w[ORC_MAXSUB];
-  int nsub = substep_weights(s->p.order, w);
+  int nsub = orc_substep_weights(s->p.order, w);
   for (int it = 0; it < nsteps; it++) {
     orc_rcrit(n, &s->p, fabs(s->p.dt), s->m, s->alive, s->x, s->v, s->rc);
     tp_rcrit(T);

@@ -78,6 +78,10 @@ int orc_bs_group(int n, const orc_params *p, int g, const int *idx, double tau, 
                  double *R, int *alive, double *x, double *v, const double *rc, double *U,
                  int *ncoll, int *coll_pairs, int coll_cap, int *bs_steps);
 
+/* Sect. 2.3: substep weights w[0..k-1] of the composition of order 2 (k = 1, Eq. z1), 4 (k = 3) or
+ * 6 (k = 7, Yoshida's solution A); substep j has the signed length w[j] * tau. Returns k. */
+int orc_substep_weights(int order, double *w);
+
 /* ---- whole simulation (main mode) ---- */
 typedef struct orc_sim orc_sim;
 orc_sim *orc_create(int n, const orc_params *p, const double *m, const double *R, const double *xh,

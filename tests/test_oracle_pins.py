@@ -434,11 +434,64 @@ def _sim(d, **kw):
 
 
 def test_yoshida_weights_golden():
+    """The oracle's substep weights (Sect. 2.3) equal Yoshida's (1990) published values, which in
+    turn satisfy the order conditions of a symmetric composition of a symmetric 2nd-order step:
+    sum w = 1, sum w^3 = 0 (order 4) and sum w^5 = 0 (order 6). A weight mistyped in its 8th digit
+    misses the golden row at 1e-14 and leaves sum w^3 ~ 1e-8."""
     rows = {r[0]: [float(s) for s in r[1:]] for r in _load_golden("yoshida.txt")}
     c = 2 ** (1 / 3)
     assert rows["order4"] == pytest.approx([1 / (2 - c), -c / (2 - c), 1 / (2 - c)], rel=1e-15)
-    assert sum(rows["order4"]) == pytest.approx(1.0, rel=1e-15)
-    assert sum(rows["order6"]) == pytest.approx(1.0, rel=1e-14)
+    for order in (4, 6):
+        w = np.array(rows[f"order{order}"])
+        assert abs(w.sum() - 1.0) < 1e-14
+        assert abs((w ** 3).sum()) < 1e-13
+        if order == 6:
+            assert abs((w ** 5).sum()) < 1e-13
+        assert list(w) == list(w[::-1])  # symmetric sequence
+        np.testing.assert_allclose(O.substep_weights(order), w, rtol=1e-14, atol=0)
+    assert list(O.substep_weights(2)) == [1.0]
+
+
+def _composed_leapfrog_error(w, h_list, mp):
+    """Global error at t = 1 of the pendulum q'' = -sin q (q, p = 1, 0.3) integrated by the
+    composition of leapfrog steps with weights w, in 40-digit arithmetic, against mpmath's Taylor
+    integrator. Leapfrog is symmetric and of order 2, so the composition has the order of w."""
+    mp.mp.dps = 40
+    f = mp.odefun(lambda t, y: [y[1], -mp.sin(y[0])], 0, [mp.mpf(1), mp.mpf("0.3")])
+    qr, pr = f(1)
+    errs = []
+    for h in h_list:
+        n = int(round(1.0 / h))
+        hh = mp.mpf(1) / n
+        q, p = mp.mpf(1), mp.mpf("0.3")
+        for _ in range(n):
+            for wk in w:
+                s = wk * hh
+                p -= s / 2 * mp.sin(q)
+                q += s * p
+                p -= s / 2 * mp.sin(q)
+        errs.append(abs(q - qr) + abs(p - pr))
+    return [float(errs[k] / errs[k + 1]) for k in range(len(errs) - 1)]
+
+
+def test_sixth_order_weights_give_sixth_order_convergence():
+    """The oracle's 6th-order weights, used in a composition of a symmetric 2nd-order step, give a
+    global error that falls by 2^6 = 64 per halving of the step down to h = 1/40 (40 digits, so
+    rounding plays no part). A weight off by 1e-8 leaves an O(h^2) error of ~1e-8 h^2, which takes
+    over at these steps (the planted-mistake test below)."""
+    mp = pytest.importorskip("mpmath")
+    w = [mp.mpf(float(x)) for x in O.substep_weights(6)]
+    ratios = _composed_leapfrog_error(w, (0.2, 0.1, 0.05, 0.025), mp)
+    assert all(58.0 < r < 70.0 for r in ratios), ratios
+
+
+def test_sixth_order_convergence_check_detects_an_eighth_digit_error():
+    mp = pytest.importorskip("mpmath")
+    w = [mp.mpf(float(x)) for x in O.substep_weights(6)]
+    w[2] = w[4] = w[2] * (1 + mp.mpf("1e-8"))  # plant the mistake in a copy of the weights
+    w[3] = 1 - 2 * (w[0] + w[1] + w[2])
+    ratios = _composed_leapfrog_error(w, (0.05, 0.025), mp)
+    assert not (58.0 < ratios[0] < 70.0), ratios
 
 
 def test_single_massless_body_step_is_exact_kepler_orbit():
@@ -499,11 +552,13 @@ def test_angular_momentum_conserved_with_encounters():
 
 
 def test_energy_error_scaling_with_order():
-    """Encounter-free system: halving tau divides the energy error by ~4 (2nd) and ~16 (4th)."""
+    """Encounter-free system: halving tau divides the energy error by ~4 (2nd), ~16 (4th) and ~64
+    (6th order: at tau = 8 and 4 days, and 16 and 8 days, the errors stay above rounding)."""
     base = _far_planets(3, seed=18)
-    for order, expect in ((2, 4.0), (4, 16.0)):
+    for order, expect, dts in ((2, 4.0, (8.0, 4.0)), (4, 16.0, (8.0, 4.0)), (6, 64.0, (8.0, 4.0)),
+                               (6, 64.0, (16.0, 8.0))):
         errs = []
-        for dt in (8.0, 4.0):
+        for dt in dts:
             d = dict(base, dt=dt, order=order)
             s = _sim(d)
             E0, _ = s.energy()
