@@ -45,11 +45,14 @@ extern "C" {
 #define GENGA_ST_KEPLER_FALLBACK 1   /* a Kepler solve did not converge; that body went to BS */
 #define GENGA_ST_BS_FAILED 2         /* a BS group exceeded its step-halving cap (state kept) */
 #define GENGA_ST_REUSE_FULLKICK 4    /* rcrit grew past pc*rcrit_old: the opening kick was recomputed */
-#define GENGA_ST_GROUP_TOO_LARGE 8   /* an encounter group of more than 64 members (its state kept, not integrated) */
+#define GENGA_ST_GROUP_TOO_LARGE 8   /* a group above the size its mode integrates (64 members in the batched
+                                        mode and the differentiable engine; its state kept, not integrated) */
 #define GENGA_ST_UNION_ROUNDS 16     /* grouping did not reach its fixpoint within its round cap */
 #define GENGA_ST_RECORD_OVERFLOW 32  /* adjoint engine: a recording buffer was too small (gradient invalid) */
 #define GENGA_ST_EJECT_OVERFLOW 64   /* more than 4096 ejection records (later ones dropped), or more than
                                         1024 bodies out of bounds in one step (the rest leave next step) */
+#define GENGA_ST_GRID_TIMEOUT 128    /* the grid-wide BS of a group above 32 members gave up waiting at one of
+                                        its grid barriers (its group keeps the state it had) */
 
 /* modes of genga_init (Sect. 3): main mode with up to 2048 massive bodies */
 #define GENGA_MODE_MASSIVE 0

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libgenga.so")
-SOURCES = ["kick.cu", "step.cu", "bs.cu", "bs_cluster.cu", "io.cu", "batch.cu", "tp.cu", "eject.cu", "adjoint.cu", "api.cu",
+SOURCES = ["kick.cu", "step.cu", "bs.cu", "bs_cluster.cu", "bs_grid.cu", "io.cu", "batch.cu", "tp.cu", "eject.cu", "adjoint.cu", "api.cu",
            "noalloc.cu"]
 HEADERS = ["genga_dev.cuh", "genga_launch.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -87,6 +87,16 @@ bool alloc_sim(Sim &S, DevMem &mem, int n, int nsub) {
   S.flags = mem.get<int>(4); S.status = mem.get<int>(1);
   S.counters = mem.get<long long>(NCOUNTERS); S.U = mem.get<double>(1);
   S.ejrec = mem.get<double>(8 * (size_t)EJ_CAP); S.nej = mem.get<int>(1);
+  // grid-wide BS of one large group at a time (up to npad members)
+  BsGridBuf &B = S.gb;
+  B.pos = mem.get<double>(2 * BS_LEVELS * np * 3);
+  B.za = mem.get<double>(BS_LEVELS * np * 6); B.zb = mem.get<double>(BS_LEVELS * np * 6);
+  B.t1 = mem.get<double>(BS_LEVELS * np * 6); B.prev = mem.get<double>(np * 6 * BS_LEVELS);
+  B.y = mem.get<double>(2 * np * 6); B.isc = mem.get<double>(np * 2);
+  B.idx = mem.get<int>(np); B.alive = mem.get<int>(np);
+  B.gm = mem.get<double>(np); B.m = mem.get<double>(np); B.R = mem.get<double>(np); B.A = mem.get<double>(np);
+  B.rcsq = mem.get<u64>(np); B.err = mem.get<u64>(2 * BS_LEVELS); B.bar = mem.get<unsigned>(4);
+  B.cont = mem.get<int>(GR_CONTACT_CAP); B.ncont = mem.get<int>(1);
   if (mem.err != cudaSuccess) return false;
   cudaMemcpy(S.items, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice);
   return cudaGetLastError() == cudaSuccess;
@@ -155,7 +165,8 @@ struct genga_ctx {
   cudaStream_t side2 = nullptr;
   cudaEvent_t ev_join2 = nullptr;
   int small_grid = 0;
-  int wide_grid = 8;  // CTAs of the wide BS kernel (groups of BS_GMAX + 1 .. BS_GWIDE members: rare)
+  int wide_grid = 8;  // CTAs of the wide BS kernel (batched groups of BS_GMAX + 1 .. BS_GWIDE members: rare)
+  int grid_blocks = 1;  // CTAs of the grid-wide BS kernel (main mode: groups above BS_GMAX members)
   bool profiling = false;
   // batched mode
   bool batched = false;
@@ -284,14 +295,14 @@ void enqueue_step(genga_ctx *c, cudaStream_t st) {
     if (tp) launch_planet_table(S, T, P, tau, st);
     launch_encounter(S, tau, S.ebm + (size_t)j * S.npad * S.W, st);
     launch_group(S, st, c->side ? c->gsplit : BS_GMAX + 1);
-    if (c->side) {  // fork: cluster kernel for the larger groups, one-CTA kernel for the rest and
-                    // the wide kernel for groups above BS_GMAX members (its CTAs leave at once when
-                    // the large-group list holds none); join
+    if (c->side) {  // fork: cluster kernel for the groups of gsplit .. BS_GMAX members, one-CTA
+                    // kernel for the smaller ones and the grid-wide kernel for groups above BS_GMAX
+                    // members (its CTAs leave at once when the large-group list holds none); join
       cudaEventRecord(c->ev_fork, st);
       cudaStreamWaitEvent(c->side, c->ev_fork, 0);
       cudaStreamWaitEvent(c->side2, c->ev_fork, 0);
       launch_bs_cluster(S, P, tau, c->gsplit, c->cl_grid, c->side);
-      launch_bs_wide(S, P, tau, c->wide_grid, c->side2);
+      launch_bs_grid(S, P, tau, BS_GMAX + 1, c->grid_blocks, c->side2);
       launch_bs(S, P, tau, c->bs_grid, st, c->gsplit);
       cudaEventRecord(c->ev_join, c->side);
       cudaEventRecord(c->ev_join2, c->side2);
@@ -417,6 +428,8 @@ int genga_init(genga_ctx **out, int n, const double *masses, const double *radii
   }
   c->gsplit = 5;  // measured: from 5 members on, a cluster per group beats one CTA per group
   c->cl_grid = bs_cluster_grid();
+  bs_grid_init_constants();
+  c->grid_blocks = bs_grid_blocks();
   cudaStream_t st = c->stream;
   if (cudaMemcpyAsync(c->sx, x, 3 * nn * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync(c->sv, v, 3 * nn * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
@@ -1034,14 +1047,28 @@ int genga_phase_bs(int n, double G, double m0, double tau, double bs_eps, int bs
   soa_copy(S.x0, S.npad, x, n, n, st);
   soa_copy(S.v0, S.npad, v, n, n, st);
   cudaMemcpyAsync(S.ngroups, &ngroups, sizeof(int), cudaMemcpyHostToDevice, st);
+  // the main mode's routing by size: one CTA per group below 5 members, a cluster per group of 5 to
+  // BS_GMAX members, the grid-wide kernel above
+  std::vector<int> gs(ngroups + 1, 0), big;
   if (ngroups > 0) {
-    int nm = 0;
-    cudaMemcpyAsync(&nm, group_start + ngroups, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(gs.data(), group_start, (ngroups + 1) * sizeof(int), cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
+    const int nm = gs[ngroups];
+    if (nm < 0 || nm > n) { mem.release(); return GENGA_EINVAL; }
     cudaMemcpyAsync(S.gstart, group_start, (ngroups + 1) * sizeof(int), cudaMemcpyDeviceToDevice, st);
     if (nm > 0) cudaMemcpyAsync(S.gmem, members, nm * sizeof(int), cudaMemcpyDeviceToDevice, st);
+    for (int k = 0; k < ngroups; ++k)
+      if (gs[k + 1] - gs[k] >= 5) big.push_back(k);
   }
-  launch_bs(S, P, tau, 2 * num_sms(), st);
+  const int nbig = (int)big.size();
+  cudaMemcpyAsync(S.nbig, &nbig, sizeof(int), cudaMemcpyHostToDevice, st);
+  if (nbig > 0) cudaMemcpyAsync(S.big, big.data(), nbig * sizeof(int), cudaMemcpyHostToDevice, st);
+  bs_cluster_init_constants();
+  bs_grid_init_constants();
+  launch_bs(S, P, tau, 2 * num_sms(), st, 5);
+  launch_bs_cluster(S, P, tau, 5, bs_cluster_grid(), st);
+  launch_bs_grid(S, P, tau, BS_GMAX + 1, bs_grid_blocks(), st);
+  cudaStreamSynchronize(st);  // the host vectors above outlive the copies
   soa_copy(x, n, S.x, S.npad, n, st);
   soa_copy(v, n, S.v, S.npad, n, st);
   cudaMemcpyAsync(m, S.m, n * sizeof(double), cudaMemcpyDeviceToDevice, st);

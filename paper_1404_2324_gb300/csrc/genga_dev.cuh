@@ -33,6 +33,7 @@ constexpr int ST_GROUP_TOO_LARGE = 8;
 constexpr int ST_UNION_ROUNDS = 16;
 constexpr int ST_RECORD_OVERFLOW = 32;  // a recording buffer of the adjoint engine was too small
 constexpr int ST_EJECT_OVERFLOW = 64;   // more ejections than EJ_CAP records, or than EJ_STEP in one step
+constexpr int ST_GRID_TIMEOUT = 128;    // the grid-wide BS kernel gave up waiting at a grid barrier
 constexpr int EJ_CAP = 4096;            // ejection records kept (8 doubles each)
 constexpr int EJ_STEP = 1024;           // bodies one step can remove in the single-system modes
 
@@ -47,6 +48,24 @@ struct DevParams {
   double rcut2, rcut_sun2;  // Sect. 3.2, Ejections: squared limits on |x|; 0: that test is off
   int nmin;                 // batched: a system left with fewer live bodies is stopped; 0: off
 };
+
+// Scratch of the grid-wide Bulirsch-Stoer kernel (bs_grid.cu) for one large group at a time; member
+// arrays hold up to npad members, chain arrays are [level][member][component].
+struct BsGridBuf {
+  double *pos;             // [2][BS_LEVELS][npad][3] midpoint positions, double-buffered by round
+  double *za, *zb;         // [BS_LEVELS][npad][6] the two newest states of each level's midpoint chain
+  double *t1;              // [BS_LEVELS][npad][6] T_{L,1}: level L's modified-midpoint result
+  double *prev;            // [npad][6][BS_LEVELS] the newest Neville row of each (member, component)
+  double *y;               // [2][npad][6] state at the attempt start / the newest diagonal T_{L,L}
+  double *isc;             // [npad][2] 1/|x|, 1/|v| at the attempt start (error scales)
+  int *idx, *alive;        // [npad] member -> body, live flag
+  double *gm, *m, *R, *A;  // [npad]
+  u64 *rcsq;               // [npad]
+  u64 *err;                // [2][BS_LEVELS] per-level error maxima, by attempt parity
+  unsigned *bar;           // grid barrier: arrivals, generation, abort flag
+  int *cont, *ncont;       // contact pairs of an accepted substep (key a * npad + b), their count
+};
+constexpr int GR_CONTACT_CAP = 4096;
 
 // All per-body arrays are SoA with leading dimension npad (a multiple of 32); vectors are stored
 // component-major: x[c * npad + i].
@@ -98,6 +117,7 @@ struct Sim {
   double *U;                     // internal energy of mergers and ejections
   double *ejrec;                 // ejection records [EJ_CAP * 8]: index, step, heliocentric x, v
   int *nej;                      // ejections so far (may exceed EJ_CAP: records past it are dropped)
+  BsGridBuf gb;                  // grid-wide BS of the largest groups (single-system modes; null otherwise)
 };
 
 // Test particles (massless, perturbed by the massive bodies of a Sim; Sect. 3.3). SoA with

@@ -48,6 +48,11 @@ void launch_bs_wide(const Sim &S, const DevParams &P, double tau, int blocks, cu
 void launch_bs_small(const Sim &S, const DevParams &P, double tau, int blocks, cudaStream_t st);
 // groups of one or two members, one warp each (no adjoint recording)
 void launch_bs_pair(const Sim &S, const DevParams &P, double tau, int blocks, cudaStream_t st);
+// bs_grid.cu: the groups of the large-group list with gmin or more members, one after another on
+// the whole GPU (single-system modes; needs Sim::gb)
+void bs_grid_init_constants();  // once per device, before any capture
+int bs_grid_blocks();
+void launch_bs_grid(const Sim &S, const DevParams &P, double tau, int gmin, int blocks, cudaStream_t st);
 // bs_cluster.cu: groups of gmin .. BS_GMAX members, one cluster of 8 CTAs (one per level) each
 void bs_cluster_init_constants();  // once per device, before any capture
 int bs_cluster_grid();

@@ -29,6 +29,8 @@ ST_REUSE_FULLKICK = 4
 ST_GROUP_TOO_LARGE = 8
 ST_RECORD_OVERFLOW = 32
 ST_UNION_ROUNDS = 16
+ST_EJECT_OVERFLOW = 64
+ST_GRID_TIMEOUT = 128
 COUNTER_NAMES = ["steps", "candidates", "encounters", "groups", "bs_steps", "kepler_fallbacks",
                  "mergers", "full_kicks"]
 

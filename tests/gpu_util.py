@@ -60,3 +60,31 @@ def rel_state_error(g, o):
     ex = np.linalg.norm(gs["x"][1:][live] - os_["x"][live], axis=1) / np.linalg.norm(os_["x"][live], axis=1)
     ev = np.linalg.norm(gs["v"][1:][live] - os_["v"][live], axis=1) / np.linalg.norm(os_["v"][live], axis=1)
     return max(ex.max(), ev.max()), same_alive
+
+
+def oracle_sensitivity(d, order, steps, trials=3, eps=1e-15, **params):
+    """How far the oracle itself moves after `steps` steps when its initial positions are perturbed
+    by eps (relative, random directions): the rounding amplification of the system's close passes.
+    Returns the largest relative state change over `trials` perturbations."""
+    op = O.params(G=d["G"], m0=d["m0"], dt=d["dt"], order=order)
+    for k, val in params.items():
+        if hasattr(op, k):
+            setattr(op, k, val)
+    base = O.Sim(op, d["m"], d["R"], d["x"], d["v"])
+    base.step(steps)
+    a = base.state()
+    base.close()
+    live = a["alive"] == 1
+    worst = 0.0
+    for k in range(trials):
+        rng = np.random.default_rng(1000 + k)
+        x = d["x"] * (1.0 + eps * rng.standard_normal(d["x"].shape))
+        o = O.Sim(op, d["m"], d["R"], x, d["v"])
+        o.step(steps)
+        b = o.state()
+        o.close()
+        both = live & (b["alive"] == 1)
+        ex = np.linalg.norm(a["x"][both] - b["x"][both], axis=1) / np.linalg.norm(a["x"][both], axis=1)
+        ev = np.linalg.norm(a["v"][both] - b["v"][both], axis=1) / np.linalg.norm(a["v"][both], axis=1)
+        worst = max(worst, ex.max(), ev.max())
+    return worst

@@ -1,15 +1,18 @@
-"""Large encounter groups on the GPU: groups of 5 or more members are integrated by the cluster BS
-kernel (one thread-block cluster per group, one CTA per extrapolation level), smaller ones by the
-one-CTA kernel, groups of 33 to 64 members by the wide one-CTA kernel (512 threads). A compact
-swarm puts one large group through these kernels; its result must follow the oracle like any
-other group (Sect. 3.2, Bulirsch-Stoer). A group above 64 members is reported, not integrated.
+"""Large encounter groups on the GPU (Sect. 3.2, Bulirsch-Stoer). In the main mode groups of 5 to 32
+members are integrated by the cluster BS kernel (one thread-block cluster per group, one CTA per
+extrapolation level), smaller ones by the one-CTA kernel, and larger ones by the grid-wide kernel
+(every SM on one group, step control on the device: the paper's split path for groups above 128
+members). In the batched mode groups of 33 to 64 members take the wide one-CTA kernel. A compact
+swarm puts one large group through these kernels; its result must follow the oracle like any other
+group. The 2048-body disk with a large velocity term in the critical radius (n2 = 0.7 and 1.5, the
+paper's Sect. 5) forms groups of tens to hundreds of members.
 """
 import numpy as np
 import pytest
 
 import oracle as O
 from paper_1404_2324_gb300 import genga, ics
-from tests.gpu_util import rel_state_error, with_central
+from tests.gpu_util import oracle_sensitivity, pair_sims, rel_state_error, with_central
 
 pytestmark = pytest.mark.gpu
 
@@ -76,8 +79,11 @@ def test_group_of_thirty_two_members():
         o.close()
 
 
-@pytest.mark.parametrize("n_swarm", [40, 64])
+@pytest.mark.parametrize("n_swarm", [40, 64, 100, 200])
 def test_groups_above_thirty_two_members(n_swarm):
+    """Groups of 40 to 200 members on the grid-wide kernel. The denser swarms are chaotic over one
+    step (the 200-member one needs 20 BS substeps): the oracle started 1e-15 away moves by up to
+    ~3e-11. The bound is 1e-12, or 10x that measured self-sensitivity where it is larger (printed)."""
     d = swarm(n_swarm, n_far=4, seed=24 + n_swarm, spread=0.003)
     g, o = _pair(d, 2)
     try:
@@ -85,10 +91,42 @@ def test_groups_above_thirty_two_members(n_swarm):
         o.step(1)
         assert max(len(k) for k in o.groups(0)) == n_swarm
         err, same = rel_state_error(g, o)
-        assert same and err <= 1e-12, err
+        sens = oracle_sensitivity(d, 2, 1)
+        print(f"swarm {n_swarm}: GPU vs oracle {err:.2e}, oracle self-sensitivity {sens:.2e}")
+        assert same and err <= max(1e-12, 10.0 * sens), (err, sens)
         code, cnt = g.status()
-        assert code & (genga.ST_BS_FAILED | genga.ST_GROUP_TOO_LARGE) == 0
+        assert code & (genga.ST_BS_FAILED | genga.ST_GROUP_TOO_LARGE | genga.ST_GRID_TIMEOUT) == 0
+        ob = o.stats()["bs_steps"]
+        if sens <= 1e-12:
+            assert cnt["bs_steps"] == ob
+        else:  # chaotic: a decision at the tolerance may flip; the counts stay close
+            assert abs(cnt["bs_steps"] - ob) <= 0.1 * ob, (cnt["bs_steps"], ob)
+    finally:
+        g.close()
+        o.close()
+
+
+@pytest.mark.parametrize("n2,order", [(0.7, 2), (1.5, 2), (1.5, 4)])
+def test_disk2048_giant_groups(n2, order):
+    """n2 = 0.7 joins 76 bodies of the 2048-body disk into one group in the first substep, n2 = 1.5
+    joins 682 (Sect. 5: large n2 forms one big group). One step within 1e-12 of the oracle, ten
+    within 1e-11 (the oracle itself moves by 2e-13 when its start is perturbed by 1e-15)."""
+    d = ics.disk2048(1)
+    g, o = pair_sims(d, order, n2=n2)
+    try:
+        g.step(1)
+        o.step(1)
+        assert max(len(k) for k in o.groups(0)) >= 70
+        err, same = rel_state_error(g, o)
+        assert same and err <= 1e-12, err
+        g.step(9)
+        o.step(9)
+        err, same = rel_state_error(g, o)
+        assert same and err <= 1e-11, err
+        code, cnt = g.status()
+        assert code & (genga.ST_BS_FAILED | genga.ST_GROUP_TOO_LARGE | genga.ST_GRID_TIMEOUT) == 0, code
         assert cnt["bs_steps"] == o.stats()["bs_steps"]
+        assert cnt["groups"] == o.stats()["groups"]
     finally:
         g.close()
         o.close()
@@ -122,12 +160,20 @@ def test_large_group_in_a_batched_system():
         genga.genga_free(h)
 
 
-def test_group_above_the_cap_is_reported():
-    d = swarm(80, n_far=4, seed=23, spread=0.003)
-    m, R, x, v = with_central(d)
-    g = genga.Genga(m, R, x, v, d["G"], d["dt"], 2)
+def test_no_group_size_is_too_large_in_the_main_mode():
+    """A 300-member swarm with its neighbours: integrated, never reported as too large."""
+    d = swarm(300, n_far=4, seed=23, spread=0.004)
+    g, o = _pair(d, 2)
     try:
         g.step(1)
-        assert g.status()[0] & genga.ST_GROUP_TOO_LARGE
+        o.step(1)
+        assert max(len(k) for k in o.groups(0)) == 300
+        code, _ = g.status()
+        assert code & (genga.ST_GROUP_TOO_LARGE | genga.ST_GRID_TIMEOUT) == 0, code
+        err, same = rel_state_error(g, o)
+        sens = oracle_sensitivity(d, 2, 1)
+        print(f"swarm 300: GPU vs oracle {err:.2e}, oracle self-sensitivity {sens:.2e}")
+        assert same and err <= max(1e-12, 10.0 * sens), (err, sens)
     finally:
         g.close()
+        o.close()

@@ -186,6 +186,75 @@ def test_bs_groups_match_oracle(kmode):
     np.testing.assert_allclose(aos(V), ref_v, rtol=0, atol=1e-11 * np.abs(ref_v).max())
 
 
+def _clumps(sizes, seed, spread=0.004, R=None):
+    """One tight clump per entry of sizes (each one encounter group), spaced around 1 AU."""
+    rng = np.random.default_rng(seed)
+    xs, vs, ms, groups, k = [], [], [], [], 0
+    for g, sz in enumerate(sizes):
+        ang = 2 * np.pi * g / len(sizes)
+        c = np.array([np.cos(ang), np.sin(ang), 0.0])
+        vc = np.sqrt(ics.G_GAUSS) * np.array([-np.sin(ang), np.cos(ang), 0.0])
+        xs.append(c + rng.normal(0, spread, (sz, 3)) * [1.0, 1.0, 0.2])
+        vs.append(vc + rng.normal(0, 2e-5, (sz, 3)))
+        ms.append(np.exp(rng.uniform(np.log(1e-10), np.log(1e-9), sz)))
+        groups.append(list(range(k, k + sz)))
+        k += sz
+    m = np.concatenate(ms)
+    Rr = ics.radius_from_mass(m) * 1e-3 if R is None else np.full(len(m), R)
+    return np.vstack(xs), np.vstack(vs), m, Rr, groups
+
+
+def _bs_phase_vs_oracle(x, v, m, R, groups, kmode=0):
+    n = len(m)
+    alive = np.ones(n, np.int32)
+    p = O.params(G=ics.G_GAUSS, m0=1.0, kmode=kmode)
+    rc = np.full(n, 0.02)
+    ref = dict(x=x.copy(), v=v.copy(), m=m.copy(), R=R.copy(), alive=alive.copy(), U=0.0, steps=0, coll=0)
+    for gi in groups:
+        out = O.bs_group(p, gi, 6.0, ref["m"], ref["R"], ref["alive"], ref["x"], ref["v"], rc)
+        assert out["status"] == 0
+        for k in ("x", "v", "m", "R", "alive"):
+            ref[k] = out[k]
+        ref["U"] += out["U"]
+        ref["steps"] += out["bs_steps"]
+        ref["coll"] += len(out["collisions"])
+    gstart = np.concatenate([[0], np.cumsum([len(g) for g in groups])]).astype(np.int32)
+    members = np.concatenate(groups).astype(np.int32)
+    X, V, M, RR, AL = soa(x), soa(v), dev(m), dev(R), dev(alive)
+    st, U = genga.genga_phase_bs(n, ics.G_GAUSS, 1.0, 6.0, 1e-12, 8, 30, kmode, 1, len(groups), dev(gstart),
+                                 dev(members), dev(rc), M, RR, AL, X, V)
+    assert st == 0, st
+    np.testing.assert_array_equal(AL.cpu().numpy(), ref["alive"])
+    np.testing.assert_allclose(M.cpu().numpy(), ref["m"], rtol=1e-15)
+    np.testing.assert_allclose(RR.cpu().numpy(), ref["R"], rtol=1e-14)
+    live = ref["alive"] == 1
+    np.testing.assert_allclose(aos(X)[live], ref["x"][live], rtol=0, atol=1e-11 * np.abs(ref["x"]).max())
+    np.testing.assert_allclose(aos(V)[live], ref["v"][live], rtol=0, atol=1e-11 * np.abs(ref["v"]).max())
+    return ref, U
+
+
+@pytest.mark.parametrize("sizes,spread", [((3, 12, 40, 100), 0.004), ((33, 64, 65, 128), 0.004), ((200,), 0.004),
+                                          ((400,), 0.004), ((1000,), 0.03)])
+def test_bs_large_groups_match_oracle(sizes, spread):
+    """Groups above 32 members run on the grid-wide BS kernel (the paper's split path above 128
+    members, Sect. 3.2); with the one-CTA and cluster kernels beside them for the smaller groups.
+    The 65- and 128-member clumps need 3 and 4 substeps, the 400-member one 10 (halvings and
+    doublings of H on the device)."""
+    x, v, m, R, groups = _clumps(sizes, seed=sum(sizes), spread=spread)
+    ref, U = _bs_phase_vs_oracle(x, v, m, R, groups)
+    assert ref["coll"] == 0 and U == 0.0
+
+
+@pytest.mark.parametrize("R", [1e-4, 3e-4])
+def test_bs_large_group_mergers_match_oracle(R):
+    """Mergers inside a 150-member group on the grid-wide kernel: 2 (R = 1e-4 AU) and 27 (3e-4 AU)
+    contacts, merged in ascending pair order as in the oracle."""
+    x, v, m, Rr, groups = _clumps((150,), seed=5, R=R)
+    ref, U = _bs_phase_vs_oracle(x, v, m, Rr, groups)
+    assert ref["coll"] >= 2
+    assert U == pytest.approx(ref["U"], rel=1e-9)
+
+
 def test_bs_merger_matches_oracle():
     m = np.array([4e-7, 1e-7, 2e-7])
     R = np.array([2e-5, 1e-5, 1e-5])
