@@ -81,6 +81,11 @@ def lib():
                 "orc_energy": (C.c_double, [C.c_int, _P, _D, _I, _D, _D]),
                 "orc_bs_group": (C.c_int, [C.c_int, _P, C.c_int, _I, C.c_double, _D, _D, _I, _D,
                                            _D, _D, _D, _I, _I, C.c_int, _I]),
+                "orc_bs_group_rec": (C.c_int, [C.c_int, _P, C.c_int, _I, C.c_double, _D, _D, _I, _D,
+                                               _D, _D, _D, _I, _I, C.c_int, _I, _D, _D, C.c_int, _I]),
+                "orc_get_collision_records": (C.c_int, [C.c_void_p, _D, C.c_int]),
+                "orc_set_spin": (None, [C.c_void_p, _D]),
+                "orc_get_spin": (None, [C.c_void_p, _D]),
                 "orc_substep_weights": (C.c_int, [C.c_int, _D]),
                 "orc_create": (C.c_void_p, [C.c_int, _P, _D, _D, _D, _D]),
                 "orc_free": (None, [C.c_void_p]),
@@ -241,23 +246,31 @@ def energy(p: Params, m, alive, x, v):
     return lib().orc_energy(len(m), C.byref(p), pm, pa, px, pv)
 
 
-def bs_group(p: Params, idx, tau, m, R, alive, x, v, rc):
-    """BS-integrate the group idx over tau; returns (x, v, m, R, alive, U, status, collisions)."""
+CREC = 24  # doubles per collision report (orc_get_collision_records)
+
+
+def bs_group(p: Params, idx, tau, m, R, alive, x, v, rc, spin=None):
+    """BS-integrate the group idx over tau; returns (x, v, m, R, alive, U, status, collisions, spin,
+    records). spin [n, 3] (None: zero) is updated by mergers; records are the collision reports."""
     n = len(m)
     idx, pidx = _i(idx)
     m = np.array(m, np.float64); R = np.array(R, np.float64)
     alive = np.array(alive, np.int32); x = np.array(x, np.float64); v = np.array(v, np.float64)
+    sp = np.zeros((n, 3)) if spin is None else np.array(spin, np.float64).reshape(n, 3)
     rc, prc = _d(rc)
     U = C.c_double(0.0)
     nc = C.c_int(0)
     coll, pcoll = _iout(2 * max(n, 1))
+    rec, prec = _dout(CREC * max(n, 1))
+    nrec = C.c_int(0)
     steps = C.c_int(0)
-    st = lib().orc_bs_group(n, C.byref(p), len(idx), pidx, float(tau), m.ctypes.data_as(_D),
-                            R.ctypes.data_as(_D), alive.ctypes.data_as(_I), x.ctypes.data_as(_D),
-                            v.ctypes.data_as(_D), prc, C.byref(U), C.byref(nc), pcoll, n,
-                            C.byref(steps))
+    st = lib().orc_bs_group_rec(n, C.byref(p), len(idx), pidx, float(tau), m.ctypes.data_as(_D),
+                                R.ctypes.data_as(_D), alive.ctypes.data_as(_I), x.ctypes.data_as(_D),
+                                v.ctypes.data_as(_D), prc, C.byref(U), C.byref(nc), pcoll, n,
+                                C.byref(steps), sp.ctypes.data_as(_D), prec, n, C.byref(nrec))
     return dict(x=x, v=v, m=m, R=R, alive=alive, U=U.value, status=st,
-                collisions=coll[: 2 * nc.value].reshape(-1, 2), bs_steps=steps.value)
+                collisions=coll[: 2 * nc.value].reshape(-1, 2), bs_steps=steps.value, spin=sp,
+                records=rec[: CREC * nrec.value].reshape(-1, CREC))
 
 
 def substep_weights(order):
@@ -340,6 +353,22 @@ class Sim:
     def ejections(self):
         """Removed bodies (Sect. 3.2, Ejections): rows of body index, step, heliocentric x[3], v[3]."""
         return _ejections(lib().orc_get_ejections, self._h)
+
+    def collision_records(self):
+        """Collision reports (Sect. 3.2): rows of CREC doubles, see orc_get_collision_records."""
+        cnt = lib().orc_get_collision_records(self._h, None, 0)
+        out, po = _dout(CREC * max(cnt, 1))
+        lib().orc_get_collision_records(self._h, po, cnt)
+        return out[: CREC * cnt].reshape(cnt, CREC)
+
+    def set_spin(self, spin):
+        sp, psp = _d(np.asarray(spin, np.float64).reshape(self.n, 3))
+        lib().orc_set_spin(self._h, psp)
+
+    def spin(self):
+        sp, psp = _dout(3 * self.n)
+        lib().orc_get_spin(self._h, psp)
+        return sp.reshape(self.n, 3)
 
 
 def _ejections(fn, h):

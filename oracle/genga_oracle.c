@@ -516,9 +516,12 @@ static int bs_attempt(const bs_ctx *c, const double *y, double H, double *out, d
 
 /* Perfect merger of bodies i and j (Sect. 3.2, Collisions): the heavier survives (equal masses:
  * the smaller index), mass and linear momentum are conserved, R = (R_i^3 + R_j^3)^(1/3), and
- * U += m_i m_j/(2(m_i+m_j)) |v_ij|^2 - G m_i m_j/r_ij is booked. The other body becomes a ghost. */
+ * U += m_i m_j/(2(m_i+m_j)) |v_ij|^2 - G m_i m_j/r_ij is booked. The other body becomes a ghost.
+ * The new body's spin follows from angular-momentum conservation: the spins of both bodies plus the
+ * orbital angular momentum of the pair about its centre of mass, mu (x_j - x_i) x (v_j - v_i) with
+ * mu = m_i m_j / (m_i + m_j) (spin may be NULL: not tracked). */
 static void merge_bodies(const orc_params *p, int gi, int gj, double *yi, double *yj, double *m,
-                         double *R, int *alive, double *U) {
+                         double *R, int *alive, double *U, double *spin) {
   double mi = m[gi], mj = m[gj], M = mi + mj;
   double dx = yj[0] - yi[0], dy = yj[1] - yi[1], dz = yj[2] - yi[2];
   double dvx = yj[3] - yi[3], dvy = yj[4] - yi[4], dvz = yj[5] - yi[5];
@@ -529,6 +532,12 @@ static void merge_bodies(const orc_params *p, int gi, int gj, double *yi, double
   double *ys, *yg;
   if (mi > mj || (mi == mj && gi < gj)) { surv = gi; ghost = gj; ys = yi; yg = yj; }
   else { surv = gj; ghost = gi; ys = yj; yg = yi; }
+  if (spin) {
+    double mu = mi * mj / M;
+    double L[3] = {mu * (dy * dvz - dz * dvy), mu * (dz * dvx - dx * dvz), mu * (dx * dvy - dy * dvx)};
+    for (int k = 0; k < 3; k++) spin[3 * surv + k] = spin[3 * gi + k] + spin[3 * gj + k] + L[k];
+    for (int k = 0; k < 3; k++) spin[3 * ghost + k] = 0.0;
+  }
   double cm[6];
   for (int k = 0; k < 6; k++) cm[k] = (mi * yi[k] + mj * yj[k]) / M;
   for (int k = 0; k < 6; k++) ys[k] = cm[k];
@@ -544,6 +553,14 @@ static void merge_bodies(const orc_params *p, int gi, int gj, double *yi, double
 int orc_bs_group(int n, const orc_params *p, int g, const int *idx, double tau, double *m,
                  double *R, int *alive, double *x, double *v, const double *rc, double *U,
                  int *ncoll, int *coll_pairs, int coll_cap, int *bs_steps) {
+  return orc_bs_group_rec(n, p, g, idx, tau, m, R, alive, x, v, rc, U, ncoll, coll_pairs, coll_cap, bs_steps,
+                          NULL, NULL, 0, NULL);
+}
+
+int orc_bs_group_rec(int n, const orc_params *p, int g, const int *idx, double tau, double *m,
+                     double *R, int *alive, double *x, double *v, const double *rc, double *U,
+                     int *ncoll, int *coll_pairs, int coll_cap, int *bs_steps, double *spin,
+                     double *crec, int crec_cap, int *ncrec) {
   (void)n;
   int d = 6 * g, kmax = p->bs_kmax;
   double *y = (double *)xcalloc((size_t)d, sizeof(double));
@@ -590,7 +607,26 @@ int orc_bs_group(int n, const orc_params *p, int g, const int *idx, double tau, 
         if (!alive[idx[a]] || !alive[idx[b]]) continue;
         if (*ncoll < coll_cap) { coll_pairs[2 * *ncoll] = idx[a]; coll_pairs[2 * *ncoll + 1] = idx[b]; }
         (*ncoll)++;
-        merge_bodies(p, idx[a], idx[b], yn + 6 * a, yn + 6 * b, m, R, alive, U);
+        if (crec && ncrec) {
+          /* the report (Sect. 3.2): both bodies' positions, velocities and spins at the last time
+           * before the contact, i.e. at the start of this BS substep; step and substep are filled in
+           * by the caller */
+          if (*ncrec < crec_cap) {
+            double *r = crec + ORC_CREC * (size_t)*ncrec;
+            int ia = idx[a], ib = idx[b];
+            int surv = (m[ia] > m[ib] || (m[ia] == m[ib] && ia < ib)) ? ia : ib;
+            r[0] = -1.0; r[1] = -1.0;
+            r[2] = tau - remaining;
+            r[3] = (double)ia; r[4] = (double)ib;
+            for (int k = 0; k < 3; k++) {
+              r[5 + k] = y[6 * a + k]; r[8 + k] = y[6 * a + 3 + k]; r[11 + k] = spin ? spin[3 * ia + k] : 0.0;
+              r[14 + k] = y[6 * b + k]; r[17 + k] = y[6 * b + 3 + k]; r[20 + k] = spin ? spin[3 * ib + k] : 0.0;
+            }
+            r[23] = (double)surv;
+          }
+          (*ncrec)++;
+        }
+        merge_bodies(p, idx[a], idx[b], yn + 6 * a, yn + 6 * b, m, R, alive, U, spin);
       }
       free(cp);
     }
@@ -649,6 +685,9 @@ struct orc_sim {
   int *gstart[ORC_MAXSUB], *gmem[ORC_MAXSUB], ngroups[ORC_MAXSUB];
   int nsub_last;
   int *coll, ncoll, coll_cap;
+  double *spin;                  /* spin angular momentum per body [3n] (Sect. 3.2, Collisions) */
+  double *crec;                  /* collision reports, ORC_CREC doubles each (orc_get_collision_records) */
+  int ncrec, crec_cap;
   double *ej;                    /* ejection records, 8 doubles each (orc_get_ejections) */
   int nej, ej_cap;
   unsigned char *is_cand;
@@ -700,6 +739,9 @@ orc_sim *orc_create(int n, const orc_params *p, const double *m, const double *R
   }
   s->coll_cap = n;
   s->coll = (int *)xcalloc((size_t)2 * s->coll_cap, sizeof(int));
+  s->spin = (double *)xcalloc((size_t)3 * n, sizeof(double));
+  s->crec_cap = n;
+  s->crec = (double *)xcalloc((size_t)ORC_CREC * s->crec_cap, sizeof(double));
   s->ej_cap = n + 1;
   s->ej = (double *)xcalloc((size_t)8 * s->ej_cap, sizeof(double));
   /* heliocentric input -> democratic (heliocentric x, barycentric v): v_b = v_h - V_cm,
@@ -728,6 +770,7 @@ void orc_free(orc_sim *s) {
   if (!s) return;
   free(s->m); free(s->R); free(s->x); free(s->v); free(s->a); free(s->x0); free(s->v0);
   free(s->rc); free(s->alive); free(s->fail); free(s->is_cand); free(s->cand); free(s->coll); free(s->ej);
+  free(s->spin); free(s->crec);
   for (int k = 0; k < ORC_MAXSUB; k++) { free(s->enc[k]); free(s->gstart[k]); free(s->gmem[k]); }
   free(s);
 }
@@ -776,9 +819,14 @@ static int substep(orc_sim *s, int js, double tau) {
         s->x[3 * idx[q] + c] = s->x0[3 * idx[q] + c];
         s->v[3 * idx[q] + c] = s->v0[3 * idx[q] + c];
       }
-    int bs_steps = 0, nc0 = s->ncoll;
-    st |= orc_bs_group(n, p, g, idx, tau, s->m, s->R, s->alive, s->x, s->v, s->rc, &s->U,
-                       &s->ncoll, s->coll, s->coll_cap, &bs_steps);
+    int bs_steps = 0, nc0 = s->ncoll, nr0 = s->ncrec;
+    st |= orc_bs_group_rec(n, p, g, idx, tau, s->m, s->R, s->alive, s->x, s->v, s->rc, &s->U,
+                           &s->ncoll, s->coll, s->coll_cap, &bs_steps, s->spin, s->crec, s->crec_cap,
+                           &s->ncrec);
+    for (int r = nr0; r < s->ncrec && r < s->crec_cap; r++) {
+      s->crec[ORC_CREC * (size_t)r] = (double)(s->stats[0] + 1);
+      s->crec[ORC_CREC * (size_t)r + 1] = (double)js;
+    }
     s->stats[5] += bs_steps;
     s->stats[7] += s->ncoll - nc0;
   }
@@ -939,6 +987,16 @@ int orc_get_collisions(const orc_sim *s, int *pairs, int cap) {
   if (pairs) memcpy(pairs, s->coll, sizeof(int) * 2 * (size_t)c);
   return s->ncoll;
 }
+
+int orc_get_collision_records(const orc_sim *s, double *rec, int cap) {
+  int k = s->ncrec < s->crec_cap ? s->ncrec : s->crec_cap;
+  if (rec) memcpy(rec, s->crec, sizeof(double) * ORC_CREC * (size_t)(k < cap ? k : cap));
+  return s->ncrec;
+}
+
+void orc_set_spin(orc_sim *s, const double *spin) { memcpy(s->spin, spin, sizeof(double) * 3 * (size_t)s->n); }
+
+void orc_get_spin(const orc_sim *s, double *spin) { memcpy(spin, s->spin, sizeof(double) * 3 * (size_t)s->n); }
 
 /* ------------------------------------------------------------------------------------------ */
 /* Sect. 3.3: test-particle mode                                                               */
@@ -1208,8 +1266,13 @@ static int tp_substep(orc_tpsim *T, int js, double tau) {
     const int *idx = s->gmem[js] + g0;
     for (int q = 0; q < g; q++)
       for (int c = 0; c < 3; c++) { s->x[3 * idx[q] + c] = s->x0[3 * idx[q] + c]; s->v[3 * idx[q] + c] = s->v0[3 * idx[q] + c]; }
-    int bs_steps = 0;
-    st |= orc_bs_group(n, p, g, idx, tau, s->m, s->R, s->alive, s->x, s->v, s->rc, &s->U, &s->ncoll, s->coll, s->coll_cap, &bs_steps);
+    int bs_steps = 0, nr0 = s->ncrec;
+    st |= orc_bs_group_rec(n, p, g, idx, tau, s->m, s->R, s->alive, s->x, s->v, s->rc, &s->U, &s->ncoll, s->coll,
+                           s->coll_cap, &bs_steps, s->spin, s->crec, s->crec_cap, &s->ncrec);
+    for (int r = nr0; r < s->ncrec && r < s->crec_cap; r++) {
+      s->crec[ORC_CREC * (size_t)r] = (double)(s->stats[0] + 1);
+      s->crec[ORC_CREC * (size_t)r + 1] = (double)js;
+    }
   }
   /* TP encounters with planets (candidates from the previous closing TP kick), then BS of every
    * TP with an encounter (or a failed Kepler solve) */

@@ -78,6 +78,19 @@ int orc_bs_group(int n, const orc_params *p, int g, const int *idx, double tau, 
                  double *R, int *alive, double *x, double *v, const double *rc, double *U,
                  int *ncoll, int *coll_pairs, int coll_cap, int *bs_steps);
 
+/* Collision reports (Sect. 3.2, Collisions): ORC_CREC doubles per merger --
+ *   [0] step (1-based), [1] substep of the composition (0-based), [2] time from the substep's start
+ *   to the start of the BS substep in which the contact was found, [3] body i, [4] body j (i < j),
+ *   [5..7] x_i, [8..10] v_i, [11..13] spin_i, [14..16] x_j, [17..19] v_j, [20..22] spin_j at that
+ *   time (heliocentric positions, barycentric velocities), [23] the surviving body.
+ * orc_bs_group_rec is orc_bs_group that also tracks spins (spin [3n], may be NULL) and writes the
+ * reports of its mergers (entries 0 and 1 set to -1: the caller knows the step). */
+#define ORC_CREC 24
+int orc_bs_group_rec(int n, const orc_params *p, int g, const int *idx, double tau, double *m,
+                     double *R, int *alive, double *x, double *v, const double *rc, double *U,
+                     int *ncoll, int *coll_pairs, int coll_cap, int *bs_steps, double *spin,
+                     double *crec, int crec_cap, int *ncrec);
+
 /* Sect. 2.3: substep weights w[0..k-1] of the composition of order 2 (k = 1, Eq. z1), 4 (k = 3) or
  * 6 (k = 7, Yoshida's solution A); substep j has the signed length w[j] * tau. Returns k. */
 int orc_substep_weights(int order, double *w);
@@ -96,6 +109,12 @@ int orc_get_encounters(const orc_sim *s, int substep, int *pairs, int cap);
 int orc_get_groups(const orc_sim *s, int substep, int *group_start, int *members, int cap);
 void orc_get_stats(const orc_sim *s, long long *stats, int nstats);
 int orc_get_collisions(const orc_sim *s, int *pairs, int cap);
+/* All collision reports so far (at most cap written; returns the count), ORC_CREC doubles each. */
+int orc_get_collision_records(const orc_sim *s, double *rec, int cap);
+/* Spin angular momentum of every body [3n] (zero at orc_create; a merger gives the survivor the sum
+ * of both spins and the pair's orbital angular momentum about its centre of mass). */
+void orc_set_spin(orc_sim *s, const double *spin);
+void orc_get_spin(const orc_sim *s, double *spin);
 /* Ejections so far (all of them; at most cap records written): record k = rec[8k .. 8k+7] =
  * body index, step (1-based, the step at whose end it was removed), heliocentric x[3] and v[3]. */
 int orc_get_ejections(const orc_sim *s, double *rec, int cap);
