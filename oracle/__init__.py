@@ -49,7 +49,8 @@ class Params(C.Structure):
     _fields_ = [("G", C.c_double), ("m0", C.c_double), ("dt", C.c_double), ("order", C.c_int),
                 ("kmode", C.c_int), ("n1", C.c_double), ("n2", C.c_double), ("pc", C.c_double),
                 ("bs_eps", C.c_double), ("bs_kmax", C.c_int), ("bs_max_halvings", C.c_int),
-                ("kepler_maxit", C.c_int), ("collisions", C.c_int), ("rcut", C.c_double), ("rcut_sun", C.c_double)]
+                ("kepler_maxit", C.c_int), ("collisions", C.c_int), ("rcut", C.c_double), ("rcut_sun", C.c_double),
+                ("precheck_substeps", C.c_int)]
 
 
 _D = C.POINTER(C.c_double)

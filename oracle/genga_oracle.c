@@ -54,6 +54,7 @@ void orc_default_params(orc_params *p) {
   p->collisions = 1;
   p->rcut = 0.0;     /* no ejections unless asked for */
   p->rcut_sun = 0.0;
+  p->precheck_substeps = 1;
 }
 
 /* ------------------------------------------------------------------------------------------ */
@@ -777,8 +778,10 @@ void orc_free(orc_sim *s) {
 
 /* One 2nd-order substep of signed length tau (Sect. 2.2, second list), entered after the
  * opening kick's accelerations s->a are known; leaves the closing kick's accelerations and the
- * new candidate list behind. */
-static int substep(orc_sim *s, int js, double tau) {
+ * new candidate list behind (with precheck_substeps = 0 only the last substep of a step, last = 1,
+ * replaces the candidate list: Sect. 2.3 applies the full scheme to each substep "but not the
+ * prechecker"). */
+static int substep(orc_sim *s, int js, double tau, int last) {
   int n = s->n, st = 0;
   orc_params *p = &s->p;
   double h = 0.5 * tau, P[3];
@@ -836,9 +839,11 @@ static int substep(orc_sim *s, int js, double tau) {
   /* closing kick tau/2 with new accelerations and the precheck */
   orc_accel_B(n, p, s->m, s->alive, s->x, s->rc, s->a);
   for (int k = 0; k < 3 * n; k++) s->v[k] += h * s->a[k];
-  s->ncand = orc_precheck(n, p, s->alive, s->x, s->rc, s->cand, s->cand_cap);
-  if (s->ncand > s->cand_cap) st |= ORC_ST_CAPACITY;
-  s->stats[2] += s->ncand;
+  if (p->precheck_substeps || last) {
+    s->ncand = orc_precheck(n, p, s->alive, s->x, s->rc, s->cand, s->cand_cap);
+    if (s->ncand > s->cand_cap) st |= ORC_ST_CAPACITY;
+    s->stats[2] += s->ncand;
+  }
   s->stats[1]++;
   return st;
 }
@@ -917,7 +922,7 @@ int orc_step(orc_sim *s, int nsteps) {
     }
     /* opening kick of the step: plain definition, all pairs with the new critical radii */
     orc_accel_B(n, &s->p, s->m, s->alive, s->x, s->rc, s->a);
-    for (int js = 0; js < nsub; js++) st |= substep(s, js, w[js] * s->p.dt);
+    for (int js = 0; js < nsub; js++) st |= substep(s, js, w[js] * s->p.dt, js == nsub - 1);
     s->nsub_last = nsub;
     s->stats[0]++;
     eject(s);

@@ -34,6 +34,9 @@ typedef struct orc_params {
   int collisions;    /* 1: perfect merging on contact (Sect. 3.2, Collisions) */
   double rcut;       /* Sect. 3.2, Ejections: a body farther than rcut from m0 is removed (0: off) */
   double rcut_sun;   /* ... and one closer than rcut_sun (0: off) */
+  int precheck_substeps; /* 1: the closing kick of every substep prechecks (its candidates feed the next
+                            substep's encounter search); 0: only the closing kick of a full step does,
+                            and its candidates serve all substeps of the next step (Sect. 2.3 as printed) */
 } orc_params;
 
 /* Status bits returned by orc_step and the phase routines. */
