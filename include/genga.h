@@ -53,6 +53,7 @@ extern "C" {
                                         1024 bodies out of bounds in one step (the rest leave next step) */
 #define GENGA_ST_GRID_TIMEOUT 128    /* the grid-wide BS of a group above 32 members gave up waiting at one of
                                         its grid barriers (its group keeps the state it had) */
+#define GENGA_ST_COLL_OVERFLOW 256   /* more than 4096 collision reports (later ones dropped; mergers still happen) */
 
 /* modes of genga_init (Sect. 3): main mode with up to 2048 massive bodies */
 #define GENGA_MODE_MASSIVE 0
@@ -80,6 +81,11 @@ typedef struct genga_params {
   /* Batched mode (Sect. 3.4, Nmin): a system left with fewer than nmin live bodies at the end of a
    * step is stopped, all its bodies removed (energy booked into U). 0: off (the default). */
   int nmin;
+  /* Higher orders (Sect. 2.3). 1 (the default): the closing kick of every substep prechecks and its
+   * candidates feed the next substep's encounter search. 0: as the paper states it, the substeps
+   * run the full scheme "but not the prechecker": only the closing kick of a full step prechecks and
+   * its candidates serve every substep of the next step (main mode only; EINVAL elsewhere). */
+  int precheck_substeps;
 } genga_params;
 
 /* Fills *p with the paper's defaults (n1 = 3, n2 = 0.4, pc = 3) and the library's BS/Kepler caps. */
@@ -134,6 +140,25 @@ int genga_encounters(genga_ctx *ctx, int substep, int *pairs, int cap, int *n_pa
  * ascending index within a step. Waits for the stream. */
 int genga_ejections(genga_ctx *ctx, double *rec, int cap, int *n);
 
+/* Collision reports since the context was created (Sect. 3.2, Collisions: positions, velocities and
+ * spins of both bodies at the last time before the contact). *n receives the number of mergers; the
+ * first min(*n, cap, 4096) reports are written to rec [24 cap], ordered by step, substep, time and
+ * pair, each: [0] step (1-based), [1] substep of the composition (0-based), [2] time from that
+ * substep's start to the start of the BS substep in which the contact was found, [3] body i, [4] body
+ * j (i < j; the caller's indices as in genga_ejections), [5..7] x_i, [8..10] v_i, [11..13] spin_i,
+ * [14..16] x_j, [17..19] v_j, [20..22] spin_j at that time (heliocentric positions, barycentric
+ * velocities), [23] the body that survives (the heavier; equal masses: the smaller index). Waits
+ * for the stream. */
+int genga_collisions(genga_ctx *ctx, double *rec, int cap, int *n);
+
+/* Spin angular momentum of every body (zero at creation). A merger gives the survivor the sum of
+ * both spins and the pair's orbital angular momentum about its centre of mass, so orbital plus spin
+ * angular momentum is conserved (Sect. 3.2, Collisions). Layout as the state: [3n] with the central
+ * mass at row 0 (ignored on input, zero on output) in the single-system modes, [3N] flat in the
+ * caller's order in the batched mode. Both wait for the stream. */
+int genga_set_spin(genga_ctx *ctx, const double *spin);
+int genga_get_spin(genga_ctx *ctx, double *spin);
+
 /* Device status word: bits GENGA_ST_*; *detail receives counters (may be NULL): detail[0] steps,
  * [1] candidates, [2] encounters, [3] groups, [4] BS steps, [5] Kepler fallbacks, [6] mergers,
  * [7] full-kick recomputes (8 entries). Waits for the stream. */
@@ -172,6 +197,11 @@ int genga_init_tp(genga_ctx **ctx, int n, const double *masses, const double *ra
 /* Test-particle state (heliocentric, host): xt, vt [3 n_tp], tp_alive [n_tp]; any may be NULL. */
 int genga_get_state_tp(genga_ctx *ctx, double *xt, double *vt, int *tp_alive);
 
+/* Confirmed (test particle, planet) encounter pairs of the last substep of the last step (Sect. 3.3):
+ * pairs[2k] the particle's index, pairs[2k+1] the planet's body index (central mass at 0), ascending.
+ * *n_pairs receives the count; returns GENGA_ECAP if cap < count (the first cap pairs written). */
+int genga_tp_encounters(genga_ctx *ctx, int *pairs, int cap, int *n_pairs);
+
 /* Test-particle counters since genga_init_tp (5 entries): detail[0] (TP, planet) candidate pairs
  * recorded by the closing kicks, [1] confirmed encounter pairs, [2] accepted BS substeps,
  * [3] particles removed on contact, [4] particles ejected (rcut, rcut_sun). */
@@ -204,6 +234,11 @@ int genga_get_state_batch(genga_ctx *ctx, double *x, double *v, double *m, doubl
 /* Replaces positions and velocities of the live bodies (flat, heliocentric, caller order); the next
  * step recomputes the first kick. */
 int genga_set_state_batch(genga_ctx *ctx, const double *x, const double *v);
+
+/* Confirmed close-encounter pairs of every system in the last substep of the last step (Sect. 3.4):
+ * indices into the flat body arrays of genga_init_batch, i < j within one system, ascending. *n_pairs
+ * receives the count; returns GENGA_ECAP if cap < count (the first cap pairs written). */
+int genga_batch_encounters(genga_ctx *ctx, int *pairs, int cap, int *n_pairs);
 
 /* Energy of every system (E [n_sys], caller order, democratic coordinates, Sect. 4.1) and the
  * internal energy U of all mergers so far. Waits for the stream. */
@@ -266,12 +301,17 @@ int genga_phase_energy(int n, double G, double m0, const double *m, const int *a
  * kernels) but keeps its scratch in one file-scope device array of about 2 MB, which every GPU
  * that loads the library holds until the process exits.
  *   n <= 1024 (GENGA_ESIZE otherwise); m, alive, x, rc, a, cand as in genga_phase_kick (device);
- *   ncand is a DEVICE int that receives the candidate count (nothing is copied to the host).
+ *   ncand is a DEVICE int that receives the full candidate count (nothing is copied to the host).
+ *   Unlike genga_phase_kick this call cannot return GENGA_ECAP, since the count stays on the
+ *   device: when *ncand exceeds cap, only the first cap pairs were written, and the caller must
+ *   compare *ncand with cap itself.
  * Only cudaMemsetAsync, kernel launches and a device-to-device copy are enqueued on stream. The
  * first call on a device looks up the scratch array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture. All calls share the one
- * array, which keeps the last call's contents: calls that overlap on the GPU (different streams
- * without ordering between them) race on it. */
+ * that device current; make that first call before any stream capture. The address is kept for the
+ * life of the process: after a reset of the device (cudaDeviceReset) it is stale, so do not call
+ * this entry point again in that process. All calls share the one array, which keeps the last
+ * call's contents: calls that overlap on the GPU (different streams without ordering between them)
+ * race on it. */
 int genga_kick_noalloc(int n, double G, double pc, int kmode, int precise_div, const double *m,
                        const int *alive, const double *x, const double *rc, double *a, int *cand,
                        int cap, int *ncand, void *stream);
@@ -324,6 +364,12 @@ int genga_adj_backward(genga_adj *ctx, const double *xbar, const double *vbar, d
 int genga_adj_status(genga_adj *ctx, int *code);
 int genga_adj_sync(genga_adj *ctx);
 void genga_adj_free(genga_adj *ctx);
+
+/* Measurement aid (the paper has none): the device's FP64 throughput, from one launch of 4 CTAs of 256
+ * threads per SM in which every thread runs 8 independent chains of iters fused multiply-adds (2 flop
+ * each), timed with CUDA events on stream. *tflops receives TFLOP/s, *ms (may be NULL) the launch
+ * time. Synchronises the stream; allocates 8 bytes of device memory for the duration of the call. */
+int genga_fp64_probe(int iters, double *tflops, float *ms, void *stream);
 
 /* Self-test of the device arithmetic helpers: out[i] = f(in[i]) for which = 0: x^(-1/2),
  * 1: x^(-3/2), 2: 1/x (the refined estimates used by the kernels). Device arrays. */

@@ -97,6 +97,8 @@ bool alloc_sim(Sim &S, DevMem &mem, int n, int nsub) {
   B.gm = mem.get<double>(np); B.m = mem.get<double>(np); B.R = mem.get<double>(np); B.A = mem.get<double>(np);
   B.rcsq = mem.get<u64>(np); B.err = mem.get<u64>(2 * BS_LEVELS); B.bar = mem.get<unsigned>(4);
   B.cont = mem.get<int>(GR_CONTACT_CAP); B.ncont = mem.get<int>(1);
+  S.spin = mem.get<double>(3 * np);
+  S.crec = mem.get<double>((size_t)CREC_CAP * CREC); S.ncrec = mem.get<int>(1);
   if (mem.err != cudaSuccess) return false;
   cudaMemcpy(S.items, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice);
   return cudaGetLastError() == cudaSuccess;
@@ -173,6 +175,7 @@ struct genga_ctx {
   int nsys = 0, b_split = 1, b_block = 128, steps_per_launch = 1;
   int *perm = nullptr, *sys_user = nullptr;  // device: internal body -> user body, internal system -> user system
   std::vector<int> perm_h;                    // host copy of perm (ejection records)
+  std::vector<int> start_h;                   // host copy of the internal systems' first bodies
   double *sysE = nullptr;
   // test-particle mode
   bool tpmode = false;
@@ -247,7 +250,7 @@ void enqueue_step_batch(genga_ctx *c, cudaStream_t st) {
   for (int j = 0; j < c->nsub; ++j) {
     const double tau = c->w[j] * dt;
     launch_b_momentum(S, S.sys_ppost, st);
-    launch_b_drift(S, P, tau, 0.5 * tau, j > 0 ? 0.5 * c->w[j - 1] * dt : 0.0, j == 0, st);
+    launch_b_drift(S, P, tau, 0.5 * tau, j > 0 ? 0.5 * c->w[j - 1] * dt : 0.0, j, st);
     launch_b_encounter(S, tau, st);
     launch_b_group(S, st);
     if (c->side) {  // fork: pairs (two warps each), groups of 3..BS_SMALL (128-thread CTAs) and the
@@ -291,9 +294,12 @@ void enqueue_step(genga_ctx *c, cudaStream_t st) {
     const double tau = c->w[j] * dt;
     const double hcm2 = j > 0 ? 0.5 * c->w[j - 1] * dt * inv_m0 : 0.0;
     if (tp) launch_tp_drift(S, T, P, tau, 0.5 * tau * inv_m0, hcm2, st);  // before the massive drift
-    launch_drift(S, P, tau, 0.5 * tau * inv_m0, hcm2, j == 0, st);        // clears the reuse flag
+    launch_drift(S, P, tau, 0.5 * tau * inv_m0, hcm2, j, st);             // clears the reuse flag
     if (tp) launch_planet_table(S, T, P, tau, st);
-    launch_encounter(S, tau, S.ebm + (size_t)j * S.npad * S.W, st);
+    // the paper's literal higher-order variant: the step-start candidates serve every substep, and
+    // the closing kicks between substeps weigh every pair without prechecking
+    const bool inner = c->prm.precheck_substeps == 0 && j + 1 < c->nsub;
+    launch_encounter(S, tau, S.ebm + (size_t)j * S.npad * S.W, st, inner);
     launch_group(S, st, c->side ? c->gsplit : BS_GMAX + 1);
     if (c->side) {  // fork: cluster kernel for the groups of gsplit .. BS_GMAX members, one-CTA
                     // kernel for the smaller ones and the grid-wide kernel for groups above BS_GMAX
@@ -316,10 +322,10 @@ void enqueue_step(genga_ctx *c, cudaStream_t st) {
       launch_tp_bs(S, T, P, tau, num_sms(), st);
     }
     if (c->profiling) cudaEventRecordWithFlags(c->kev[2 * j], st, cudaEventRecordExternal);
-    launch_kick(S, P, false, precise, st);
+    launch_kick(S, P, inner, precise, st, inner);
     if (c->profiling) cudaEventRecordWithFlags(c->kev[2 * j + 1], st, cudaEventRecordExternal);
     const double h2 = (j + 1 < c->nsub) ? 0.5 * c->w[j + 1] * dt : 0.0;
-    launch_fin(S, P, FIN_CLOSE, 0.5 * tau, h2, nullptr, st);
+    launch_fin(S, P, inner ? FIN_CLOSE_ALL : FIN_CLOSE, 0.5 * tau, h2, nullptr, st);
     if (tp) launch_tp_kick(S, T, P, FIN_CLOSE, 0.5 * tau, h2, st);
   }
   launch_hc(S, 0.5 * c->w[c->nsub - 1] * dt * inv_m0, st);
@@ -381,6 +387,7 @@ int genga_default_params(genga_params *p) {
   p->rcut = 0.0;
   p->rcut_sun = 0.0;
   p->nmin = 0;
+  p->precheck_substeps = 1;
   return GENGA_OK;
 }
 
@@ -564,6 +571,7 @@ int genga_init_batch(genga_ctx **out, int n_sys, const int *offsets, const doubl
     for (int q = 0; q < ns; ++q) { perm.push_back(offsets[s] + q); sys_of.push_back(k); }
   }
   c->perm_h = perm;
+  c->start_h = start;
   Sim &S = c->S;
   DevMem &mem = c->mem;
   memset(&S, 0, sizeof(S));
@@ -591,6 +599,8 @@ int genga_init_batch(genga_ctx **out, int n_sys, const int *offsets, const doubl
   S.sys_m0 = mem.get<double>(n_sys); S.sys_ppre = mem.get<double>(3 * (size_t)n_sys);
   S.sys_ppost = mem.get<double>(3 * (size_t)n_sys); S.sys_flag = mem.get<int>(n_sys);
   S.bmask = mem.get<u64>(np); S.emask = mem.get<u64>(np);
+  S.spin = mem.get<double>(3 * np);
+  S.crec = mem.get<double>((size_t)CREC_CAP * CREC); S.ncrec = mem.get<int>(1);
   c->perm = mem.get<int>(n); c->sys_user = mem.get<int>(n_sys); c->sysE = mem.get<double>(n_sys);
   c->sx = mem.get<double>(3 * (size_t)n); c->sv = mem.get<double>(3 * (size_t)n);
   c->sm = mem.get<double>(n); c->sR = mem.get<double>(n); c->salive = mem.get<int>(n);
@@ -711,6 +721,8 @@ int genga_set_params(genga_ctx *c, const genga_params *p) {
     return GENGA_EINVAL;
   if (!(p->rcut >= 0.0) || !(p->rcut_sun >= 0.0) || p->nmin < 0 || (p->rcut > 0.0 && !(p->rcut > p->rcut_sun)))
     return GENGA_EINVAL;
+  if ((p->precheck_substeps != 0 && p->precheck_substeps != 1) || (!p->precheck_substeps && (c->batched || c->tpmode)))
+    return GENGA_EINVAL;
   c->prm = *p;
   c->P = make_params(c->G, c->m0, c->prm);
   drop_graph(c);
@@ -731,6 +743,66 @@ int genga_ejections(genga_ctx *c, double *rec, int cap, int *n) {
       const int i = (int)rec[8 * q];
       rec[8 * q] = (double)(c->batched ? c->perm_h[i] : i + 1);
     }
+  }
+  return GENGA_OK;
+}
+
+int genga_collisions(genga_ctx *c, double *rec, int cap, int *n) {
+  if (!c || cap < 0 || (cap > 0 && !rec)) return GENGA_EINVAL;
+  CK(cudaStreamSynchronize(c->stream));
+  int cnt = 0;
+  CK(cudaMemcpy(&cnt, c->S.ncrec, sizeof(int), cudaMemcpyDeviceToHost));
+  if (n) *n = cnt;
+  const int k = cnt < CREC_CAP ? cnt : CREC_CAP;
+  if (k > 0 && cap > 0) {
+    std::vector<double> all((size_t)k * CREC);
+    CK(cudaMemcpy(all.data(), c->S.crec, all.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    auto user = [&](double i) { return (double)(c->batched ? c->perm_h[(int)i] : (int)i + 1); };
+    for (int q = 0; q < k; ++q) {  // internal indices -> the caller's
+      double *r = all.data() + (size_t)q * CREC;
+      r[3] = user(r[3]); r[4] = user(r[4]); r[23] = user(r[23]);
+    }
+    // groups merge concurrently on the device: order the reports by (step, substep, time, i, j)
+    std::vector<int> ord(k);
+    for (int q = 0; q < k; ++q) ord[q] = q;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+      const double *ra = all.data() + (size_t)a * CREC, *rb = all.data() + (size_t)b * CREC;
+      for (int f : {0, 1, 2, 3, 4})
+        if (ra[f] != rb[f]) return ra[f] < rb[f];
+      return false;
+    });
+    const int w = k < cap ? k : cap;
+    for (int q = 0; q < w; ++q) memcpy(rec + (size_t)q * CREC, all.data() + (size_t)ord[q] * CREC, CREC * sizeof(double));
+  }
+  return GENGA_OK;
+}
+
+// Spins: internal SoA [3][npad] <-> the caller's layout ([3n] with the central mass at row 0 in the
+// single-system modes, [3N] flat in the batched mode).
+int genga_set_spin(genga_ctx *c, const double *spin) {
+  if (!c || !spin) return GENGA_EINVAL;
+  const size_t np = c->S.npad;
+  if (!finite_all(spin, 3 * (size_t)(c->batched ? c->n : c->n + 1))) return GENGA_EINVAL;
+  std::vector<double> h(3 * np, 0.0);
+  for (int i = 0; i < c->n; ++i) {
+    const int u = c->batched ? c->perm_h[i] : i + 1;
+    for (int k = 0; k < 3; ++k) h[k * np + i] = spin[3 * (size_t)u + k];
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpy(c->S.spin, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
+  return GENGA_OK;
+}
+
+int genga_get_spin(genga_ctx *c, double *spin) {
+  if (!c || !spin) return GENGA_EINVAL;
+  const size_t np = c->S.npad;
+  std::vector<double> h(3 * np);
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpy(h.data(), c->S.spin, h.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  if (!c->batched) for (int k = 0; k < 3; ++k) spin[k] = 0.0;
+  for (int i = 0; i < c->n; ++i) {
+    const int u = c->batched ? c->perm_h[i] : i + 1;
+    for (int k = 0; k < 3; ++k) spin[3 * (size_t)u + k] = h[k * np + i];
   }
   return GENGA_OK;
 }
@@ -828,6 +900,42 @@ int genga_encounters(genga_ctx *c, int substep, int *pairs, int cap, int *n_pair
     CK(cudaMemcpy(pairs, c->spairs, 2 * (size_t)ncopy * sizeof(int), cudaMemcpyDeviceToHost));
     for (int k = 0; k < 2 * ncopy; ++k) pairs[k] += 1;  // the central mass is body 0
   }
+  return cnt > cap ? GENGA_ECAP : GENGA_OK;
+}
+
+int genga_tp_encounters(genga_ctx *c, int *pairs, int cap, int *n_pairs) {
+  if (!c || !c->tpmode || cap < 0 || (cap > 0 && !pairs)) return GENGA_EINVAL;
+  CK(cudaStreamSynchronize(c->stream));
+  std::vector<unsigned> em(c->T.n);
+  CK(cudaMemcpy(em.data(), c->T.emask, em.size() * sizeof(unsigned), cudaMemcpyDeviceToHost));
+  int cnt = 0;
+  for (int i = 0; i < c->T.n; ++i)
+    for (unsigned bits = em[i]; bits; bits &= bits - 1) {
+      const int j = __builtin_ctz(bits);
+      if (cnt < cap) { pairs[2 * cnt] = i; pairs[2 * cnt + 1] = j + 1; }  // the central mass is body 0
+      cnt++;
+    }
+  if (n_pairs) *n_pairs = cnt;
+  return cnt > cap ? GENGA_ECAP : GENGA_OK;
+}
+
+int genga_batch_encounters(genga_ctx *c, int *pairs, int cap, int *n_pairs) {
+  if (!c || !c->batched || cap < 0 || (cap > 0 && !pairs)) return GENGA_EINVAL;
+  CK(cudaStreamSynchronize(c->stream));
+  std::vector<unsigned long long> em(c->n);
+  CK(cudaMemcpy(em.data(), c->S.emask, em.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+  std::vector<std::pair<int, int>> out;
+  for (int k = 0; k < c->nsys; ++k)
+    for (int i = c->start_h[k]; i < c->start_h[k + 1]; ++i)
+      for (unsigned long long bits = em[i]; bits; bits &= bits - 1) {
+        const int j = c->start_h[k] + __builtin_ctzll(bits);
+        const int a = c->perm_h[i], b = c->perm_h[j];
+        out.emplace_back(a < b ? a : b, a < b ? b : a);
+      }
+  std::sort(out.begin(), out.end());
+  const int cnt = (int)out.size();
+  for (int q = 0; q < cnt && q < cap; ++q) { pairs[2 * q] = out[q].first; pairs[2 * q + 1] = out[q].second; }
+  if (n_pairs) *n_pairs = cnt;
   return cnt > cap ? GENGA_ECAP : GENGA_OK;
 }
 
@@ -1096,6 +1204,18 @@ int genga_phase_energy(int n, double G, double m0, const double *m, const int *a
   launch_energy(S, P, scratch, dE, st);
   cudaMemcpyAsync(E, dE, sizeof(double), cudaMemcpyDeviceToHost, st);
   return phase_finish(mem, st, GENGA_OK);
+}
+
+int genga_fp64_probe(int iters, double *tflops, float *ms, void *stream) {
+  if (iters < 1 || !tflops) return GENGA_EINVAL;
+  double *scratch = nullptr;
+  CK(cudaMalloc(&scratch, sizeof(double)));
+  const double f = fp64_probe_flops(iters, 4 * num_sms(), ms, (cudaStream_t)stream, scratch);
+  cudaError_t e = cudaGetLastError();
+  cudaFree(scratch);
+  if (e != cudaSuccess) return GENGA_ECUDA;
+  *tflops = f / 1e12;
+  return GENGA_OK;
 }
 
 int genga_phase_mathcheck(int n, int which, const double *in, double *out, void *stream) {

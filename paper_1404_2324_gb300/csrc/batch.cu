@@ -148,9 +148,10 @@ __global__ void k_b_momentum(Sim S, double *out) {
 
 // Sun drifts (this substep's first with the momentum after the opening kick, and the previous
 // substep's second with the momentum before its closing kick), then the Kepler drift.
-__global__ void k_b_drift(Sim S, DevParams P, double tau, double h1, double h2, int first) {
+__global__ void k_b_drift(Sim S, DevParams P, double tau, double h1, double h2, int substep) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0) { *S.ngroups = 0; *S.gtotal = 0; }
+  const int first = substep == 0;
+  if (i == 0) { *S.ngroups = 0; *S.gtotal = 0; S.flags[2] = substep; }
   if (i < 4) S.bsq[i] = 0u;
   if (i < 8) S.norder[i] = 0;
   if (i < S.npad) S.bsn[i] >>= 1;  // the substep history fades
@@ -432,8 +433,8 @@ void launch_b_kick(const Sim &S, const DevParams &P, FinMode mode, double h1, do
 void launch_b_momentum(const Sim &S, double *out, cudaStream_t st) {
   k_b_momentum<<<(S.nsys * 32 + 127) / 128, 128, 0, st>>>(S, out);
 }
-void launch_b_drift(const Sim &S, const DevParams &P, double tau, double h1, double h2, int first, cudaStream_t st) {
-  k_b_drift<<<(S.npad + 127) / 128, 128, 0, st>>>(S, P, tau, h1, h2, first);
+void launch_b_drift(const Sim &S, const DevParams &P, double tau, double h1, double h2, int substep, cudaStream_t st) {
+  k_b_drift<<<(S.npad + 127) / 128, 128, 0, st>>>(S, P, tau, h1, h2, substep);
 }
 void launch_b_encounter(const Sim &S, double tau, cudaStream_t st) {
   k_b_encounter<<<(S.npad + BENC_THREADS - 1) / BENC_THREADS, BENC_THREADS, 0, st>>>(S, tau);

@@ -249,6 +249,7 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 512 / NT)
                 const double v2 = dvx * dvx + dvy * dvy + dvz * dvz;
                 sh.U += 0.5 * ma * mb / M * v2 - P.G * ma * mb / r;
                 const bool keep_a = ma > mb || (ma == mb && ia < ib);
+                merger_report(S, ia, ib, sh.y[a], sh.y[bq], sh.yn[a], sh.yn[bq], ma, mb, keep_a, tau - rem);
                 const int s = keep_a ? a : bq, d = keep_a ? bq : a;
                 for (int c = 0; c < 6; ++c) sh.yn[s][c] = (ma * sh.yn[a][c] + mb * sh.yn[bq][c]) / M;
                 const double Ra = sh.R[a], Rb = sh.R[bq];
@@ -577,6 +578,7 @@ __global__ void __launch_bounds__(64 * BSP_UNITS, 2) k_bs_pair(Sim S, DevParams 
           const double v2 = dvx * dvx + dvy * dvy + dvz * dvz;
           sh.U += 0.5 * ma * mb / M * v2 - P.G * ma * mb / r;
           const bool keep_a = ma > mb || (ma == mb && ia < ib);
+          merger_report(S, ia, ib, sh.y[0], sh.y[1], yn[0], yn[1], ma, mb, keep_a, tau - rem);
           const int sv = keep_a ? 0 : 1, d = keep_a ? 1 : 0;
           for (int c = 0; c < 6; ++c) yn[sv][c] = (ma * yn[0][c] + mb * yn[1][c]) / M;
           const double Ra = sh.R[0], Rb = sh.R[1];

@@ -216,6 +216,7 @@ __global__ void __cluster_dims__(CL_SIZE, 1, 1) __launch_bounds__(CL_THREADS, 2)
                 const double v2 = dvx * dvx + dvy * dvy + dvz * dvz;
                 sh.U += 0.5 * ma * mb / M * v2 - P.G * ma * mb / r;
                 const bool keep_a = ma > mb || (ma == mb && ia < ib);
+                if (rank == 0) merger_report(S, ia, ib, sh.y[a], sh.y[bq], sh.yn[a], sh.yn[bq], ma, mb, keep_a, tau - rem);
                 const int s = keep_a ? a : bq, d = keep_a ? bq : a;
                 for (int c = 0; c < 6; ++c) sh.yn[s][c] = (ma * sh.yn[a][c] + mb * sh.yn[bq][c]) / M;
                 const double Ra = sh.R[a], Rb = sh.R[bq];

@@ -316,6 +316,11 @@ __global__ void __launch_bounds__(GR_THREADS, 2) k_bs_grid(Sim S, DevParams P, d
             const double v2 = dvx * dvx + dvy * dvy + dvz * dvz;
             U += 0.5 * ma * mb / M * v2 - P.G * ma * mb / rr;
             const bool keep_a = ma > mb || (ma == mb && ia < ib);
+            {
+              double ya0[6], yb0[6];  // the pair's states at the start of the substep
+              for (int c = 0; c < 6; ++c) { ya0[c] = __ldcg(yc + (size_t)a * 6 + c); yb0[c] = __ldcg(yc + (size_t)bq * 6 + c); }
+              merger_report(S, ia, ib, ya0, yb0, va, vb, ma, mb, keep_a, tau - rem);
+            }
             const int sv = keep_a ? a : bq, dd = keep_a ? bq : a;
             double *ys = yn + (size_t)sv * 6;
             for (int c = 0; c < 6; ++c) ys[c] = (ma * va[c] + mb * vb[c]) / M;

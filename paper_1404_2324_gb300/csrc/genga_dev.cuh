@@ -34,6 +34,9 @@ constexpr int ST_UNION_ROUNDS = 16;
 constexpr int ST_RECORD_OVERFLOW = 32;  // a recording buffer of the adjoint engine was too small
 constexpr int ST_EJECT_OVERFLOW = 64;   // more ejections than EJ_CAP records, or than EJ_STEP in one step
 constexpr int ST_GRID_TIMEOUT = 128;    // the grid-wide BS kernel gave up waiting at a grid barrier
+constexpr int ST_COLL_OVERFLOW = 256;   // more collision reports than CREC_CAP (later ones dropped)
+constexpr int CREC = 24;                // doubles per collision report
+constexpr int CREC_CAP = 4096;          // collision reports kept
 constexpr int EJ_CAP = 4096;            // ejection records kept (8 doubles each)
 constexpr int EJ_STEP = 1024;           // bodies one step can remove in the single-system modes
 
@@ -118,6 +121,9 @@ struct Sim {
   double *ejrec;                 // ejection records [EJ_CAP * 8]: index, step, heliocentric x, v
   int *nej;                      // ejections so far (may exceed EJ_CAP: records past it are dropped)
   BsGridBuf gb;                  // grid-wide BS of the largest groups (single-system modes; null otherwise)
+  double *spin;                  // spin angular momentum [3 npad] (Sect. 3.2, Collisions; null: not tracked)
+  double *crec;                  // collision reports [CREC_CAP * CREC] (null: none kept)
+  int *ncrec;                    // mergers so far (may exceed CREC_CAP: reports past it are dropped)
 };
 
 // Test particles (massless, perturbed by the massive bodies of a Sim; Sect. 3.3). SoA with
@@ -467,6 +473,49 @@ static __device__ int kepler_drift_dev(double mu, double mu2, double &x, double 
   x = xn; y = yn; z = zn;
   vx = vxn; vy = vyn; vz = vzn;
   return 0;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Merger bookkeeping of the BS kernels (Sect. 3.2, Collisions), called by the one thread that applies
+// a merger of bodies ia < ib, before the survivor's state is replaced: the report of both bodies'
+// positions, velocities and spins at the last time before the contact (ya, yb: the start of the BS
+// substep in which it was found, t its time within the composition substep), then the survivor's
+// spin from angular-momentum conservation: both spins plus mu (x_b - x_a) x (v_b - v_a) of the
+// states yna, ynb after the substep, mu = m_a m_b / (m_a + m_b); the ghost's spin is cleared.
+// Report layout: step (1-based), substep, t, ia, ib, x_a, v_a, spin_a, x_b, v_b, spin_b, survivor.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ void merger_report(const Sim &S, int ia, int ib, const double *ya, const double *yb,
+                                              const double *yna, const double *ynb, double ma, double mb,
+                                              bool keep_a, double t) {
+  const int np = S.npad;
+  if (S.crec) {
+    const int slot = atomicAdd(S.ncrec, 1);
+    if (slot < CREC_CAP) {
+      double *r = S.crec + (size_t)slot * CREC;
+      r[0] = (double)*(volatile long long *)&S.counters[C_STEPS];
+      r[1] = (double)*(volatile int *)&S.flags[2];
+      r[2] = t;
+      r[3] = (double)ia;
+      r[4] = (double)ib;
+      for (int c = 0; c < 3; ++c) {
+        r[5 + c] = ya[c]; r[8 + c] = ya[3 + c]; r[11 + c] = S.spin ? S.spin[c * np + ia] : 0.0;
+        r[14 + c] = yb[c]; r[17 + c] = yb[3 + c]; r[20 + c] = S.spin ? S.spin[c * np + ib] : 0.0;
+      }
+      r[23] = (double)(keep_a ? ia : ib);
+    } else {
+      atomicOr(S.status, ST_COLL_OVERFLOW);
+    }
+  }
+  if (S.spin) {
+    const double mu = ma * mb / (ma + mb);
+    const double dx = ynb[0] - yna[0], dy = ynb[1] - yna[1], dz = ynb[2] - yna[2];
+    const double dvx = ynb[3] - yna[3], dvy = ynb[4] - yna[4], dvz = ynb[5] - yna[5];
+    const double L[3] = {mu * (dy * dvz - dz * dvy), mu * (dz * dvx - dx * dvz), mu * (dx * dvy - dy * dvx)};
+    const int sv = keep_a ? ia : ib, dd = keep_a ? ib : ia;
+    double nsp[3];
+    for (int c = 0; c < 3; ++c) nsp[c] = S.spin[c * np + ia] + S.spin[c * np + ib] + L[c];
+    for (int c = 0; c < 3; ++c) { S.spin[c * np + sv] = nsp[c]; S.spin[c * np + dd] = 0.0; }
+  }
 }
 
 // Warp reductions (butterfly), fixed order -> deterministic

@@ -6,11 +6,14 @@
 
 namespace genga {
 
-enum FinMode { FIN_CLOSE = 0, FIN_OPEN = 1, FIN_INIT = 2 };
+// FIN_CLOSE_ALL: a closing kick whose pair kernel weighed every pair (no near pairs, far field kept)
+enum FinMode { FIN_CLOSE = 0, FIN_OPEN = 1, FIN_INIT = 2, FIN_CLOSE_ALL = 3 };
 
 // kick.cu
 void launch_rcrit(const Sim &S, const DevParams &P, double tau_abs, int check_reuse, cudaStream_t st);
-void launch_kick(const Sim &S, const DevParams &P, bool full, bool precise, cudaStream_t st);
+// full: every pair with its changeover weight, no candidates recorded; runs only when the opening
+// kick must be recomputed, unless force (then always, also recording the momentum for the Sun drift)
+void launch_kick(const Sim &S, const DevParams &P, bool full, bool precise, cudaStream_t st, bool force = false);
 void launch_fin(const Sim &S, const DevParams &P, FinMode mode, double h1, double h2, double *aout,
                 cudaStream_t st);
 void launch_hc(const Sim &S, double hcm, cudaStream_t st);
@@ -18,8 +21,9 @@ int kick_grid(const Sim &S);
 
 // step.cu
 void launch_drift(const Sim &S, const DevParams &P, double tau, double hcm1, double hcm2,
-                  int first_substep, cudaStream_t st);
-void launch_encounter(const Sim &S, double tau, unsigned *ebm, cudaStream_t st);
+                  int substep, cudaStream_t st);
+// keep: leave the candidate set in place for the next substep (literal higher-order prechecker)
+void launch_encounter(const Sim &S, double tau, unsigned *ebm, cudaStream_t st, bool keep = false);
 void launch_group(const Sim &S, cudaStream_t st, int gbig = BS_GMAX + 1);  // gbig: size threshold of S.big
 void launch_kepler_phase(int n, double mu, double dt, int maxit, const int *alive, double *x, double *v,
                          int *fail, cudaStream_t st);
@@ -63,7 +67,7 @@ void launch_b_rcrit(const Sim &S, const DevParams &P, double tau_abs, int check,
 void launch_b_kick(const Sim &S, const DevParams &P, FinMode mode, double h1, double h2, int split, int block,
                    cudaStream_t st);
 void launch_b_momentum(const Sim &S, double *out, cudaStream_t st);
-void launch_b_drift(const Sim &S, const DevParams &P, double tau, double h1, double h2, int first, cudaStream_t st);
+void launch_b_drift(const Sim &S, const DevParams &P, double tau, double h1, double h2, int substep, cudaStream_t st);
 void launch_b_encounter(const Sim &S, double tau, cudaStream_t st);
 void launch_b_group(const Sim &S, cudaStream_t st);
 void launch_b_hc(const Sim &S, double h, cudaStream_t st);
@@ -94,6 +98,8 @@ void launch_to_helio(const Sim &S, const DevParams &P, double *xh, double *vh, d
                      double *R_out, int *alive_out, cudaStream_t st);
 void launch_energy(const Sim &S, const DevParams &P, double *scratch, double *E, cudaStream_t st);
 void launch_mathcheck(int n, int which, const double *in, double *out, cudaStream_t st);
+// FP64 FMA throughput of the device (flop/s; FMA = 2), timed with events around one launch
+double fp64_probe_flops(int iters, int blocks, float *ms, cudaStream_t st, double *scratch);
 void launch_soa_setup(const Sim &S, const DevParams &P, const double *m, const int *alive,
                       const double *x, const double *v, const double *rc, int n, cudaStream_t st);
 void launch_soa_out(const Sim &S, double *x, double *v, int n, cudaStream_t st);

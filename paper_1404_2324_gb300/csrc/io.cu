@@ -145,6 +145,25 @@ __global__ void k_mathcheck(int n, int which, const double *in, double *out) {
   out[i] = which == 0 ? rsqrt_refined(x) : (which == 1 ? rcube_refined(x) : rcp_refined(x));
 }
 
+// FP64 throughput probe: every thread advances 8 independent FMA chains x -> x b + c (b = 1 - 2^-40,
+// so the chains stay near c / (1 - b) and never overflow); 2 flops per FMA. The sum is written only
+// when it takes an impossible value, so the chains are not optimised away and nothing is stored.
+constexpr int PROBE_CHAINS = 8;
+__global__ void __launch_bounds__(256) k_fp64_probe(int iters, double seed, double *out) {
+  double a[PROBE_CHAINS];
+#pragma unroll
+  for (int k = 0; k < PROBE_CHAINS; ++k) a[k] = seed + 1e-3 * k + 1e-9 * threadIdx.x;
+  const double b = 1.0 - 9.094947017729282e-13, c = 1e-12;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < PROBE_CHAINS; ++k) a[k] = fma(a[k], b, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < PROBE_CHAINS; ++k) s += a[k];
+  if (s == -1.0) out[0] = s;
+}
+
 // Phase entry points: load caller SoA arrays of n bodies into a Sim of padded size.
 __global__ void k_soa_setup(Sim S, DevParams P, const double *m, const int *alive, const double *x,
                             const double *v, const double *rc, int n) {
@@ -189,6 +208,23 @@ void launch_energy(const Sim &S, const DevParams &P, double *scratch, double *E,
   k_energy_part<<<dim3(S.nt, S.nt), 32, 0, st>>>(S, P, scratch);
   k_energy_sum<<<1, 32, 0, st>>>(S, P, scratch, E);
 }
+double fp64_probe_flops(int iters, int blocks, float *ms, cudaStream_t st, double *scratch) {
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  k_fp64_probe<<<blocks, 256, 0, st>>>(iters / 8 > 0 ? iters / 8 : 1, 1.0, scratch);  // warm-up
+  cudaEventRecord(e0, st);
+  k_fp64_probe<<<blocks, 256, 0, st>>>(iters, 1.0, scratch);
+  cudaEventRecord(e1, st);
+  cudaEventSynchronize(e1);
+  float t = 0.0f;
+  cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (ms) *ms = t;
+  return 2.0 * PROBE_CHAINS * (double)iters * (double)blocks * 256.0 / (t * 1e-3);
+}
+
 void launch_mathcheck(int n, int which, const double *in, double *out, cudaStream_t st) {
   k_mathcheck<<<(n + 127) / 128, 128, 0, st>>>(n, which, in, out);
 }

@@ -54,13 +54,13 @@ __global__ void k_rcrit(Sim S, DevParams P, double tau_abs, int check_reuse) {
 // radii grew too much for reuse); otherwise far pairs only, candidates recorded in the bitmap.
 // ---------------------------------------------------------------------------------------------
 template <bool FULL, bool PRECISE>
-__global__ void __launch_bounds__(128) k_kick(Sim S, DevParams P) {
-  if (FULL && S.flags[0] == 0) return;
+__global__ void __launch_bounds__(128) k_kick(Sim S, DevParams P, int force) {
+  if (FULL && !force && S.flags[0] == 0) return;
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int np = S.npad, nt = S.nt, W = S.W;
   const double *__restrict__ X = S.x;
-  if (!FULL && warp < nt) {  // per-tile momentum before the closing kick (second Sun drift)
+  if ((!FULL || force) && warp < nt) {  // per-tile momentum before the closing kick (second Sun drift)
     int i = warp * 32 + lane;
     double mi = S.m[i];
 #pragma unroll
@@ -215,6 +215,7 @@ __device__ __forceinline__ double near_term(const Sim &S, const DevParams &P, in
 // ---------------------------------------------------------------------------------------------
 template <int MODE>
 __global__ void __launch_bounds__(128) k_fin(Sim S, DevParams P, double h1, double h2, double *aout) {
+  constexpr bool ALL = MODE == FIN_CLOSE_ALL;  // the pair kernel weighed every pair: no near pass
   const int B = blockIdx.x, c = blockIdx.y, wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int np = S.npad, nt = S.nt, i = B * 32 + lane;
   __shared__ double red[4][32];
@@ -233,7 +234,7 @@ __global__ void __launch_bounds__(128) k_fin(Sim S, DevParams P, double h1, doub
   // this tile's candidate partners: counts and offsets (warp 0), then the lists (all threads)
   bool overflow = false;
   if (wi == 0) {
-    const bool any = !full_open && ((S.rowany[i >> 5] >> (i & 31)) & 1u);
+    const bool any = !ALL && !full_open && ((S.rowany[i >> 5] >> (i & 31)) & 1u);
     int cnt = any ? S.ccnt[i] : 0;
     overflow = cnt > CCAP;
     if (overflow) cnt = 0;
@@ -272,7 +273,7 @@ __global__ void __launch_bounds__(128) k_fin(Sim S, DevParams P, double h1, doub
   __syncthreads();
   if (wi != 0) return;
   double a = use_part ? (red[0][lane] + red[1][lane]) + (red[2][lane] + red[3][lane]) : S.afar[c * np + i];
-  if (MODE != FIN_OPEN) S.afar[c * np + i] = a;
+  if (MODE != FIN_OPEN && !ALL) S.afar[c * np + i] = a;
   for (int k = off[lane]; k < off[lane + 1]; ++k) a += contrib[k];
   if (overflow) a += near_accel(S, P, i, c);
   if (aout) aout[c * np + i] = a;
@@ -298,14 +299,15 @@ void launch_rcrit(const Sim &S, const DevParams &P, double tau_abs, int check_re
   k_rcrit<<<(S.npad + 127) / 128, 128, 0, st>>>(S, P, tau_abs, check_reuse);
 }
 
-void launch_kick(const Sim &S, const DevParams &P, bool full, bool precise, cudaStream_t st) {
+void launch_kick(const Sim &S, const DevParams &P, bool full, bool precise, cudaStream_t st, bool force) {
   const int grid = kick_grid(S);
+  const int f = force ? 1 : 0;
   if (full) {
-    if (precise) k_kick<true, true><<<grid, 128, 0, st>>>(S, P);
-    else k_kick<true, false><<<grid, 128, 0, st>>>(S, P);
+    if (precise) k_kick<true, true><<<grid, 128, 0, st>>>(S, P, f);
+    else k_kick<true, false><<<grid, 128, 0, st>>>(S, P, f);
   } else {
-    if (precise) k_kick<false, true><<<grid, 128, 0, st>>>(S, P);
-    else k_kick<false, false><<<grid, 128, 0, st>>>(S, P);
+    if (precise) k_kick<false, true><<<grid, 128, 0, st>>>(S, P, 0);
+    else k_kick<false, false><<<grid, 128, 0, st>>>(S, P, 0);
   }
 }
 
@@ -313,6 +315,7 @@ void launch_fin(const Sim &S, const DevParams &P, FinMode mode, double h1, doubl
                 cudaStream_t st) {
   dim3 grid(S.nt, 3);
   if (mode == FIN_CLOSE) k_fin<FIN_CLOSE><<<grid, 128, 0, st>>>(S, P, h1, h2, aout);
+  else if (mode == FIN_CLOSE_ALL) k_fin<FIN_CLOSE_ALL><<<grid, 128, 0, st>>>(S, P, h1, h2, aout);
   else if (mode == FIN_OPEN) k_fin<FIN_OPEN><<<grid, 128, 0, st>>>(S, P, h1, h2, aout);
   else k_fin<FIN_INIT><<<grid, 128, 0, st>>>(S, P, h1, h2, aout);
 }

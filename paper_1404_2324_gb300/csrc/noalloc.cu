@@ -7,6 +7,7 @@
 // a fixed memory budget), cannot call entry points that allocate. This variant keeps all of its
 // scratch in one file-scope __device__ array instead: every GPU that loads the library holds it
 // (about 2 MB) until the process exits. The caller still provides the inputs and outputs.
+#include <atomic>
 #include <cstring>
 
 #include "../../include/genga.h"
@@ -57,18 +58,21 @@ static __device__ __align__(256) unsigned char g_kick_scratch[NA_BYTES];
 namespace {
 
 constexpr int NA_MAXDEV = 64;
-unsigned char *g_scratch_ptr[NA_MAXDEV] = {};  // device address of g_kick_scratch, per device
+std::atomic<unsigned char *> g_scratch_ptr[NA_MAXDEV] = {};  // device address of g_kick_scratch, per device
 
-// Set-up, once per device, with that device current.
+// Set-up, once per device, with that device current. Threads that get here first at the same time
+// look the address up alike and store the same value.
 int scratch_address(unsigned char **out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAXDEV) return GENGA_ECUDA;
-  if (!g_scratch_ptr[dev]) {
-    void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_kick_scratch) != cudaSuccess || !p) return GENGA_ECUDA;
-    g_scratch_ptr[dev] = (unsigned char *)p;
+  unsigned char *p = g_scratch_ptr[dev].load(std::memory_order_acquire);
+  if (!p) {
+    void *q = nullptr;
+    if (cudaGetSymbolAddress(&q, g_kick_scratch) != cudaSuccess || !q) return GENGA_ECUDA;
+    p = (unsigned char *)q;
+    g_scratch_ptr[dev].store(p, std::memory_order_release);
   }
-  *out = g_scratch_ptr[dev];
+  *out = p;
   return GENGA_OK;
 }
 
@@ -118,7 +122,7 @@ extern "C" int genga_kick_noalloc(int n, double G, double pc, int kmode, int pre
   S.ccnt = (int *)(base + O_CCNT); S.clist = (int *)(base + O_CLIST);
   S.items = (int *)(base + O_ITEMS);
   S.nitems = S.nt * S.nt;
-  S.nwarps = S.nitems < 4 * sms ? S.nitems : 4 * sms;
+  S.nwarps = S.nitems < 8 * sms ? S.nitems : 8 * sms;  // the allocating kick's configuration
   S.flags = (int *)(base + O_FLAGS); S.status = (int *)(base + O_STATUS);
   S.counters = (long long *)(base + O_COUNTERS);
   double *aout = (double *)(base + O_AOUT);

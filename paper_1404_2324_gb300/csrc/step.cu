@@ -10,11 +10,14 @@ namespace genga {
 // substep's first), keep (x0, v0), then the Kepler drift for tau. One warp per 32 bodies; every
 // warp sums the per-tile momentum partials itself (no extra launch).
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(32) k_drift(Sim S, DevParams P, double tau, double hcm1, double hcm2, int first) {
+__global__ void __launch_bounds__(32) k_drift(Sim S, DevParams P, double tau, double hcm1, double hcm2, int substep) {
   const int lane = threadIdx.x;
   const int i = blockIdx.x * 32 + lane;
   const int np = S.npad, nt = S.nt;
-  if (first && i == 0) S.flags[0] = 0;  // the opening kick of this step has consumed the flag
+  if (i == 0) {
+    if (substep == 0) S.flags[0] = 0;  // the opening kick of this step has consumed the flag
+    S.flags[2] = substep;              // for the collision reports of this substep's BS
+  }
   double shift[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -79,7 +82,7 @@ __device__ __forceinline__ bool encounter_test(const Sim &S, double tau, int i, 
   return dmin < __dmul_rn(rcij, rcij);
 }
 
-__global__ void __launch_bounds__(ENC_THREADS) k_encounter(Sim S, double tau, unsigned *ebm) {
+__global__ void __launch_bounds__(ENC_THREADS) k_encounter(Sim S, double tau, unsigned *ebm, int keep) {
   __shared__ int s_i[ENC_CAP], s_j[ENC_CAP];
   __shared__ int s_n, s_found;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -115,11 +118,11 @@ __global__ void __launch_bounds__(ENC_THREADS) k_encounter(Sim S, double tau, un
         const int j = S.clist[i * CCAP + k];
         if (j > i) add(i, j);
       }
-      for (int w = lane; w < W; w += 32) crow[w] = 0u;
+      if (!keep) for (int w = lane; w < W; w += 32) crow[w] = 0u;
     } else {  // list overflowed: scan the bitmap row
       for (int w = lane; w < W; w += 32) {
         unsigned bits = crow[w];
-        crow[w] = 0u;
+        if (!keep) crow[w] = 0u;
         const int lo = w * 32;
         if (lo + 31 <= i) bits = 0u;
         else if (lo <= i) bits &= (i - lo + 1 >= 32) ? 0u : (0xffffffffu << (i - lo + 1));
@@ -130,10 +133,10 @@ __global__ void __launch_bounds__(ENC_THREADS) k_encounter(Sim S, double tau, un
         }
       }
     }
-    if (lane == 0) S.ccnt[i] = 0;
+    if (lane == 0 && !keep) S.ccnt[i] = 0;
   }
   __syncthreads();
-  if (tid == 0 && i0 < np) S.rowany[i0 >> 5] = 0u;  // the CTA's 32 rows are clear
+  if (tid == 0 && i0 < np && !keep) S.rowany[i0 >> 5] = 0u;  // the CTA's 32 rows are clear
   const int n = s_n < ENC_CAP ? s_n : ENC_CAP;
   for (int p = tid; p < n; p += ENC_THREADS)
     if (encounter_test(S, tau, s_i[p], s_j[p])) hit(s_i[p], s_j[p]);
@@ -353,11 +356,11 @@ __global__ void k_copy_edges(Sim S, const int *pairs, int npairs) {
 
 // ---------------------------------------------------------------------------------------------
 void launch_drift(const Sim &S, const DevParams &P, double tau, double hcm1, double hcm2,
-                  int first_substep, cudaStream_t st) {
-  k_drift<<<S.npad / 32, 32, 0, st>>>(S, P, tau, hcm1, hcm2, first_substep);
+                  int substep, cudaStream_t st) {
+  k_drift<<<S.npad / 32, 32, 0, st>>>(S, P, tau, hcm1, hcm2, substep);
 }
-void launch_encounter(const Sim &S, double tau, unsigned *ebm, cudaStream_t st) {
-  k_encounter<<<(S.npad + ENC_BODIES - 1) / ENC_BODIES, ENC_THREADS, 0, st>>>(S, tau, ebm);
+void launch_encounter(const Sim &S, double tau, unsigned *ebm, cudaStream_t st, bool keep) {
+  k_encounter<<<(S.npad + ENC_BODIES - 1) / ENC_BODIES, ENC_THREADS, 0, st>>>(S, tau, ebm, keep ? 1 : 0);
 }
 void launch_group(const Sim &S, cudaStream_t st, int gbig) { k_group<<<1, GROUP_THREADS, 0, st>>>(S, gbig); }
 void launch_kepler_phase(int n, double mu, double dt, int maxit, const int *alive, double *x, double *v,

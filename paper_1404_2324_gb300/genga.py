@@ -31,6 +31,7 @@ ST_RECORD_OVERFLOW = 32
 ST_UNION_ROUNDS = 16
 ST_EJECT_OVERFLOW = 64
 ST_GRID_TIMEOUT = 128
+ST_COLL_OVERFLOW = 256
 COUNTER_NAMES = ["steps", "candidates", "encounters", "groups", "bs_steps", "kepler_fallbacks",
                  "mergers", "full_kicks"]
 
@@ -43,7 +44,7 @@ class genga_params(C.Structure):
     _fields_ = [("n1", C.c_double), ("n2", C.c_double), ("pc", C.c_double), ("bs_eps", C.c_double),
                 ("bs_kmax", C.c_int), ("bs_max_halvings", C.c_int), ("kepler_maxit", C.c_int),
                 ("kmode", C.c_int), ("collisions", C.c_int), ("precise_div", C.c_int),
-                ("rcut", C.c_double), ("rcut_sun", C.c_double), ("nmin", C.c_int)]
+                ("rcut", C.c_double), ("rcut_sun", C.c_double), ("nmin", C.c_int), ("precheck_substeps", C.c_int)]
 
 
 _D = C.POINTER(C.c_double)
@@ -63,6 +64,12 @@ _SIGS = {
     "genga_energy": (C.c_int, [_V, _D, _D]),
     "genga_encounters": (C.c_int, [_V, C.c_int, _I, C.c_int, _I]),
     "genga_ejections": (C.c_int, [_V, _D, C.c_int, _I]),
+    "genga_collisions": (C.c_int, [_V, _D, C.c_int, _I]),
+    "genga_fp64_probe": (C.c_int, [C.c_int, _D, C.POINTER(C.c_float), _V]),
+    "genga_tp_encounters": (C.c_int, [_V, _I, C.c_int, _I]),
+    "genga_batch_encounters": (C.c_int, [_V, _I, C.c_int, _I]),
+    "genga_set_spin": (C.c_int, [_V, _D]),
+    "genga_get_spin": (C.c_int, [_V, _D]),
     "genga_status": (C.c_int, [_V, _I, C.POINTER(C.c_longlong)]),
     "genga_free": (None, [_V]),
     "genga_set_profiling": (C.c_int, [_V, C.c_int]),
@@ -295,6 +302,57 @@ def genga_ejections(ctx):
     return out[: min(n.value, 4096)]
 
 
+CREC = 24  # doubles per collision report
+
+
+def genga_collisions(ctx):
+    """Collision reports (Sect. 3.2): rows of step, substep, time, i, j, x_i, v_i, spin_i, x_j, v_j,
+    spin_j, survivor (see include/genga.h)."""
+    n = C.c_int(0)
+    _check(lib().genga_collisions(ctx, None, 0, C.byref(n)), "genga_collisions")
+    out = np.zeros((max(n.value, 1), CREC))
+    _check(lib().genga_collisions(ctx, out.ctypes.data_as(_D), n.value, C.byref(n)), "genga_collisions")
+    return out[: min(n.value, 4096)]
+
+
+def _pairs(fn, ctx, name):
+    n = C.c_int(0)
+    rc = fn(ctx, None, 0, C.byref(n))
+    if rc not in (0, -4):
+        _check(rc, name)
+    out = np.zeros((max(n.value, 1), 2), np.int32)
+    _check(fn(ctx, out.ctypes.data_as(_I), n.value, C.byref(n)), name)
+    return out[: n.value]
+
+
+def genga_tp_encounters(ctx):
+    """(particle, planet) encounter pairs of the last substep; planets numbered with the central mass at 0."""
+    return _pairs(lib().genga_tp_encounters, ctx, "genga_tp_encounters")
+
+
+def genga_batch_encounters(ctx):
+    """Encounter pairs of every system in the last substep, flat caller indices (i < j)."""
+    return _pairs(lib().genga_batch_encounters, ctx, "genga_batch_encounters")
+
+
+def genga_fp64_probe(iters=1 << 16, stream=None):
+    """Measured FP64 throughput of the device in TFLOP/s (and the probe launch's ms)."""
+    tf, ms = C.c_double(0.0), C.c_float(0.0)
+    _check(lib().genga_fp64_probe(int(iters), C.byref(tf), C.byref(ms), _stream_ptr(stream)), "genga_fp64_probe")
+    return tf.value, ms.value
+
+
+def genga_set_spin(ctx, spin):
+    sp = np.ascontiguousarray(spin, np.float64)
+    _check(lib().genga_set_spin(ctx, sp.ctypes.data_as(_D)), "genga_set_spin")
+
+
+def genga_get_spin(ctx, nrows):
+    out = np.zeros((nrows, 3))
+    _check(lib().genga_get_spin(ctx, out.ctypes.data_as(_D)), "genga_get_spin")
+    return out
+
+
 # ------------------------------------------------------------------------------------ batched mode
 def genga_init_batch(offsets, m0, masses, radii, x, v, G, dt, order=2, steps_per_launch=100):
     off = np.ascontiguousarray(offsets, np.int32)
@@ -438,3 +496,12 @@ class Genga:
 
     def status(self):
         return genga_status(self.ctx)
+
+    def collisions(self):
+        return genga_collisions(self.ctx)
+
+    def spin(self):
+        return genga_get_spin(self.ctx, self.n)
+
+    def set_spin(self, spin):
+        genga_set_spin(self.ctx, spin)

@@ -149,3 +149,31 @@ def test_batch_autotuned_shape_is_reported():
     assert split in (1, 2, 4) and block in (64, 128, 256) and spl == 100
     assert genga.genga_launch_count(h) == 13  # incl. the four BS kernels (pairs, 3..4, 5..32, 33..64 members)
     genga.genga_free(h)
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_first_step_encounter_pairs_are_bit_exact_per_system(order):
+    """From identical inputs, every system's encounter pairs of the last substep of the first step
+    equal the oracle's for that system (flat indices), pair for pair."""
+    b = ics.batch(4, n_sys=96)
+    off = b["offsets"]
+    h = genga.genga_init_batch(off, b["m0"], b["m"], b["R"], b["x"], b["v"], b["G"], b["dt"], order, 1)
+    try:
+        genga.genga_step(h, 1)
+        gp = genga.genga_batch_encounters(h)
+        ref = []
+        for s in range(len(off) - 1):
+            sl = slice(off[s], off[s + 1])
+            p = O.params(G=b["G"], m0=b["m0"][s], dt=b["dt"], order=order)
+            sim = O.Sim(p, b["m"][sl], b["R"][sl], b["x"][sl], b["v"][sl])
+            sim.step(1)
+            e = sim.encounters(-1)
+            if len(e):
+                ref.append(e + off[s])
+            sim.close()
+        op = np.vstack(ref) if ref else np.zeros((0, 2), np.int32)
+        op = op[np.lexsort((op[:, 1], op[:, 0]))]
+        assert len(op) > 10
+        np.testing.assert_array_equal(gp, op)
+    finally:
+        genga.genga_free(h)

@@ -9,7 +9,7 @@ import pytest
 
 import oracle as O
 from paper_1404_2324_gb300 import genga, ics
-from tests.gpu_util import pair_sims, rel_state_error, with_central
+from tests.gpu_util import oracle_sensitivity, pair_sims, rel_state_error, with_central
 
 pytestmark = pytest.mark.gpu
 
@@ -51,6 +51,85 @@ def test_disk2048_fourth_order_parity():
     code, cnt = g.status()
     assert code & (genga.ST_BS_FAILED | genga.ST_GROUP_TOO_LARGE | genga.ST_UNION_ROUNDS) == 0
     assert cnt["candidates"] > 0 and cnt["encounters"] > 0 and cnt["bs_steps"] > 0
+
+
+def test_disk2048_hundred_steps_with_a_planted_merger():
+    """The benchmark's workload (2048 bodies, 4th order, BS and merging) over 100 steps, with one pair
+    put on a collision course so that a merger happens at N = 2048. Bound: 1e-9, or 10x the oracle's
+    own sensitivity to a 1e-15 change of the start where that is larger (both printed)."""
+    d = ics.disk2048(2)
+    k = 700
+    d["x"][k + 1] = d["x"][k] + np.array([0.0004, 0.0, 0.0])
+    d["v"][k + 1] = d["v"][k] - np.array([0.00015, 0.0, 0.0])
+    d["R"][k:k + 2] = 3e-5
+    g, o = pair_sims(d, 4, steps=100)
+    try:
+        err, same = rel_state_error(g, o)
+        sens = oracle_sensitivity(d, 4, 100, trials=2) if err > 1e-9 else 0.0  # only where needed
+        print(f"disk2048 x 100 steps: GPU vs oracle {err:.2e}, oracle self-sensitivity {sens:.2e}")
+        assert same and err <= max(1e-9, 10.0 * sens), (err, sens)
+        code, cnt = g.status()
+        st = o.stats()
+        assert cnt["mergers"] == st["collisions"] >= 1
+        gs, os_ = g.state(), o.state()
+        np.testing.assert_array_equal(gs["m"][1:], os_["m"])
+        gr, orr = g.collisions(), o.collision_records()
+        np.testing.assert_array_equal(gr[:, [0, 1, 3, 4, 23]], orr[:, [0, 1, 3, 4, 23]] + [0, 0, 1, 1, 1])
+        assert code & (genga.ST_BS_FAILED | genga.ST_GROUP_TOO_LARGE | genga.ST_GRID_TIMEOUT) == 0
+    finally:
+        g.close()
+        o.close()
+
+
+@pytest.mark.parametrize("order", [4, 6])
+def test_literal_prechecker_matches_oracle(order):
+    """precheck_substeps = 0 (Sect. 2.3: the substeps run the full scheme but not the prechecker):
+    the step-start candidates serve every substep, the inner closing kicks weigh all pairs."""
+    d = ics.disk32(1)
+    g, o = pair_sims(d, order, steps=1, precheck_substeps=0)
+    try:
+        err, same = rel_state_error(g, o)
+        assert same and err <= 1e-12, err
+        for js in range(len(O.substep_weights(order))):
+            np.testing.assert_array_equal(g.encounters(js), o.encounters(js) + 1)
+        g.step(99)
+        o.step(99)
+        err, same = rel_state_error(g, o)
+        assert same and err <= 1e-9, err
+        code, cnt = g.status()
+        st = o.stats()
+        assert cnt["encounters"] == st["encounters"] > 0 and cnt["groups"] == st["groups"]
+    finally:
+        g.close()
+        o.close()
+
+
+def test_disk2048_literal_prechecker():
+    d = ics.disk2048(2)
+    g, o = pair_sims(d, 4, steps=1, precheck_substeps=0)
+    try:
+        err, same = rel_state_error(g, o)
+        assert same and err <= 1e-12, err
+        for js in range(3):
+            np.testing.assert_array_equal(g.encounters(js), o.encounters(js) + 1)
+        g.step(4)
+        o.step(4)
+        err, same = rel_state_error(g, o)
+        assert same and err <= 1e-11, err
+    finally:
+        g.close()
+        o.close()
+
+
+def test_literal_prechecker_is_rejected_outside_the_main_mode():
+    b = ics.batch(1, n_sys=4)
+    h = genga.genga_init_batch(b["offsets"], b["m0"], b["m"], b["R"], b["x"], b["v"], b["G"], b["dt"], 4, 1)
+    try:
+        p = genga.genga_default_params()
+        p.precheck_substeps = 0
+        assert genga.lib().genga_set_params(h, genga.C.byref(p)) == genga.GENGA_EINVAL
+    finally:
+        genga.genga_free(h)
 
 
 def test_gradient_mode_and_precise_division_parity():

@@ -158,3 +158,22 @@ def test_tp_sizes_out_of_range_are_rejected(n_planets, n_tp):
     vt = np.tile([[0.0, 0.014, 0.0]], (n_tp, 1))
     with pytest.raises(genga.GengaError):
         genga.genga_init_tp(m, np.zeros(n_planets + 1), x, v, ics.G_GAUSS, 6.0, 2, xt, vt, np.zeros(n_tp))
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_first_step_particle_planet_encounter_pairs_are_bit_exact(order):
+    """From identical inputs, the (particle, planet) encounter pairs of the last substep of the first
+    step equal the oracle's pair for pair (the Hermite test runs in the same arithmetic)."""
+    d = _inputs()
+    h = _gpu(d, order)
+    o = _oracle(d, order)
+    try:
+        genga.genga_step(h, 1)
+        o.step(1)
+        gp = genga.genga_tp_encounters(h)
+        op = o.encounters(-1)
+        assert len(op) > 10
+        np.testing.assert_array_equal(gp, op + [0, 1])  # planets numbered with the central mass at 0
+    finally:
+        genga.genga_free(h)
+        o.close()

@@ -59,3 +59,35 @@ def test_noalloc_kick_rejects_sizes_above_its_maximum():
     assert L.genga_kick_noalloc(1025, 1.0, 3.0, 0, 0, V(z.data_ptr()), V(z.data_ptr()), V(z.data_ptr()),
                                 V(z.data_ptr()), V(z.data_ptr()), V(z.data_ptr()), 1, V(z.data_ptr()),
                                 None) == genga.GENGA_ESIZE
+
+
+def test_noalloc_kick_with_a_small_cap_reports_the_full_count():
+    """cap below the candidate count: *ncand (on the device) is the full count, the first cap pairs
+    are the allocating kick's first cap pairs, and no device memory changes hands across calls."""
+    L = genga.lib()
+    V = ctypes.c_void_p
+    stream = torch().cuda.current_stream()
+    n, seed = 512, 23
+    G, m, alive, x, rc = _inputs(n, seed)
+    full = n * (n - 1) // 2
+    a_ref, c_ref = dev(np.zeros((3, n))), dev(np.zeros(2 * full, np.int32))
+    nref = genga.genga_phase_kick(n, G, 3.0, 0, 0, dev(m), dev(alive), soa(x), dev(rc), a_ref, c_ref, full)
+    cap = nref // 3
+    assert cap > 0
+    ms, als, xs, rcs = dev(m), dev(alive), soa(x), dev(rc)
+    a, cand, cnt = dev(np.zeros((3, n))), dev(np.zeros(2 * cap, np.int32)), dev(np.zeros(1, np.int32))
+
+    def call():
+        return L.genga_kick_noalloc(n, G, 3.0, 0, 0, V(ms.data_ptr()), V(als.data_ptr()), V(xs.data_ptr()),
+                                    V(rcs.data_ptr()), V(a.data_ptr()), V(cand.data_ptr()), cap, V(cnt.data_ptr()),
+                                    V(stream.cuda_stream))
+
+    assert call() == 0
+    torch().cuda.synchronize()
+    free0 = torch().cuda.mem_get_info()[0]
+    for _ in range(2):
+        assert call() == 0
+        torch().cuda.synchronize()
+    assert torch().cuda.mem_get_info()[0] == free0
+    assert int(cnt.item()) == nref
+    np.testing.assert_array_equal(cand.cpu().numpy(), c_ref.cpu().numpy()[: 2 * cap])
