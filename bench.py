@@ -12,7 +12,12 @@ Prints ONE JSON line. value: steps/s with the state resident in HBM, timed with 
 step on the launching stream, L2 flushed (256 MiB write) before every timed step. e2e: the same
 metric through the public API with host buffers: each step uploads the state from pinned host
 memory (genga_set_state), steps, and reads it back (genga_get_state). roofline: the pairwise
-kick kernel (dominant), FP64-ALU bound. cpu_baseline: the CPU oracle on a bounded sample.
+kick kernel (dominant), FP64-ALU bound, against the derived FP64 peak and against the FP64
+throughput measured in the same run (genga_fp64_probe); step_fp64: the kick flops over the whole
+step's time. cpu_baseline: the CPU oracle on a bounded sample, single-threaded and built with
+OpenMP on all host cores. Further legs: the batched many-systems mode, the test-particle mode,
+the differentiable engine (adjoint/forward), config 1 (32 bodies, 2nd order) and the n1/n2 sweep
+of Sect. 5 (energy error and time).
 With --gpus N > 1 (torchrun) every rank runs an independent replica (the method does not shard
 at this N); value counts the steps of all ranks over the slowest rank's time, and only the main
 line runs (the batched, test-particle and adjoint legs are single-GPU measurements).
@@ -85,11 +90,11 @@ def committed_traffic():
 
 
 # ------------------------------------------------------------------------------------ oracle arm
-def run_oracle(steps, warmup):
+def run_oracle(steps, warmup, omp=False):
     import oracle as O
     d, *_ = make_input()
     p = O.params(G=d["G"], m0=d["m0"], dt=d["dt"], order=ORDER)
-    sim = O.Sim(p, d["m"], d["R"], d["x"], d["v"])
+    sim = O.Sim(p, d["m"], d["R"], d["x"], d["v"], omp=omp)
     sim.step(warmup)
     t0 = time.perf_counter()
     sim.step(steps)
@@ -98,11 +103,21 @@ def run_oracle(steps, warmup):
     return steps / dt, dt
 
 
-def cpu_baseline_entry(steps, warmup):
+def cpu_baseline_entry(steps, warmup, omp=False):
     rate, secs = run_oracle(steps, warmup)
-    return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} full steps of the same N=2048 4th-order disk after {warmup} warm-up steps, "
-                      f"single-threaded C oracle ({secs:.1f} s)"}
+    out = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{steps} full steps of the same N=2048 4th-order disk after {warmup} warm-up steps, "
+                     f"single-threaded C oracle ({secs:.1f} s)"}
+    if omp:
+        import oracle as O
+        if O.lib_omp() is not None:
+            r2, s2 = run_oracle(steps, warmup, omp=True)
+            out["all_cores"] = {"value": r2, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"the same {steps} steps, the oracle built with OpenMP (its pair sums split "
+                                          f"over bodies, results bit-identical), {os.cpu_count()} threads ({s2:.1f} s)"}
+        else:
+            out["all_cores"] = {"unavailable": "gcc without OpenMP on this host"}
+    return out
 
 
 # ------------------------------------------------------------------------------------ clocks
@@ -409,6 +424,90 @@ def run_adjoint(args):
                       f"steps, merging off; state resident in HBM (no L2 flush: each timed region is seconds long)"}
 
 
+# ------------------------------------------------------------------------------------ config 1 and the n1/n2 sweep
+def run_config1(args):
+    """The plain 2nd-order step of 32 planetesimals (config 1 of the recipe, Sect. 4.1's energy runs):
+    1000 steps timed as one stretch of graph replays (32 bodies: everything stays in L2)."""
+    import torch
+    from paper_1404_2324_gb300 import genga, ics
+    d = ics.disk32(1)
+    m = np.concatenate([[d["m0"]], d["m"]]); R = np.concatenate([[0.0], d["R"]])
+    x = np.vstack([np.zeros(3), d["x"]]); v = np.vstack([np.zeros(3), d["v"]])
+    ctx = genga.genga_init(m, R, x, v, d["G"], d["dt"], 2)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    genga.genga_set_stream(ctx, stream)
+    genga.genga_step(ctx, 20)
+    torch.cuda.synchronize()
+    steps = 1000
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    genga.genga_step(ctx, steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    kps = genga.genga_launch_count(ctx)
+    genga.genga_free(ctx)
+    import oracle as O
+    p = O.params(G=d["G"], m0=d["m0"], dt=d["dt"], order=2)
+    sim = O.Sim(p, d["m"], d["R"], d["x"], d["v"])
+    t0 = time.perf_counter()
+    sim.step(steps)
+    osec = time.perf_counter() - t0
+    sim.close()
+    return {"metric": "config-1 steps/s", "value": steps / (ms * 1e-3), "unit": "steps/s", "steps": steps,
+            "ms_per_step": ms / steps, "gpu_launches": kps * steps,
+            "cpu_baseline": {"value": steps / osec, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"the same {steps} steps, single-threaded C oracle ({osec:.2f} s)"},
+            "config": "disk32 seed 1: 32 planetesimals, m log-U[1e-8,1e-6], a U[0.5,1.5] AU, 2nd order, dt 6 d; "
+                      "no L2 flush (the 32-body state is a few KB)"}
+
+
+def run_sweep(args):
+    """The paper's Sect. 5 experiment: cumulative energy error and execution time against the
+    critical-radius parameters, n2 with n1 = 3 and n1 with n2 = 0, on a 32-body disk (2000 steps,
+    2nd order); and the 2048-body disk at 4th order for growing n2, where the encounter groups merge
+    into one large group (Sect. 5)."""
+    import torch
+    from paper_1404_2324_gb300 import genga, ics
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def run(d, order, n1, n2, steps, chunk):
+        m = np.concatenate([[d["m0"]], d["m"]]); R = np.concatenate([[0.0], d["R"]])
+        x = np.vstack([np.zeros(3), d["x"]]); v = np.vstack([np.zeros(3), d["v"]])
+        ctx = genga.genga_init(m, R, x, v, d["G"], d["dt"], order)
+        prm = genga.genga_default_params()
+        prm.n1, prm.n2 = n1, n2
+        genga.genga_set_params(ctx, prm)
+        genga.genga_set_stream(ctx, stream)
+        E0, U0 = genga.genga_energy(ctx)
+        err, ms = 0.0, 0.0
+        for _ in range(steps // chunk):
+            e0.record(stream)
+            genga.genga_step(ctx, chunk)
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            E, U = genga.genga_energy(ctx)
+            err = max(err, abs((E + U - E0 - U0) / E0))
+        code, cnt = genga.genga_status(ctx)
+        genga.genga_free(ctx)
+        return {"n1": n1, "n2": n2, "energy_error": err, "ms": ms, "ms_per_step": ms / steps,
+                "encounters_per_step": cnt["encounters"] / steps, "bs_steps_per_step": cnt["bs_steps"] / steps,
+                "status": code}
+
+    d32 = ics.disk32(1)
+    small = [run(d32, 2, 3.0, n2, 2000, 100) for n2 in (0.0, 0.4, 0.7, 1.0, 1.5)]
+    small += [run(d32, 2, n1, 0.0, 2000, 100) for n1 in (1.0, 7.0, 15.0, 30.0)]
+    d2048 = ics.disk2048(SEED, n=N_BODIES, order=ORDER)
+    large = [run(d2048, ORDER, 3.0, n2, 20, 10) for n2 in (0.4, 0.7, 1.0, 1.5)]
+    return {"disk32": small, "disk2048": large,
+            "config": "disk32 seed 1, 2nd order, dt 6 d, 2000 steps, energy sampled every 100 steps; "
+                      f"disk2048 seed {SEED}, 4th order, 20 steps each; n1 = 3 where n2 varies, n2 = 0 where n1 varies"}
+
+
 # ------------------------------------------------------------------------------------ ranks
 def rank_max(x, world, device=None):
     """The largest x over all ranks (the slowest replica sets the job's time); x itself at N = 1."""
@@ -497,6 +596,7 @@ def run_gpu(args, rank, world):
     props = torch.cuda.get_device_properties(dev)
     sm_max = clocks.get("sm_max_mhz") or 2070.0
     peak_tflops = props.multi_processor_count * FMA_LANES_PER_SM_CLK * 2 * sm_max * 1e6 / 1e12
+    probe_tflops, probe_ms = genga.genga_fp64_probe(1 << 15)
     kick_avg_s = (kick_ms / max(kick_launches, 1)) * 1e-3
     algo_flops = FLOPS_PER_PAIR * N_BODIES * (N_BODIES - 1)
     achieved = algo_flops / kick_avg_s / 1e12
@@ -507,11 +607,21 @@ def run_gpu(args, rank, world):
                 "kick_launches": kick_launches,
                 "peak_basis": f"FP64: {props.multi_processor_count} SMs x {FMA_LANES_PER_SM_CLK} FMA/clk x 2 flop x "
                               f"{sm_max:.0f} MHz (derived)",
+                "peak_probe": probe_tflops, "frac_probe": achieved / probe_tflops,
+                "peak_probe_basis": f"measured in this run: genga_fp64_probe, 8 independent FMA chains per thread, "
+                                    f"4 x 256 threads per SM, {probe_ms:.1f} ms",
                 "achieved_basis": f"{FLOPS_PER_PAIR} flop x N(N-1) ordered pairs per launch"}
+    kicks_per_step = kick_launches / max(args.steps, 1)
+    step_flops = kicks_per_step * algo_flops
+    step_tflops = step_flops / (t_max / args.steps * 1e-3) / 1e12
+    step_fp64 = {"achieved": step_tflops, "unit": "TFLOP/s", "frac": step_tflops / peak_tflops,
+                 "frac_probe": step_tflops / probe_tflops,
+                 "basis": f"{kicks_per_step:.0f} pairwise kicks x {FLOPS_PER_PAIR} flop x N(N-1) per step over the "
+                          f"whole step's time (drift, encounters, BS and the small kernels included)"}
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": workload_config(), "roofline": roofline, "e2e": e2e,
+           "config": workload_config(), "roofline": roofline, "step_fp64": step_fp64, "e2e": e2e,
            "gpu_launches": kernels_per_step * args.steps, "kernels_per_step": kernels_per_step,
            "clocks": clocks, "status": code, "counters": counters}
     return res
@@ -545,6 +655,8 @@ def main():
     ap.add_argument("--no-tp", action="store_true")
     ap.add_argument("--adj-steps", type=int, default=ADJ_STEPS, help="steps of the differentiable-engine leg")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-config1", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
     args = ap.parse_args()
     if args.warmup < 0 or args.steps < 1:
         ap.error("need --steps >= 1 and --warmup >= 0")
@@ -579,11 +691,15 @@ def main():
             res["test_particles"] = run_tp(args, measured_peaks(res))
         if not args.no_adjoint:
             res["adjoint"] = run_adjoint(args)
+        if not args.no_config1:
+            res["config1"] = run_config1(args)
+        if not args.no_sweep:
+            res["sweep"] = run_sweep(args)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             import oracle
             oracle.build()
-            res["cpu_baseline"] = cpu_baseline_entry(args.cpu_steps, 2)
+            res["cpu_baseline"] = cpu_baseline_entry(args.cpu_steps, 2, omp=True)
             if "batched" in res:
                 res["batched"]["cpu_baseline"] = batched_cpu_baseline()
             if "test_particles" in res:

@@ -19,8 +19,10 @@ _SRC = os.path.join(_HERE, "genga_oracle.c")
 _HDR = os.path.join(_HERE, "genga_oracle.h")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+_OMP_PATH = os.path.join(_OUT_DIR, "liboracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 CFLAGS = ["-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
 
@@ -45,6 +47,21 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+def build_omp(force: bool = False):
+    """The same source built with OpenMP (the pair sums split over bodies; results are bit-identical
+    to the plain build), for timing the oracle on all host cores. Returns the path, or None where the
+    compiler has no OpenMP."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if force or not os.path.exists(_OMP_PATH) or os.path.getmtime(_OMP_PATH) < newest:
+        tmp = _OMP_PATH + f".{os.getpid()}.tmp"
+        res = subprocess.run(["gcc", *CFLAGS, "-fopenmp", "-o", tmp, _SRC, "-lm"], capture_output=True)
+        if res.returncode != 0:
+            return None
+        os.replace(tmp, _OMP_PATH)
+    return _OMP_PATH
+
+
 class Params(C.Structure):
     _fields_ = [("G", C.c_double), ("m0", C.c_double), ("dt", C.c_double), ("order", C.c_int),
                 ("kmode", C.c_int), ("n1", C.c_double), ("n2", C.c_double), ("pc", C.c_double),
@@ -58,62 +75,78 @@ _I = C.POINTER(C.c_int)
 _P = C.POINTER(Params)
 
 
+def lib_omp():
+    """The OpenMP build (see build_omp), or None."""
+    global _lib_omp
+    with _lock:
+        if _lib_omp is None:
+            path = build_omp()
+            if path is None:
+                return None
+            _lib_omp = _declare(C.CDLL(path))
+    return _lib_omp
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = C.CDLL(build())
-            sig = {
-                "orc_default_params": (None, [_P]),
-                "orc_changeover": (C.c_double, [C.c_double, C.c_double]),
-                "orc_changeover_dr": (C.c_double, [C.c_double, C.c_double]),
-                "orc_weight_B": (C.c_double, [C.c_double, C.c_double, C.c_int]),
-                "orc_rcrit": (None, [C.c_int, _P, C.c_double, _D, _I, _D, _D, _D]),
-                "orc_accel_B": (None, [C.c_int, _P, _D, _I, _D, _D, _D]),
-                "orc_precheck": (C.c_int, [C.c_int, _P, _I, _D, _D, _I, C.c_int]),
-                "orc_momentum": (None, [C.c_int, _D, _I, _D, _D]),
-                "orc_sun_drift": (None, [C.c_int, _P, _I, _D, _D, C.c_double]),
-                "orc_stumpff": (None, [C.c_double, _D]),
-                "orc_kepler_drift": (C.c_int, [C.c_double, _D, _D, C.c_double, C.c_int, _I]),
-                "orc_hermite_min": (C.c_double, [_D, _D, _D, _D, C.c_double]),
-                "orc_encounters": (C.c_int, [C.c_int, _I, _D, _D, _D, _D, _D, _I, C.c_int,
-                                             C.c_double, _I, C.c_int]),
-                "orc_groups": (C.c_int, [C.c_int, _I, C.c_int, _I, _I, _I]),
-                "orc_energy": (C.c_double, [C.c_int, _P, _D, _I, _D, _D]),
-                "orc_bs_group": (C.c_int, [C.c_int, _P, C.c_int, _I, C.c_double, _D, _D, _I, _D,
-                                           _D, _D, _D, _I, _I, C.c_int, _I]),
-                "orc_bs_group_rec": (C.c_int, [C.c_int, _P, C.c_int, _I, C.c_double, _D, _D, _I, _D,
-                                               _D, _D, _D, _I, _I, C.c_int, _I, _D, _D, C.c_int, _I]),
-                "orc_get_collision_records": (C.c_int, [C.c_void_p, _D, C.c_int]),
-                "orc_set_spin": (None, [C.c_void_p, _D]),
-                "orc_get_spin": (None, [C.c_void_p, _D]),
-                "orc_substep_weights": (C.c_int, [C.c_int, _D]),
-                "orc_create": (C.c_void_p, [C.c_int, _P, _D, _D, _D, _D]),
-                "orc_free": (None, [C.c_void_p]),
-                "orc_step": (C.c_int, [C.c_void_p, C.c_int]),
-                "orc_get_state": (None, [C.c_void_p, _D, _D, _D, _D, _I]),
-                "orc_get_internal": (None, [C.c_void_p, _D, _D, _D, _D]),
-                "orc_get_energy": (C.c_double, [C.c_void_p, _D]),
-                "orc_get_candidates": (C.c_int, [C.c_void_p, _I, C.c_int]),
-                "orc_get_encounters": (C.c_int, [C.c_void_p, C.c_int, _I, C.c_int]),
-                "orc_get_groups": (C.c_int, [C.c_void_p, C.c_int, _I, _I, C.c_int]),
-                "orc_get_stats": (None, [C.c_void_p, C.POINTER(C.c_longlong), C.c_int]),
-                "orc_get_collisions": (C.c_int, [C.c_void_p, _I, C.c_int]),
-                "orc_get_ejections": (C.c_int, [C.c_void_p, _D, C.c_int]),
-                "orc_tp_get_ejections": (C.c_int, [C.c_void_p, _D, C.c_int]),
-                "orc_tp_create": (C.c_void_p, [C.c_int, _P, _D, _D, _D, _D, C.c_int, _D, _D, _D]),
-                "orc_tp_free": (None, [C.c_void_p]),
-                "orc_tp_step": (C.c_int, [C.c_void_p, C.c_int]),
-                "orc_tp_get_state": (None, [C.c_void_p, _D, _D, _D, _I, _D, _D, _I]),
-                "orc_tp_get_stats": (None, [C.c_void_p, C.POINTER(C.c_longlong), C.c_int]),
-                "orc_tp_get_encounters": (C.c_int, [C.c_void_p, C.c_int, _I, C.c_int]),
-            }
-            for name, (res, args) in sig.items():
-                f = getattr(L, name)
-                f.restype = res
-                f.argtypes = args
-            _lib = L
+            _lib = _declare(C.CDLL(build()))
     return _lib
+
+
+def _declare(L):
+    """Argument and result types of the oracle's C functions on the loaded library L."""
+    sig = {
+        "orc_default_params": (None, [_P]),
+        "orc_changeover": (C.c_double, [C.c_double, C.c_double]),
+        "orc_changeover_dr": (C.c_double, [C.c_double, C.c_double]),
+        "orc_weight_B": (C.c_double, [C.c_double, C.c_double, C.c_int]),
+        "orc_rcrit": (None, [C.c_int, _P, C.c_double, _D, _I, _D, _D, _D]),
+        "orc_accel_B": (None, [C.c_int, _P, _D, _I, _D, _D, _D]),
+        "orc_precheck": (C.c_int, [C.c_int, _P, _I, _D, _D, _I, C.c_int]),
+        "orc_momentum": (None, [C.c_int, _D, _I, _D, _D]),
+        "orc_sun_drift": (None, [C.c_int, _P, _I, _D, _D, C.c_double]),
+        "orc_stumpff": (None, [C.c_double, _D]),
+        "orc_kepler_drift": (C.c_int, [C.c_double, _D, _D, C.c_double, C.c_int, _I]),
+        "orc_hermite_min": (C.c_double, [_D, _D, _D, _D, C.c_double]),
+        "orc_encounters": (C.c_int, [C.c_int, _I, _D, _D, _D, _D, _D, _I, C.c_int,
+                                     C.c_double, _I, C.c_int]),
+        "orc_groups": (C.c_int, [C.c_int, _I, C.c_int, _I, _I, _I]),
+        "orc_energy": (C.c_double, [C.c_int, _P, _D, _I, _D, _D]),
+        "orc_bs_group": (C.c_int, [C.c_int, _P, C.c_int, _I, C.c_double, _D, _D, _I, _D,
+                                   _D, _D, _D, _I, _I, C.c_int, _I]),
+        "orc_bs_group_rec": (C.c_int, [C.c_int, _P, C.c_int, _I, C.c_double, _D, _D, _I, _D,
+                                       _D, _D, _D, _I, _I, C.c_int, _I, _D, _D, C.c_int, _I]),
+        "orc_get_collision_records": (C.c_int, [C.c_void_p, _D, C.c_int]),
+        "orc_set_spin": (None, [C.c_void_p, _D]),
+        "orc_get_spin": (None, [C.c_void_p, _D]),
+        "orc_substep_weights": (C.c_int, [C.c_int, _D]),
+        "orc_create": (C.c_void_p, [C.c_int, _P, _D, _D, _D, _D]),
+        "orc_free": (None, [C.c_void_p]),
+        "orc_step": (C.c_int, [C.c_void_p, C.c_int]),
+        "orc_get_state": (None, [C.c_void_p, _D, _D, _D, _D, _I]),
+        "orc_get_internal": (None, [C.c_void_p, _D, _D, _D, _D]),
+        "orc_get_energy": (C.c_double, [C.c_void_p, _D]),
+        "orc_get_candidates": (C.c_int, [C.c_void_p, _I, C.c_int]),
+        "orc_get_encounters": (C.c_int, [C.c_void_p, C.c_int, _I, C.c_int]),
+        "orc_get_groups": (C.c_int, [C.c_void_p, C.c_int, _I, _I, C.c_int]),
+        "orc_get_stats": (None, [C.c_void_p, C.POINTER(C.c_longlong), C.c_int]),
+        "orc_get_collisions": (C.c_int, [C.c_void_p, _I, C.c_int]),
+        "orc_get_ejections": (C.c_int, [C.c_void_p, _D, C.c_int]),
+        "orc_tp_get_ejections": (C.c_int, [C.c_void_p, _D, C.c_int]),
+        "orc_tp_create": (C.c_void_p, [C.c_int, _P, _D, _D, _D, _D, C.c_int, _D, _D, _D]),
+        "orc_tp_free": (None, [C.c_void_p]),
+        "orc_tp_step": (C.c_int, [C.c_void_p, C.c_int]),
+        "orc_tp_get_state": (None, [C.c_void_p, _D, _D, _D, _I, _D, _D, _I]),
+        "orc_tp_get_stats": (None, [C.c_void_p, C.POINTER(C.c_longlong), C.c_int]),
+        "orc_tp_get_encounters": (C.c_int, [C.c_void_p, C.c_int, _I, C.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
 
 
 def params(**kw) -> Params:
@@ -285,90 +318,93 @@ def substep_weights(order):
 class Sim:
     """Main-mode simulation on the oracle (n orbiting bodies, central mass in params)."""
 
-    def __init__(self, p: Params, m, R, xh, vh):
+    def __init__(self, p: Params, m, R, xh, vh, omp: bool = False):
         self.p = p
         self.n = len(m)
+        self._L = lib_omp() if omp else lib()
+        if self._L is None:
+            raise RuntimeError("the OpenMP build of the oracle is unavailable")
         m, pm = _d(m); R, pR = _d(R); xh, px = _d(xh); vh, pv = _d(vh)
-        self._h = lib().orc_create(self.n, C.byref(p), pm, pR, px, pv)
+        self._h = self._L.orc_create(self.n, C.byref(p), pm, pR, px, pv)
         if not self._h:
             raise RuntimeError("orc_create failed")
 
     def close(self):
         if getattr(self, "_h", None):
-            lib().orc_free(self._h)
+            self._L.orc_free(self._h)
             self._h = None
 
     __del__ = close
 
     def step(self, nsteps=1) -> int:
-        return lib().orc_step(self._h, int(nsteps))
+        return self._L.orc_step(self._h, int(nsteps))
 
     def state(self):
         n = self.n
         x, px = _dout(3 * n); v, pv = _dout(3 * n); m, pm = _dout(n); R, pR = _dout(n)
         al, pa = _iout(n)
-        lib().orc_get_state(self._h, px, pv, pm, pR, pa)
+        self._L.orc_get_state(self._h, px, pv, pm, pR, pa)
         return dict(x=x.reshape(n, 3), v=v.reshape(n, 3), m=m, R=R, alive=al)
 
     def internal(self):
         n = self.n
         x, px = _dout(3 * n); v, pv = _dout(3 * n); a, pa = _dout(3 * n); rc, prc = _dout(n)
-        lib().orc_get_internal(self._h, px, pv, pa, prc)
+        self._L.orc_get_internal(self._h, px, pv, pa, prc)
         return dict(x=x.reshape(n, 3), v=v.reshape(n, 3), a=a.reshape(n, 3), rc=rc)
 
     def energy(self):
         U = C.c_double(0.0)
-        E = lib().orc_get_energy(self._h, C.byref(U))
+        E = self._L.orc_get_energy(self._h, C.byref(U))
         return E, U.value
 
     def candidates(self):
-        cnt = lib().orc_get_candidates(self._h, None, 0)
+        cnt = self._L.orc_get_candidates(self._h, None, 0)
         out, po = _iout(2 * max(cnt, 1))
-        lib().orc_get_candidates(self._h, po, cnt)
+        self._L.orc_get_candidates(self._h, po, cnt)
         return out[: 2 * cnt].reshape(cnt, 2)
 
     def encounters(self, substep=-1):
-        cnt = lib().orc_get_encounters(self._h, substep, None, 0)
+        cnt = self._L.orc_get_encounters(self._h, substep, None, 0)
         out, po = _iout(2 * max(cnt, 1))
-        lib().orc_get_encounters(self._h, substep, po, cnt)
+        self._L.orc_get_encounters(self._h, substep, po, cnt)
         return out[: 2 * cnt].reshape(cnt, 2)
 
     def groups(self, substep=-1):
         n = self.n
         gs, pgs = _iout(n + 1)
         mem, pm = _iout(max(n, 1))
-        ng = lib().orc_get_groups(self._h, substep, pgs, pm, n)
+        ng = self._L.orc_get_groups(self._h, substep, pgs, pm, n)
         return [mem[gs[k]:gs[k + 1]].copy() for k in range(ng)]
 
     def stats(self):
         arr = (C.c_longlong * 12)()
-        lib().orc_get_stats(self._h, arr, 12)
+        self._L.orc_get_stats(self._h, arr, 12)
         return dict(zip(STAT_NAMES, list(arr)))
 
     def collisions(self):
-        cnt = lib().orc_get_collisions(self._h, None, 0)
+        cnt = self._L.orc_get_collisions(self._h, None, 0)
         out, po = _iout(2 * max(cnt, 1))
-        lib().orc_get_collisions(self._h, po, cnt)
+        self._L.orc_get_collisions(self._h, po, cnt)
         return out[: 2 * cnt].reshape(-1, 2)
 
     def ejections(self):
         """Removed bodies (Sect. 3.2, Ejections): rows of body index, step, heliocentric x[3], v[3]."""
-        return _ejections(lib().orc_get_ejections, self._h)
+        return _ejections(self._L.orc_get_ejections, self._h)
 
     def collision_records(self):
         """Collision reports (Sect. 3.2): rows of CREC doubles, see orc_get_collision_records."""
-        cnt = lib().orc_get_collision_records(self._h, None, 0)
+        cnt = self._L.orc_get_collision_records(self._h, None, 0)
         out, po = _dout(CREC * max(cnt, 1))
-        lib().orc_get_collision_records(self._h, po, cnt)
+        self._L.orc_get_collision_records(self._h, po, cnt)
         return out[: CREC * cnt].reshape(cnt, CREC)
 
     def set_spin(self, spin):
         sp, psp = _d(np.asarray(spin, np.float64).reshape(self.n, 3))
-        lib().orc_set_spin(self._h, psp)
+        self._L.orc_set_spin(self._h, psp)
 
     def spin(self):
         sp, psp = _dout(3 * self.n)
-        lib().orc_get_spin(self._h, psp)
+        self._L.orc_get_spin(self._h, psp)
         return sp.reshape(self.n, 3)
 
 

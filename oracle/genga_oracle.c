@@ -119,6 +119,10 @@ void orc_rcrit(int n, const orc_params *p, double tau_abs, const double *m, cons
  * radius is max(rc_i, rc_j) (Sect. 2.1). */
 void orc_accel_B(int n, const orc_params *p, const double *m, const int *alive, const double *x,
                  const double *rc, double *a) {
+  /* bodies are independent (each sum runs over j ascending); a multi-threaded build splits them */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
   for (int i = 0; i < n; i++) {
     double ax = 0.0, ay = 0.0, az = 0.0;
     if (alive[i]) {
@@ -907,6 +911,10 @@ int orc_step(orc_sim *s, int nsteps) {
     memset(s->is_cand, 0, (size_t)n * n);
     for (int k = 0; k < s->ncand && k < s->cand_cap; k++)
       s->is_cand[(size_t)s->cand[2 * k] * n + s->cand[2 * k + 1]] = 1;
+    long long viol = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : viol)
+#endif
     for (int i = 0; i < n; i++) {
       if (!s->alive[i]) continue;
       for (int j = i + 1; j < n; j++) {
@@ -914,12 +922,11 @@ int orc_step(orc_sim *s, int nsteps) {
         double dx = s->x[3 * j] - s->x[3 * i], dy = s->x[3 * j + 1] - s->x[3 * i + 1],
                dz = s->x[3 * j + 2] - s->x[3 * i + 2];
         double rcij = s->rc[i] > s->rc[j] ? s->rc[i] : s->rc[j];
-        if (orc_weight_B(pair_r2(dx, dy, dz), rcij, s->p.kmode) != 1.0) {
-          s->stats[8]++;
-          st |= ORC_ST_REUSE_VIOLATION;
-        }
+        if (orc_weight_B(pair_r2(dx, dy, dz), rcij, s->p.kmode) != 1.0) viol++;
       }
     }
+    s->stats[8] += viol;
+    if (viol) st |= ORC_ST_REUSE_VIOLATION;
     /* opening kick of the step: plain definition, all pairs with the new critical radii */
     orc_accel_B(n, &s->p, s->m, s->alive, s->x, s->rc, s->a);
     for (int js = 0; js < nsub; js++) st |= substep(s, js, w[js] * s->p.dt, js == nsub - 1);
