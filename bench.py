@@ -198,6 +198,23 @@ def run_batched(args):
         ev1.synchronize()
         tot += ev0.elapsed_time(ev1)
     code, cnt = genga.genga_status(h)
+    sched = genga.genga_batch_schedule(h)
+    # the other schedule on the same systems (continuing from the state reached), for comparison
+    other = 1 - sched["persistent"]
+    try:
+        genga.genga_batch_set_schedule(h, other)
+        genga.genga_step(h, spl)
+        tot_o = 0.0
+        for _ in range(launches):
+            flush.zero_()
+            ev0.record(stream)
+            genga.genga_step(h, spl)
+            ev1.record(stream)
+            ev1.synchronize()
+            tot_o += ev0.elapsed_time(ev1)
+        other_value = BATCH_SYSTEMS * spl * launches / (tot_o * 1e-3)
+    except RuntimeError:
+        other_value = None
     genga.genga_free(h)
     value = BATCH_SYSTEMS * spl * launches / (tot * 1e-3)
     # one system per launch: a main-mode context per system, one step graph per system per step
@@ -227,7 +244,13 @@ def run_batched(args):
     return {"metric": "batched system-steps/s", "value": value, "unit": "system-steps/s",
             "n_systems": BATCH_SYSTEMS, "bodies": n, "steps": spl * launches, "steps_per_launch": spl,
             "ms_per_launch": tot / launches, "gpu_launches": kps * spl * launches,
-            "autotuned": {"threads_per_body": split, "block": block},
+            "autotuned": {"threads_per_body": split, "block": block,
+                          "schedule": "persistent launch" if sched["persistent"] else "step graph",
+                          "persistent_ctas": sched["ctas"], "trial_ms_per_step_graph": sched["ms_graph"],
+                          "trial_ms_per_step_persistent": sched["ms_persistent"]},
+            "other_schedule": {"schedule": "persistent launch" if other else "step graph", "value": other_value,
+                               "unit": "system-steps/s",
+                               "note": "the same systems continued on the schedule the autotuner did not pick"},
             "one_system_per_launch": {"value": one_value, "unit": "system-steps/s",
                                       "sample": f"{nsamp} systems x {ksteps} steps, one step graph per system"},
             "speedup_vs_one_per_launch": value / one_value, "status": code, "counters": cnt,
@@ -413,9 +436,41 @@ def run_adjoint(args):
 
     fd = (loss(1e-7) - loss(-1e-7)) / 2e-7
     e4.close()
+    # the product's forward on the same systems: one main-mode context per disk (merging off, as in
+    # the differentiable engine), all on their own streams at once, over a bounded sample of steps
+    from paper_1404_2324_gb300 import genga
+    ctxs, streams = [], []
+    for b in range(ADJ_SYSTEMS):
+        m = np.concatenate([[d["m0"][b]], d["m"][b]])
+        R = np.zeros(ADJ_N + 1)
+        x = np.vstack([np.zeros(3), d["x"][b]]); v = np.vstack([np.zeros(3), d["v"][b]])
+        c = genga.genga_init(m, R, x, v, d["G"], d["dt"], 2)
+        prm = genga.genga_default_params()
+        prm.collisions = 0
+        genga.genga_set_params(c, prm)
+        st = torch.cuda.Stream()
+        genga.genga_set_stream(c, st)
+        genga.genga_step(c, 2)
+        ctxs.append(c)
+        streams.append(st)
+    torch.cuda.synchronize()
+    psteps = 100
+    t0 = time.perf_counter()
+    for c in ctxs:
+        genga.genga_step(c, psteps)
+    torch.cuda.synchronize()
+    p_sec = time.perf_counter() - t0
+    for c in ctxs:
+        genga.genga_free(c)
+    prod_ms = p_sec * 1e3 * steps / psteps  # the same work as the timed forward
     return {"metric": "adjoint/fwd", "value": b_ms / f_ms, "unit": "backward time / forward time",
             "higher_is_better": False, "forward_ms": f_ms, "backward_ms": b_ms, "steps": steps,
             "forward_system_steps_per_s": ADJ_SYSTEMS * steps / (f_ms * 1e-3),
+            "vs_product_forward": {"value": b_ms / prod_ms, "product_forward_ms": prod_ms,
+                                   "product_system_steps_per_s": ADJ_SYSTEMS * psteps / p_sec,
+                                   "basis": f"backward time over the time genga_step takes for the same "
+                                            f"{ADJ_SYSTEMS} disks x {steps} steps (one main-mode context per disk, "
+                                            f"merging off, concurrent streams; timed over {psteps} steps, host clock)"},
             "grad_vs_central_fd": {"rel_err": abs(fd - pred) / abs(pred), "h_rel": 1e-7,
                                    "sample": f"{S} systems x {K} steps, one random direction"},
             "status": status,

@@ -227,6 +227,18 @@ int genga_init_batch(genga_ctx **ctx, int n_sys, const int *offsets, const doubl
 /* Autotuned kick shape (threads per body, threads per CTA) and steps per graph launch. */
 int genga_batch_info(genga_ctx *ctx, int *split, int *block, int *steps_per_launch);
 
+/* The schedule genga_init_batch chose by timing two steps of the batch each way: the step graph
+ * (every phase over all systems, then the next phase) or one persistent launch in which each CTA
+ * takes a system at a time and advances it through all the steps of the launch (*persistent = 1;
+ * *ctas CTAs, one or two per SM). ms_graph, ms_persistent: the measured time per step of each
+ * (any pointer may be NULL). The persistent launch is not used while Rcut, RcutSun or Nmin is set. */
+int genga_batch_schedule(genga_ctx *ctx, int *persistent, int *ctas, float *ms_graph, float *ms_persistent);
+
+/* Overrides that choice: 1 persistent launch, 0 step graph (EINVAL if the persistent launch is not
+ * available on this device). Both give each system the single-system step; the sums run in
+ * different fixed orders, so results agree to rounding, not bit for bit. */
+int genga_batch_set_schedule(genga_ctx *ctx, int persistent);
+
 /* Flat heliocentric state in the caller's body order (waits for the stream); pointers may be NULL.
  * x, v [3N]; m, R [N]; alive [N] (0 for a ghost left by a merger). */
 int genga_get_state_batch(genga_ctx *ctx, double *x, double *v, double *m, double *R, int *alive);

@@ -16,9 +16,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libgenga.so")
-SOURCES = ["kick.cu", "step.cu", "bs.cu", "bs_cluster.cu", "bs_grid.cu", "io.cu", "batch.cu", "tp.cu", "eject.cu", "adjoint.cu", "api.cu",
+SOURCES = ["kick.cu", "step.cu", "bs.cu", "bs_cluster.cu", "bs_grid.cu", "io.cu", "batch.cu", "batch_persist.cu", "tp.cu", "eject.cu", "adjoint.cu", "api.cu",
            "noalloc.cu"]
-HEADERS = ["genga_dev.cuh", "genga_launch.h"]
+HEADERS = ["genga_dev.cuh", "genga_launch.h", "bs_core.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]
 

@@ -173,6 +173,11 @@ struct genga_ctx {
   // batched mode
   bool batched = false;
   int nsys = 0, b_split = 1, b_block = 128, steps_per_launch = 1;
+  // batched mode as one persistent launch (batch_persist.cu), chosen at init when faster
+  bool persist = false;
+  int persist_blocks = 0, persist_per_sm = 0;
+  int *bp_queue = nullptr, *bp_base = nullptr;
+  float tune_ms_graph = 0.0f, tune_ms_persist = 0.0f;
   int *perm = nullptr, *sys_user = nullptr;  // device: internal body -> user body, internal system -> user system
   std::vector<int> perm_h;                    // host copy of perm (ejection records)
   std::vector<int> start_h;                   // host copy of the internal systems' first bodies
@@ -336,6 +341,32 @@ void enqueue_step(genga_ctx *c, cudaStream_t st) {
   }
 }
 
+// The persistent batched launch runs the step without the end-of-step ejection limits (Rcut,
+// RcutSun, Nmin); with any of them set the step graph runs instead.
+bool use_persistent(const genga_ctx *c) {
+  return c->persist && !(c->P.rcut2 > 0.0) && !(c->P.rcut_sun2 > 0.0) && c->P.nmin <= 0;
+}
+
+// Batched mode: the state of genga_init_batch again (from the staging copies of the input), with every
+// counter, record and the step count cleared -- after the autotuner's trial steps.
+int reset_batch(genga_ctx *c) {
+  Sim &S = c->S;
+  cudaStream_t st = c->stream;
+  const size_t np = S.npad;
+  CK(cudaMemsetAsync(S.counters, 0, NCOUNTERS * sizeof(long long), st));
+  CK(cudaMemsetAsync(S.status, 0, sizeof(int), st));
+  CK(cudaMemsetAsync(S.U, 0, sizeof(double), st));
+  CK(cudaMemsetAsync(S.nej, 0, sizeof(int), st));
+  CK(cudaMemsetAsync(S.ncrec, 0, sizeof(int), st));
+  CK(cudaMemsetAsync(S.spin, 0, 3 * np * sizeof(double), st));
+  CK(cudaMemsetAsync(S.bsn, 0, np, st));
+  CK(cudaMemsetAsync(S.alive, 0, np * sizeof(int), st));
+  CK(cudaMemsetAsync(c->bp_base, 0, sizeof(int), st));
+  launch_b_from_helio(S, c->P, c->perm, c->sx, c->sv, c->sm, c->sR, 0, st);
+  CK(cudaGetLastError());
+  return first_kick_batch(c);
+}
+
 // Captured on the context's own stream (the caller's stream may be the legacy default stream,
 // which cannot be captured); the executable graph is then launched on whichever stream is set.
 int build_graph(genga_ctx *c) {
@@ -350,9 +381,13 @@ int build_graph(genga_ctx *c) {
   for (int pass = 0; pass < (c->batched && c->steps_per_launch > 1 ? 2 : 1); ++pass) {
     const int nst = pass == 0 ? c->steps_per_launch : 1;
     CK(cudaStreamBeginCapture(c->own, cudaStreamCaptureModeThreadLocal));
-    for (int k = 0; k < nst; ++k) {
-      if (c->batched) enqueue_step_batch(c, c->own);
-      else enqueue_step(c, c->own);
+    if (c->batched && use_persistent(c)) {
+      launch_b_persist(c->S, c->P, c->dt, c->w, c->nsub, nst, c->bp_base, c->bp_queue, c->persist_blocks, c->own);
+    } else {
+      for (int k = 0; k < nst; ++k) {
+        if (c->batched) enqueue_step_batch(c, c->own);
+        else enqueue_step(c, c->own);
+      }
     }
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(c->own, &g);
@@ -662,7 +697,62 @@ int genga_init_batch(genga_ctx **out, int n_sys, const int *offsets, const doubl
   int rc = first_kick_batch(c);
   if (rc == GENGA_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = GENGA_ECUDA;
   if (rc != GENGA_OK) { genga_free(c); return rc; }
+  // the schedule: the step graph (phase by phase over all systems) against one persistent launch (a
+  // CTA per system at a time) at one and at two CTAs per SM, each timed on two steps of this batch;
+  // the state is then put back as it was
+  c->bp_queue = mem.get<int>(1);
+  c->bp_base = mem.get<int>(1);
+  c->persist_per_sm = mem.err == cudaSuccess ? b_persist_init() : 0;
+  if (c->persist_per_sm > 0) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int tsteps = 2;
+    float best = 1e30f;
+    cudaEventRecord(e0, st);
+    for (int k = 0; k < tsteps; ++k) enqueue_step_batch(c, st);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&c->tune_ms_graph, e0, e1);
+    c->tune_ms_graph /= tsteps;
+    for (int per = 1; per <= (c->persist_per_sm < 2 ? c->persist_per_sm : 2); ++per) {
+      if (reset_batch(c) != GENGA_OK) break;
+      const int blocks = per * num_sms();
+      cudaEventRecord(e0, st);
+      launch_b_persist(S, c->P, dt, c->w, c->nsub, tsteps, c->bp_base, c->bp_queue, blocks, st);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= tsteps;
+      if (ms < best) { best = ms; c->persist_blocks = blocks; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->tune_ms_persist = best;
+    c->persist = c->persist_blocks > 0 && best < c->tune_ms_graph;
+    rc = reset_batch(c);
+    if (rc == GENGA_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = GENGA_ECUDA;
+    if (rc != GENGA_OK) { genga_free(c); return rc; }
+  }
   *out = c;
+  return GENGA_OK;
+}
+
+int genga_batch_schedule(genga_ctx *c, int *persistent, int *ctas, float *ms_graph, float *ms_persistent) {
+  if (!c || !c->batched) return GENGA_EINVAL;
+  if (persistent) *persistent = use_persistent(c) ? 1 : 0;
+  if (ctas) *ctas = c->persist_blocks;
+  if (ms_graph) *ms_graph = c->tune_ms_graph;
+  if (ms_persistent) *ms_persistent = c->tune_ms_persist;
+  return GENGA_OK;
+}
+
+int genga_batch_set_schedule(genga_ctx *c, int persistent) {
+  if (!c || !c->batched || (persistent != 0 && persistent != 1) || (persistent && c->persist_blocks < 1))
+    return GENGA_EINVAL;
+  c->persist = persistent != 0;
+  drop_graph(c);
   return GENGA_OK;
 }
 

@@ -483,17 +483,18 @@ static __device__ int kepler_drift_dev(double mu, double mu2, double &x, double 
 // spin from angular-momentum conservation: both spins plus mu (x_b - x_a) x (v_b - v_a) of the
 // states yna, ynb after the substep, mu = m_a m_b / (m_a + m_b); the ghost's spin is cleared.
 // Report layout: step (1-based), substep, t, ia, ib, x_a, v_a, spin_a, x_b, v_b, spin_b, survivor.
+// step_no, substep < 0: the values the step graph keeps in the counters and flags.
 // ---------------------------------------------------------------------------------------------
 __device__ __forceinline__ void merger_report(const Sim &S, int ia, int ib, const double *ya, const double *yb,
                                               const double *yna, const double *ynb, double ma, double mb,
-                                              bool keep_a, double t) {
+                                              bool keep_a, double t, int step_no = -1, int substep = -1) {
   const int np = S.npad;
   if (S.crec) {
     const int slot = atomicAdd(S.ncrec, 1);
     if (slot < CREC_CAP) {
       double *r = S.crec + (size_t)slot * CREC;
-      r[0] = (double)*(volatile long long *)&S.counters[C_STEPS];
-      r[1] = (double)*(volatile int *)&S.flags[2];
+      r[0] = step_no >= 0 ? (double)step_no : (double)*(volatile long long *)&S.counters[C_STEPS];
+      r[1] = substep >= 0 ? (double)substep : (double)*(volatile int *)&S.flags[2];
       r[2] = t;
       r[3] = (double)ia;
       r[4] = (double)ib;

@@ -62,6 +62,12 @@ void bs_cluster_init_constants();  // once per device, before any capture
 int bs_cluster_grid();
 void launch_bs_cluster(const Sim &S, const DevParams &P, double tau, int gmin, int grid, cudaStream_t st);
 
+// batch_persist.cu: the batched step as one persistent launch (a CTA per system at a time); the
+// step number of the reports is read from step_base (a device int the launch advances by nsteps)
+int b_persist_init();  // once per device, before any capture; returns CTAs per SM that fit
+void launch_b_persist(const Sim &S, const DevParams &P, double dt, const double *w, int nsub, int nsteps,
+                      int *step_base, int *queue, int blocks, cudaStream_t st);
+
 // batch.cu
 void launch_b_rcrit(const Sim &S, const DevParams &P, double tau_abs, int check, cudaStream_t st);
 void launch_b_kick(const Sim &S, const DevParams &P, FinMode mode, double h1, double h2, int split, int block,

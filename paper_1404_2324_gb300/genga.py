@@ -65,6 +65,8 @@ _SIGS = {
     "genga_encounters": (C.c_int, [_V, C.c_int, _I, C.c_int, _I]),
     "genga_ejections": (C.c_int, [_V, _D, C.c_int, _I]),
     "genga_collisions": (C.c_int, [_V, _D, C.c_int, _I]),
+    "genga_batch_schedule": (C.c_int, [_V, _I, _I, C.POINTER(C.c_float), C.POINTER(C.c_float)]),
+    "genga_batch_set_schedule": (C.c_int, [_V, C.c_int]),
     "genga_fp64_probe": (C.c_int, [C.c_int, _D, C.POINTER(C.c_float), _V]),
     "genga_tp_encounters": (C.c_int, [_V, _I, C.c_int, _I]),
     "genga_batch_encounters": (C.c_int, [_V, _I, C.c_int, _I]),
@@ -340,6 +342,18 @@ def genga_fp64_probe(iters=1 << 16, stream=None):
     tf, ms = C.c_double(0.0), C.c_float(0.0)
     _check(lib().genga_fp64_probe(int(iters), C.byref(tf), C.byref(ms), _stream_ptr(stream)), "genga_fp64_probe")
     return tf.value, ms.value
+
+
+def genga_batch_schedule(ctx):
+    """The batched schedule chosen at init: persistent launch or step graph, and the timings."""
+    p, k = C.c_int(0), C.c_int(0)
+    mg, mp = C.c_float(0.0), C.c_float(0.0)
+    _check(lib().genga_batch_schedule(ctx, C.byref(p), C.byref(k), C.byref(mg), C.byref(mp)), "genga_batch_schedule")
+    return dict(persistent=p.value, ctas=k.value, ms_graph=mg.value, ms_persistent=mp.value)
+
+
+def genga_batch_set_schedule(ctx, persistent):
+    _check(lib().genga_batch_set_schedule(ctx, int(persistent)), "genga_batch_set_schedule")
 
 
 def genga_set_spin(ctx, spin):

@@ -90,13 +90,19 @@ def test_forward_matches_oracle(order, batch):
     ref = _oracle_run(x, v, m, order, 30)
     assert sum(r[2]["bs_steps"] for r in ref) > 0
     rng = np.random.default_rng(3)
+    exc = []
     for b in range(len(m)):
         e = max(_rel(xo[b].cpu().numpy(), ref[b][0]), _rel(vo[b].cpu().numpy(), ref[b][1]))
         if e > 1e-9:  # a chaotic close pass: compare with the oracle's own sensitivity
             pert = [1e-15 * rng.standard_normal(x[k].shape) for k in range(len(m))]
             alt = _oracle_run(x, v, m, order, 30, perturb=pert)
             sens = max(_rel(alt[b][0], ref[b][0]), _rel(alt[b][1], ref[b][1]))
+            exc.append((b, e, sens))
             assert e <= 30 * sens, (b, e, sens)
+    print(f"{batch} batch, order {order}, 30 steps: {len(exc)} of {len(m)} systems above 1e-9"
+          + (f"; largest {max(q[1] for q in exc):.2e}, largest error/sensitivity {max(q[1] / q[2] for q in exc):.1f}"
+             if exc else ""))
+    assert len(exc) <= 0.1 * len(m) + 1
     eng.close()
 
 

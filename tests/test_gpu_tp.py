@@ -77,6 +77,10 @@ def _check(g, os_, sens, tol, mult):
     e, live = _tp_err(g, os_)
     s = sens[live]
     bad = (e > tol) & (e > mult * s)
+    over = e > tol
+    print(f"{int(over.sum())} of {len(e)} particles above {tol:g}"
+          + (f"; largest {e[over].max():.2e}, largest error/sensitivity {(e[over] / np.maximum(s[over], 1e-300)).max():.1f}"
+             if over.any() else ""))
     assert not bad.any(), list(zip(np.where(live)[0][bad], e[bad], s[bad]))
     return e, live
 
@@ -161,19 +165,31 @@ def test_tp_sizes_out_of_range_are_rejected(n_planets, n_tp):
 
 
 @pytest.mark.parametrize("order", [2, 4])
-def test_first_step_particle_planet_encounter_pairs_are_bit_exact(order):
+def test_first_step_particle_planet_encounter_pairs_match(order):
     """From identical inputs, the (particle, planet) encounter pairs of the last substep of the first
-    step equal the oracle's pair for pair (the Hermite test runs in the same arithmetic)."""
+    step match the oracle's (the Hermite test runs in the same arithmetic; the states it sees differ
+    by rounding): any pair in which the lists differ must flip in the oracle itself under a 1e-15
+    change of the particles' start."""
     d = _inputs()
     h = _gpu(d, order)
     o = _oracle(d, order)
     try:
         genga.genga_step(h, 1)
         o.step(1)
-        gp = genga.genga_tp_encounters(h)
-        op = o.encounters(-1)
-        assert len(op) > 10
-        np.testing.assert_array_equal(gp, op + [0, 1])  # planets numbered with the central mass at 0
+        gp = {tuple(p) for p in genga.genga_tp_encounters(h)}
+        op = {(i, j + 1) for i, j in o.encounters(-1)}  # planets numbered with the central mass at 0
     finally:
         genga.genga_free(h)
         o.close()
+    assert len(op) > 10
+    diff = gp ^ op
+    flip = set()
+    rng = np.random.default_rng(0)
+    for _ in range(8 if diff else 0):
+        dp = dict(d, x_tp=d["x_tp"] * (1 + 1e-15 * rng.standard_normal(d["x_tp"].shape)))
+        q = _oracle(dp, order)
+        q.step(1)
+        flip |= op ^ {(i, j + 1) for i, j in q.encounters(-1)}
+        q.close()
+    print(f"order {order}: {len(op)} pairs, {len(diff)} differ, {len(diff & flip)} of them at the threshold")
+    assert diff <= flip, sorted(diff - flip)
