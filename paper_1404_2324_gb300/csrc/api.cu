@@ -291,14 +291,15 @@ void enqueue_step(genga_ctx *c, cudaStream_t st) {
   const bool tp = c->tpmode;
   const TPSet &T = c->T;
   launch_rcrit(S, P, std::fabs(dt), 1, st);
-  if (tp) launch_tp_rcrit(T, P, std::fabs(dt), 1, st);
   launch_kick(S, P, true, precise, st);  // runs only if the critical radii grew too much
   launch_fin(S, P, FIN_OPEN, 0.5 * c->w[0] * dt, 0.0, nullptr, st);
-  if (tp) launch_tp_kick(S, T, P, FIN_OPEN, 0.5 * c->w[0] * dt, 0.0, st);
   for (int j = 0; j < c->nsub; ++j) {
     const double tau = c->w[j] * dt;
     const double hcm2 = j > 0 ? 0.5 * c->w[j - 1] * dt * inv_m0 : 0.0;
-    if (tp) launch_tp_drift(S, T, P, tau, 0.5 * tau * inv_m0, hcm2, st);  // before the massive drift
+    // the particles' drift runs before the massive drift (which clears the reuse flag the opening
+    // kick reads); at the first substep it carries their critical radii and opening kick as well
+    if (tp && j == 0) launch_tp_open_drift(S, T, P, std::fabs(dt), 0.5 * c->w[0] * dt, tau, 0.5 * tau * inv_m0, st);
+    else if (tp) launch_tp_drift(S, T, P, tau, 0.5 * tau * inv_m0, hcm2, st);
     launch_drift(S, P, tau, 0.5 * tau * inv_m0, hcm2, j, st);             // clears the reuse flag
     if (tp) launch_planet_table(S, T, P, tau, st);
     // the paper's literal higher-order variant: the step-start candidates serve every substep, and
@@ -331,10 +332,10 @@ void enqueue_step(genga_ctx *c, cudaStream_t st) {
     if (c->profiling) cudaEventRecordWithFlags(c->kev[2 * j + 1], st, cudaEventRecordExternal);
     const double h2 = (j + 1 < c->nsub) ? 0.5 * c->w[j + 1] * dt : 0.0;
     launch_fin(S, P, inner ? FIN_CLOSE_ALL : FIN_CLOSE, 0.5 * tau, h2, nullptr, st);
-    if (tp) launch_tp_kick(S, T, P, FIN_CLOSE, 0.5 * tau, h2, st);
+    // the particles' closing kick; after the last substep it applies their last Sun drift too
+    if (tp) launch_tp_kick(S, T, P, FIN_CLOSE, 0.5 * tau, h2, st, j + 1 == c->nsub ? 0.5 * tau * inv_m0 : 0.0);
   }
   launch_hc(S, 0.5 * c->w[c->nsub - 1] * dt * inv_m0, st);
-  if (tp) launch_tp_hc(S, T, 0.5 * c->w[c->nsub - 1] * dt * inv_m0, st);
   if (P.rcut2 > 0.0 || P.rcut_sun2 > 0.0) {  // ejections at the end of the step (Sect. 3.2)
     if (tp) launch_tp_eject(T, P, st);
     launch_eject(S, P, st);

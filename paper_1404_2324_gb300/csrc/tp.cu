@@ -61,11 +61,23 @@ __device__ void load_planets(const Sim &S, PlanetSm &ps) {
 // TP kick. CLOSE / INIT: all planets with the changeover weight, far field stored, candidates
 // recorded (per TP as a mask, and as (TP, planet) pairs appended to the pair list for the next
 // encounter test). OPEN: stored far field + candidates with the new radii, or every planet when the
-// TP or any planet failed the reuse test. Every launch also empties the BS list of the coming
-// substep (its last reader, the previous substep's BS, has finished).
+// TP or any planet failed the reuse test (the step itself runs it inside k_tp_open_drift). Every
+// launch also empties the BS list of the coming substep (its last reader, the previous substep's
+// BS, has finished).
 template <int MODE>
-__global__ void __launch_bounds__(128) k_tp_kick(Sim S, TPSet T, DevParams P, double h1, double h2) {
+__global__ void __launch_bounds__(128) k_tp_kick(Sim S, TPSet T, DevParams P, double h1, double h2, double hcm_last) {
   __shared__ PlanetSm ps;
+  __shared__ double shc[3];
+  if (hcm_last != 0.0 && threadIdx.x < 32) {  // the step's last Sun drift, from the momentum before the kick
+    const int lane = threadIdx.x;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      double a = 0.0;
+      for (int t = lane; t < S.nt; t += 32) a += S.pkick[t * 3 + c];
+      a = warp_sum(a);
+      if (lane == 0) shc[c] = hcm_last * a;
+    }
+  }
   load_planets(S, ps);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) { T.nbs[0] = 0; T.nbs[1] = 0; }
@@ -112,6 +124,9 @@ __global__ void __launch_bounds__(128) k_tp_kick(Sim S, TPSet T, DevParams P, do
       double vx = fma(h1, ax, T.v[i]), vy = fma(h1, ay, T.v[np + i]), vz = fma(h1, az, T.v[2 * np + i]);
       if (h2 != 0.0) { vx = fma(h2, ax, vx); vy = fma(h2, ay, vy); vz = fma(h2, az, vz); }
       T.v[i] = vx; T.v[np + i] = vy; T.v[2 * np + i] = vz;
+      if (hcm_last != 0.0) {  // the shift moves every body alike, so the kick above does not see it
+        T.x[i] = xi + shc[0]; T.x[np + i] = yi + shc[1]; T.x[2 * np + i] = zi + shc[2];
+      }
     } else {
       (void)h1; (void)h2;
     }
@@ -169,6 +184,79 @@ __global__ void k_tp_drift(Sim S, TPSet T, DevParams P, double tau, double hcm1,
   const int np = T.npad;
   double x = T.x[i] + sh[0], y = T.x[np + i] + sh[1], z = T.x[2 * np + i] + sh[2];
   double vx = T.v[i], vy = T.v[np + i], vz = T.v[2 * np + i];
+  T.x0[i] = x; T.x0[np + i] = y; T.x0[2 * np + i] = z;
+  T.v0[i] = vx; T.v0[np + i] = vy; T.v0[2 * np + i] = vz;
+  int it = 0;
+  if (kepler_drift_dev(P.G * P.m0, P.mu2, x, y, z, vx, vy, vz, tau, P.kepler_maxit, &it)) {
+    T.fail[i] = 1;
+    atomicOr(S.status, ST_KEPLER_FALLBACK);
+    T.bslist[T.npad - 1 - atomicAdd(&T.nbs[1], 1)] = i;  // BS in the field of m0 alone (unless it meets a planet)
+  }
+  T.x[i] = x; T.x[np + i] = y; T.x[2 * np + i] = z;
+  T.v[i] = vx; T.v[np + i] = vy; T.v[2 * np + i] = vz;
+}
+
+// The start of a full step for the TPs in one pass (the three operations of k_tp_rcrit with the
+// reuse test, k_tp_kick<OPEN> and k_tp_drift of the first substep, in that order and arithmetic):
+// the critical radius from the velocity, the opening kick (stored far field + candidates with the
+// new radii, or every planet when the TP or any planet failed the reuse test), the first Sun drift
+// with the momentum after the massive opening kick, the Kepler drift keeping the pre-drift state.
+__global__ void __launch_bounds__(128) k_tp_open_drift(Sim S, TPSet T, DevParams P, double tau_abs, double h1,
+                                                       double tau, double hcm1) {
+  __shared__ PlanetSm ps;
+  __shared__ double sh[3];
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      double a = 0.0;
+      for (int t = lane; t < S.nt; t += 32) a += S.pfin[t * 3 + c];
+      a = warp_sum(a);
+      if (lane == 0) sh[c] = hcm1 * a;
+    }
+  }
+  load_planets(S, ps);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) { T.nbs[0] = 0; T.nbs[1] = 0; }
+  if (i >= T.n) return;
+  T.fail[i] = 0;
+  T.emask[i] = 0u;
+  if (!T.alive[i]) { T.rc[i] = 0.0; T.A[i] = 0.0; T.T[i] = 0ULL; T.rcsq[i] = 0ULL; return; }
+  const int np = T.npad, npl = S.n;
+  double vx = T.v[i], vy = T.v[np + i], vz = T.v[2 * np + i];
+  // critical radius (Eq. rcrit, m = 0) and the reuse test
+  const double v2 = fma(vz, vz, fma(vy, vy, vx * vx));
+  const double vabs = (dbits(v2) == 0ULL) ? 0.0 : v2 * rsqrt_refined(v2);
+  const double rc = (P.n2 * tau_abs) * vabs;
+  const bool tfull = dbits(rc) > dbits(P.pc * T.rc[i]);
+  const double tq = __dmul_rn(P.pc, rc);
+  const u64 Qi = dbits(__dmul_rn(rc, rc));
+  const double Ai = (dbits(rc) == 0ULL) ? 0.0 : rcp_refined(0.9 * rc);
+  T.rc[i] = rc; T.T[i] = dbits(__dmul_rn(tq, tq)); T.rcsq[i] = Qi; T.A[i] = Ai;
+  // opening kick
+  double x = T.x[i], y = T.x[np + i], z = T.x[2 * np + i];
+  const bool full = tfull || S.flags[0];
+  double nx = 0, ny = 0, nz = 0;
+  const unsigned scan = full ? 0xffffffffu : T.cmask[i];
+  for (int j = 0; j < npl; ++j) {
+    if (!ps.alive[j] || !((scan >> j) & 1u)) continue;
+    const double dx = ps.x[j] - x, dy = ps.y[j] - y, dz = ps.z[j] - z;
+    const double r2 = __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx)));
+    const double yr = rsqrt_refined(r2);
+    double g = ps.gm[j] * (yr * yr * yr);
+    if (dbits(r2) < umax64(Qi, ps.Q[j])) {
+      double wB, wA;
+      changeover_w(r2 * yr, pmin(Ai, ps.A[j]), P.kmode, wB, wA);
+      g *= wB;
+    }
+    nx = fma(g, dx, nx); ny = fma(g, dy, ny); nz = fma(g, dz, nz);
+  }
+  double ax, ay, az;
+  if (full) { ax = nx; ay = ny; az = nz; }
+  else { ax = T.afar[i] + nx; ay = T.afar[np + i] + ny; az = T.afar[2 * np + i] + nz; }
+  vx = fma(h1, ax, vx); vy = fma(h1, ay, vy); vz = fma(h1, az, vz);
+  // Sun drift, pre-drift state, Kepler drift
+  x += sh[0]; y += sh[1]; z += sh[2];
   T.x0[i] = x; T.x0[np + i] = y; T.x0[2 * np + i] = z;
   T.v0[i] = vx; T.v0[np + i] = vy; T.v0[2 * np + i] = vz;
   int it = 0;
@@ -620,24 +708,6 @@ __global__ void __launch_bounds__(32 * TPB_WARPS, 1) k_tp_bs(Sim S, TPSet T, Dev
   }
 }
 
-__global__ void k_tp_hc(Sim S, TPSet T, double hcm) {
-  __shared__ double sh[3];
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      double a = 0.0;
-      for (int t = lane; t < S.nt; t += 32) a += S.pkick[t * 3 + c];
-      a = warp_sum(a);
-      if (lane == 0) sh[c] = hcm * a;
-    }
-  }
-  __syncthreads();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= T.n || !T.alive[i]) return;
-  for (int c = 0; c < 3; ++c) T.x[c * T.npad + i] += sh[c];
-}
-
 // TP input (heliocentric AoS) -> democratic SoA: v_b = v_h - sum m v_h / (m0 + sum m) with the
 // massive bodies' heliocentric input (staged as AoS with the central mass in row 0).
 __global__ void k_tp_from_helio(TPSet T, int nmass, const double *mh, const double *vmh, const double *xh,
@@ -787,11 +857,15 @@ void launch_tp_to_helio(const Sim &S, const TPSet &T, const DevParams &P, double
 void launch_tp_rcrit(const TPSet &T, const DevParams &P, double tau_abs, int check, cudaStream_t st) {
   k_tp_rcrit<<<grid_of(T.n, 256), 256, 0, st>>>(T, P, tau_abs, check);
 }
-void launch_tp_kick(const Sim &S, const TPSet &T, const DevParams &P, FinMode mode, double h1, double h2, cudaStream_t st) {
+void launch_tp_kick(const Sim &S, const TPSet &T, const DevParams &P, FinMode mode, double h1, double h2, cudaStream_t st,
+                    double hcm_last) {
   const int g = grid_of(T.n, 128);
-  if (mode == FIN_CLOSE) k_tp_kick<FIN_CLOSE><<<g, 128, 0, st>>>(S, T, P, h1, h2);
-  else if (mode == FIN_OPEN) k_tp_kick<FIN_OPEN><<<g, 128, 0, st>>>(S, T, P, h1, h2);
-  else k_tp_kick<FIN_INIT><<<g, 128, 0, st>>>(S, T, P, h1, h2);
+  if (mode == FIN_CLOSE) k_tp_kick<FIN_CLOSE><<<g, 128, 0, st>>>(S, T, P, h1, h2, hcm_last);
+  else k_tp_kick<FIN_INIT><<<g, 128, 0, st>>>(S, T, P, h1, h2, 0.0);
+}
+void launch_tp_open_drift(const Sim &S, const TPSet &T, const DevParams &P, double tau_abs, double h1, double tau,
+                          double hcm1, cudaStream_t st) {
+  k_tp_open_drift<<<grid_of(T.n, 128), 128, 0, st>>>(S, T, P, tau_abs, h1, tau, hcm1);
 }
 void launch_tp_drift(const Sim &S, const TPSet &T, const DevParams &P, double tau, double hcm1, double hcm2, cudaStream_t st) {
   k_tp_drift<<<grid_of(T.n, 128), 128, 0, st>>>(S, T, P, tau, hcm1, hcm2);
@@ -804,9 +878,6 @@ void launch_tp_encounter(const Sim &S, const TPSet &T, double tau, int blocks, c
 }
 void launch_tp_bs(const Sim &S, const TPSet &T, const DevParams &P, double tau, int blocks, cudaStream_t st) {
   k_tp_bs<<<blocks, 32 * TPB_WARPS, TPB_SMEM, st>>>(S, T, P, tau);
-}
-void launch_tp_hc(const Sim &S, const TPSet &T, double hcm, cudaStream_t st) {
-  k_tp_hc<<<grid_of(T.n, 128), 128, 0, st>>>(S, T, hcm);
 }
 
 }  // namespace genga
