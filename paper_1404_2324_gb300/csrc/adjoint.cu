@@ -289,13 +289,14 @@ __global__ void __launch_bounds__(256) k_ad_group(Sim S, AdjDev D, double tau) {
   for (int k = tid; k < nc; k += blockDim.x) {
     const int pr = D.cand[(size_t)b * D.ccap + k];
     const int i = pr >> 16, j = pr & 0xffff, gi = base + i, gj = base + j;
-    const double dmin = hermite_min_exact(
+    const double rcij = pmax(S.rc[gi], S.rc[gj]);
+    const double thr = __dmul_rn(rcij, rcij);
+    const double dmin = hermite_min_capped(
         __dsub_rn(S.x0[gj], S.x0[gi]), __dsub_rn(S.x0[NB + gj], S.x0[NB + gi]), __dsub_rn(S.x0[2 * NB + gj], S.x0[2 * NB + gi]),
         __dsub_rn(S.v0[gj], S.v0[gi]), __dsub_rn(S.v0[NB + gj], S.v0[NB + gi]), __dsub_rn(S.v0[2 * NB + gj], S.v0[2 * NB + gi]),
         __dsub_rn(S.x[gj], S.x[gi]), __dsub_rn(S.x[NB + gj], S.x[NB + gi]), __dsub_rn(S.x[2 * NB + gj], S.x[2 * NB + gi]),
-        __dsub_rn(S.v[gj], S.v[gi]), __dsub_rn(S.v[NB + gj], S.v[NB + gi]), __dsub_rn(S.v[2 * NB + gj], S.v[2 * NB + gi]), tau);
-    const double rcij = pmax(S.rc[gi], S.rc[gj]);
-    if (dmin < __dmul_rn(rcij, rcij)) {
+        __dsub_rn(S.v[gj], S.v[gi]), __dsub_rn(S.v[NB + gj], S.v[NB + gi]), __dsub_rn(S.v[2 * NB + gj], S.v[2 * NB + gi]), tau, thr);
+    if (dmin < thr) {
       const int e = atomicAdd(&ne, 1);
       if (e < 1024) { edges[2 * e] = i; edges[2 * e + 1] = j; }
     }

@@ -200,13 +200,14 @@ __global__ void __launch_bounds__(BENC_THREADS) k_b_encounter(Sim S, double tau)
   auto test = [&](int i, int b) {  // pair (i, system index b > i's): sets the bit in i's mask
     const int j = S.sys_start[S.sys_of[i]] + b;
     if (!S.alive[j]) return;
-    const double dmin = hermite_min_exact(
+    const double rcij = pmax(S.rc[i], S.rc[j]);
+    const double thr = __dmul_rn(rcij, rcij);
+    const double dmin = hermite_min_capped(
         __dsub_rn(S.x0[j], S.x0[i]), __dsub_rn(S.x0[np + j], S.x0[np + i]), __dsub_rn(S.x0[2 * np + j], S.x0[2 * np + i]),
         __dsub_rn(S.v0[j], S.v0[i]), __dsub_rn(S.v0[np + j], S.v0[np + i]), __dsub_rn(S.v0[2 * np + j], S.v0[2 * np + i]),
         __dsub_rn(S.x[j], S.x[i]), __dsub_rn(S.x[np + j], S.x[np + i]), __dsub_rn(S.x[2 * np + j], S.x[2 * np + i]),
-        __dsub_rn(S.v[j], S.v[i]), __dsub_rn(S.v[np + j], S.v[np + i]), __dsub_rn(S.v[2 * np + j], S.v[2 * np + i]), tau);
-    const double rcij = pmax(S.rc[i], S.rc[j]);
-    if (dmin < __dmul_rn(rcij, rcij)) atomicOr(&s_em[i - i0], 1ULL << b);
+        __dsub_rn(S.v[j], S.v[i]), __dsub_rn(S.v[np + j], S.v[np + i]), __dsub_rn(S.v[2 * np + j], S.v[2 * np + i]), tau, thr);
+    if (dmin < thr) atomicOr(&s_em[i - i0], 1ULL << b);
   };
   const int i = i0 + tid;
   if (i < np && S.alive[i]) {

@@ -192,12 +192,12 @@ __device__ void bp_big_group(BpBig &sh, const Sim &S, const DevParams &P, double
         const int b = a + 1 + rest;
         unsigned char hit = 0;
         if (sh.alive[a] && sh.alive[b]) {
-          const double dmin = hermite_min_exact(
+          const double rr = sh.R[a] + sh.R[b];
+          const double dmin = hermite_min_capped(
               __dsub_rn(sh.y[b][0], sh.y[a][0]), __dsub_rn(sh.y[b][1], sh.y[a][1]), __dsub_rn(sh.y[b][2], sh.y[a][2]),
               __dsub_rn(sh.y[b][3], sh.y[a][3]), __dsub_rn(sh.y[b][4], sh.y[a][4]), __dsub_rn(sh.y[b][5], sh.y[a][5]),
               __dsub_rn(sh.yn[b][0], sh.yn[a][0]), __dsub_rn(sh.yn[b][1], sh.yn[a][1]), __dsub_rn(sh.yn[b][2], sh.yn[a][2]),
-              __dsub_rn(sh.yn[b][3], sh.yn[a][3]), __dsub_rn(sh.yn[b][4], sh.yn[a][4]), __dsub_rn(sh.yn[b][5], sh.yn[a][5]), H);
-          const double rr = sh.R[a] + sh.R[b];
+              __dsub_rn(sh.yn[b][3], sh.yn[a][3]), __dsub_rn(sh.yn[b][4], sh.yn[a][4]), __dsub_rn(sh.yn[b][5], sh.yn[a][5]), H, rr * rr);
           hit = dmin < rr * rr;
         }
         sh.cont[pi] = hit;
@@ -464,13 +464,14 @@ __global__ void __launch_bounds__(BP_THREADS, 2) k_b_persist(Sim S, DevParams P,
         for (int p = tid; p < sy.npairs; p += BP_THREADS) {
           const int a = sy.pa[p], b = sy.pb[p];
           if (!sy.alive[b]) continue;
-          const double dmin = hermite_min_exact(
+          const double rcij = pmax(sy.rc[a], sy.rc[b]);
+          const double thr = __dmul_rn(rcij, rcij);
+          const double dmin = hermite_min_capped(
               __dsub_rn(sy.x0[0][b], sy.x0[0][a]), __dsub_rn(sy.x0[1][b], sy.x0[1][a]), __dsub_rn(sy.x0[2][b], sy.x0[2][a]),
               __dsub_rn(sy.v0[0][b], sy.v0[0][a]), __dsub_rn(sy.v0[1][b], sy.v0[1][a]), __dsub_rn(sy.v0[2][b], sy.v0[2][a]),
               __dsub_rn(sy.x[0][b], sy.x[0][a]), __dsub_rn(sy.x[1][b], sy.x[1][a]), __dsub_rn(sy.x[2][b], sy.x[2][a]),
-              __dsub_rn(sy.v[0][b], sy.v[0][a]), __dsub_rn(sy.v[1][b], sy.v[1][a]), __dsub_rn(sy.v[2][b], sy.v[2][a]), tau);
-          const double rcij = pmax(sy.rc[a], sy.rc[b]);
-          if (dmin < __dmul_rn(rcij, rcij)) {
+              __dsub_rn(sy.v[0][b], sy.v[0][a]), __dsub_rn(sy.v[1][b], sy.v[1][a]), __dsub_rn(sy.v[2][b], sy.v[2][a]), tau, thr);
+          if (dmin < thr) {
             atomicOr(&sy.em[a], 1ULL << b);
             atomicAdd(&sy.nenc, 1);
           }

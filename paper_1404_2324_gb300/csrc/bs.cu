@@ -284,12 +284,12 @@ __global__ void __launch_bounds__(64 * BSP_UNITS, 2) k_bs_pair(Sim S, DevParams 
       // accepted: substep H from sh.y to sh.yn[use]
       if (spec == 0 && P.collisions && g == 2 && lane == 0 && sh.alive[0] && sh.alive[1]) {  // contact over the substep
         double (*yn)[6] = sh.yn[use];
-        const double dmin = hermite_min_exact(
+        const double rr = sh.R[0] + sh.R[1];
+        const double dmin = hermite_min_capped(
             __dsub_rn(sh.y[1][0], sh.y[0][0]), __dsub_rn(sh.y[1][1], sh.y[0][1]), __dsub_rn(sh.y[1][2], sh.y[0][2]),
             __dsub_rn(sh.y[1][3], sh.y[0][3]), __dsub_rn(sh.y[1][4], sh.y[0][4]), __dsub_rn(sh.y[1][5], sh.y[0][5]),
             __dsub_rn(yn[1][0], yn[0][0]), __dsub_rn(yn[1][1], yn[0][1]), __dsub_rn(yn[1][2], yn[0][2]),
-            __dsub_rn(yn[1][3], yn[0][3]), __dsub_rn(yn[1][4], yn[0][4]), __dsub_rn(yn[1][5], yn[0][5]), H);
-        const double rr = sh.R[0] + sh.R[1];
+            __dsub_rn(yn[1][3], yn[0][3]), __dsub_rn(yn[1][4], yn[0][4]), __dsub_rn(yn[1][5], yn[0][5]), H, rr * rr);
         if (dmin < rr * rr) {  // perfect merger (Sect. 3.2, Collisions), as in k_bs
           const int ia = sh.idx[0], ib = sh.idx[1];
           const double ma = sh.m[0], mb = sh.m[1], M = ma + mb;

@@ -278,12 +278,12 @@ __global__ void __launch_bounds__(GR_THREADS, 2) k_bs_grid(Sim S, DevParams P, d
             if (!__ldcg(B.alive + b)) continue;
             double yb[6], ynb[6];
             for (int c = 0; c < 6; ++c) { yb[c] = __ldcg(yc + (size_t)b * 6 + c); ynb[c] = __ldcg(yn + (size_t)b * 6 + c); }
-            const double dmin = hermite_min_exact(
+            const double rr = Ra + __ldcg(B.R + b);
+            const double dmin = hermite_min_capped(
                 __dsub_rn(yb[0], ya[0]), __dsub_rn(yb[1], ya[1]), __dsub_rn(yb[2], ya[2]),
                 __dsub_rn(yb[3], ya[3]), __dsub_rn(yb[4], ya[4]), __dsub_rn(yb[5], ya[5]),
                 __dsub_rn(ynb[0], yna[0]), __dsub_rn(ynb[1], yna[1]), __dsub_rn(ynb[2], yna[2]),
-                __dsub_rn(ynb[3], yna[3]), __dsub_rn(ynb[4], yna[4]), __dsub_rn(ynb[5], yna[5]), H);
-            const double rr = Ra + __ldcg(B.R + b);
+                __dsub_rn(ynb[3], yna[3]), __dsub_rn(ynb[4], yna[4]), __dsub_rn(ynb[5], yna[5]), H, rr * rr);
             if (dmin < rr * rr) {
               const int s = atomicAdd(B.ncont, 1);
               if (s < GR_CONTACT_CAP) B.cont[s] = a * gcap + b;

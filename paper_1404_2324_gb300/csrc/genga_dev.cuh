@@ -347,6 +347,25 @@ static __device__ double hermite_min_exact(double dx0, double dy0, double dz0, d
   return dmin;
 }
 
+// hermite_min_exact where the minimum can fall below thr, else +infinity: the same decision for
+// every test "minimum < thr" at a fraction of the cost when the pair stays far apart. Over t in
+// [0, 1] the interpolant is h00 P0 + h01 P1 + tau (h10 Pd0 + h11 Pd1) with h00 + h01 = 1, h00, h01 >= 0
+// and |h10|, |h11| <= 4/27, so it is at least min(P0, P1) - (4/27) |tau| (|Pd0| + |Pd1|). A bound that
+// clears thr by 1e-12 of the terms' size (thousands of times the rounding of either evaluation)
+// proves that the full minimum, rounding included, is not below thr; NaN takes the full path.
+static __device__ double hermite_min_capped(double dx0, double dy0, double dz0, double dvx0, double dvy0, double dvz0,
+                                            double dx1, double dy1, double dz1, double dvx1, double dvy1, double dvz1,
+                                            double tau, double thr) {
+  const double P0 = r2_exact(dx0, dy0, dz0);
+  const double P1 = r2_exact(dx1, dy1, dz1);
+  const double Pd0 = __dmul_rn(2.0, dot_exact(dx0, dy0, dz0, dvx0, dvy0, dvz0));
+  const double Pd1 = __dmul_rn(2.0, dot_exact(dx1, dy1, dz1, dvx1, dvy1, dvz1));
+  const double spread = (4.0 / 27.0) * fabs(tau) * (fabs(Pd0) + fabs(Pd1));
+  const double lb = (P0 < P1 ? P0 : P1) - spread;
+  if (lb - 1e-12 * (P0 + P1 + spread) > thr) return __longlong_as_double(0x7ff0000000000000LL);
+  return hermite_min_exact(dx0, dy0, dz0, dvx0, dvy0, dvz0, dx1, dy1, dz1, dvx1, dvy1, dvz1, tau);
+}
+
 // ---------------------------------------------------------------------------------------------
 // Stumpff functions (Danby 1988): c_k(z), reduced by quartering z until |z| <= 0.1, Taylor series
 // of c2 and c3, then the quadrupling identities c0(4z) = 2c0^2 - 1, c1(4z) = c0 c1,

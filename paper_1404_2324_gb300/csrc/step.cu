@@ -73,13 +73,14 @@ constexpr int ENC_CAP = 1024;    // gathered pairs per CTA; further pairs are te
 __device__ __forceinline__ bool encounter_test(const Sim &S, double tau, int i, int j) {
   const int np = S.npad;
   if (!S.alive[i] || !S.alive[j]) return false;
-  const double dmin = hermite_min_exact(
+  const double rcij = pmax(S.rc[i], S.rc[j]);
+  const double thr = __dmul_rn(rcij, rcij);
+  const double dmin = hermite_min_capped(
       __dsub_rn(S.x0[j], S.x0[i]), __dsub_rn(S.x0[np + j], S.x0[np + i]), __dsub_rn(S.x0[2 * np + j], S.x0[2 * np + i]),
       __dsub_rn(S.v0[j], S.v0[i]), __dsub_rn(S.v0[np + j], S.v0[np + i]), __dsub_rn(S.v0[2 * np + j], S.v0[2 * np + i]),
       __dsub_rn(S.x[j], S.x[i]), __dsub_rn(S.x[np + j], S.x[np + i]), __dsub_rn(S.x[2 * np + j], S.x[2 * np + i]),
-      __dsub_rn(S.v[j], S.v[i]), __dsub_rn(S.v[np + j], S.v[np + i]), __dsub_rn(S.v[2 * np + j], S.v[2 * np + i]), tau);
-  const double rcij = pmax(S.rc[i], S.rc[j]);
-  return dmin < __dmul_rn(rcij, rcij);
+      __dsub_rn(S.v[j], S.v[i]), __dsub_rn(S.v[np + j], S.v[np + i]), __dsub_rn(S.v[2 * np + j], S.v[2 * np + i]), tau, thr);
+  return dmin < thr;
 }
 
 __global__ void __launch_bounds__(ENC_THREADS) k_encounter(Sim S, double tau, unsigned *ebm, int keep) {

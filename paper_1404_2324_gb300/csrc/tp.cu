@@ -358,13 +358,14 @@ __global__ void __launch_bounds__(256) k_tp_encounter(Sim S, TPSet T, double tau
     const int i = (int)(pr >> 5), j = (int)(pr & 31u);
     if (!T.alive[i] || !S.alive[j]) continue;
     const double *pf = T.ptab + ((size_t)j * TP_TAB + tab_index(1, 2)) * 6;  // t = tau
-    const double dmin = hermite_min_exact(
+    const double rcij = pmax(T.rc[i], S.rc[j]);
+    const double thr = __dmul_rn(rcij, rcij);
+    const double dmin = hermite_min_capped(
         __dsub_rn(S.x0[j], T.x0[i]), __dsub_rn(S.x0[pp + j], T.x0[np + i]), __dsub_rn(S.x0[2 * pp + j], T.x0[2 * np + i]),
         __dsub_rn(S.v0[j], T.v0[i]), __dsub_rn(S.v0[pp + j], T.v0[np + i]), __dsub_rn(S.v0[2 * pp + j], T.v0[2 * np + i]),
         __dsub_rn(pf[0], T.x[i]), __dsub_rn(pf[1], T.x[np + i]), __dsub_rn(pf[2], T.x[2 * np + i]),
-        __dsub_rn(pf[3], T.v[i]), __dsub_rn(pf[4], T.v[np + i]), __dsub_rn(pf[5], T.v[2 * np + i]), tau);
-    const double rcij = pmax(T.rc[i], S.rc[j]);
-    if (dmin < __dmul_rn(rcij, rcij)) {
+        __dsub_rn(pf[3], T.v[i]), __dsub_rn(pf[4], T.v[np + i]), __dsub_rn(pf[5], T.v[2 * np + i]), tau, thr);
+    if (dmin < thr) {
       const unsigned old = atomicOr(&T.emask[i], 1u << j);
       atomicAdd((unsigned long long *)&T.counters[1], 1ULL);
       // a pass inside a tenth of the critical radius (the planet's pull entirely in BS) needs the
@@ -684,12 +685,12 @@ __global__ void __launch_bounds__(32 * TPB_WARPS, 1) k_tp_bs(Sim S, TPSet T, Dev
             planet_state_at(S, T, P, j, t0, i2tau, pa);
             planet_state_at(S, T, P, j, t0 + H, i2tau, pb);
           }
-          const double dmin = hermite_min_exact(
+          const double rr = T.R[i] + S.R[j];
+          const double dmin = hermite_min_capped(
               __dsub_rn(pa[0], y[0]), __dsub_rn(pa[1], y[1]), __dsub_rn(pa[2], y[2]),
               __dsub_rn(pa[3], y[3]), __dsub_rn(pa[4], y[4]), __dsub_rn(pa[5], y[5]),
               __dsub_rn(pb[0], yn[0]), __dsub_rn(pb[1], yn[1]), __dsub_rn(pb[2], yn[2]),
-              __dsub_rn(pb[3], yn[3]), __dsub_rn(pb[4], yn[4]), __dsub_rn(pb[5], yn[5]), H);
-          const double rr = T.R[i] + S.R[j];
+              __dsub_rn(pb[3], yn[3]), __dsub_rn(pb[4], yn[4]), __dsub_rn(pb[5], yn[5]), H, rr * rr);
           hit = dmin < rr * rr;
         }
         if (hit) { for (int c = 0; c < 6; ++c) y[c] = yn[c]; removed = true; break; }
