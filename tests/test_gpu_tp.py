@@ -193,3 +193,29 @@ def test_first_step_particle_planet_encounter_pairs_match(order):
         q.close()
     print(f"order {order}: {len(op)} pairs, {len(diff)} differ, {len(diff & flip)} of them at the threshold")
     assert diff <= flip, sorted(diff - flip)
+
+
+def test_particles_meeting_a_planet_in_a_group_match_oracle():
+    """Particles deep in the Hill sphere of a planet that is itself in a close encounter with a second
+    planet (the paper's reading: the particle's Bulirsch-Stoer sees the planet on its Kepler path, see
+    tests/test_oracle_tp_reading.py for the size of that approximation): the GPU follows the oracle."""
+    from tests.test_oracle_tp_reading import config
+    m, R, x, v, xt, vt = config(True)
+    d = dict(G=ics.G_GAUSS, m0=1.0, dt=6.0, m=m, R=R, x=x, v=v, x_tp=xt, v_tp=vt, R_tp=np.zeros(len(xt)))
+    h = _gpu(d, 4)
+    o = _oracle(d, 4)
+    try:
+        genga.genga_step(h, 1)
+        o.step(1)
+        assert (1, 2) in {tuple(p) for p in genga.genga_encounters(h)}  # the planets' group (central mass at 0)
+        met = {int(i) for i, j in genga.genga_tp_encounters(h) if j == 1}
+        assert len(met) >= 8
+        g = genga.genga_get_state_tp(h, len(xt))
+        _check(g, o.state(), _sensitivity(d, 4, 1), 1e-12, 10.0)
+        genga.genga_step(h, 4)
+        o.step(4)
+        g = genga.genga_get_state_tp(h, len(xt))
+        _check(g, o.state(), _sensitivity(d, 4, 5), 1e-10, 30.0)
+    finally:
+        genga.genga_free(h)
+        o.close()
