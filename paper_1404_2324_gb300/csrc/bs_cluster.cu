@@ -6,7 +6,9 @@
 // has an SM of its own. After every second evaluation the CTAs meet at a cluster barrier; level Lc
 // is then complete in CTA Lc - 1, every CTA reads its T_{Lc,1} from that CTA's shared memory
 // (distributed shared memory), extends its own copy of the Neville tableau and tests level Lc, with
-// the same arithmetic and order as the one-CTA kernel. All CTAs therefore take the same decision
+// the same arithmetic and order in every CTA. Groups of more than 8 members evaluate each pair
+// once (Newton's third law), so that up to 15 members take one FP64 round per SM sub-partition per
+// force evaluation. All CTAs therefore take the same decision
 // and follow the same control flow: every cluster barrier is reached by all 8 CTAs the same number
 // of times. Level results are double-buffered by attempt parity. Cluster k takes the k-th entry of
 // the large-group list that the grouping kernel writes.
@@ -21,6 +23,8 @@ namespace genga {
 constexpr int CL_SIZE = BS_LEVELS;  // CTAs per cluster, one per level
 constexpr int CL_THREADS = 256;
 constexpr int CL_TPS = CL_THREADS / BS_GMAX;  // lanes per member (8)
+constexpr int CL_PAIRS = BS_GMAX * (BS_GMAX - 1) / 2;
+constexpr int CL_ITEMS = BS_GMAX + CL_PAIRS;  // a force evaluation's terms: one per member, one per pair
 
 // 1/((L/(L-j))^2 - 1), the Neville factors (same values as the one-CTA kernel's table)
 __constant__ double c_facinv_cl[BS_LEVELS + 1][BS_LEVELS];
@@ -32,6 +36,9 @@ struct BsClShared {
   double y[BS_GMAX][6], yn[BS_GMAX][6];
   double isc[BS_GMAX][2];                // 1/|x|, 1/|v| at the start of the attempt
   double pos[2][BS_GMAX][3];             // chain positions, double-buffered by evaluation
+  double term[CL_ITEMS][3];              // this evaluation's terms: central pulls, then pair factors
+  double acc[BS_GMAX][3];                // this evaluation's accelerations
+  unsigned char pa[CL_PAIRS], pb[CL_PAIRS];  // pair k = (pa[k], pb[k]), pa < pb, row by row
   double T1[2][BS_GMAX][6];              // this level's result, double-buffered by attempt
   u64 err[BS_LEVELS];
   unsigned char cont[BS_GMAX * (BS_GMAX - 1) / 2];
@@ -43,8 +50,9 @@ struct BsClShared {
   unsigned char seqk[BS_SEQCAP];
 };
 
-// Terms of member q over partners p = sub, sub + CL_TPS, ... (p == q: the central mass), summed
-// over the member's lanes; the same straight-line code on every lane (see bs.cu).
+// Groups of up to CL_TPS members: the terms of member q over partners p = sub, sub + CL_TPS, ...
+// (p == q: the central mass; one term per lane), summed over the member's lanes by a butterfly;
+// the same straight-line code on every lane (see bs.cu).
 __device__ __forceinline__ void cl_terms(const BsClShared &sh, const DevParams &P, double Gm0, int g, int q, int sub,
                                          const double (*pos)[3], bool q_alive, double &ax, double &ay, double &az) {
   ax = ay = az = 0.0;
@@ -69,6 +77,52 @@ __device__ __forceinline__ void cl_terms(const BsClShared &sh, const DevParams &
     ay += __shfl_xor_sync(0xffffffffu, ay, o);
     az += __shfl_xor_sync(0xffffffffu, az, o);
   }
+}
+
+// Groups of more than CL_TPS members: one force evaluation at positions pos, by all threads of the
+// CTA, into sh.acc.
+// Every unordered pair is evaluated once (Newton's third law), beside the central mass's pull on
+// each member: term t < g is member t's central pull G m0 d / r^3 (d from the member to the central
+// mass; zero for a ghost), term g + k the factor w d / r^3 of pair k = (a, b), d = x_b - x_a, w the
+// (1 - K) weight inside the pair's critical radius and 0 outside or for a ghost. Then member a sums,
+// one component per thread group, its central pull and G m_b times its pair factors (with the sign
+// of d) over the partners b in a fixed order. Item after item, every lane runs the same
+// straight-line code; a group of up to 15 members needs one FP64 round per SM sub-partition, where
+// a thread per (member, partner slot) needs two.
+__device__ __forceinline__ void cl_eval(BsClShared &sh, const DevParams &P, double Gm0, int g, const double (*pos)[3]) {
+  const int tid = threadIdx.x;
+  const int nitems = g + g * (g - 1) / 2;
+  for (int t = tid; t < nitems; t += CL_THREADS) {
+    const bool cen = t < g;
+    const int a = cen ? t : sh.pa[t - g], b = cen ? t : sh.pb[t - g];
+    const double dx = (cen ? 0.0 : pos[b][0]) - pos[a][0], dy = (cen ? 0.0 : pos[b][1]) - pos[a][1],
+                 dz = (cen ? 0.0 : pos[b][2]) - pos[a][2];
+    const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+    const double yr = rsqrt_refined(r2);
+    const bool inside = sh.alive[a] && sh.alive[b] && dbits(r2) < umax64(sh.rcsq[a], sh.rcsq[b]);
+    const double wA = changeover_wA_clamped(r2 * yr, pmin(sh.A[a], sh.A[b]), P.kmode);
+    const double w = cen ? (sh.alive[a] ? Gm0 : 0.0) : (inside ? wA : 0.0);
+    const double f = w * (yr * yr * yr);
+    sh.term[t][0] = f * dx; sh.term[t][1] = f * dy; sh.term[t][2] = f * dz;
+  }
+  __syncthreads();
+  // member a, component c: ns threads, thread s takes the partners b = s, s + ns, ... (s = 0 also
+  // the central pull), partial sums combined by a butterfly over the ns lanes
+  const int ns = 24 * g <= CL_THREADS ? 8 : (12 * g <= CL_THREADS ? 4 : 2);
+  const int a = tid / (3 * ns), c = (tid / ns) % 3, sl = tid % ns;
+  double v = 0.0;
+  if (a < g) {
+    if (sl == 0) v = sh.term[a][c];
+    const int rowa = g + a * (g - 1) - a * (a - 1) / 2 - a - 1;  // term of pair (a, b > a): rowa + b
+    for (int bq = sl; bq < g; bq += ns) {
+      if (bq == a) continue;
+      if (bq > a) v = fma(sh.gm[bq], sh.term[rowa + bq][c], v);
+      else v = fma(-sh.gm[bq], sh.term[g + bq * (g - 1) - bq * (bq - 1) / 2 + a - bq - 1][c], v);
+    }
+  }
+  for (int o = ns >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (a < g && sl == 0) sh.acc[a][c] = v;
+  __syncthreads();
 }
 
 __global__ void __cluster_dims__(CL_SIZE, 1, 1) __launch_bounds__(CL_THREADS, 2)
@@ -99,6 +153,12 @@ __global__ void __cluster_dims__(CL_SIZE, 1, 1) __launch_bounds__(CL_THREADS, 2)
       for (int c = 0; c < 3; ++c) { sh.y[tid][c] = S.x0[c * np + i]; sh.y[tid][3 + c] = S.v0[c * np + i]; }
     }
     if (tid == 0) { sh.H = tau; sh.rem = tau; sh.U = 0.0; sh.nseq = 0; }
+    for (int k = tid; k < g * (g - 1) / 2; k += CL_THREADS) {
+      int pa = 0, rest = k;
+      while (rest >= g - 1 - pa) { rest -= g - 1 - pa; pa++; }
+      sh.pa[k] = (unsigned char)pa;
+      sh.pb[k] = (unsigned char)(pa + 1 + rest);
+    }
     __syncthreads();
     int halvings = 0, attempts = 0, steps = 0, buf = 0;
     while (true) {
@@ -129,7 +189,12 @@ __global__ void __cluster_dims__(CL_SIZE, 1, 1) __launch_bounds__(CL_THREADS, 2)
       if (tid < BS_LEVELS) sh.err[tid] = 0ULL;
       __syncthreads();
       double ax = 0.0, ay = 0.0, az = 0.0;
-      if (__any_sync(0xffffffffu, act)) cl_terms(sh, P, Gm0, g, act ? q : 0, sub, sh.pos[0], qa, ax, ay, az);
+      if (g > CL_TPS) {
+        cl_eval(sh, P, Gm0, g, sh.pos[0]);
+        if (act) { ax = sh.acc[q][0]; ay = sh.acc[q][1]; az = sh.acc[q][2]; }
+      } else if (__any_sync(0xffffffffu, act)) {
+        cl_terms(sh, P, Gm0, g, act ? q : 0, sub, sh.pos[0], qa, ax, ay, az);
+      }
       if (qa) {
         zB[0] = fma(h, zA[3], zA[0]); zB[1] = fma(h, zA[4], zA[1]); zB[2] = fma(h, zA[5], zA[2]);
         zB[3] = fma(h, ax, zA[3]); zB[4] = fma(h, ay, zA[4]); zB[5] = fma(h, az, zA[5]);
@@ -147,7 +212,12 @@ __global__ void __cluster_dims__(CL_SIZE, 1, 1) __launch_bounds__(CL_THREADS, 2)
         if (lv) {
           if (act && sub == 0) for (int c = 0; c < 3; ++c) sh.pos[b][q][c] = zB[c];
           __syncthreads();
-          if (__any_sync(0xffffffffu, act)) cl_terms(sh, P, Gm0, g, act ? q : 0, sub, sh.pos[b], qa, ax, ay, az);
+          if (g > CL_TPS) {
+            cl_eval(sh, P, Gm0, g, sh.pos[b]);
+            if (act) { ax = sh.acc[q][0]; ay = sh.acc[q][1]; az = sh.acc[q][2]; }
+          } else if (__any_sync(0xffffffffu, act)) {
+            cl_terms(sh, P, Gm0, g, act ? q : 0, sub, sh.pos[b], qa, ax, ay, az);
+          }
           if (qa) {
             if (e < nk) {
               double zn[6];
