@@ -186,6 +186,7 @@ __device__ void bp_big_group(BpBig &sh, const Sim &S, const DevParams &P, double
     __syncthreads();
     if (P.collisions) {  // contact over the substep (Hermite, threshold (R_a + R_b)^2), pre-merge states
       const int npair = g * (g - 1) / 2;
+      int anyhit = 0;
       for (int pi = tid; pi < npair; pi += BP_THREADS) {
         int a = 0, rest = pi;
         while (rest >= g - 1 - a) { rest -= g - 1 - a; a++; }
@@ -201,9 +202,9 @@ __device__ void bp_big_group(BpBig &sh, const Sim &S, const DevParams &P, double
           hit = dmin < rr * rr;
         }
         sh.cont[pi] = hit;
+        anyhit |= hit;
       }
-      __syncthreads();
-      if (tid == 0) {  // mergers in ascending pair order on the post-substep states
+      if (__syncthreads_or(anyhit) && tid == 0) {  // mergers in ascending pair order, post-substep states (none without contact)
         int pi = 0;
         for (int a = 0; a < g; ++a)
           for (int b = a + 1; b < g; ++b, ++pi) {

@@ -256,6 +256,7 @@ __global__ void __cluster_dims__(CL_SIZE, 1, 1) __launch_bounds__(CL_THREADS, 2)
         __syncthreads();
         if (P.collisions) {  // contact test and mergers, redundantly in every CTA; globals by rank 0
           const int npair = g * (g - 1) / 2;
+          int anyhit = 0;
           for (int pi = tid; pi < npair; pi += CL_THREADS) {
             int a = 0, rest = pi;
             while (rest >= g - 1 - a) { rest -= g - 1 - a; a++; }
@@ -271,9 +272,9 @@ __global__ void __cluster_dims__(CL_SIZE, 1, 1) __launch_bounds__(CL_THREADS, 2)
               hit = dmin < rr * rr;
             }
             sh.cont[pi] = hit;
+            anyhit |= hit;
           }
-          __syncthreads();
-          if (tid == 0) {  // mergers in ascending pair order on the post-substep states
+          if (__syncthreads_or(anyhit) && tid == 0) {  // mergers in ascending pair order, post-substep states (none without contact)
             int pi = 0;
             for (int a = 0; a < g; ++a)
               for (int bq = a + 1; bq < g; ++bq, ++pi) {

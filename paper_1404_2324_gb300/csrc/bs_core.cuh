@@ -191,6 +191,7 @@ __device__ void bs_group(BsSharedT<GM> &sh, const Sim &S, const DevParams &P, do
       __syncthreads();
       if (P.collisions) {  // contact test over the accepted substep (Hermite, threshold (R_a + R_b)^2)
         const int npair = g * (g - 1) / 2;
+        int anyhit = 0;
         for (int pi = tid; pi < npair; pi += NT) {
           int a = 0, rest = pi;
           while (rest >= g - 1 - a) { rest -= g - 1 - a; a++; }
@@ -206,9 +207,9 @@ __device__ void bs_group(BsSharedT<GM> &sh, const Sim &S, const DevParams &P, do
             hit = dmin < rr * rr;
           }
           sh.cont[pi] = hit;
+          anyhit |= hit;
         }
-        __syncthreads();
-        if (tid == 0) {  // mergers in ascending pair order on the post-substep states
+        if (__syncthreads_or(anyhit) && tid == 0) {  // mergers in ascending pair order, post-substep states (none without contact)
           int pi = 0;
           for (int a = 0; a < g; ++a)
             for (int bq = a + 1; bq < g; ++bq, ++pi) {
