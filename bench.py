@@ -258,7 +258,7 @@ def run_batched(args):
     one_value = nsamp * ksteps / (t_one * 1e-3)
     return {"metric": "batched system-steps/s", "value": value, "unit": "system-steps/s",
             "n_systems": BATCH_SYSTEMS, "bodies": n, "steps": spl * launches, "steps_per_launch": spl,
-            "ms_per_launch": tot / launches, "gpu_launches": kps * spl * launches,
+            "ms_per_launch": tot / launches, "gpu_launches": kps * launches,
             "autotuned": {"threads_per_body": split, "block": block,
                           "schedule": "persistent launch" if sched["persistent"] else "step graph",
                           "persistent_ctas": sched["ctas"], "trial_ms_per_step_graph": sched["ms_graph"],

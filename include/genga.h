@@ -172,8 +172,9 @@ int genga_set_profiling(genga_ctx *ctx, int on);
  * of the most recent step and in *launches their number (profiling must be on). */
 int genga_kick_time(genga_ctx *ctx, float *ms, int *launches);
 
-/* Number of kernel launches one genga_step enqueues (kernel nodes of the captured step graph;
- * captures it if needed). */
+/* Number of kernel launches one step enqueues (kernel nodes of the captured step graph; captures
+ * it if needed). Batched mode: the kernels of one launch of the batch's steps_per_launch steps
+ * (the step graph of that many steps, or the persistent kernel and its step counter). */
 int genga_launch_count(genga_ctx *ctx, int *kernels_per_step);
 
 /* Frees the context and every device buffer it owns. */

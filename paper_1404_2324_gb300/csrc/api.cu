@@ -1081,7 +1081,7 @@ int genga_launch_count(genga_ctx *c, int *kernels_per_step) {
     CK(cudaGraphNodeGetType(nd, &t));
     if (t == cudaGraphNodeTypeKernel) k++;
   }
-  *kernels_per_step = c->batched ? k / c->steps_per_launch : k;
+  *kernels_per_step = k;  // batched mode: per launch of steps_per_launch steps
   return GENGA_OK;
 }
 

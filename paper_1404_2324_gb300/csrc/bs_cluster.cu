@@ -25,6 +25,10 @@ constexpr int CL_THREADS = 256;
 constexpr int CL_TPS = CL_THREADS / BS_GMAX;  // lanes per member (8)
 constexpr int CL_PAIRS = BS_GMAX * (BS_GMAX - 1) / 2;
 constexpr int CL_ITEMS = BS_GMAX + CL_PAIRS;  // a force evaluation's terms: one per member, one per pair
+// the first level whose convergence is tested: groups of five or more members converge at level 5
+// or later in practice, and a level below it that converges is still found (its row is kept), at
+// the cost of the evaluations up to this level
+constexpr int CL_FIRST_CHECK = 4;
 
 // 1/((L/(L-j))^2 - 1), the Neville factors (same values as the one-CTA kernel's table)
 __constant__ double c_facinv_cl[BS_LEVELS + 1][BS_LEVELS];
@@ -240,15 +244,31 @@ __global__ void __cluster_dims__(CL_SIZE, 1, 1) __launch_bounds__(CL_THREADS, 2)
         }
         if (e & 1) continue;
         const int Lc = e >> 1;
-        cluster.sync();  // T_{Lc,1} is complete in CTA Lc - 1
+        // the rows of the levels below the first check are built with it: the same rows and the same
+        // first converged level as a check per level, one cluster barrier instead of CL_FIRST_CHECK
+        const int fc = lmax < CL_FIRST_CHECK ? lmax : CL_FIRST_CHECK;
+        if (Lc < fc) continue;
+        cluster.sync();  // T_{r,1} is complete in CTA r - 1 for every r <= Lc
+        const int r0 = Lc == fc ? 1 : Lc;
+        double tk[CL_FIRST_CHECK + 1];  // T_{r,r} of the rows built at the first check
         if (rowth) {
-          const double *rt = cluster.map_shared_rank(&sh.T1[buf][0][0], (unsigned)(Lc - 1));
-          double before;
-          tlast = neville_row(rt[qc * 6 + cc], Lc, [&](int j) { return c_facinv_cl[Lc][j]; }, prev, before);
-          if (Lc >= 2 && sh.alive[qc]) atomicMax(&sh.err[Lc - 1], absbits((tlast - before) * scale));
+#pragma unroll
+          for (int r = 1; r <= BS_LEVELS; ++r) {
+            if (r < r0 || r > Lc) continue;
+            const double *rt = cluster.map_shared_rank(&sh.T1[buf][0][0], (unsigned)(r - 1));
+            double before;
+            tlast = neville_row(rt[qc * 6 + cc], r, [&](int j) { return c_facinv_cl[r][j]; }, prev, before);
+            if (r >= 2 && sh.alive[qc]) atomicMax(&sh.err[r - 1], absbits((tlast - before) * scale));
+            if (r <= CL_FIRST_CHECK) tk[r] = tlast;
+          }
         }
         __syncthreads();
-        if (Lc >= 2 && sh.err[Lc - 1] <= eps) { acc = Lc; break; }
+        for (int r = r0 < 2 ? 2 : r0; r <= Lc; ++r)  // uniform: every thread reads the same errors
+          if (sh.err[r - 1] <= eps) { acc = r; break; }
+        if (acc) {
+          if (acc < Lc && rowth) tlast = tk[acc];
+          break;
+        }
       }
       if (acc && rowth) sh.yn[qc][cc] = tlast;  // the accepted row is the last one built
       buf ^= 1;

@@ -30,7 +30,7 @@ struct BsSharedT {
   double y[GM][6], yn[GM][6];
   double pos[2][BS_LEVELS][GM][3];
   double tab[BS_LEVELS][GM][6];
-  u64 err[BS_LEVELS];
+  u64 err[BS_LEVELS], err2[BS_LEVELS];  // per level: the attempt at H, the speculative one at H/2
   unsigned char cont[GM * (GM - 1) / 2];
   double H, rem, U;
   int accept, next;
@@ -96,6 +96,17 @@ __device__ void bs_group(BsSharedT<GM> &sh, const Sim &S, const DevParams &P, do
   const int lev = act ? slot / g : 0;  // level k = lev + 1, n_k = 2k substeps
   const int q = act ? slot % g : 0;
   const int L = lev + 1, nk = 2 * L;
+  // Speculation (groups of one or two members, whose slots leave two of their four threads idle):
+  // threads 2, 3 of a slot run the attempt at H/2 from the same state, with the same arithmetic, in
+  // the same warp instructions; its members sit at index 16 + q of the position and tableau arrays,
+  // its tableau rows on threads 64 + (member, component). Its result is taken exactly when the
+  // serial step control's next attempt would be that one (the attempt at H failed), so results and
+  // decisions are the serial algorithm's, and a failed attempt no longer costs a round of its own.
+  const bool spec = g <= 2 && tps == 4 && NT >= 128 && GM >= 18;  // uniform
+  const int half = spec ? (sub >> 1) : 0, tsub = spec ? (sub & 1) : sub, ttps = spec ? 2 : tps;
+  const int qm = q + 16 * half;  // this thread's member in its attempt's position and tableau arrays
+  const int trow = (spec && tid >= 64) ? tid - 64 : tid;  // tableau thread of attempt (spec && tid >= 64)
+  const int thalf = (spec && tid >= 64) ? 1 : 0;
   if (tid < g) {
     const int i = S.gmem[g0 + tid];
     sh.idx[tid] = i;
@@ -118,12 +129,12 @@ __device__ void bs_group(BsSharedT<GM> &sh, const Sim &S, const DevParams &P, do
     // right away (thread (qc, cc) holds member qc's component cc of the previous row), and the
     // attempt stops at the first converged level: the same decision as building the whole
     // tableau first, but attempts that converge at level 4-6 (almost all) skip the deeper chains.
-    const double h = __ddiv_rn(H, (double)nk), h2 = 2.0 * h;
+    const double h = __ddiv_rn(half ? 0.5 * H : H, (double)nk), h2 = 2.0 * h;
     const bool qa = act && sh.alive[q];
     double zA[6], zB[6], out[6];
     for (int c = 0; c < 6; ++c) zA[c] = sh.y[q][c];
-    if (act && sub == 0) for (int c = 0; c < 3; ++c) sh.pos[0][lev][q][c] = zA[c];
-    const int qc = tid / 6, cc = tid % 6;
+    if (act && tsub == 0) for (int c = 0; c < 3; ++c) sh.pos[0][lev][qm][c] = zA[c];
+    const int qc = trow / 6, cc = trow % 6;
     const bool rowth = qc < g;
     double scale = 0.0;  // error scale of (qc, cc): 1/|x| or 1/|v| at the start of the attempt
     if (rowth) {
@@ -131,12 +142,12 @@ __device__ void bs_group(BsSharedT<GM> &sh, const Sim &S, const DevParams &P, do
       const double s2 = fma(yq[2], yq[2], fma(yq[1], yq[1], yq[0] * yq[0]));
       scale = dbits(s2) == 0ULL ? 4.49423283715579e307 : rsqrt_refined(s2);
     }
-    if (tid < BS_LEVELS) sh.err[tid] = 0ULL;
+    if (tid < BS_LEVELS) { sh.err[tid] = 0ULL; sh.err2[tid] = 0ULL; }
     __syncthreads();
     double ax = 0.0, ay = 0.0, az = 0.0;
     // every lane of a warp that holds any active slot takes part (the term sums shuffle across
     // lanes); warps without active slots stay off the FP64 pipe
-    if (__any_sync(0xffffffffu, act)) bs_terms(sh, P, Gm0, g, q, sub, tps, sh.pos[0][lev], qa, ax, ay, az);
+    if (__any_sync(0xffffffffu, act)) bs_terms(sh, P, Gm0, g, q, tsub, ttps, sh.pos[0][lev] + 16 * half, qa, ax, ay, az);
     if (qa) {
       zB[0] = fma(h, zA[3], zA[0]); zB[1] = fma(h, zA[4], zA[1]); zB[2] = fma(h, zA[5], zA[2]);
       zB[3] = fma(h, ax, zA[3]); zB[4] = fma(h, ay, zA[4]); zB[5] = fma(h, az, zA[5]);
@@ -146,13 +157,13 @@ __device__ void bs_group(BsSharedT<GM> &sh, const Sim &S, const DevParams &P, do
     const int lmax = P.bs_kmax < BS_LEVELS ? P.bs_kmax : BS_LEVELS;
     const u64 eps = dbits(P.bs_eps);
     double prev[BS_LEVELS], tlast = 0.0;  // previous tableau row; T_{Lc,Lc} of the current one
-    int acc = 0;
+    int acc = 0, accB = 0;
     int b = 1;
     for (int e = 1; e <= 2 * lmax; ++e) {
       const bool lv = act && e <= nk;
-      if (lv && sub == 0) for (int c = 0; c < 3; ++c) sh.pos[b][lev][q][c] = zB[c];
+      if (lv && tsub == 0) for (int c = 0; c < 3; ++c) sh.pos[b][lev][qm][c] = zB[c];
       __syncthreads();
-      if (__any_sync(0xffffffffu, lv)) bs_terms(sh, P, Gm0, g, q, sub, tps, sh.pos[b][lev], qa, ax, ay, az);
+      if (__any_sync(0xffffffffu, lv)) bs_terms(sh, P, Gm0, g, q, tsub, ttps, sh.pos[b][lev] + 16 * half, qa, ax, ay, az);
       if (lv) {
         if (qa) {
           if (e < nk) {
@@ -171,7 +182,7 @@ __device__ void bs_group(BsSharedT<GM> &sh, const Sim &S, const DevParams &P, do
         } else if (e == nk) {
           for (int c = 0; c < 6; ++c) out[c] = zA[c];
         }
-        if (e == nk && sub == 0) for (int c = 0; c < 6; ++c) sh.tab[lev][q][c] = out[c];  // T_{L,1}
+        if (e == nk && tsub == 0) for (int c = 0; c < 6; ++c) sh.tab[lev][qm][c] = out[c];  // T_{L,1}
       }
       b ^= 1;
       if (e & 1) continue;
@@ -180,13 +191,41 @@ __device__ void bs_group(BsSharedT<GM> &sh, const Sim &S, const DevParams &P, do
       __syncthreads();
       if (rowth) {
         double before;
-        tlast = neville_row(sh.tab[Lc - 1][qc][cc], Lc, [&](int j) { return c_facinv[Lc][j]; }, prev, before);
-        if (Lc >= 2 && sh.alive[qc]) atomicMax(&sh.err[Lc - 1], absbits((tlast - before) * scale));
+        tlast = neville_row(sh.tab[Lc - 1][qc + 16 * thalf][cc], Lc, [&](int j) { return c_facinv[Lc][j]; }, prev, before);
+        if (Lc >= 2 && sh.alive[qc]) atomicMax(thalf ? &sh.err2[Lc - 1] : &sh.err[Lc - 1], absbits((tlast - before) * scale));
       }
       __syncthreads();
+      if (spec && !accB && Lc >= 2 && sh.err2[Lc - 1] <= eps) {  // the attempt at H/2 converged (uniform)
+        accB = Lc;
+        if (thalf && rowth) sh.yn[qc + 16][cc] = tlast;
+      }
       if (Lc >= 2 && sh.err[Lc - 1] <= eps) { acc = Lc; break; }  // uniform: every thread reads the same error
     }
-    if (acc && rowth) sh.yn[qc][cc] = tlast;  // the accepted row is the last one built
+    if (acc && rowth && !thalf) sh.yn[qc][cc] = tlast;  // the accepted row is the last one built
+    double Hs = H;  // length of the accepted substep
+    if (!acc && spec) {  // the serial control halves H; its next attempt is the one at H/2
+      if (++halvings > P.bs_max_halvings) {
+        if (tid == 0) atomicOr(S.status, ST_BS_FAILED);
+        __syncthreads();
+        break;
+      }
+      ++attempts;
+      if (accB) {
+        acc = accB;
+        Hs = 0.5 * H;
+        __syncthreads();
+        if (tid < 6 * g) sh.yn[tid / 6][tid % 6] = sh.yn[tid / 6 + 16][tid % 6];
+      } else {  // that attempt failed too: the serial control halves again
+        if (tid == 0) sh.H = 0.25 * H;
+        if (++halvings > P.bs_max_halvings) {
+          if (tid == 0) atomicOr(S.status, ST_BS_FAILED);
+          __syncthreads();
+          break;
+        }
+        __syncthreads();
+        continue;
+      }
+    }
     if (acc) {
       __syncthreads();
       if (P.collisions) {  // contact test over the accepted substep (Hermite, threshold (R_a + R_b)^2)
@@ -203,7 +242,7 @@ __device__ void bs_group(BsSharedT<GM> &sh, const Sim &S, const DevParams &P, do
                 __dsub_rn(sh.y[bq][0], sh.y[a][0]), __dsub_rn(sh.y[bq][1], sh.y[a][1]), __dsub_rn(sh.y[bq][2], sh.y[a][2]),
                 __dsub_rn(sh.y[bq][3], sh.y[a][3]), __dsub_rn(sh.y[bq][4], sh.y[a][4]), __dsub_rn(sh.y[bq][5], sh.y[a][5]),
                 __dsub_rn(sh.yn[bq][0], sh.yn[a][0]), __dsub_rn(sh.yn[bq][1], sh.yn[a][1]), __dsub_rn(sh.yn[bq][2], sh.yn[a][2]),
-                __dsub_rn(sh.yn[bq][3], sh.yn[a][3]), __dsub_rn(sh.yn[bq][4], sh.yn[a][4]), __dsub_rn(sh.yn[bq][5], sh.yn[a][5]), H, rr * rr);
+                __dsub_rn(sh.yn[bq][3], sh.yn[a][3]), __dsub_rn(sh.yn[bq][4], sh.yn[a][4]), __dsub_rn(sh.yn[bq][5], sh.yn[a][5]), Hs, rr * rr);
             hit = dmin < rr * rr;
           }
           sh.cont[pi] = hit;
@@ -243,8 +282,8 @@ __device__ void bs_group(BsSharedT<GM> &sh, const Sim &S, const DevParams &P, do
         for (int c = 0; c < 6; ++c)
           S.y_scratch[(((size_t)rec_slot * BS_SEQCAP + steps) * BS_GMAX + tid) * 6 + c] = sh.yn[tid][c];
       if (tid == 0) {
-        sh.rem = rem - H; sh.H = 2.0 * H;
-        if (sh.nseq < BS_SEQCAP) { sh.seqH[sh.nseq] = H; sh.seqk[sh.nseq] = (unsigned char)acc; }
+        sh.rem = rem - Hs; sh.H = 2.0 * Hs;
+        if (sh.nseq < BS_SEQCAP) { sh.seqH[sh.nseq] = Hs; sh.seqk[sh.nseq] = (unsigned char)acc; }
         sh.nseq++;
       }
       halvings = 0;

@@ -151,7 +151,10 @@ def test_batch_autotuned_shape_is_reported():
     h = genga.genga_init_batch(b["offsets"], b["m0"], b["m"], b["R"], b["x"], b["v"], b["G"], b["dt"], 2, 100)
     split, block, spl = genga.genga_batch_info(h)
     assert split in (1, 2, 4) and block in (64, 128, 256) and spl == 100
-    assert genga.genga_launch_count(h) == 13  # incl. the four BS kernels (pairs, 3..4, 5..32, 33..64 members)
+    # per launch of 100 steps: the step graph's 13 kernels a step (incl. the four BS kernels: pairs,
+    # 3..4, 5..32, 33..64 members), or the persistent kernel and its step counter
+    persistent = genga.genga_batch_schedule(h)["persistent"]
+    assert genga.genga_launch_count(h) == (2 if persistent else 13 * spl)
     genga.genga_free(h)
 
 
