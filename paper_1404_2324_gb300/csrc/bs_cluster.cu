@@ -251,16 +251,18 @@ __global__ void __cluster_dims__(CL_SIZE, 1, 1) __launch_bounds__(CL_THREADS, 2)
         cluster.sync();  // T_{r,1} is complete in CTA r - 1 for every r <= Lc
         const int r0 = Lc == fc ? 1 : Lc;
         double tk[CL_FIRST_CHECK + 1];  // T_{r,r} of the rows built at the first check
-        if (rowth) {
 #pragma unroll
-          for (int r = 1; r <= BS_LEVELS; ++r) {
-            if (r < r0 || r > Lc) continue;
+        for (int r = 1; r <= BS_LEVELS; ++r) {
+          if (r < r0 || r > Lc) continue;  // uniform
+          u64 ev = 0ULL;
+          if (rowth) {
             const double *rt = cluster.map_shared_rank(&sh.T1[buf][0][0], (unsigned)(r - 1));
             double before;
             tlast = neville_row(rt[qc * 6 + cc], r, [&](int j) { return c_facinv_cl[r][j]; }, prev, before);
-            if (r >= 2 && sh.alive[qc]) atomicMax(&sh.err[r - 1], absbits((tlast - before) * scale));
+            if (r >= 2 && sh.alive[qc]) ev = absbits((tlast - before) * scale);
             if (r <= CL_FIRST_CHECK) tk[r] = tlast;
           }
+          if (r >= 2) warp_max_to(&sh.err[r - 1], ev);
         }
         __syncthreads();
         for (int r = r0 < 2 ? 2 : r0; r <= Lc; ++r)  // uniform: every thread reads the same errors

@@ -189,11 +189,13 @@ __device__ void bs_group(BsSharedT<GM> &sh, const Sim &S, const DevParams &P, do
       // level Lc = e/2 is complete: its tableau row (polynomial extrapolation in h^2, Neville)
       const int Lc = e >> 1;
       __syncthreads();
+      u64 ev = 0ULL;
       if (rowth) {
         double before;
         tlast = neville_row(sh.tab[Lc - 1][qc + 16 * thalf][cc], Lc, [&](int j) { return c_facinv[Lc][j]; }, prev, before);
-        if (Lc >= 2 && sh.alive[qc]) atomicMax(thalf ? &sh.err2[Lc - 1] : &sh.err[Lc - 1], absbits((tlast - before) * scale));
+        if (Lc >= 2 && sh.alive[qc]) ev = absbits((tlast - before) * scale);
       }
+      if (Lc >= 2) warp_max_to(thalf ? &sh.err2[Lc - 1] : &sh.err[Lc - 1], ev);  // thalf is uniform per warp
       __syncthreads();
       if (spec && !accB && Lc >= 2 && sh.err2[Lc - 1] <= eps) {  // the attempt at H/2 converged (uniform)
         accB = Lc;

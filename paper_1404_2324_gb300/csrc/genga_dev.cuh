@@ -538,6 +538,17 @@ __device__ __forceinline__ void merger_report(const Sim &S, int ia, int ib, cons
   }
 }
 
+// Largest v over the warp into *dst (shared memory; one atomic per warp instead of one per thread,
+// which serialised on the single address). All 32 lanes call it; v = 0 adds nothing.
+__device__ __forceinline__ void warp_max_to(u64 *dst, u64 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const u64 t = __shfl_xor_sync(0xffffffffu, v, o);
+    v = t > v ? t : v;
+  }
+  if ((threadIdx.x & 31) == 0 && v) atomicMax((unsigned long long *)dst, (unsigned long long)v);
+}
+
 // Warp reductions (butterfly), fixed order -> deterministic
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
