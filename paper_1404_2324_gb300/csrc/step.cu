@@ -149,9 +149,9 @@ __global__ void __launch_bounds__(ENC_THREADS) k_encounter(Sim S, double tau, un
 // ---------------------------------------------------------------------------------------------
 // Grouping (Appendix): one CTA. LINK[i] = i; every edge hooks the larger root onto the smaller
 // with atomicMin; pointer jumping compresses the links; repeat until no edge joins two roots.
-// Then the members (bodies in an edge or in the Kepler-fallback list) are sorted by
-// (root, index) with a bitonic sort, which yields groups ordered by smallest member and members
-// ascending -- the same lists as a breadth-first search.
+// Then the members (bodies in an edge or in the Kepler-fallback list) are placed by root with a
+// counting placement, which yields groups ordered by smallest member and members ascending -- the
+// same lists as a breadth-first search.
 // ---------------------------------------------------------------------------------------------
 constexpr int GROUP_THREADS = 1024;
 constexpr int GROUP_MAX_ROUNDS = 64;
@@ -188,6 +188,41 @@ __device__ int block_compact(int n, Pred pred, Emit emit, int *wtot, int *s_base
   return *s_base;
 }
 
+// In-place exclusive scan of v[0, n) by one CTA of GROUP_THREADS threads (ordered, exact).
+__device__ void block_scan_excl(int *v, int n, int *wtot, int *s_base) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) *s_base = 0;
+  __syncthreads();
+  for (int c0 = 0; c0 < n; c0 += GROUP_THREADS) {
+    const int i = c0 + tid;
+    const int x = i < n ? v[i] : 0;
+    int incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) wtot[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      const int w = wtot[lane];
+      int winc = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, winc, o);
+        if (lane >= o) winc += t;
+      }
+      wtot[lane] = winc - w;  // exclusive offsets of the warps
+    }
+    __syncthreads();
+    const int base = *s_base;
+    if (i < n) v[i] = base + wtot[wid] + incl - x;
+    __syncthreads();
+    if (tid == GROUP_THREADS - 1) *s_base = base + wtot[wid] + incl;
+    __syncthreads();
+  }
+}
+
 __device__ __forceinline__ int find_root(const int *link, int r) {
   for (int k = 0; k < NMAX + 2; ++k) {
     const int l = link[r];
@@ -200,6 +235,7 @@ __device__ __forceinline__ int find_root(const int *link, int r) {
 __global__ void __launch_bounds__(GROUP_THREADS) k_group(Sim S, int gbig) {
   __shared__ int link[NMAX];
   __shared__ int key[NMAX];
+  __shared__ int gcnt[NMAX];
   __shared__ unsigned char part[NMAX];
   __shared__ int wtot[GROUP_THREADS / 32];
   __shared__ int s_changed, s_base, s_ng;
@@ -227,30 +263,35 @@ __global__ void __launch_bounds__(GROUP_THREADS) k_group(Sim S, int gbig) {
     if (!s_changed) break;
   }
   if (round >= GROUP_MAX_ROUNDS && tid == 0) atomicOr(S.status, ST_UNION_ROUNDS);
-  // compact the participants as keys root * npad + i (block-wide ordered scan)
-  const int cnt = block_compact(np, [&](int i) { return part[i] != 0; },
-                                [&](int i, int pos) { key[pos] = link[i] * np + i; }, wtot, &s_base);
-  int M = 1;
-  while (M < cnt) M <<= 1;
-  for (int t = cnt + tid; t < M; t += GROUP_THREADS) key[t] = 0x7fffffff;
+  // Groups by root (the smallest member: links only ever point to smaller indices), members
+  // ascending. The participants in ascending order; members counted per root; an ordered scan
+  // gives each root's first position; one warp walks the participants in order and puts each at
+  // its root's next free position (lanes with the same root take consecutive ones).
+  const int cnt = block_compact(np, [&](int i) { return part[i] != 0; }, [&](int i, int pos) { key[pos] = i; },
+                                wtot, &s_base);
+  for (int i = tid; i < np; i += GROUP_THREADS) gcnt[i] = 0;
   __syncthreads();
-  for (int k = 2; k <= M; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int t = tid; t < M; t += GROUP_THREADS) {
-        const int u = t ^ j;
-        if (u > t) {
-          const int a = key[t], b = key[u];
-          const bool up = (t & k) == 0;
-          if ((a > b) == up) { key[t] = b; key[u] = a; }
-        }
+  for (int k = tid; k < cnt; k += GROUP_THREADS) atomicAdd(&gcnt[link[key[k]]], 1);
+  __syncthreads();
+  block_scan_excl(gcnt, np, wtot, &s_base);  // gcnt[r]: the first position of root r's group
+  s_ng = block_compact(np, [&](int r) { return part[r] != 0 && link[r] == r; },
+                       [&](int r, int g) { S.gstart[g] = gcnt[r]; }, wtot, &s_base);
+  if (wid == 0) {
+    for (int c0 = 0; c0 < cnt; c0 += 32) {
+      const int k = c0 + lane;
+      const bool ok = k < cnt;
+      const int i = ok ? key[k] : 0, r = ok ? link[i] : -1 - lane;  // idle lanes: roots of their own
+      const unsigned m = __match_any_sync(0xffffffffu, r);
+      const int pos = ok ? gcnt[r] + __popc(m & ((1u << lane) - 1u)) : 0;
+      __syncwarp();
+      if (ok) {
+        S.gmem[pos] = i;
+        if (lane == __ffs(m) - 1) gcnt[r] += __popc(m);
       }
-      __syncthreads();
+      __syncwarp();
     }
   }
-  for (int t = tid; t < cnt; t += GROUP_THREADS) S.gmem[t] = key[t] % np;
-  // a new group starts where the root changes; ordered scan of the start flags numbers them
-  s_ng = block_compact(cnt, [&](int t) { return t == 0 || key[t] / np != key[t - 1] / np; },
-                       [&](int t, int g) { S.gstart[g] = t; }, wtot, &s_base);
+  __syncthreads();
   if (tid == 0) {
     S.gstart[s_ng] = cnt;
     *S.ngroups = s_ng;
