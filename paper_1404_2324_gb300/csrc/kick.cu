@@ -224,12 +224,12 @@ __global__ void __launch_bounds__(128) k_fin(Sim S, DevParams P, double h1, doub
   __shared__ int off[33], s_cnt[32];
   const bool use_part = (MODE != FIN_OPEN) || (S.flags[0] != 0);
   const bool full_open = (MODE == FIN_OPEN) && (S.flags[0] != 0);
-  if (use_part) {
-    const int nslot = 2 * nt, s0 = wi * nslot / 4, s1 = (wi + 1) * nslot / 4;
-    const double *base = S.part + (size_t)B * nt * 2 * 96 + c * 32 + lane;
-    double acc = 0.0;
-    for (int s = s0; s < s1; ++s) acc += base[(size_t)s * 96];
-    red[wi][lane] = acc;
+  // the loads of the final update first (warp 0), so that their latency passes under the sums
+  double a_far = 0.0, v_old = 0.0, m_i = 0.0;
+  bool alive = false;
+  if (wi == 0) {
+    if (!use_part) a_far = S.afar[c * np + i];
+    if (MODE != FIN_INIT) { v_old = S.v[c * np + i]; m_i = S.m[i]; alive = S.alive[i] != 0; }
   }
   // this tile's candidate partners: counts and offsets (warp 0), then the lists (all threads)
   bool overflow = false;
@@ -247,6 +247,15 @@ __global__ void __launch_bounds__(128) k_fin(Sim S, DevParams P, double h1, doub
     off[lane + 1] = incl;
     s_cnt[lane] = cnt;
     if (lane == 0) off[0] = 0;
+  }
+  if (use_part) {  // far-field partial sums: each warp a quarter of the slots, two chains of alternate slots
+    const int nslot = 2 * nt, s0 = wi * nslot / 4, s1 = (wi + 1) * nslot / 4;
+    const double *base = S.part + (size_t)B * nt * 2 * 96 + c * 32 + lane;
+    double acc0 = 0.0, acc1 = 0.0;
+    int s = s0;
+    for (; s + 1 < s1; s += 2) { acc0 += base[(size_t)s * 96]; acc1 += base[(size_t)(s + 1) * 96]; }
+    if (s < s1) acc0 += base[(size_t)s * 96];
+    red[wi][lane] = acc0 + acc1;
   }
   __syncthreads();
   const int M = off[32];
@@ -272,20 +281,19 @@ __global__ void __launch_bounds__(128) k_fin(Sim S, DevParams P, double h1, doub
   for (int k = threadIdx.x; k < M; k += 128) contrib[k] = near_term(S, P, B * 32 + owner(k), ent[k], c);
   __syncthreads();
   if (wi != 0) return;
-  double a = use_part ? (red[0][lane] + red[1][lane]) + (red[2][lane] + red[3][lane]) : S.afar[c * np + i];
+  double a = use_part ? (red[0][lane] + red[1][lane]) + (red[2][lane] + red[3][lane]) : a_far;
   if (MODE != FIN_OPEN && !ALL) S.afar[c * np + i] = a;
   for (int k = off[lane]; k < off[lane + 1]; ++k) a += contrib[k];
   if (overflow) a += near_accel(S, P, i, c);
   if (aout) aout[c * np + i] = a;
   if (MODE == FIN_INIT) return;
-  const bool alive = S.alive[i] != 0;
-  double v = S.v[c * np + i];
+  double v = v_old;
   if (alive) {
     v = fma(h1, a, v);
     if (h2 != 0.0) v = fma(h2, a, v);
     S.v[c * np + i] = v;
   }
-  const double pm = warp_sum(S.m[i] * v);
+  const double pm = warp_sum(m_i * v);
   if (lane == 0) S.pfin[B * 3 + c] = pm;
 }
 
