@@ -204,14 +204,14 @@ def _clumps(sizes, seed, spread=0.004, R=None):
     return np.vstack(xs), np.vstack(vs), m, Rr, groups
 
 
-def _bs_phase_vs_oracle(x, v, m, R, groups, kmode=0):
+def _bs_phase_vs_oracle(x, v, m, R, groups, kmode=0, tau=6.0):
     n = len(m)
     alive = np.ones(n, np.int32)
     p = O.params(G=ics.G_GAUSS, m0=1.0, kmode=kmode)
     rc = np.full(n, 0.02)
     ref = dict(x=x.copy(), v=v.copy(), m=m.copy(), R=R.copy(), alive=alive.copy(), U=0.0, steps=0, coll=0)
     for gi in groups:
-        out = O.bs_group(p, gi, 6.0, ref["m"], ref["R"], ref["alive"], ref["x"], ref["v"], rc)
+        out = O.bs_group(p, gi, tau, ref["m"], ref["R"], ref["alive"], ref["x"], ref["v"], rc)
         assert out["status"] == 0
         for k in ("x", "v", "m", "R", "alive"):
             ref[k] = out[k]
@@ -221,7 +221,7 @@ def _bs_phase_vs_oracle(x, v, m, R, groups, kmode=0):
     gstart = np.concatenate([[0], np.cumsum([len(g) for g in groups])]).astype(np.int32)
     members = np.concatenate(groups).astype(np.int32)
     X, V, M, RR, AL = soa(x), soa(v), dev(m), dev(R), dev(alive)
-    st, U = genga.genga_phase_bs(n, ics.G_GAUSS, 1.0, 6.0, 1e-12, 8, 30, kmode, 1, len(groups), dev(gstart),
+    st, U = genga.genga_phase_bs(n, ics.G_GAUSS, 1.0, tau, 1e-12, 8, 30, kmode, 1, len(groups), dev(gstart),
                                  dev(members), dev(rc), M, RR, AL, X, V)
     assert st == 0, st
     np.testing.assert_array_equal(AL.cpu().numpy(), ref["alive"])
@@ -243,6 +243,26 @@ def test_bs_large_groups_match_oracle(sizes, spread):
     x, v, m, R, groups = _clumps(sizes, seed=sum(sizes), spread=spread)
     ref, U = _bs_phase_vs_oracle(x, v, m, R, groups)
     assert ref["coll"] == 0 and U == 0.0
+
+
+@pytest.mark.parametrize("tau", [6.0, 0.05])
+def test_bs_cluster_group_sizes_match_oracle(tau):
+    """Groups of 5..32 members on the cluster kernel: up to 8 members one term per lane, above that
+    every pair once (Newton's third law) with 8, 4 or 2 threads per member component in the sums
+    (up to 10, 21 and 32 members). At tau = 0.05 d the groups converge at low levels, which the
+    kernel tests together at level 4 before testing each level as it completes."""
+    x, v, m, R, groups = _clumps((5, 8, 9, 10, 11, 16, 21, 22, 32), seed=77)
+    ref, U = _bs_phase_vs_oracle(x, v, m, R, groups, tau=tau)
+    assert ref["coll"] == 0 and U == 0.0
+
+
+def test_bs_cluster_group_mergers_match_oracle():
+    """Contacts and mergers inside groups of 12 and 20 members on the cluster kernel (2 and 6 in the
+    oracle)."""
+    x, v, m, Rr, groups = _clumps((12, 20), seed=9, spread=0.001, R=3e-4)
+    ref, U = _bs_phase_vs_oracle(x, v, m, Rr, groups)
+    assert ref["coll"] >= 4
+    assert U == pytest.approx(ref["U"], rel=1e-9)
 
 
 @pytest.mark.parametrize("R", [1e-4, 3e-4])
