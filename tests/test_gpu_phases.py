@@ -256,6 +256,15 @@ def test_bs_cluster_group_sizes_match_oracle(tau):
     assert ref["coll"] == 0 and U == 0.0
 
 
+def test_bs_pairs_needing_several_substeps_match_oracle():
+    """Tight pairs whose first attempt fails (1, 2 and 9 substeps in the oracle): the one-CTA kernel
+    runs the attempt at H/2 beside the one at H in the lanes a pair leaves idle and takes it exactly
+    when the serial control would try it next, so the result is the serial algorithm's."""
+    x, v, m, R, groups = _clumps((2, 2, 2, 2, 1), seed=4, spread=0.0002)
+    ref, U = _bs_phase_vs_oracle(x, v, m, R, groups)
+    assert ref["steps"] >= 12
+
+
 def test_bs_cluster_group_mergers_match_oracle():
     """Contacts and mergers inside groups of 12 and 20 members on the cluster kernel (2 and 6 in the
     oracle)."""
