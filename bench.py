@@ -660,7 +660,7 @@ def run_gpu(args, rank, world):
     t_e2e = rank_max(time.perf_counter() - t0, world, "cuda")
     e2e = {"value": job_rate(e2e_steps, world, t_e2e), "unit": UNIT, "h2d_bytes_per_step": int(hx.nbytes + hv.nbytes),
            "d2h_bytes_per_step": int(hx.nbytes + hv.nbytes), "steps": e2e_steps,
-           "note": "genga_set_state + genga_step + genga_get_state per step; set_state recomputes the first kick"}
+           "note": "genga_set_state + genga_step + genga_get_state per step; the step after set_state opens with the full pair kick"}
     genga.genga_free(ctx)
 
     props = torch.cuda.get_device_properties(dev)

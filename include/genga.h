@@ -98,12 +98,14 @@ int genga_default_params(genga_params *p);
  *   x, v     [3n] heliocentric positions and velocities (row 0 ignored)
  *   G        gravitational constant; dt the step tau (sign gives the direction of time)
  *   order    2 (Eq. z1), 4 or 6 (Yoshida compositions, Sect. 2.3); mode GENGA_MODE_MASSIVE
- * The first kick's accelerations and precheck candidates are computed here (Sect. 2.2). The host
- * buffers are not retained. Returns 0 or a negative code; *ctx is NULL on failure. */
+ * The first step opens with the full pair kick (no stored far field yet), which also records the
+ * precheck candidates of its first substep (Sect. 2.2). The host buffers are not retained. Returns 0
+ * or a negative code; *ctx is NULL on failure. */
 int genga_init(genga_ctx **ctx, int n, const double *masses, const double *radii, const double *x,
                const double *v, double G, double dt, int order, int mode);
 
-/* Replaces the method parameters; the next genga_step recomputes the first kick. */
+/* Replaces the method parameters; the next genga_step opens with the full pair kick, as after
+ * genga_init. */
 int genga_set_params(genga_ctx *ctx, const genga_params *p);
 
 /* Makes the context launch on the given cudaStream_t (NULL: the context's own stream). */
@@ -117,7 +119,7 @@ int genga_step(genga_ctx *ctx, int n_steps);
 int genga_sync(genga_ctx *ctx);
 
 /* Replaces positions and velocities (heliocentric, host, [3n] with row 0 ignored) of all bodies;
- * masses and radii stay. The next step recomputes the first kick, as after genga_init. */
+ * masses and radii stay. The next step opens with the full pair kick, as after genga_init. */
 int genga_set_state(genga_ctx *ctx, const double *x, const double *v);
 
 /* Copies the state back (waits for the stream). Any pointer may be NULL. x, v [3n] heliocentric;

@@ -222,6 +222,15 @@ int first_kick(genga_ctx *c) {
   CK(cudaMemsetAsync(S.nedges, 0, sizeof(int), st));
   CK(cudaMemsetAsync(S.nfail, 0, sizeof(int), st));
   launch_rcrit(S, c->P, std::fabs(c->dt), 0, st);
+  if (!c->tpmode) {
+    // the main mode's next step opens with the full pair kick (the plain definition of the opening
+    // kick), which also records the precheck candidates of its first substep: flags 0 and 3, which
+    // that step's drift clears; a separate first kick would compute the same sums once more
+    CK(cudaMemsetAsync(S.flags, 1, sizeof(int), st));
+    CK(cudaMemsetAsync(S.flags + 3, 1, sizeof(int), st));
+    CK(cudaGetLastError());
+    return GENGA_OK;
+  }
   launch_kick(S, c->P, false, c->prm.precise_div != 0, st);
   launch_fin(S, c->P, FIN_INIT, 0.0, 0.0, nullptr, st);
   if (c->tpmode) {

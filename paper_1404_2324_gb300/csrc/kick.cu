@@ -56,6 +56,8 @@ __global__ void k_rcrit(Sim S, DevParams P, double tau_abs, int check_reuse) {
 template <bool FULL, bool PRECISE>
 __global__ void __launch_bounds__(128) k_kick(Sim S, DevParams P, int force) {
   if (FULL && !force && S.flags[0] == 0) return;
+  // a full opening kick after a new state also records the precheck candidates (flag 3)
+  const bool record = FULL && !force && S.flags[3] != 0;
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int np = S.npad, nt = S.nt, W = S.W;
@@ -118,8 +120,9 @@ __global__ void __launch_bounds__(128) k_kick(Sim S, DevParams P, int force) {
           changeover_w(r, pmin(Ai, Aj), P.kmode, wB, wA);
           gj *= wB; gi *= wB;
         }
-      } else if (act && rb < umax64(Ti, Tj)) {  // precheck candidate: handled by the near pass
-        gj = 0.0; gi = 0.0;
+      }
+      if ((!FULL || record) && act && rb < umax64(Ti, Tj)) {  // precheck candidate
+        if (!FULL) { gj = 0.0; gi = 0.0; }  // handled by the near pass
         const int j = J * 32 + jl;
         atomicOr(&S.cbm[(size_t)i * W + (j >> 5)], 1u << (j & 31));
         atomicOr(&S.cbm[(size_t)j * W + (i >> 5)], 1u << (i & 31));

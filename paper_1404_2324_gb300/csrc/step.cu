@@ -15,7 +15,7 @@ __global__ void __launch_bounds__(32) k_drift(Sim S, DevParams P, double tau, do
   const int i = blockIdx.x * 32 + lane;
   const int np = S.npad, nt = S.nt;
   if (i == 0) {
-    if (substep == 0) S.flags[0] = 0;  // the opening kick of this step has consumed the flag
+    if (substep == 0) { S.flags[0] = 0; S.flags[3] = 0; }  // the opening kick of this step has consumed the flags
     S.flags[2] = substep;              // for the collision reports of this substep's BS
   }
   double shift[3];
