@@ -155,64 +155,100 @@ __global__ void k_ad_rcrit(Sim S, AdjDev D, DevParams P, double tau_abs, const d
 }
 
 // ---------------------------------------------------------------------------------------------
-// Kick (Eq. Hb weighted by K): a block holds 32 bodies i of one system (one per lane) and its four
-// warps split the partners j; the partial sums are added in a fixed order (deterministic).
-// MODE 0: opening kick; 1: closing kick + prechecker; 2: prechecker only.
+// Kick (Eq. Hb weighted by K), every unordered pair once (Newton's third law): one warp per pair of
+// 32-body tiles (I <= J) of one system; lane l holds body I*32 + l, the bodies of tile J and their
+// accumulators rotate through the lanes by warp shuffles. Partial sums per (tile, partner tile)
+// are added by k_ad_kick_fin in a fixed order (deterministic).
+// MODE 0: opening kick; 1: closing kick + prechecker; 2: prechecker only (no sums).
 // ---------------------------------------------------------------------------------------------
 template <int MODE>
-__global__ void __launch_bounds__(128) k_ad_kick(Sim S, AdjDev D, DevParams P, double h, double *rec_x) {
-  extern __shared__ double sm[];
-  const int b = blockIdx.y, Np = D.Np, NB = D.NB;
-  double *sx = sm, *sy = sx + Np, *sz = sy + Np, *sgm = sz + Np, *sA = sgm + Np;
-  u64 *sT = (u64 *)(sA + Np), *sQ = sT + Np;
-  int *sal = (int *)(sQ + Np);
-  __shared__ double part[4][3][32];
-  const int base = b * Np;
-  for (int j = threadIdx.x; j < Np; j += blockDim.x) {
-    const int g = base + j;
-    sx[j] = S.x[g]; sy[j] = S.x[NB + g]; sz[j] = S.x[2 * NB + g];
-    sgm[j] = S.gm[g]; sA[j] = S.A[g]; sT[j] = S.T[g]; sQ[j] = S.rcsq[g]; sal[j] = S.alive[g];
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int i = blockIdx.x * 32 + lane;
-  const double xi = sx[i], yi = sy[i], zi = sz[i], Ai = sA[i];
-  const u64 Ti = sT[i], Qi = sQ[i];
-  const bool ai = sal[i];
-  double ax = 0.0, ay = 0.0, az = 0.0;
-  const int q = Np >> 2, j0 = w * q, j1 = j0 + q;
-  if (ai) {
-    for (int j = j0; j < j1; ++j) {
-      if (j == i || !sal[j]) continue;
-      const double dx = sx[j] - xi, dy = sy[j] - yi, dz = sz[j] - zi;
-      const double r2 = r2_exact(dx, dy, dz);
-      const u64 rb = dbits(r2);
-      if (MODE >= 1 && j > i && rb < umax64(Ti, sT[j])) {
-        const int k = atomicAdd(&D.ccount[b], 1);
-        if (k < D.ccap) D.cand[(size_t)b * D.ccap + k] = (i << 16) | j;
-        else atomicOr(S.status, ST_RECORD_OVERFLOW);
-      }
-      if (MODE == 2) continue;
-      const double yr = rsqrt_refined(r2);
-      double gg = sgm[j] * (yr * yr * yr);
-      if (rb < umax64(Qi, sQ[j])) {
-        double wB, wA;
-        changeover_w(r2 * yr, pmin(Ai, sA[j]), 0, wB, wA);
-        gg *= wB;
-      }
-      ax = fma(gg, dx, ax); ay = fma(gg, dy, ay); az = fma(gg, dz, az);
+__global__ void __launch_bounds__(128) k_ad_kick_sym(Sim S, AdjDev D, double *part) {
+  const int T = D.Np >> 5, npair = T * (T + 1) / 2, NB = D.NB;
+  const int lane = threadIdx.x & 31;
+  const int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (item >= D.B * npair) return;  // uniform within the warp
+  const int b = item / npair;
+  int k = item % npair, I = 0;
+  while (k >= T - I) { k -= T - I; ++I; }
+  const int J = I + k;
+  const int base = b * D.Np;
+  const int gi = base + I * 32 + lane;
+  const double xi = S.x[gi], yi = S.x[NB + gi], zi = S.x[2 * NB + gi], gmi = S.gm[gi], Ai = S.A[gi];
+  const u64 Ti = S.T[gi], Qi = S.rcsq[gi];
+  const bool ali = S.alive[gi] != 0;
+  const int gj0 = base + J * 32 + lane;
+  double xj = S.x[gj0], yj = S.x[NB + gj0], zj = S.x[2 * NB + gj0], gmj = S.gm[gj0], Aj = S.A[gj0];
+  u64 Tj = S.T[gj0], Qj = S.rcsq[gj0];
+  int alj = S.alive[gj0];
+  double aix = 0.0, aiy = 0.0, aiz = 0.0, ajx = 0.0, ajy = 0.0, ajz = 0.0;
+  const int src = (lane + 1) & 31;
+  const bool diag = I == J;
+  auto rotate = [&]() {
+    xj = __shfl_sync(0xffffffffu, xj, src); yj = __shfl_sync(0xffffffffu, yj, src);
+    zj = __shfl_sync(0xffffffffu, zj, src); gmj = __shfl_sync(0xffffffffu, gmj, src);
+    Aj = __shfl_sync(0xffffffffu, Aj, src); Tj = __shfl_sync(0xffffffffu, Tj, src);
+    Qj = __shfl_sync(0xffffffffu, Qj, src); alj = __shfl_sync(0xffffffffu, alj, src);
+    ajx = __shfl_sync(0xffffffffu, ajx, src); ajy = __shfl_sync(0xffffffffu, ajy, src);
+    ajz = __shfl_sync(0xffffffffu, ajz, src);
+  };
+  const int nsteps = diag ? 16 : 32;
+  for (int st = 0; st < nsteps; ++st) {
+    if (diag) rotate();  // diagonal tile: lane l meets l + st + 1
+    const int jl = diag ? ((lane + st + 1) & 31) : ((lane + st) & 31);
+    const bool act = (!diag || st < 15 || lane < 16) && ali && alj;
+    const double dx = xj - xi, dy = yj - yi, dz = zj - zi;
+    const double r2 = r2_exact(dx, dy, dz);
+    const u64 rb = dbits(r2);
+    if (MODE >= 1 && act && rb < umax64(Ti, Tj)) {
+      const int i = I * 32 + lane, j = J * 32 + jl;
+      const int lo = i < j ? i : j, hi = i < j ? j : i;
+      const int kk = atomicAdd(&D.ccount[b], 1);
+      if (kk < D.ccap) D.cand[(size_t)b * D.ccap + kk] = (lo << 16) | hi;
+      else atomicOr(S.status, ST_RECORD_OVERFLOW);
     }
+    if (MODE != 2) {
+      const double yr = rsqrt_refined(r2);
+      double w3 = act ? yr * yr * yr : 0.0;
+      if (act && rb < umax64(Qi, Qj)) {
+        double wB, wA;
+        changeover_w(r2 * yr, pmin(Ai, Aj), 0, wB, wA);
+        w3 *= wB;
+      }
+      const double fi = gmj * w3, fj = gmi * w3;
+      aix = fma(fi, dx, aix); aiy = fma(fi, dy, aiy); aiz = fma(fi, dz, aiz);
+      ajx = fma(-fj, dx, ajx); ajy = fma(-fj, dy, ajy); ajz = fma(-fj, dz, ajz);
+    }
+    if (!diag) rotate();  // after 32 rotations every j value and sum is back on its owning lane
   }
   if (MODE == 2) return;
-  part[w][0][lane] = ax; part[w][1][lane] = ay; part[w][2][lane] = az;
-  __syncthreads();
-  if (w == 0 && ai) {
-    const int g = base + i;
-    for (int c = 0; c < 3; ++c) {
-      const double a = ((part[0][c][lane] + part[1][c][lane]) + part[2][c][lane]) + part[3][c][lane];
-      S.v[c * NB + g] = fma(h, a, S.v[c * NB + g]);
-      if (rec_x) rec_x[c * NB + g] = S.x[c * NB + g];
-    }
+  double *pb = part + (size_t)b * T * T * 96;
+  if (diag) {  // the j sums return to the lane that owns body I*32 + lane
+    const int home = (lane + 16) & 31;
+    ajx = __shfl_sync(0xffffffffu, ajx, home);
+    ajy = __shfl_sync(0xffffffffu, ajy, home);
+    ajz = __shfl_sync(0xffffffffu, ajz, home);
+    double *p = pb + ((size_t)I * T + I) * 96 + lane;
+    p[0] = aix + ajx; p[32] = aiy + ajy; p[64] = aiz + ajz;
+  } else {
+    double *p = pb + ((size_t)I * T + J) * 96 + lane;
+    p[0] = aix; p[32] = aiy; p[64] = aiz;
+    double *q = pb + ((size_t)J * T + I) * 96 + lane;
+    q[0] = ajx; q[32] = ajy; q[64] = ajz;
+  }
+}
+
+// v += h a with a the sum of body g's tile partials over the partner tiles in ascending order;
+// records the positions the kick saw when asked.
+__global__ void k_ad_kick_fin(Sim S, AdjDev D, double h, const double *part, double *rec_x) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= D.NB || !S.alive[g]) return;
+  const int NB = D.NB, T = D.Np >> 5, b = g / D.Np, i = g % D.Np, I = i >> 5, lane = i & 31;
+  const double *p = part + ((size_t)b * T * T + (size_t)I * T) * 96 + lane;
+  for (int c = 0; c < 3; ++c) {
+    double a = 0.0;
+    for (int J = 0; J < T; ++J) a += p[(size_t)J * 96 + 32 * c];
+    S.v[c * NB + g] = fma(h, a, S.v[c * NB + g]);
+    if (rec_x) rec_x[c * NB + g] = S.x[c * NB + g];
   }
 }
 
@@ -1170,8 +1206,7 @@ struct genga_adj {
   double *y_pool = nullptr, *y_scratch = nullptr;
   long long *y_count = nullptr, *yoff_rec = nullptr;
   int bs_blocks = 0, bs_fwd_grid = 0;
-  size_t kick_smem = 0;
-  double *kv_part = nullptr;  // kick-VJP tile partials [B][T][T][5][32]
+  double *kv_part = nullptr;  // kick tile partials: VJP [B][T][T][5][32], forward [B][T][T][3][32]
 };
 
 namespace {
@@ -1200,10 +1235,12 @@ SubRec subrec(genga_adj *c, int slot) {
 int *seq_len_of(genga_adj *c, int slot) { return c->grec + (size_t)c->K * c->nsub * (4 * c->NB + 2) + (size_t)slot * c->NB; }
 
 void launch_kick(genga_adj *c, int mode, double h, double *rec_x) {
-  dim3 grid(c->Np / 32, c->B);
-  if (mode == 0) k_ad_kick<0><<<grid, 128, c->kick_smem, c->stream>>>(c->S, c->D, c->P, h, rec_x);
-  else if (mode == 1) k_ad_kick<1><<<grid, 128, c->kick_smem, c->stream>>>(c->S, c->D, c->P, h, rec_x);
-  else k_ad_kick<2><<<grid, 128, c->kick_smem, c->stream>>>(c->S, c->D, c->P, h, rec_x);
+  const int T = c->Np / 32, items = c->B * T * (T + 1) / 2;
+  const int grid = (items * 32 + 127) / 128;
+  if (mode == 2) { k_ad_kick_sym<2><<<grid, 128, 0, c->stream>>>(c->S, c->D, c->kv_part); return; }
+  if (mode == 0) k_ad_kick_sym<0><<<grid, 128, 0, c->stream>>>(c->S, c->D, c->kv_part);
+  else k_ad_kick_sym<1><<<grid, 128, 0, c->stream>>>(c->S, c->D, c->kv_part);
+  k_ad_kick_fin<<<(c->NB + 127) / 128, 128, 0, c->stream>>>(c->S, c->D, h, c->kv_part, rec_x);
 }
 
 void launch_kick_vjp(genga_adj *c, double h, const double *xk) {
@@ -1358,10 +1395,6 @@ int genga_adj_init(genga_adj **out, int n_sys, int n, const double *m0, double G
   for (size_t g = 0; g < NB; ++g) sys[g] = (int)(g / c->Np);
   cudaMemcpy(S.sys_of, sys.data(), NB * sizeof(int), cudaMemcpyHostToDevice);
   cudaMemcpy(S.sys_m0, m0, c->B * sizeof(double), cudaMemcpyHostToDevice);
-  c->kick_smem = (size_t)c->Np * (5 * sizeof(double) + 2 * sizeof(u64) + sizeof(int));
-  cudaFuncSetAttribute(k_ad_kick<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->kick_smem);
-  cudaFuncSetAttribute(k_ad_kick<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->kick_smem);
-  cudaFuncSetAttribute(k_ad_kick<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->kick_smem);
   cudaFuncSetAttribute(k_ad_bs_vjp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(BSV_WARPS * sizeof(LevShared)));
   cudaFuncSetAttribute(k_ad_bs_vjp4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(BSV4_GROUPS * sizeof(GrpVjp4)));
   bs_init_constants();
