@@ -95,14 +95,13 @@ __global__ void __launch_bounds__(128) k_tp_kick(Sim S, TPSet T, DevParams P, do
       if (!ps.alive[j] || !((scan >> j) & 1u)) continue;
       const double dx = ps.x[j] - xi, dy = ps.y[j] - yi, dz = ps.z[j] - zi;
       const double r2 = __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx)));
-      const double yr = rsqrt_refined(r2);
       const u64 rb = dbits(r2);
-      double g = ps.gm[j] * (yr * yr * yr);
+      double g = ps.gm[j] * rcube_refined(r2);
       const bool cand = (MODE != FIN_OPEN) && rb < umax64(Ti, ps.T[j]);
       if (MODE == FIN_OPEN || cand) {
-        if (rb < umax64(Qi, ps.Q[j])) {
+        if (rb < umax64(Qi, ps.Q[j])) {  // inside the changeover zone (rare): the weight needs r
           double wB, wA;
-          changeover_w(r2 * yr, pmin(Ai, ps.A[j]), P.kmode, wB, wA);
+          changeover_w(r2 * rsqrt_refined(r2), pmin(Ai, ps.A[j]), P.kmode, wB, wA);
           g *= wB;
         }
         if (cand) cm |= 1u << j;
