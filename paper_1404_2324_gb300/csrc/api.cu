@@ -314,8 +314,7 @@ void enqueue_step(genga_ctx *c, cudaStream_t st) {
     // the paper's literal higher-order variant: the step-start candidates serve every substep, and
     // the closing kicks between substeps weigh every pair without prechecking
     const bool inner = c->prm.precheck_substeps == 0 && j + 1 < c->nsub;
-    launch_encounter(S, tau, S.ebm + (size_t)j * S.npad * S.W, st, inner);
-    launch_group(S, st, c->side ? c->gsplit : BS_GMAX + 1);
+    launch_encounter_group(S, tau, S.ebm + (size_t)j * S.npad * S.W, st, inner, c->side ? c->gsplit : BS_GMAX + 1);
     if (c->side) {  // fork: cluster kernel for the groups of gsplit .. BS_GMAX members, one-CTA
                     // kernel for the smaller ones and the grid-wide kernel for groups above BS_GMAX
                     // members (its CTAs leave at once when the large-group list holds none); join

@@ -25,6 +25,8 @@ void launch_drift(const Sim &S, const DevParams &P, double tau, double hcm1, dou
 // keep: leave the candidate set in place for the next substep (literal higher-order prechecker)
 void launch_encounter(const Sim &S, double tau, unsigned *ebm, cudaStream_t st, bool keep = false);
 void launch_group(const Sim &S, cudaStream_t st, int gbig = BS_GMAX + 1);  // gbig: size threshold of S.big
+// the two in one launch (the last CTA of the encounter test groups the edges of all)
+void launch_encounter_group(const Sim &S, double tau, unsigned *ebm, cudaStream_t st, bool keep, int gbig);
 void launch_kepler_phase(int n, double mu, double dt, int maxit, const int *alive, double *x, double *v,
                          int *fail, cudaStream_t st);
 void launch_pairs_to_bitmap(const Sim &S, const int *pairs, int npairs, cudaStream_t st);

@@ -83,14 +83,15 @@ __device__ __forceinline__ bool encounter_test(const Sim &S, double tau, int i, 
   return dmin < thr;
 }
 
-__global__ void __launch_bounds__(ENC_THREADS) k_encounter(Sim S, double tau, unsigned *ebm, int keep) {
-  __shared__ int s_i[ENC_CAP], s_j[ENC_CAP];
-  __shared__ int s_n, s_found;
+// The encounter test of the NBOD bodies of this CTA (NT threads; the gathered pairs in s_i, s_j of CAP).
+template <int NT, int NBOD, int CAP>
+__device__ void encounter_body(const Sim &S, double tau, unsigned *ebm, int keep, int *s_i, int *s_j, int &s_n,
+                               int &s_found) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int np = S.npad, W = S.W;
-  const int i0 = blockIdx.x * ENC_BODIES;
+  const int i0 = blockIdx.x * NBOD;
   if (tid == 0) { s_n = 0; s_found = 0; }
-  for (int k = tid; k < ENC_BODIES * W; k += ENC_THREADS) {  // this substep's rows start empty
+  for (int k = tid; k < NBOD * W; k += NT) {  // this substep's rows start empty
     const int i = i0 + k / W;
     if (i < np) ebm[(size_t)i * W + k % W] = 0u;
   }
@@ -105,13 +106,12 @@ __global__ void __launch_bounds__(ENC_THREADS) k_encounter(Sim S, double tau, un
   };
   auto add = [&](int i, int j) {  // gather, or test at once if the shared list is full
     const int p = atomicAdd(&s_n, 1);
-    if (p < ENC_CAP) { s_i[p] = i; s_j[p] = j; }
+    if (p < CAP) { s_i[p] = i; s_j[p] = j; }
     else if (encounter_test(S, tau, i, j)) hit(i, j);
   };
-  const unsigned rows = i0 < np ? S.rowany[i0 >> 5] : 0u;
-  for (int b = wid; b < ENC_BODIES; b += ENC_THREADS / 32) {
+  for (int b = wid; b < NBOD; b += NT / 32) {
     const int i = i0 + b;
-    if (i >= np || !((rows >> b) & 1u)) continue;  // uniform within the warp
+    if (i >= np || !((S.rowany[i >> 5] >> (i & 31)) & 1u)) continue;  // uniform within the warp
     unsigned *crow = S.cbm + (size_t)i * W;
     const int cnt = S.ccnt[i];
     if (cnt <= CCAP) {  // partners from the list
@@ -137,13 +137,19 @@ __global__ void __launch_bounds__(ENC_THREADS) k_encounter(Sim S, double tau, un
     if (lane == 0 && !keep) S.ccnt[i] = 0;
   }
   __syncthreads();
-  if (tid == 0 && i0 < np && !keep) S.rowany[i0 >> 5] = 0u;  // the CTA's 32 rows are clear
-  const int n = s_n < ENC_CAP ? s_n : ENC_CAP;
-  for (int p = tid; p < n; p += ENC_THREADS)
+  if (tid < NBOD / 32 && i0 + 32 * tid < np && !keep) S.rowany[(i0 >> 5) + tid] = 0u;  // the CTA's rows are clear
+  const int n = s_n < CAP ? s_n : CAP;
+  for (int p = tid; p < n; p += NT)
     if (encounter_test(S, tau, s_i[p], s_j[p])) hit(s_i[p], s_j[p]);
   if (found) atomicAdd(&s_found, found);
   __syncthreads();
   if (tid == 0 && s_found) atomicAdd((unsigned long long *)&S.counters[C_ENC], (unsigned long long)s_found);
+}
+
+__global__ void __launch_bounds__(ENC_THREADS) k_encounter(Sim S, double tau, unsigned *ebm, int keep) {
+  __shared__ int s_i[ENC_CAP], s_j[ENC_CAP];
+  __shared__ int s_n, s_found;
+  encounter_body<ENC_THREADS, ENC_BODIES, ENC_CAP>(S, tau, ebm, keep, s_i, s_j, s_n, s_found);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -232,26 +238,32 @@ __device__ __forceinline__ int find_root(const int *link, int r) {
   return r;
 }
 
-__global__ void __launch_bounds__(GROUP_THREADS) k_group(Sim S, int gbig) {
-  __shared__ int link[NMAX];
-  __shared__ int key[NMAX];
-  __shared__ int gcnt[NMAX];
-  __shared__ unsigned char part[NMAX];
-  __shared__ int wtot[GROUP_THREADS / 32];
-  __shared__ int s_changed, s_base, s_ng;
+struct GroupShared {
+  int link[NMAX], key[NMAX], gcnt[NMAX];
+  unsigned char part[NMAX];
+  int wtot[GROUP_THREADS / 32];
+  int s_changed, s_base, s_ng;
+};
+
+// The grouping by one CTA of GROUP_THREADS threads. The edge list is read past L1 (the fused
+// encounter kernel's other CTAs wrote it in the same launch).
+__device__ void group_body(const Sim &S, int gbig, GroupShared &sm) {
+  int *link = sm.link, *key = sm.key, *gcnt = sm.gcnt, *wtot = sm.wtot;
+  unsigned char *part = sm.part;
+  int &s_changed = sm.s_changed, &s_base = sm.s_base, &s_ng = sm.s_ng;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int np = S.npad;
-  const int ne = *S.nedges, nf = *S.nfail;
+  const int ne = __ldcg(S.nedges), nf = __ldcg(S.nfail);
   for (int i = tid; i < np; i += GROUP_THREADS) { link[i] = i; part[i] = 0; }
   __syncthreads();
-  for (int e = tid; e < ne; e += GROUP_THREADS) { part[S.edges[2 * e]] = 1; part[S.edges[2 * e + 1]] = 1; }
-  for (int f = tid; f < nf; f += GROUP_THREADS) part[S.fail[f]] = 1;
+  for (int e = tid; e < ne; e += GROUP_THREADS) { part[__ldcg(S.edges + 2 * e)] = 1; part[__ldcg(S.edges + 2 * e + 1)] = 1; }
+  for (int f = tid; f < nf; f += GROUP_THREADS) part[__ldcg(S.fail + f)] = 1;
   int round = 0;
   for (; round < GROUP_MAX_ROUNDS; ++round) {
     if (tid == 0) s_changed = 0;
     __syncthreads();
     for (int e = tid; e < ne; e += GROUP_THREADS) {
-      const int ru = find_root(link, S.edges[2 * e]), rv = find_root(link, S.edges[2 * e + 1]);
+      const int ru = find_root(link, __ldcg(S.edges + 2 * e)), rv = find_root(link, __ldcg(S.edges + 2 * e + 1));
       if (ru != rv) {
         atomicMin(&link[ru > rv ? ru : rv], ru < rv ? ru : rv);
         s_changed = 1;
@@ -305,6 +317,32 @@ __global__ void __launch_bounds__(GROUP_THREADS) k_group(Sim S, int gbig) {
                                  [&](int g, int pos) { S.big[pos] = g; }, wtot, &s_base);
     if (tid == 0) *S.nbig = nb;
   }
+}
+
+__global__ void __launch_bounds__(GROUP_THREADS) k_group(Sim S, int gbig) {
+  __shared__ GroupShared sm;
+  group_body(S, gbig, sm);
+}
+
+// The encounter test and the grouping in one launch: CTAs of GROUP_THREADS threads test the pairs
+// of EG_BODIES bodies each; the last CTA to finish (a device-wide counter, fenced) groups the edges
+// of all of them. Saves the launch between the two and the grouping kernel's ramp-up.
+constexpr int EG_BODIES = 32;
+constexpr int EG_CAP = 1024;
+__global__ void __launch_bounds__(GROUP_THREADS) k_encounter_group(Sim S, double tau, unsigned *ebm, int keep, int gbig) {
+  __shared__ int s_i[EG_CAP], s_j[EG_CAP];
+  __shared__ int s_n, s_found, s_last;
+  __shared__ GroupShared sm;
+  encounter_body<GROUP_THREADS, EG_BODIES, EG_CAP>(S, tau, ebm, keep, s_i, s_j, s_n, s_found);
+  if (threadIdx.x == 0) {
+    __threadfence();  // this CTA's edges before its count
+    s_last = atomicAdd(&S.flags[1], 1) == (int)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;  // uniform
+  __threadfence();
+  if (threadIdx.x == 0) S.flags[1] = 0;  // the counter of the next launch
+  group_body(S, gbig, sm);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -405,6 +443,9 @@ void launch_encounter(const Sim &S, double tau, unsigned *ebm, cudaStream_t st, 
   k_encounter<<<(S.npad + ENC_BODIES - 1) / ENC_BODIES, ENC_THREADS, 0, st>>>(S, tau, ebm, keep ? 1 : 0);
 }
 void launch_group(const Sim &S, cudaStream_t st, int gbig) { k_group<<<1, GROUP_THREADS, 0, st>>>(S, gbig); }
+void launch_encounter_group(const Sim &S, double tau, unsigned *ebm, cudaStream_t st, bool keep, int gbig) {
+  k_encounter_group<<<(S.npad + EG_BODIES - 1) / EG_BODIES, GROUP_THREADS, 0, st>>>(S, tau, ebm, keep ? 1 : 0, gbig);
+}
 void launch_kepler_phase(int n, double mu, double dt, int maxit, const int *alive, double *x, double *v,
                          int *fail, cudaStream_t st) {
   k_kepler_phase<<<(n + 31) / 32, 32, 0, st>>>(n, mu, dt, maxit, alive, x, v, fail);

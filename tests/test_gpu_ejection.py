@@ -184,6 +184,6 @@ def test_off_by_default_changes_nothing():
     try:
         g.step(300)
         assert g.state()["alive"].all() and len(genga.genga_ejections(g.ctx)) == 0
-        assert genga.genga_launch_count(g.ctx) == 4 + 8  # no ejection kernel in the step graph
+        assert genga.genga_launch_count(g.ctx) == 4 + 7  # no ejection kernel in the step graph
     finally:
         g.close()

@@ -214,7 +214,7 @@ def test_profiling_events_and_launch_count():
     for order, nsub in ((2, 1), (4, 3)):
         s = genga.Genga(m, R, x, v, d["G"], d["dt"], order)
         genga.genga_set_profiling(s.ctx, True)
-        assert genga.genga_launch_count(s.ctx) == 4 + 8 * nsub  # incl. the cluster and wide BS kernels per substep
+        assert genga.genga_launch_count(s.ctx) == 4 + 7 * nsub  # incl. the cluster and grid-wide BS kernels per substep
         s.step(2)
         ms, n = genga.genga_kick_time(s.ctx)
         assert n == nsub and 0.0 < ms < 50.0
