@@ -235,8 +235,9 @@ int first_kick(genga_ctx *c) {
   launch_fin(S, c->P, FIN_INIT, 0.0, 0.0, nullptr, st);
   if (c->tpmode) {
     CK(cudaMemsetAsync(c->T.npairs, 0, sizeof(unsigned), st));
+    CK(cudaMemsetAsync(c->T.bsnext, 0, (4 + 4 * TP_BS_MAXBLOCKS) * sizeof(unsigned), st));
     launch_tp_rcrit(c->T, c->P, std::fabs(c->dt), 0, st);
-    launch_tp_kick(S, c->T, c->P, FIN_INIT, 0.0, 0.0, st);
+    launch_tp_kick(S, c->T, c->P, st);
   }
   CK(cudaGetLastError());
   return GENGA_OK;
@@ -331,17 +332,22 @@ void enqueue_step(genga_ctx *c, cudaStream_t st) {
     } else {
       launch_bs(S, P, tau, c->bs_grid, st);
     }
-    if (tp) {
-      launch_tp_encounter(S, T, tau, c->tp_grid, st);
-      launch_tp_bs(S, T, P, tau, num_sms(), st);
+    if (tp) {  // the particles' encounter test beside the massive closing kick
+      cudaEventRecord(c->ev_fork, st);
+      cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+      launch_tp_encounter(S, T, tau, c->tp_grid, c->side);
+      cudaEventRecord(c->ev_join, c->side);
     }
     if (c->profiling) cudaEventRecordWithFlags(c->kev[2 * j], st, cudaEventRecordExternal);
     launch_kick(S, P, inner, precise, st, inner);
     if (c->profiling) cudaEventRecordWithFlags(c->kev[2 * j + 1], st, cudaEventRecordExternal);
     const double h2 = (j + 1 < c->nsub) ? 0.5 * c->w[j + 1] * dt : 0.0;
     launch_fin(S, P, inner ? FIN_CLOSE_ALL : FIN_CLOSE, 0.5 * tau, h2, nullptr, st);
-    // the particles' closing kick; after the last substep it applies their last Sun drift too
-    if (tp) launch_tp_kick(S, T, P, FIN_CLOSE, 0.5 * tau, h2, st, j + 1 == c->nsub ? 0.5 * tau * inv_m0 : 0.0);
+    if (tp) {  // join; the particles' BS and every particle's closing kick (after the last substep
+               // with their last Sun drift, from the massive momentum before the closing kick)
+      cudaStreamWaitEvent(st, c->ev_join, 0);
+      launch_tp_bs(S, T, P, tau, 0.5 * tau, h2, j + 1 == c->nsub ? 0.5 * tau * inv_m0 : 0.0, num_sms(), st);
+    }
   }
   launch_hc(S, 0.5 * c->w[c->nsub - 1] * dt * inv_m0, st);
   if (P.rcut2 > 0.0 || P.rcut_sun2 > 0.0) {  // ejections at the end of the step (Sect. 3.2)
@@ -520,7 +526,7 @@ int genga_init_tp(genga_ctx **out, int n, const double *masses, const double *ra
   T.T = mem.get<u64>(np); T.rcsq = mem.get<u64>(np);
   T.alive = mem.get<int>(np); T.full = mem.get<int>(np); T.fail = mem.get<int>(np);
   T.cmask = mem.get<unsigned>(np); T.emask = mem.get<unsigned>(np);
-  T.bslist = mem.get<int>(np); T.nbs = mem.get<int>(2); T.bsnext = mem.get<unsigned>(1);
+  T.bslist = mem.get<int>(np); T.nbs = mem.get<int>(2); T.bsnext = mem.get<unsigned>(4 + 4 * TP_BS_MAXBLOCKS);
   T.pairs = mem.get<unsigned>(np * (size_t)(n - 1)); T.npairs = mem.get<unsigned>(1);
   T.ptab = mem.get<double>(TP_MAXPL * TP_TAB * 6);
   T.ppoly = mem.get<double>(TP_MAXPL * 6 * TP_CHEB); T.pcok = mem.get<int>(TP_MAXPL);

@@ -137,7 +137,9 @@ struct TPSet {
   unsigned *cmask, *emask;       // candidate / encountered planets per TP
   int *bslist, *nbs;             // TPs that need Bulirsch-Stoer this substep: nbs[0] from the front of
                                  // bslist (deep encounters), nbs[1] from its back (the rest)
-  unsigned *bsnext;              // next list entry a BS warp takes
+  unsigned *bsnext;              // [0] next list entry a BS warp takes, [1] next block of closing kicks,
+                                 // [2] encounter blocks done, [3] BS-pass warps done, [4 + 4 b + q]
+                                 // warps of BS-pass block b on sub-partition q done with their BS entries
   unsigned *pairs, *npairs;      // candidate (TP, planet) pairs of the last closing kick: i * 32 + j
   double *ptab;                  // planets' Kepler paths at the BS midpoint times [TP_MAXPL * TP_TAB * 6]
   double *ppoly;                 // planets' paths over the substep, polynomials in s = 2t/tau - 1 [TP_MAXPL * 6 * TP_CHEB]
@@ -145,6 +147,7 @@ struct TPSet {
   long long *counters;           // candidates, encounters, BS steps, removed, ejected
 };
 constexpr int TP_MAXPL = 32;     // planets in test-particle mode
+constexpr int TP_BS_MAXBLOCKS = 1024;  // blocks of the TP BS pass (one per SM)
 constexpr int TP_TAB = 80;       // sum over BS levels k = 1..8 of the 2k + 1 midpoint times
 constexpr int TP_CHEB = 16;      // Chebyshev nodes per planet path
 

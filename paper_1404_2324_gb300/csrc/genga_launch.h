@@ -88,16 +88,18 @@ void launch_b_energy(const Sim &S, const DevParams &P, const int *sys_user, doub
 // tp.cu
 int tp_init_constants();  // Neville factors of the TP Bulirsch-Stoer (call outside stream capture)
 void launch_tp_rcrit(const TPSet &T, const DevParams &P, double tau_abs, int check, cudaStream_t st);
-// hcm_last != 0 (the closing kick of a step's last substep): the step's last Sun drift too, x += hcm_last P
-void launch_tp_kick(const Sim &S, const TPSet &T, const DevParams &P, FinMode mode, double h1, double h2, cudaStream_t st,
-                    double hcm_last = 0.0);
+// the first kick after a new state: far field and candidates of every TP, no velocity change
+void launch_tp_kick(const Sim &S, const TPSet &T, const DevParams &P, cudaStream_t st);
 // the step's start for the TPs in one pass: rcrit (reuse test), opening kick, first Sun drift, Kepler drift
 void launch_tp_open_drift(const Sim &S, const TPSet &T, const DevParams &P, double tau_abs, double h1, double tau,
                           double hcm1, cudaStream_t st);
 void launch_tp_drift(const Sim &S, const TPSet &T, const DevParams &P, double tau, double hcm1, double hcm2, cudaStream_t st);
 void launch_planet_table(const Sim &S, const TPSet &T, const DevParams &P, double tau, cudaStream_t st);
 void launch_tp_encounter(const Sim &S, const TPSet &T, double tau, int blocks, cudaStream_t st);
-void launch_tp_bs(const Sim &S, const TPSet &T, const DevParams &P, double tau, int blocks, cudaStream_t st);
+// the BS pass of a substep and the closing kick of every TP (v += (h1 + h2) a; hcm_last != 0: the
+// step's last Sun drift)
+void launch_tp_bs(const Sim &S, const TPSet &T, const DevParams &P, double tau, double h1, double h2, double hcm_last,
+                  int blocks, cudaStream_t st);
 void launch_tp_from_helio(const TPSet &T, int nmass, const double *mh, const double *vmh, const double *xh,
                           const double *vh, const double *Rh, int keep, cudaStream_t st);
 void launch_tp_to_helio(const Sim &S, const TPSet &T, const DevParams &P, double *xh, double *vh, int *alive,

@@ -58,18 +58,119 @@ __device__ void load_planets(const Sim &S, PlanetSm &ps) {
   __syncthreads();
 }
 
-// TP kick. CLOSE / INIT: all planets with the changeover weight, far field stored, candidates
-// recorded (per TP as a mask, and as (TP, planet) pairs appended to the pair list for the next
-// encounter test). OPEN: stored far field + candidates with the new radii, or every planet when the
-// TP or any planet failed the reuse test (the step itself runs it inside k_tp_open_drift). Every
-// launch also empties the BS list of the coming substep (its last reader, the previous substep's
-// BS, has finished).
-template <int MODE>
-__global__ void __launch_bounds__(128) k_tp_kick(Sim S, TPSet T, DevParams P, double h1, double h2, double hcm_last) {
-  __shared__ PlanetSm ps;
-  __shared__ double shc[3];
-  if (hcm_last != 0.0 && threadIdx.x < 32) {  // the step's last Sun drift, from the momentum before the kick
-    const int lane = threadIdx.x;
+// The closing (or first) kick's forces on K TPs at once (independent FP64 chains for the pipe), TP
+// i[k] at x[k], every planet in order, prechecked: pairs outside the precheck threshold add to the
+// far field, candidates (with the changeover weight inside rc) to the near field. For each active TP
+// stores the far field and the candidate mask for the next step's opening kick; returns the masks
+// in cm, the total accelerations in acc.
+template <int K>
+__device__ __forceinline__ void tp_close_forces_k(const TPSet &T, const DevParams &P, const PlanetSm &ps, int npl,
+                                                  const int (&i)[K], const bool (&act)[K], const double (&x)[K][3],
+                                                  double (&acc)[K][3], unsigned (&cm)[K]) {
+  const int np = T.npad;
+  u64 Ti[K], Qi[K];
+  double Ai[K], f[K][3], n[K][3];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    Ti[k] = act[k] ? T.T[i[k]] : 0ULL;
+    Qi[k] = act[k] ? T.rcsq[i[k]] : 0ULL;
+    Ai[k] = act[k] ? T.A[i[k]] : 0.0;
+    cm[k] = 0u;
+    for (int c = 0; c < 3; ++c) f[k][c] = n[k][c] = 0.0;
+  }
+  for (int j = 0; j < npl; ++j) {
+    if (!ps.alive[j]) continue;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const double dx = ps.x[j] - x[k][0], dy = ps.y[j] - x[k][1], dz = ps.z[j] - x[k][2];
+      const double r2 = __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx)));
+      const u64 rb = dbits(r2);
+      double g = ps.gm[j] * rcube_refined(r2);
+      if (rb < umax64(Ti[k], ps.T[j])) {
+        if (rb < umax64(Qi[k], ps.Q[j])) {  // inside the changeover zone (rare): the weight needs r
+          double wB, wA;
+          changeover_w(r2 * rsqrt_refined(r2), pmin(Ai[k], ps.A[j]), P.kmode, wB, wA);
+          g *= wB;
+        }
+        cm[k] |= 1u << j;
+        n[k][0] = fma(g, dx, n[k][0]); n[k][1] = fma(g, dy, n[k][1]); n[k][2] = fma(g, dz, n[k][2]);
+      } else {
+        f[k][0] = fma(g, dx, f[k][0]); f[k][1] = fma(g, dy, f[k][1]); f[k][2] = fma(g, dz, f[k][2]);
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (!act[k]) { cm[k] = 0u; continue; }
+    T.afar[i[k]] = f[k][0]; T.afar[np + i[k]] = f[k][1]; T.afar[2 * np + i[k]] = f[k][2];
+    T.cmask[i[k]] = cm[k];
+    for (int c = 0; c < 3; ++c) acc[k][c] = f[k][c] + n[k][c];
+  }
+}
+
+// One TP (see tp_close_forces_k); returns its mask, the acceleration in (ax, ay, az).
+__device__ __forceinline__ unsigned tp_close_forces(const TPSet &T, const DevParams &P, const PlanetSm &ps, int npl,
+                                                    int i, double xi, double yi, double zi, double &ax, double &ay,
+                                                    double &az) {
+  const int ii[1] = {i};
+  const bool act[1] = {true};
+  const double x[1][3] = {{xi, yi, zi}};
+  double acc[1][3];
+  unsigned cm[1];
+  tp_close_forces_k<1>(T, P, ps, npl, ii, act, x, acc, cm);
+  ax = acc[0][0]; ay = acc[0][1]; az = acc[0][2];
+  return cm[0];
+}
+
+// v += (h1 + h2) a as two kicks (the closing kick of this substep and the opening kick of the next);
+// after the step's last substep also the last Sun drift, x += shc (the shift moves every body
+// alike, so the kick does not see it).
+__device__ __forceinline__ void tp_close_update(const TPSet &T, int i, double xi, double yi, double zi, double ax,
+                                                double ay, double az, double h1, double h2, const double *shc) {
+  const int np = T.npad;
+  double vx = fma(h1, ax, T.v[i]), vy = fma(h1, ay, T.v[np + i]), vz = fma(h1, az, T.v[2 * np + i]);
+  if (h2 != 0.0) { vx = fma(h2, ax, vx); vy = fma(h2, ay, vy); vz = fma(h2, az, vz); }
+  T.v[i] = vx; T.v[np + i] = vy; T.v[2 * np + i] = vz;
+  if (shc) { T.x[i] = xi + shc[0]; T.x[np + i] = yi + shc[1]; T.x[2 * np + i] = zi + shc[2]; }
+}
+
+// Appends the candidate (TP, planet) pairs of the warp's lanes (lane's TP i, mask cm) to the pair
+// list of the next encounter test with one atomic; counts them when the kick closes a substep.
+__device__ __forceinline__ void tp_append_pairs(const TPSet &T, int i, unsigned cm, bool count) {
+  const int lane = threadIdx.x & 31;
+  const unsigned cnt = __popc(cm);
+  unsigned incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+  unsigned base = 0u;
+  if (lane == 31 && total) {
+    base = atomicAdd(T.npairs, total);
+    if (count) atomicAdd((unsigned long long *)&T.counters[0], (unsigned long long)total);
+  }
+  base = __shfl_sync(0xffffffffu, base, 31);
+  unsigned pos = base + incl - cnt;
+  while (cm) {
+    const int j = __ffs(cm) - 1;
+    cm &= cm - 1;
+    T.pairs[pos++] = ((unsigned)i << 5) | (unsigned)j;
+  }
+}
+
+// The planets (as load_planets) and the step's last Sun drift's shift, hcm_last times the massive
+// momentum before the closing kick (the per-tile partials of the massive kick), by one warp for
+// itself: no block barrier.
+__device__ __forceinline__ void warp_load_planets(const Sim &S, double hcm_last, PlanetSm &ps, double *shc) {
+  const int lane = threadIdx.x & 31, np = S.npad;
+  const bool ok = lane < S.n && S.alive[lane];
+  ps.alive[lane] = ok;
+  ps.x[lane] = ok ? S.x[lane] : 0.0; ps.y[lane] = ok ? S.x[np + lane] : 0.0; ps.z[lane] = ok ? S.x[2 * np + lane] : 0.0;
+  ps.gm[lane] = ok ? S.gm[lane] : 0.0; ps.A[lane] = ok ? S.A[lane] : 0.0;
+  ps.T[lane] = ok ? S.T[lane] : 0ULL; ps.Q[lane] = ok ? S.rcsq[lane] : 0ULL;
+  if (hcm_last != 0.0) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       double a = 0.0;
@@ -78,81 +179,22 @@ __global__ void __launch_bounds__(128) k_tp_kick(Sim S, TPSet T, DevParams P, do
       if (lane == 0) shc[c] = hcm_last * a;
     }
   }
+  __syncwarp();
+}
+
+// The first kick after a new state: forces, far field and candidates of every TP (no velocity
+// change). Also empties the BS list of the coming substep.
+__global__ void __launch_bounds__(128) k_tp_kick(Sim S, TPSet T, DevParams P) {
+  __shared__ PlanetSm ps;
   load_planets(S, ps);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) { T.nbs[0] = 0; T.nbs[1] = 0; }
-  const bool act = i < T.n && T.alive[i];
   unsigned cm = 0u;
-  if (act) {
-    const int np = T.npad, npl = S.n;
-    const double xi = T.x[i], yi = T.x[np + i], zi = T.x[2 * np + i];
-    const u64 Ti = T.T[i], Qi = T.rcsq[i];
-    const double Ai = T.A[i];
-    const bool full = (MODE == FIN_OPEN) && (T.full[i] || S.flags[0]);
-    double fx = 0, fy = 0, fz = 0, nx = 0, ny = 0, nz = 0;
-    const unsigned scan = (MODE == FIN_OPEN && !full) ? T.cmask[i] : 0xffffffffu;
-    for (int j = 0; j < npl; ++j) {
-      if (!ps.alive[j] || !((scan >> j) & 1u)) continue;
-      const double dx = ps.x[j] - xi, dy = ps.y[j] - yi, dz = ps.z[j] - zi;
-      const double r2 = __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx)));
-      const u64 rb = dbits(r2);
-      double g = ps.gm[j] * rcube_refined(r2);
-      const bool cand = (MODE != FIN_OPEN) && rb < umax64(Ti, ps.T[j]);
-      if (MODE == FIN_OPEN || cand) {
-        if (rb < umax64(Qi, ps.Q[j])) {  // inside the changeover zone (rare): the weight needs r
-          double wB, wA;
-          changeover_w(r2 * rsqrt_refined(r2), pmin(Ai, ps.A[j]), P.kmode, wB, wA);
-          g *= wB;
-        }
-        if (cand) cm |= 1u << j;
-        nx = fma(g, dx, nx); ny = fma(g, dy, ny); nz = fma(g, dz, nz);
-      } else {
-        fx = fma(g, dx, fx); fy = fma(g, dy, fy); fz = fma(g, dz, fz);
-      }
-    }
+  if (i < T.n && T.alive[i]) {
     double ax, ay, az;
-    if (MODE == FIN_OPEN) {
-      if (full) { ax = nx; ay = ny; az = nz; }
-      else { ax = T.afar[i] + nx; ay = T.afar[np + i] + ny; az = T.afar[2 * np + i] + nz; }
-    } else {
-      T.afar[i] = fx; T.afar[np + i] = fy; T.afar[2 * np + i] = fz;
-      T.cmask[i] = cm;
-      ax = fx + nx; ay = fy + ny; az = fz + nz;
-    }
-    if (MODE != FIN_INIT) {
-      double vx = fma(h1, ax, T.v[i]), vy = fma(h1, ay, T.v[np + i]), vz = fma(h1, az, T.v[2 * np + i]);
-      if (h2 != 0.0) { vx = fma(h2, ax, vx); vy = fma(h2, ay, vy); vz = fma(h2, az, vz); }
-      T.v[i] = vx; T.v[np + i] = vy; T.v[2 * np + i] = vz;
-      if (hcm_last != 0.0) {  // the shift moves every body alike, so the kick above does not see it
-        T.x[i] = xi + shc[0]; T.x[np + i] = yi + shc[1]; T.x[2 * np + i] = zi + shc[2];
-      }
-    } else {
-      (void)h1; (void)h2;
-    }
+    cm = tp_close_forces(T, P, ps, S.n, i, T.x[i], T.x[T.npad + i], T.x[2 * T.npad + i], ax, ay, az);
   }
-  if (MODE != FIN_OPEN) {  // append this warp's candidate pairs with one atomic
-    const int lane = threadIdx.x & 31;
-    const unsigned cnt = __popc(cm);
-    unsigned incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
-    }
-    const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
-    unsigned base = 0u;
-    if (lane == 31 && total) {
-      base = atomicAdd(T.npairs, total);
-      if (MODE == FIN_CLOSE) atomicAdd((unsigned long long *)&T.counters[0], (unsigned long long)total);
-    }
-    base = __shfl_sync(0xffffffffu, base, 31);
-    unsigned pos = base + incl - cnt;
-    while (cm) {
-      const int j = __ffs(cm) - 1;
-      cm &= cm - 1;
-      T.pairs[pos++] = ((unsigned)i << 5) | (unsigned)j;
-    }
-  }
+  tp_append_pairs(T, i, cm, false);
 }
 
 // Sun drifts with the massive momentum (the same partials the massive drift reads), keep the
@@ -195,11 +237,13 @@ __global__ void k_tp_drift(Sim S, TPSet T, DevParams P, double tau, double hcm1,
   T.v[i] = vx; T.v[np + i] = vy; T.v[2 * np + i] = vz;
 }
 
-// The start of a full step for the TPs in one pass (the three operations of k_tp_rcrit with the
-// reuse test, k_tp_kick<OPEN> and k_tp_drift of the first substep, in that order and arithmetic):
-// the critical radius from the velocity, the opening kick (stored far field + candidates with the
-// new radii, or every planet when the TP or any planet failed the reuse test), the first Sun drift
-// with the momentum after the massive opening kick, the Kepler drift keeping the pre-drift state.
+// The start of a full step for the TPs in one pass (the operations of k_tp_rcrit with the reuse
+// test, the opening kick and k_tp_drift of the first substep, in that order and arithmetic): the
+// critical radius from the velocity, the opening kick (stored far field + candidates with the new
+// radii, or every planet when the TP or any planet failed the reuse test), the first Sun drift with
+// the momentum after the massive opening kick, the Kepler drift keeping the pre-drift state. The BS
+// list is empty on entry (the last warp of the previous substep's BS pass, or the first kick,
+// emptied it), so a failed solve appends to it.
 __global__ void __launch_bounds__(128) k_tp_open_drift(Sim S, TPSet T, DevParams P, double tau_abs, double h1,
                                                        double tau, double hcm1) {
   __shared__ PlanetSm ps;
@@ -216,7 +260,6 @@ __global__ void __launch_bounds__(128) k_tp_open_drift(Sim S, TPSet T, DevParams
   }
   load_planets(S, ps);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0) { T.nbs[0] = 0; T.nbs[1] = 0; }
   if (i >= T.n) return;
   T.fail[i] = 0;
   T.emask[i] = 0u;
@@ -349,9 +392,10 @@ __global__ void __launch_bounds__(128) k_planet_table(Sim S, TPSet T, DevParams 
 // one pair per thread (bit-exact with the oracle). A TP's first encounter lists it for BS, unless
 // its failed Kepler solve listed it already.
 __global__ void __launch_bounds__(256) k_tp_encounter(Sim S, TPSet T, double tau) {
+  __shared__ int s_last;
   const unsigned npairs = *T.npairs;
   const int np = T.npad, pp = S.npad;
-  if (blockIdx.x == 0 && threadIdx.x == 0) *T.bsnext = 0u;  // the BS that follows starts at the head
+  if (blockIdx.x == 0 && threadIdx.x == 0) { T.bsnext[0] = 0u; T.bsnext[1] = 0u; }  // the BS pass starts at the heads
   for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < npairs; q += gridDim.x * blockDim.x) {
     const unsigned pr = T.pairs[q];
     const int i = (int)(pr >> 5), j = (int)(pr & 31u);
@@ -375,6 +419,12 @@ __global__ void __launch_bounds__(256) k_tp_encounter(Sim S, TPSet T, double tau
       }
     }
   }
+  // the last block to finish empties the pair list for the closing kicks of the BS pass (every block
+  // read its length on entry)
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&T.bsnext[2], 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (s_last && threadIdx.x == 0) { *T.npairs = 0u; T.bsnext[2] = 0u; }
 }
 
 // A planet's path polynomial (components c0 .. c0 + 2, powers of s) at s in [-1, 1] (Horner).
@@ -518,26 +568,57 @@ __device__ unsigned char d_prep_first[TP_PREP_MAX + 1];  // class u owns slots [
 __device__ unsigned char d_prep_slot[2 * TP_TAB];        // hf * TP_TAB + tab_index(k, m)
 
 constexpr int TPB_WARPS = 12;
+constexpr int TP_WAIT_MAX = 500;  // naps of about 2 us
 constexpr int TPB_WPOS = TP_PRE * TP_TAB * 3;
 constexpr size_t TPB_SMEM = (size_t)TPB_WARPS * (2 * TPB_WPOS + 2 * 16) * sizeof(double);
-__global__ void __launch_bounds__(32 * TPB_WARPS, 1) k_tp_bs(Sim S, TPSet T, DevParams P, double tau) {
+
+// A warp of the BS pass is done; the last of all empties the BS list for the next substep (every
+// warp read its length on entry).
+__device__ __forceinline__ void tp_bs_warp_done(const TPSet &T) {
+  if ((threadIdx.x & 31) == 0 && atomicAdd(&T.bsnext[3], 1u) == gridDim.x * TPB_WARPS - 1) {
+    T.nbs[0] = 0; T.nbs[1] = 0; T.bsnext[3] = 0u;
+    for (unsigned k = 0; k < 4 * gridDim.x; ++k) T.bsnext[4 + k] = 0u;  // the sub-partition counts
+  }
+}
+
+// The closing kick of a TP after its BS substep (kept out of line: the BS loop holds the registers).
+__device__ __noinline__ unsigned tp_bs_close(const TPSet &T, const DevParams &P, const PlanetSm &ps, int npl, int i,
+                                             double xi, double yi, double zi, double h1, double h2, const double *shc) {
+  double ax, ay, az;
+  const unsigned cm = tp_close_forces(T, P, ps, npl, i, xi, yi, zi, ax, ay, az);
+  tp_close_update(T, i, xi, yi, zi, ax, ay, az, h1, h2, shc);
+  return cm;
+}
+
+// The BS pass of a substep and the closing kick of every TP. Warps take the listed TPs first (the
+// front entries first, each alone on its sub-partition), integrate each over the substep and give
+// it its closing kick; then they take the other TPs, 32 at a time, for their closing kick. The
+// closing kick has the arithmetic of the first kick and reads the planets at the end of the
+// substep; h1 + h2 as in tp_close_update, hcm_last != 0 adds the step's last Sun drift.
+__global__ void __launch_bounds__(32 * TPB_WARPS, 1) k_tp_bs(Sim S, TPSet T, DevParams P, double tau, double h1,
+                                                           double h2, double hcm_last) {
   constexpr int WPOS = TPB_WPOS;
   extern __shared__ double tpb_smem[];  // per warp: planet positions of both attempts, then s_zt
+  __shared__ PlanetSm s_ps[TPB_WARPS];  // per warp: the planets at the end of the substep, for the
+  __shared__ double s_shc[TPB_WARPS][3];  // closing kicks, and the last Sun drift's shift
   const int lane = threadIdx.x & 31, half = lane >> 4, l16 = lane & 15, warp = threadIdx.x >> 5;
   double *wpos0 = tpb_smem + warp * 2 * WPOS;
   double (*s_zt)[16] = reinterpret_cast<double (*)[16]>(tpb_smem + TPB_WARPS * 2 * WPOS + warp * 32);
   const int nfront = T.nbs[0], nlist = nfront + T.nbs[1], nprep = d_prep_n;
   const int np = T.npad;
   const double i2tau = 2.0 / tau;
-  if (blockIdx.x == 0 && threadIdx.x == 0) *T.npairs = 0u;  // consumed by the encounter test
   const int niso = nfront < (int)gridDim.x ? nfront : (int)gridDim.x;  // front entries placed alone
   const bool iso = (int)blockIdx.x < niso;
-  if (iso && warp != 0 && (warp & 3) == 0) return;  // sub-partition 0 belongs to warp 0's entry
+  if (iso && warp != 0 && (warp & 3) == 0) {  // sub-partition 0 belongs to warp 0's entry
+    tp_bs_warp_done(T);
+    return;
+  }
+  warp_load_planets(S, hcm_last, s_ps[warp], s_shc[warp]);
   for (bool first = true;; first = false) {
     int w = 0;
     if (iso && warp == 0 && first) w = blockIdx.x;
     else {
-      if (lane == 0) w = niso + (int)atomicAdd(T.bsnext, 1u);
+      if (lane == 0) w = niso + (int)atomicAdd(&T.bsnext[0], 1u);
       w = __shfl_sync(0xffffffffu, w, 0);
     }
     if (w >= nlist) break;
@@ -699,13 +780,58 @@ __global__ void __launch_bounds__(32 * TPB_WARPS, 1) k_tp_bs(Sim S, TPSet T, Dev
       rem -= H;
       H *= 2.0;
     }
+    unsigned cm = 0u;
     if (lane == 0) {
       for (int c = 0; c < 3; ++c) { T.x[c * np + i] = y[c]; T.v[c * np + i] = y[3 + c]; }
       if (removed) { T.alive[i] = 0; atomicAdd((unsigned long long *)&T.counters[3], 1ULL); }
       if (failed) atomicOr(S.status, ST_BS_FAILED);
       atomicAdd((unsigned long long *)&T.counters[2], (unsigned long long)steps);
+      if (!removed)
+        cm = tp_bs_close(T, P, s_ps[threadIdx.x >> 5], S.n, i, y[0], y[1], y[2], h1, h2,
+                         hcm_last != 0.0 ? s_shc[threadIdx.x >> 5] : nullptr);
+    }
+    tp_append_pairs(T, i, cm, true);
+  }
+  // A warp on a sub-partition where another warp of the block still integrates a TP waits (up to
+  // TP_WAIT_MAX naps) until that one is done or the closing kicks are all taken: a kick warp beside
+  // it would take two thirds of the sub-partition's FP64 issue from a BS chain that may be the last
+  // of the pass.
+  unsigned *sp_done = T.bsnext + 4 + 4 * blockIdx.x + (warp & 3);
+  if (lane == 0) atomicAdd(sp_done, 1u);
+  for (int nap = 0; !iso && nap < TP_WAIT_MAX; ++nap) {
+    unsigned ok = 0u;
+    if (lane == 0) ok = __ldcg(sp_done) >= TPB_WARPS / 4 || (long long)__ldcg(&T.bsnext[1]) * 64 >= (long long)T.n;
+    if (__shfl_sync(0xffffffffu, ok, 0)) break;
+    __nanosleep(2000);
+  }
+  // the closing kick of the TPs outside the BS list (no encounter, no failed solve), 64 a warp: two
+  // a lane side by side
+  while (!iso) {
+    unsigned c = 0u;
+    if (lane == 0) c = atomicAdd(&T.bsnext[1], 1u);
+    c = __shfl_sync(0xffffffffu, c, 0);
+    if ((long long)c * 64 >= (long long)T.n) break;
+    int ii[2];
+    bool act[2];
+    double x[2][3], acc[2][3];
+    unsigned cm[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int i = (int)c * 64 + 32 * k + lane;
+      ii[k] = i;
+      act[k] = i < T.n && T.alive[i] && T.emask[i] == 0u && !T.fail[i];
+      for (int q = 0; q < 3; ++q) x[k][q] = act[k] ? T.x[q * np + i] : 0.0;
+    }
+    tp_close_forces_k<2>(T, P, s_ps[warp], S.n, ii, act, x, acc, cm);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      if (act[k])
+        tp_close_update(T, ii[k], x[k][0], x[k][1], x[k][2], acc[k][0], acc[k][1], acc[k][2], h1, h2,
+                        hcm_last != 0.0 ? s_shc[warp] : nullptr);
+      tp_append_pairs(T, ii[k], cm[k], true);
     }
   }
+  tp_bs_warp_done(T);
 }
 
 // TP input (heliocentric AoS) -> democratic SoA: v_b = v_h - sum m v_h / (m0 + sum m) with the
@@ -857,11 +983,8 @@ void launch_tp_to_helio(const Sim &S, const TPSet &T, const DevParams &P, double
 void launch_tp_rcrit(const TPSet &T, const DevParams &P, double tau_abs, int check, cudaStream_t st) {
   k_tp_rcrit<<<grid_of(T.n, 256), 256, 0, st>>>(T, P, tau_abs, check);
 }
-void launch_tp_kick(const Sim &S, const TPSet &T, const DevParams &P, FinMode mode, double h1, double h2, cudaStream_t st,
-                    double hcm_last) {
-  const int g = grid_of(T.n, 128);
-  if (mode == FIN_CLOSE) k_tp_kick<FIN_CLOSE><<<g, 128, 0, st>>>(S, T, P, h1, h2, hcm_last);
-  else k_tp_kick<FIN_INIT><<<g, 128, 0, st>>>(S, T, P, h1, h2, 0.0);
+void launch_tp_kick(const Sim &S, const TPSet &T, const DevParams &P, cudaStream_t st) {
+  k_tp_kick<<<grid_of(T.n, 128), 128, 0, st>>>(S, T, P);
 }
 void launch_tp_open_drift(const Sim &S, const TPSet &T, const DevParams &P, double tau_abs, double h1, double tau,
                           double hcm1, cudaStream_t st) {
@@ -876,8 +999,10 @@ void launch_planet_table(const Sim &S, const TPSet &T, const DevParams &P, doubl
 void launch_tp_encounter(const Sim &S, const TPSet &T, double tau, int blocks, cudaStream_t st) {
   k_tp_encounter<<<blocks, 256, 0, st>>>(S, T, tau);
 }
-void launch_tp_bs(const Sim &S, const TPSet &T, const DevParams &P, double tau, int blocks, cudaStream_t st) {
-  k_tp_bs<<<blocks, 32 * TPB_WARPS, TPB_SMEM, st>>>(S, T, P, tau);
+void launch_tp_bs(const Sim &S, const TPSet &T, const DevParams &P, double tau, double h1, double h2, double hcm_last,
+                  int blocks, cudaStream_t st) {
+  if (blocks > TP_BS_MAXBLOCKS) blocks = TP_BS_MAXBLOCKS;
+  k_tp_bs<<<blocks, 32 * TPB_WARPS, TPB_SMEM, st>>>(S, T, P, tau, h1, h2, hcm_last);
 }
 
 }  // namespace genga
