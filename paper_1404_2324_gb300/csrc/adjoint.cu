@@ -455,7 +455,7 @@ __device__ __forceinline__ void pair_vjp_zone(double dx, double dy, double dz, d
 // Kick VJP, Newton's third law: every unordered pair once, on 32x32 tile pairs of one system with a
 // warp-shuffle ring (lane l holds body i = I*32 + l, the j data and j-side sums rotate), as in the
 // forward kick. Outside the changeover zone a body's sums are S1 = sum Gm_p/r^3, V = sum u_p/r^3,
-// Wd = sum 3 (d.w)/r^5 d (d pointing from the body to its partner) and Mb = sum (d.u_p)/r^3, and
+// Wd = 3 sum (d.w)/r^5 d (d pointing from the body to its partner) and Mb = sum (d.u_p)/r^3, and
 // xbar = -u S1 + Gm V + Wd, mbar = -G Mb: the exact regrouping of sum_p -J w, w = Gm_p u - Gm u_p,
 // J = (I - 3 d d^T / r^2)/r^3, d.w = Gm_p (d.u) - Gm (d.u_p). Work item k of system
 // b is the tile pair (I, J), I <= J; its sums for tile I go to part[b][I][J], those for tile J to
@@ -513,7 +513,7 @@ __device__ __forceinline__ void vjp_pair(const VjpBody &Pa, const VjpBody &Pb, i
   const double dua = fma(dz, ua[2], fma(dy, ua[1], dx * ua[0]));
   const double dub = fma(dz, ub[2], fma(dy, ub[1], dx * ub[0]));
   const double dw = fma(Pb.gm, dua, -Pa.gm * dub);  // d.w with w = Gm_b u_a - Gm_a u_b
-  const double cc = 3.0 * yr3 * yr2 * dw;
+  const double cc = yr3 * yr2 * dw;                 // the factor 3 of Wd is applied to the sums
   aa.S1 = fma(Pb.gm, yr3, aa.S1);
   aa.V0 = fma(yr3, ub[0], aa.V0); aa.V1 = fma(yr3, ub[1], aa.V1); aa.V2 = fma(yr3, ub[2], aa.V2);
   aa.W0 = fma(cc, dx, aa.W0); aa.W1 = fma(cc, dy, aa.W1); aa.W2 = fma(cc, dz, aa.W2);
@@ -526,9 +526,9 @@ __device__ __forceinline__ void vjp_pair(const VjpBody &Pa, const VjpBody &Pb, i
 
 // The five per-body outputs of a set of sums.
 __device__ __forceinline__ void vjp_store(double *p, const VjpAcc &a, const VjpBody &B, double G) {
-  p[0] = a.e0 + fma(-B.u0, a.S1, fma(B.gm, a.V0, a.W0));
-  p[32] = a.e1 + fma(-B.u1, a.S1, fma(B.gm, a.V1, a.W1));
-  p[64] = a.e2 + fma(-B.u2, a.S1, fma(B.gm, a.V2, a.W2));
+  p[0] = a.e0 + fma(-B.u0, a.S1, fma(B.gm, a.V0, 3.0 * a.W0));
+  p[32] = a.e1 + fma(-B.u1, a.S1, fma(B.gm, a.V1, 3.0 * a.W1));
+  p[64] = a.e2 + fma(-B.u2, a.S1, fma(B.gm, a.V2, 3.0 * a.W2));
   p[96] = fma(-G, a.Mb, a.me);
   p[128] = a.rcb;
 }
@@ -1207,6 +1207,10 @@ struct genga_adj {
   long long *y_count = nullptr, *yoff_rec = nullptr;
   int bs_blocks = 0, bs_fwd_grid = 0;
   double *kv_part = nullptr;  // kick tile partials: VJP [B][T][T][5][32], forward [B][T][T][3][32]
+  // the reverse sweep's branches: the Kepler-drift VJP and the large-group BS VJP beside the
+  // small-group BS VJP (they touch disjoint bodies)
+  cudaStream_t side = nullptr, side2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
 };
 
 namespace {
@@ -1400,6 +1404,14 @@ int genga_adj_init(genga_adj **out, int n_sys, int n, const double *m0, double G
   bs_init_constants();
   init_lambda();
   init_dstumpff();
+  if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->side2, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming) != cudaSuccess) {
+    genga_adj_free(c);
+    return GENGA_ECUDA;
+  }
   if (cudaDeviceSynchronize() != cudaSuccess || cudaGetLastError() != cudaSuccess) { genga_adj_free(c); return GENGA_ECUDA; }
   *out = c;
   return GENGA_OK;
@@ -1474,12 +1486,22 @@ int genga_adj_backward(genga_adj *c, const double *xbar, const double *vbar, dou
                                                         nullptr, nullptr);
         launch_kick_vjp(c, h, R.x3);
         k_ad_sundrift_vjp<<<c->B, 256, 0, st>>>(c->S, c->D, h, R.v2);
-        cudaMemsetAsync(c->D.ingrp, 0, NB * sizeof(int), st);
-        k_ad_mark<<<c->bs_blocks, 32, 0, st>>>(c->D, R.gstart, R.gsize, R.gmem, R.ngroups);
-        k_ad_kepler_vjp<<<(NB + 127) / 128, 128, 0, st>>>(c->S, c->D, tau, R.x1, R.v1, R.s);
+        // fork: the small-group BS VJP (the longest) here, the Kepler-drift VJP of the bodies outside
+        // groups and the large-group BS VJP beside it; join
+        cudaEventRecord(c->ev_fork, st);
+        cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+        cudaStreamWaitEvent(c->side2, c->ev_fork, 0);
         k_ad_bs_vjp4<<<2 * c->bs_blocks, 32 * BSV4_GROUPS, BSV4_GROUPS * sizeof(GrpVjp4), st>>>(c->S, c->D, R, R.x1,
                                                                                                R.v1);
-        k_ad_bs_vjp<<<c->bs_blocks, 32 * BSV_WARPS, BSV_WARPS * sizeof(LevShared), st>>>(c->S, c->D, R, R.x1, R.v1);
+        cudaMemsetAsync(c->D.ingrp, 0, NB * sizeof(int), c->side);
+        k_ad_mark<<<c->bs_blocks, 32, 0, c->side>>>(c->D, R.gstart, R.gsize, R.gmem, R.ngroups);
+        k_ad_kepler_vjp<<<(NB + 127) / 128, 128, 0, c->side>>>(c->S, c->D, tau, R.x1, R.v1, R.s);
+        k_ad_bs_vjp<<<c->bs_blocks, 32 * BSV_WARPS, BSV_WARPS * sizeof(LevShared), c->side2>>>(c->S, c->D, R, R.x1,
+                                                                                               R.v1);
+        cudaEventRecord(c->ev_join, c->side);
+        cudaEventRecord(c->ev_join2, c->side2);
+        cudaStreamWaitEvent(st, c->ev_join, 0);
+        cudaStreamWaitEvent(st, c->ev_join2, 0);
         k_ad_sundrift_vjp<<<c->B, 256, 0, st>>>(c->S, c->D, h, R.v1);
         launch_kick_vjp(c, h, R.x);
       }
@@ -1507,6 +1529,11 @@ int genga_adj_sync(genga_adj *c) {
 void genga_adj_free(genga_adj *c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->ev_join2) cudaEventDestroy(c->ev_join2);
+  if (c->side) cudaStreamDestroy(c->side);
+  if (c->side2) cudaStreamDestroy(c->side2);
   for (void *p : c->allocs) cudaFree(p);
   delete c;
 }
