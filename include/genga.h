@@ -227,8 +227,16 @@ int genga_init_batch(genga_ctx **ctx, int n_sys, const int *offsets, const doubl
                      const double *radii, const double *x, const double *v, double G, double dt, int order,
                      int steps_per_launch);
 
-/* Autotuned kick shape (threads per body, threads per CTA) and steps per graph launch. */
+/* Autotuned kick shape and steps per graph launch: *split = threads per body (1, 2, 4) of the
+ * one-body-per-thread kick, or 0 for the Newton's-third-law kick (every pair of a system once, one
+ * warp per system of 33..64 bodies or per pack of smaller systems; the opening kick's candidate
+ * recomputation keeps one thread per body); *block = threads per CTA. */
 int genga_batch_info(genga_ctx *ctx, int *split, int *block, int *steps_per_launch);
+
+/* Overrides the autotuned kick shape: split 0 (Newton's third law), 1, 2 or 4 threads per body;
+ * block 64, 128 or 256 threads per CTA. Results agree to rounding (the sums' order differs).
+ * Takes effect from the next step. Returns GENGA_EINVAL for other values or a non-batched ctx. */
+int genga_batch_set_kick(genga_ctx *ctx, int split, int block);
 
 /* The schedule genga_init_batch chose by timing two steps of the batch each way: the step graph
  * (every phase over all systems, then the next phase) or one persistent launch in which each CTA

@@ -649,6 +649,28 @@ int genga_init_batch(genga_ctx **out, int n_sys, const int *offsets, const doubl
   S.sys_m0 = mem.get<double>(n_sys); S.sys_ppre = mem.get<double>(3 * (size_t)n_sys);
   S.sys_ppost = mem.get<double>(3 * (size_t)n_sys); S.sys_flag = mem.get<int>(n_sys);
   S.bmask = mem.get<u64>(np); S.emask = mem.get<u64>(np);
+  // the symmetric kick's warp work items: a system of 33..64 bodies alone, smaller ones packed in
+  // lane segments of the next power of two of their size (systems are ordered by size, largest first)
+  std::vector<int> kjobs;
+  for (int k = 0; k < n_sys;) {
+    const int ns = start[k + 1] - start[k];
+    if (ns > 32) { kjobs.push_back(k); kjobs.push_back(64 << 8 | 1); ++k; continue; }
+    int w = 1;
+    while (w < ns) w <<= 1;
+    const int k0 = k;
+    int cnt = 0;
+    while (k < n_sys && cnt < 32 / w) {
+      const int m = start[k + 1] - start[k];
+      int wm = 1;
+      while (wm < m) wm <<= 1;
+      if (m > 32 || wm != w) break;
+      ++cnt;
+      ++k;
+    }
+    kjobs.push_back(k0); kjobs.push_back(w << 8 | cnt);
+  }
+  S.nkjobs = (int)kjobs.size() / 2;
+  S.kjobs = mem.get<int>(kjobs.size());
   S.spin = mem.get<double>(3 * np);
   S.crec = mem.get<double>((size_t)CREC_CAP * CREC); S.ncrec = mem.get<int>(1);
   c->perm = mem.get<int>(n); c->sys_user = mem.get<int>(n_sys); c->sysE = mem.get<double>(n_sys);
@@ -675,6 +697,7 @@ int genga_init_batch(genga_ctx **out, int n_sys, const int *offsets, const doubl
   cudaStream_t st = c->stream;
   if (cudaMemcpy(S.sys_of, sys_of.data(), np * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(S.sys_start, start.data(), (n_sys + 1) * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(S.kjobs, kjobs.data(), kjobs.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(S.sys_m0, sm0.data(), n_sys * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(c->perm, perm.data(), n * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(c->sys_user, sys_user.data(), n_sys * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -687,15 +710,16 @@ int genga_init_batch(genga_ctx **out, int n_sys, const int *offsets, const doubl
   }
   bs_init_constants();
   launch_b_from_helio(S, c->P, c->perm, c->sx, c->sv, c->sm, c->sR, 0, st);
-  // autotune the kick's tile shape (threads per body x block size) on the first kick
+  // autotune the kick's shape on the first kick: threads per body x block size, or (split 0) the
+  // Newton's-third-law kernel (one warp per work item) x block size
   launch_b_rcrit(S, c->P, std::fabs(dt), 0, st);
   {
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    const int splits[3] = {1, 2, 4}, blocks[3] = {64, 128, 256};
-    for (int a = 0; a < 3; ++a)
+    const int splits[4] = {0, 1, 2, 4}, blocks[3] = {64, 128, 256};
+    for (int a = 0; a < 4; ++a)
       for (int b = 0; b < 3; ++b) {
         launch_b_kick(S, c->P, FIN_INIT, 0.0, 0.0, splits[a], blocks[b], st);  // warm
         cudaEventRecord(e0, st);
@@ -767,6 +791,16 @@ int genga_batch_set_schedule(genga_ctx *c, int persistent) {
   if (!c || !c->batched || (persistent != 0 && persistent != 1) || (persistent && c->persist_blocks < 1))
     return GENGA_EINVAL;
   c->persist = persistent != 0;
+  drop_graph(c);
+  return GENGA_OK;
+}
+
+int genga_batch_set_kick(genga_ctx *c, int split, int block) {
+  if (!c || !c->batched || (split != 0 && split != 1 && split != 2 && split != 4) ||
+      (block != 64 && block != 128 && block != 256))
+    return GENGA_EINVAL;
+  c->b_split = split;
+  c->b_block = block;
   drop_graph(c);
   return GENGA_OK;
 }

@@ -3,9 +3,10 @@
 //
 // Bodies of one system are contiguous and systems are ordered by size, so neighbouring lanes
 // loop over partner sets of similar length (the paper masks "false interactions" of a thread
-// that runs past its system; here no lane ever reads another system). Every kick thread (or
-// SPLIT threads, autotuned) sums the whole acceleration of its body, so no partial-sum buffers
-// or atomics are needed. Candidate and encounter partners are per-body 64-bit masks (bit = index
+// that runs past its system; here no lane ever reads another system). The kick is autotuned at
+// init between one thread (or SPLIT threads) per body summing its whole acceleration, and a
+// Newton's-third-law kernel that visits every pair of a system once on one warp; neither needs
+// partial-sum buffers or atomics. Candidate and encounter partners are per-body 64-bit masks (bit = index
 // within the system). Groups are found by one warp per system and integrated by the
 // Bulirsch-Stoer kernel of the single-system mode, which reads the group's central mass.
 #include "genga_launch.h"
@@ -130,6 +131,172 @@ __global__ void k_b_kick(Sim S, DevParams P, double h1, double h2) {
   double vx = fma(h1, ax, S.v[i]), vy = fma(h1, ay, S.v[np + i]), vz = fma(h1, az, S.v[2 * np + i]);
   if (h2 != 0.0) { vx = fma(h2, ax, vx); vy = fma(h2, ay, vy); vz = fma(h2, az, vz); }
   S.v[i] = vx; S.v[np + i] = vy; S.v[2 * np + i] = vz;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Kick with Newton's third law (CLOSE / INIT): every unordered pair of a system once, on one warp,
+// the same terms as k_b_kick (the pull on each side is the partner's Gm r^-3, times the changeover
+// weight inside rc). Systems of up to 32 bodies sit in lane segments of width W (the next power of
+// two), 32 / W systems a warp; a segment of n bodies runs a ring: at step s = 1 .. floor(n/2) lane
+// u meets body (u + s) mod n, whose data and pair sums rotate one lane a step (the last step of an
+// even n takes half the lanes). A system of 33..64 bodies takes a warp: the ring of bodies 0..31,
+// the ring of bodies 32..n-1, and their cross pairs, for which the second block (padded to P, a
+// power of two) is replicated 32 / P times around the warp, so that P one-lane rotations meet every
+// cross pair once; the replicas' sums are then added by a butterfly. Each body's far field, near
+// field and candidate mask are summed in a fixed order, so results do not depend on the schedule.
+// Work item k (one warp): kjobs[2k] = first system, kjobs[2k + 1] = W << 8 | systems (W = 64: one
+// system of 33..64 bodies).
+// ---------------------------------------------------------------------------------------------
+struct BkBody {
+  double x, y, z, gm, A;
+  u64 T, Q;
+  int al;
+};
+struct BkAcc {
+  double f0, f1, f2, n0, n1, n2;  // far field, near field (candidates)
+  u64 mask;                       // candidate partners (bit = index in the system)
+};
+
+__device__ __forceinline__ void bk_load(const Sim &S, int i, BkBody &B) {  // i < 0: no body
+  const int np = S.npad;
+  const bool ok = i >= 0 && S.alive[i];
+  B.al = ok;
+  B.x = ok ? S.x[i] : 0.0; B.y = ok ? S.x[np + i] : 0.0; B.z = ok ? S.x[2 * np + i] : 0.0;
+  B.gm = ok ? S.gm[i] : 0.0; B.A = ok ? S.A[i] : 0.0;
+  B.T = ok ? S.T[i] : 0ULL; B.Q = ok ? S.rcsq[i] : 0ULL;
+}
+__device__ __forceinline__ void bk_shfl(BkBody &B, int src) {
+  B.x = __shfl_sync(0xffffffffu, B.x, src); B.y = __shfl_sync(0xffffffffu, B.y, src);
+  B.z = __shfl_sync(0xffffffffu, B.z, src); B.gm = __shfl_sync(0xffffffffu, B.gm, src);
+  B.A = __shfl_sync(0xffffffffu, B.A, src); B.T = __shfl_sync(0xffffffffu, B.T, src);
+  B.Q = __shfl_sync(0xffffffffu, B.Q, src); B.al = __shfl_sync(0xffffffffu, B.al, src);
+}
+__device__ __forceinline__ void bk_zero(BkAcc &a) { a.f0 = a.f1 = a.f2 = a.n0 = a.n1 = a.n2 = 0.0; a.mask = 0ULL; }
+__device__ __forceinline__ void bk_acc_shfl(BkAcc &a, int src) {
+  a.f0 = __shfl_sync(0xffffffffu, a.f0, src); a.f1 = __shfl_sync(0xffffffffu, a.f1, src);
+  a.f2 = __shfl_sync(0xffffffffu, a.f2, src); a.n0 = __shfl_sync(0xffffffffu, a.n0, src);
+  a.n1 = __shfl_sync(0xffffffffu, a.n1, src); a.n2 = __shfl_sync(0xffffffffu, a.n2, src);
+  a.mask = __shfl_sync(0xffffffffu, a.mask, src);
+}
+__device__ __forceinline__ void bk_acc_add(BkAcc &a, const BkAcc &b) {
+  a.f0 += b.f0; a.f1 += b.f1; a.f2 += b.f2; a.n0 += b.n0; a.n1 += b.n1; a.n2 += b.n2; a.mask |= b.mask;
+}
+
+// The pair (i, j), d = x_j - x_i; ui, uj: their indices in the system (mask bits).
+__device__ __forceinline__ void bk_pair(const DevParams &P, const BkBody &Bi, const BkBody &Bj, int ui, int uj,
+                                        bool act, BkAcc &ai, BkAcc &aj) {
+  if (!act || !Bi.al || !Bj.al) return;
+  const double dx = Bj.x - Bi.x, dy = Bj.y - Bi.y, dz = Bj.z - Bi.z;
+  const double r2 = __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx)));
+  const double w3 = rcube_refined(r2);
+  const u64 rb = dbits(r2);
+  double gi = Bj.gm * w3, gj = Bi.gm * w3;  // the pull on i (along d) and on j (against d)
+  if (rb < umax64(Bi.T, Bj.T)) {            // precheck candidate: near field, recorded
+    if (rb < umax64(Bi.Q, Bj.Q)) {          // inside the changeover zone (rare): the weight needs r
+      double wB, wA;
+      changeover_w(r2 * rsqrt_refined(r2), pmin(Bi.A, Bj.A), P.kmode, wB, wA);
+      gi *= wB; gj *= wB;
+    }
+    ai.mask |= 1ULL << uj; aj.mask |= 1ULL << ui;
+    ai.n0 = fma(gi, dx, ai.n0); ai.n1 = fma(gi, dy, ai.n1); ai.n2 = fma(gi, dz, ai.n2);
+    aj.n0 = fma(-gj, dx, aj.n0); aj.n1 = fma(-gj, dy, aj.n1); aj.n2 = fma(-gj, dz, aj.n2);
+  } else {
+    ai.f0 = fma(gi, dx, ai.f0); ai.f1 = fma(gi, dy, ai.f1); ai.f2 = fma(gi, dz, ai.f2);
+    aj.f0 = fma(-gj, dx, aj.f0); aj.f1 = fma(-gj, dy, aj.f1); aj.f2 = fma(-gj, dz, aj.f2);
+  }
+}
+
+// Body i's far field, candidates and (CLOSE) velocity from its sums.
+template <int MODE>
+__device__ __forceinline__ void bk_finish(const Sim &S, int i, const BkAcc &a, double h1, double h2) {
+  const int np = S.npad;
+  S.afar[i] = a.f0; S.afar[np + i] = a.f1; S.afar[2 * np + i] = a.f2;
+  S.bmask[i] = a.mask;
+  if (a.mask) atomicAdd((unsigned long long *)&S.counters[C_CAND], (unsigned long long)__popcll(a.mask));
+  if (MODE == FIN_INIT) return;
+  const double ax = a.f0 + a.n0, ay = a.f1 + a.n1, az = a.f2 + a.n2;
+  double vx = fma(h1, ax, S.v[i]), vy = fma(h1, ay, S.v[np + i]), vz = fma(h1, az, S.v[2 * np + i]);
+  if (h2 != 0.0) { vx = fma(h2, ax, vx); vy = fma(h2, ay, vy); vz = fma(h2, az, vz); }
+  S.v[i] = vx; S.v[np + i] = vy; S.v[2 * np + i] = vz;
+}
+
+// The ring of a segment of n bodies (lanes base .. base + n - 1 hold them in Bi) over R steps
+// (R >= floor(n/2); the steps past floor(n/2) only rotate): the i-side sums in ai, the j-side sums
+// returned to their owners and added.
+__device__ __forceinline__ void bk_ring(const DevParams &P, const BkBody &Bi, int base, int n, int R, BkAcc &ai) {
+  const int lane = threadIdx.x & 31, u = lane - base;
+  const bool own = u >= 0 && u < n;
+  const int src = own ? base + (u + 1 == n ? 0 : u + 1) : lane;
+  BkBody Bj = Bi;
+  BkAcc aj;
+  bk_zero(aj);
+  int jb = own ? u : 0;
+  for (int s = 1; s <= R; ++s) {
+    bk_shfl(Bj, src);
+    bk_acc_shfl(aj, src);
+    jb = (jb + 1 == n) ? 0 : jb + 1;  // lane u now holds body (u + s) mod n
+    const bool act = own && (2 * s < n || (2 * s == n && u < s));
+    bk_pair(P, Bi, Bj, u, jb, act, ai, aj);
+  }
+  const int back = own ? base + (u + n - R % n) % n : lane;  // body u's j sums are R lanes on
+  bk_acc_shfl(aj, back);
+  if (own) bk_acc_add(ai, aj);
+}
+
+template <int MODE>
+__global__ void k_b_kick_sym(Sim S, DevParams P, double h1, double h2) {
+  const int lane = threadIdx.x & 31;
+  const int nwarp = (gridDim.x * blockDim.x) >> 5;
+  for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < S.nkjobs; k += nwarp) {
+    const int s0 = S.kjobs[2 * k], code = S.kjobs[2 * k + 1], W = code >> 8, cnt = code & 255;
+    if (W <= 32) {  // segments of W lanes, one system each
+      const int seg = lane / W, base = seg * W;
+      int st = 0, n = 0;
+      if (seg < cnt) { st = S.sys_start[s0 + seg]; n = S.sys_start[s0 + seg + 1] - st; }
+      const int u = lane - base;
+      const bool own = u < n;
+      BkBody Bi;
+      bk_load(S, own ? st + u : -1, Bi);
+      BkAcc ai;
+      bk_zero(ai);
+      const int R = (S.sys_start[s0 + 1] - S.sys_start[s0]) >> 1;  // the pack's first system is its largest
+      bk_ring(P, Bi, base, n, R, ai);
+      if (own && Bi.al) bk_finish<MODE>(S, st + u, ai, h1, h2);
+    } else {  // one system of 33..64 bodies: blocks A = 0..31, B = 32..n-1
+      const int st = S.sys_start[s0], nB = S.sys_start[s0 + 1] - st - 32;
+      BkBody Ba, Bb;
+      bk_load(S, st + lane, Ba);
+      bk_load(S, lane < nB ? st + 32 + lane : -1, Bb);
+      BkAcc aa, ab;
+      bk_zero(aa);
+      bk_zero(ab);
+      bk_ring(P, Ba, 0, 32, 16, aa);
+      bk_ring(P, Bb, 0, nB, nB >> 1, ab);
+      // cross pairs: lane l starts with B body l mod Pp and meets B body (l + s) mod Pp at step s
+      int Pp = 1;
+      while (Pp < nB) Pp <<= 1;
+      BkBody Bj = Bb;
+      bk_shfl(Bj, lane & (Pp - 1));
+      BkAcc aj;
+      bk_zero(aj);
+      const int src = (lane + 1) & 31;
+      for (int s = 0; s < Pp; ++s) {
+        const int b = (lane + s) & (Pp - 1);
+        bk_pair(P, Ba, Bj, lane, 32 + b, b < nB, aa, aj);
+        bk_shfl(Bj, src);
+        bk_acc_shfl(aj, src);
+      }
+      // lane l holds one replica of B body l mod Pp's sums: add the 32 / Pp replicas
+      for (int o = Pp; o < 32; o <<= 1) {
+        BkAcc t = aj;
+        bk_acc_shfl(t, lane ^ o);
+        bk_acc_add(aj, t);
+      }
+      if (lane < nB) bk_acc_add(ab, aj);
+      if (Ba.al) bk_finish<MODE>(S, st + lane, aa, h1, h2);
+      if (lane < nB && Bb.al) bk_finish<MODE>(S, st + 32 + lane, ab, h1, h2);
+    }
+  }
 }
 
 // Momentum of every system (one warp per system, fixed order).
@@ -417,6 +584,14 @@ void launch_b_rcrit(const Sim &S, const DevParams &P, double tau_abs, int check,
 
 template <int MODE>
 static void b_kick_split(const Sim &S, const DevParams &P, double h1, double h2, int split, int block, cudaStream_t st) {
+  if (split == 0) {  // Newton's third law, one warp per work item (CLOSE / INIT; OPEN takes split 1)
+    if constexpr (MODE != FIN_OPEN) {
+      const int grid = (int)(((long)S.nkjobs * 32 + block - 1) / block);
+      k_b_kick_sym<MODE><<<grid > 0 ? grid : 1, block, 0, st>>>(S, P, h1, h2);
+      return;
+    }
+    split = 1;
+  }
   const long threads = (long)S.npad * split;
   const int grid = (int)((threads + block - 1) / block);
   if (split == 1) k_b_kick<MODE, 1><<<grid, block, 0, st>>>(S, P, h1, h2);

@@ -96,6 +96,8 @@ struct Sim {
   double *sys_m0, *sys_ppre, *sys_ppost;  // central masses [nsys], momenta [3 nsys]
   int *sys_flag;                 // per system: opening kick must be recomputed in full
   u64 *bmask, *emask;            // per body: candidate / encounter partners (bit = index in system)
+  int *kjobs, nkjobs;            // warp work items of the symmetric kick: [2k] first system, [2k + 1]
+                                 // lane-segment width << 8 | systems (width 64: one system of 33..64)
   int *gsize;                    // batched groups: member count per group (gstart = first member)
   int *gtotal;                   // batched groups: members placed so far
   unsigned *bsq;                 // batched groups: next group of queue 0 (1-2 members, pair kernel), queue 1

@@ -104,6 +104,7 @@ _SIGS = {
     "genga_init_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, _I, _D, _D, _D, _D, _D, C.c_double,
                                    C.c_double, C.c_int, C.c_int]),
     "genga_batch_info": (C.c_int, [_V, _I, _I, _I]),
+    "genga_batch_set_kick": (C.c_int, [_V, C.c_int, C.c_int]),
     "genga_get_state_batch": (C.c_int, [_V, _D, _D, _D, _D, _I]),
     "genga_set_state_batch": (C.c_int, [_V, _D, _D]),
     "genga_energy_batch": (C.c_int, [_V, _D, _D]),
@@ -382,6 +383,10 @@ def genga_init_batch(offsets, m0, masses, radii, x, v, G, dt, order=2, steps_per
     _check(lib().genga_init_batch(C.byref(h), nsys, _ip(off), _dp(m0a), _dp(m), _dp(R), _dp(xx), _dp(vv), float(G),
                                   float(dt), int(order), int(steps_per_launch)), "genga_init_batch")
     return h
+
+
+def genga_batch_set_kick(ctx, split, block):
+    _check(lib().genga_batch_set_kick(ctx, int(split), int(block)), "genga_batch_set_kick")
 
 
 def genga_batch_info(ctx):

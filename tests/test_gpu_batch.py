@@ -118,6 +118,40 @@ def test_batch_with_distinct_central_masses_and_edge_sizes():
         genga.genga_free(h)
 
 
+@pytest.mark.parametrize("split", [0, 1, 4])
+def test_every_kick_shape_matches_oracle(split):
+    """The kick shapes the autotuner chooses from, each forced: Newton's third law on one warp per
+    system or pack of systems (split 0; systems of 1 to 64 bodies give packs of every lane-segment
+    width and many sizes of a system's second block of 32) and one or four threads per body. The
+    pair terms are the same; only the order of the sums differs."""
+    b = ics.batch(7, n_sys=64, n_lo=2, n_hi=65)  # 1 to 64 orbiting bodies per system
+    n = b["offsets"][-1]
+    h = genga.genga_init_batch(b["offsets"], b["m0"], b["m"], b["R"], b["x"], b["v"], b["G"], b["dt"], 2, 1)
+    try:
+        genga.genga_batch_set_kick(h, split, 128)
+        assert genga.genga_batch_info(h)[:2] == (split, 128)
+        genga.genga_step(h, 1)
+        g = genga.genga_get_state_batch(h, n)
+        o = _oracle_batch(b, 2, 1)
+        assert np.array_equal(g["alive"], o["alive"])
+        assert _rel_err(g, o) <= 1e-12
+        genga.genga_step(h, 4)
+        g = genga.genga_get_state_batch(h, n)
+        o = _oracle_batch(b, 2, 5)
+        assert np.array_equal(g["alive"], o["alive"])
+        assert _rel_err(g, o) <= 1e-11
+        code, cnt = genga.genga_status(h)
+        assert cnt["candidates"] > 0 and code & genga.ST_BS_FAILED == 0
+    finally:
+        genga.genga_free(h)
+    with pytest.raises(RuntimeError):
+        h = genga.genga_init_batch(b["offsets"], b["m0"], b["m"], b["R"], b["x"], b["v"], b["G"], b["dt"], 2, 1)
+        try:
+            genga.genga_batch_set_kick(h, 3, 128)
+        finally:
+            genga.genga_free(h)
+
+
 def test_batch_graph_launch_size_does_not_change_results():
     b = ics.batch(8, n_sys=50)
     n = b["offsets"][-1]
@@ -150,7 +184,7 @@ def test_batch_autotuned_shape_is_reported():
     b = ics.batch(9, n_sys=20)
     h = genga.genga_init_batch(b["offsets"], b["m0"], b["m"], b["R"], b["x"], b["v"], b["G"], b["dt"], 2, 100)
     split, block, spl = genga.genga_batch_info(h)
-    assert split in (1, 2, 4) and block in (64, 128, 256) and spl == 100
+    assert split in (0, 1, 2, 4) and block in (64, 128, 256) and spl == 100
     # per launch of 100 steps: the step graph's 13 kernels a step (incl. the four BS kernels: pairs,
     # 3..4, 5..32, 33..64 members), or the persistent kernel and its step counter
     persistent = genga.genga_batch_schedule(h)["persistent"]
