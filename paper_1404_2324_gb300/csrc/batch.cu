@@ -220,10 +220,11 @@ __device__ __forceinline__ void bk_finish(const Sim &S, int i, const BkAcc &a, d
   S.v[i] = vx; S.v[np + i] = vy; S.v[2 * np + i] = vz;
 }
 
-// The ring of a segment of n bodies (lanes base .. base + n - 1 hold them in Bi) over R steps
-// (R >= floor(n/2); the steps past floor(n/2) only rotate): the i-side sums in ai, the j-side sums
-// returned to their owners and added.
-__device__ __forceinline__ void bk_ring(const DevParams &P, const BkBody &Bi, int base, int n, int R, BkAcc &ai) {
+// The ring of a segment of n bodies (lanes base .. base + n - 1 hold them in Bi; the first is body
+// off of its system) over R steps (R >= floor(n/2); the steps past floor(n/2) only rotate): the
+// i-side sums in ai, the j-side sums returned to their owners and added.
+__device__ __forceinline__ void bk_ring(const DevParams &P, const BkBody &Bi, int base, int n, int off, int R,
+                                        BkAcc &ai) {
   const int lane = threadIdx.x & 31, u = lane - base;
   const bool own = u >= 0 && u < n;
   const int src = own ? base + (u + 1 == n ? 0 : u + 1) : lane;
@@ -236,7 +237,7 @@ __device__ __forceinline__ void bk_ring(const DevParams &P, const BkBody &Bi, in
     bk_acc_shfl(aj, src);
     jb = (jb + 1 == n) ? 0 : jb + 1;  // lane u now holds body (u + s) mod n
     const bool act = own && (2 * s < n || (2 * s == n && u < s));
-    bk_pair(P, Bi, Bj, u, jb, act, ai, aj);
+    bk_pair(P, Bi, Bj, off + u, off + jb, act, ai, aj);
   }
   const int back = own ? base + (u + n - R % n) % n : lane;  // body u's j sums are R lanes on
   bk_acc_shfl(aj, back);
@@ -260,7 +261,7 @@ __global__ void k_b_kick_sym(Sim S, DevParams P, double h1, double h2) {
       BkAcc ai;
       bk_zero(ai);
       const int R = (S.sys_start[s0 + 1] - S.sys_start[s0]) >> 1;  // the pack's first system is its largest
-      bk_ring(P, Bi, base, n, R, ai);
+      bk_ring(P, Bi, base, n, 0, R, ai);
       if (own && Bi.al) bk_finish<MODE>(S, st + u, ai, h1, h2);
     } else {  // one system of 33..64 bodies: blocks A = 0..31, B = 32..n-1
       const int st = S.sys_start[s0], nB = S.sys_start[s0 + 1] - st - 32;
@@ -270,8 +271,8 @@ __global__ void k_b_kick_sym(Sim S, DevParams P, double h1, double h2) {
       BkAcc aa, ab;
       bk_zero(aa);
       bk_zero(ab);
-      bk_ring(P, Ba, 0, 32, 16, aa);
-      bk_ring(P, Bb, 0, nB, nB >> 1, ab);
+      bk_ring(P, Ba, 0, 32, 0, 16, aa);
+      bk_ring(P, Bb, 0, nB, 32, nB >> 1, ab);
       // cross pairs: lane l starts with B body l mod Pp and meets B body (l + s) mod Pp at step s
       int Pp = 1;
       while (Pp < nB) Pp <<= 1;

@@ -126,6 +126,14 @@ def test_every_kick_shape_matches_oracle(split):
     pair terms are the same; only the order of the sums differs."""
     b = ics.batch(7, n_sys=64, n_lo=2, n_hi=65)  # 1 to 64 orbiting bodies per system
     n = b["offsets"][-1]
+    # in every system of 42+ bodies, body 41 starts 0.01 AU from body 40 (both in the second block
+    # of 32): a candidate pair of the precheck from the first kick on, and an encounter
+    planted = set()
+    for s0, s1 in zip(b["offsets"][:-1], b["offsets"][1:]):
+        if s1 - s0 >= 42:
+            b["x"][s0 + 41] = b["x"][s0 + 40] + np.array([0.01, 0.0, 0.0])
+            b["v"][s0 + 41] = b["v"][s0 + 40]
+            planted.add((int(s0) + 40, int(s0) + 41))
     h = genga.genga_init_batch(b["offsets"], b["m0"], b["m"], b["R"], b["x"], b["v"], b["G"], b["dt"], 2, 1)
     try:
         genga.genga_batch_set_kick(h, split, 128)
@@ -135,11 +143,17 @@ def test_every_kick_shape_matches_oracle(split):
         o = _oracle_batch(b, 2, 1)
         assert np.array_equal(g["alive"], o["alive"])
         assert _rel_err(g, o) <= 1e-12
+        gp = {tuple(int(q) for q in p) for p in genga.genga_batch_encounters(h)}
+        op = _oracle_batch_pairs(b, 2)
+        assert len(planted) > 10 and planted <= gp and planted <= op
+        assert len(gp ^ op) <= 2  # a pair within rounding of the threshold may flip
         genga.genga_step(h, 4)
         g = genga.genga_get_state_batch(h, n)
         o = _oracle_batch(b, 2, 5)
         assert np.array_equal(g["alive"], o["alive"])
-        assert _rel_err(g, o) <= 1e-11
+        # the planted pairs pass each other at 0.01 AU, which amplifies the sums' rounding: the
+        # 100-step bound of the other tests
+        assert _rel_err(g, o) <= 1e-9
         code, cnt = genga.genga_status(h)
         assert cnt["candidates"] > 0 and code & genga.ST_BS_FAILED == 0
     finally:
