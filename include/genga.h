@@ -222,7 +222,12 @@ int genga_tp_status(genga_ctx *ctx, long long *detail);
  *   then single steps for the remainder).
  * Each system follows exactly the single-system step of genga_init (same parameters for all
  * systems except m0, Sect. 3.4). The kick's tile shape is autotuned here on the first kick
- * (genga_batch_info reports it). Returns 0 or a negative code; *ctx is NULL on failure. */
+ * (genga_batch_info reports it). From 2048 systems on, the batch runs in parts of about 1024
+ * consecutive systems (at most 8), each with its own step graph on its own stream, forked from the
+ * context's stream at every call and joined back; the parts all run the step graph and one kick
+ * shape, timed with all parts at once. Every call of this section behaves the same either way
+ * (arrays in the caller's order; counters summed over the parts, the step count once).
+ * Returns 0 or a negative code; *ctx is NULL on failure. */
 int genga_init_batch(genga_ctx **ctx, int n_sys, const int *offsets, const double *m0, const double *masses,
                      const double *radii, const double *x, const double *v, double G, double dt, int order,
                      int steps_per_launch);

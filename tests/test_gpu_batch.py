@@ -166,6 +166,61 @@ def test_every_kick_shape_matches_oracle(split):
             genga.genga_free(h)
 
 
+def test_large_batch_in_parts_equals_its_halves_and_the_oracle():
+    """A batch of 2048 systems runs in two parts of 1024 systems, stepped side by side: every result
+    equals that of two separate batches made of the same halves (the same kernels and kick shape,
+    bit for bit), and the first step matches the oracle per system; the whole-batch calls (state,
+    energies, encounter pairs, counters, spins) put the parts back in the caller's order."""
+    b = ics.batch(11, n_sys=2048, n_lo=2, n_hi=10)  # 1 to 9 orbiting bodies per system
+    off, n = b["offsets"], b["offsets"][-1]
+    h = genga.genga_init_batch(off, b["m0"], b["m"], b["R"], b["x"], b["v"], b["G"], b["dt"], 2, 4)
+    halves = []
+    try:
+        split, block, _ = genga.genga_batch_info(h)
+        genga.genga_set_state_batch(h, b["x"], b["v"])  # the first kick again, in the common shape
+        for s0, s1 in ((0, 1024), (1024, 2048)):
+            o0, o1 = off[s0], off[s1]
+            hh = genga.genga_init_batch(off[s0:s1 + 1] - o0, b["m0"][s0:s1], b["m"][o0:o1], b["R"][o0:o1],
+                                        b["x"][o0:o1], b["v"][o0:o1], b["G"], b["dt"], 2, 4)
+            genga.genga_batch_set_kick(hh, split, block)
+            genga.genga_batch_set_schedule(hh, 0)
+            genga.genga_set_state_batch(hh, b["x"][o0:o1], b["v"][o0:o1])
+            halves.append((hh, s0, s1, o0, o1))
+        assert genga.genga_batch_schedule(h)["persistent"] == 0
+        genga.genga_step(h, 1)
+        g = genga.genga_get_state_batch(h, n)
+        o = _oracle_batch(b, 2, 1)
+        assert np.array_equal(g["alive"], o["alive"])
+        assert _rel_err(g, o) <= 1e-12
+        op = _oracle_batch_pairs(b, 2)
+        gp = {tuple(int(q) for q in p) for p in genga.genga_batch_encounters(h)}
+        assert len(op) > 10 and len(gp ^ op) <= 2
+        genga.genga_step(h, 9)  # two 4-step graph launches and a single step
+        g = genga.genga_get_state_batch(h, n)
+        E, U = genga.genga_energy_batch(h, 2048)
+        code, cnt = genga.genga_status(h)
+        assert cnt["steps"] == 10 and cnt["candidates"] > 0 and code & genga.ST_BS_FAILED == 0
+        spin = np.random.default_rng(3).standard_normal((n, 3)) * 1e-9
+        genga.genga_set_spin(h, spin)
+        assert np.array_equal(genga.genga_get_spin(h, n), spin)
+        cand = 0
+        for hh, s0, s1, o0, o1 in halves:
+            genga.genga_step(hh, 10)
+            gh = genga.genga_get_state_batch(hh, o1 - o0)
+            for k in ("x", "v", "m", "alive"):
+                assert np.array_equal(g[k][o0:o1], gh[k]), k
+            Eh, _ = genga.genga_energy_batch(hh, s1 - s0)
+            assert np.array_equal(E[s0:s1], Eh)
+            _, ch = genga.genga_status(hh)
+            assert ch["steps"] == 10
+            cand += ch["candidates"]
+        assert cnt["candidates"] == cand
+    finally:
+        genga.genga_free(h)
+        for hh, *_ in halves:
+            genga.genga_free(hh)
+
+
 def test_batch_graph_launch_size_does_not_change_results():
     b = ics.batch(8, n_sys=50)
     n = b["offsets"][-1]
