@@ -221,6 +221,58 @@ def test_large_batch_in_parts_equals_its_halves_and_the_oracle():
             genga.genga_free(hh)
 
 
+def test_batch_in_parts_reports_like_its_halves():
+    """Ejection and collision records of a batch in two parts: in each half of 1024 systems an
+    escaping system and a disk of enlarged bodies among small systems, RcutSun removing the
+    innermost bodies. The records (the caller's body indices) are those of the two halves run as
+    separate batches, offset by the half's first body."""
+    from tests.test_gpu_ejection import _escape_system, _gpu_params
+    q = ics.batch(12, n_sys=2044, n_lo=2, n_hi=6)
+    d = ics.disk32(3)
+    d["R"] = d["R"] * 1000.0
+    esc = _escape_system()
+    parts, m0 = [], []
+    for half in range(2):
+        for s in range(1022 * half, 1022 * (half + 1)):
+            sl = slice(q["offsets"][s], q["offsets"][s + 1])
+            parts.append((q["m"][sl], q["R"][sl], q["x"][sl], q["v"][sl]))
+        parts += [esc, (d["m"], d["R"], d["x"], d["v"])]
+    off = np.cumsum([0] + [len(p_[0]) for p_ in parts])
+    cat = [np.concatenate([p_[k] for p_ in parts]) for k in range(4)]
+    prm = _gpu_params(rcut=8.0, rcut_sun=0.3)
+    h = genga.genga_init_batch(off, np.ones(2048), *cat, q["G"], 6.0, 2, 10)
+    halves = []
+    try:
+        split, block, _ = genga.genga_batch_info(h)
+        genga.genga_set_params(h, prm)
+        for s0, s1 in ((0, 1024), (1024, 2048)):
+            o0, o1 = off[s0], off[s1]
+            hh = genga.genga_init_batch(off[s0:s1 + 1] - o0, np.ones(1024), *[a[o0:o1] for a in cat], q["G"], 6.0, 2, 10)
+            genga.genga_batch_set_kick(hh, split, block)
+            genga.genga_batch_set_schedule(hh, 0)
+            genga.genga_set_params(hh, prm)
+            halves.append((hh, o0))
+        genga.genga_step(h, 100)
+        ge, gc = genga.genga_ejections(h), genga.genga_collisions(h)
+        he, hc = [], []
+        for hh, o0 in halves:
+            genga.genga_step(hh, 100)
+            e, c = genga.genga_ejections(hh), genga.genga_collisions(hh)
+            e[:, 0] += o0
+            c[:, [3, 4, 23]] += o0
+            he.append(e)
+            hc.append(c)
+        he, hc = np.vstack(he), np.vstack(hc)
+        key = lambda r: np.lexsort((r[:, 0], r[:, 1]))
+        assert len(ge) > 6 and np.array_equal(ge[key(ge)], he[key(he)])
+        hc = hc[np.lexsort(tuple(hc[:, f] for f in (4, 3, 2, 1, 0)))]
+        assert len(gc) >= 6 and np.array_equal(gc, hc)
+    finally:
+        genga.genga_free(h)
+        for hh, _ in halves:
+            genga.genga_free(hh)
+
+
 def test_batch_graph_launch_size_does_not_change_results():
     b = ics.batch(8, n_sys=50)
     n = b["offsets"][-1]
