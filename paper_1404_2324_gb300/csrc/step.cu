@@ -246,24 +246,27 @@ struct GroupShared {
 };
 
 // The grouping by one CTA of GROUP_THREADS threads. The edge list is read past L1 (the fused
-// encounter kernel's other CTAs wrote it in the same launch).
-__device__ void group_body(const Sim &S, int gbig, GroupShared &sm) {
+// encounter kernel's other CTAs wrote it in the same launch), or from the shared-memory copy
+// (ei[e], ej[e]) when the caller made one.
+__device__ void group_body(const Sim &S, int gbig, GroupShared &sm, const int *ei = nullptr, const int *ej = nullptr) {
   int *link = sm.link, *key = sm.key, *gcnt = sm.gcnt, *wtot = sm.wtot;
   unsigned char *part = sm.part;
   int &s_changed = sm.s_changed, &s_base = sm.s_base, &s_ng = sm.s_ng;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int np = S.npad;
   const int ne = __ldcg(S.nedges), nf = __ldcg(S.nfail);
+  auto eu = [&](int e) { return ei ? ei[e] : __ldcg(S.edges + 2 * e); };
+  auto ev = [&](int e) { return ej ? ej[e] : __ldcg(S.edges + 2 * e + 1); };
   for (int i = tid; i < np; i += GROUP_THREADS) { link[i] = i; part[i] = 0; }
   __syncthreads();
-  for (int e = tid; e < ne; e += GROUP_THREADS) { part[__ldcg(S.edges + 2 * e)] = 1; part[__ldcg(S.edges + 2 * e + 1)] = 1; }
+  for (int e = tid; e < ne; e += GROUP_THREADS) { part[eu(e)] = 1; part[ev(e)] = 1; }
   for (int f = tid; f < nf; f += GROUP_THREADS) part[__ldcg(S.fail + f)] = 1;
   int round = 0;
   for (; round < GROUP_MAX_ROUNDS; ++round) {
     if (tid == 0) s_changed = 0;
     __syncthreads();
     for (int e = tid; e < ne; e += GROUP_THREADS) {
-      const int ru = find_root(link, __ldcg(S.edges + 2 * e)), rv = find_root(link, __ldcg(S.edges + 2 * e + 1));
+      const int ru = find_root(link, eu(e)), rv = find_root(link, ev(e));
       if (ru != rv) {
         atomicMin(&link[ru > rv ? ru : rv], ru < rv ? ru : rv);
         s_changed = 1;
@@ -342,7 +345,16 @@ __global__ void __launch_bounds__(GROUP_THREADS) k_encounter_group(Sim S, double
   if (!s_last) return;  // uniform
   __threadfence();
   if (threadIdx.x == 0) S.flags[1] = 0;  // the counter of the next launch
-  group_body(S, gbig, sm);
+  // the edges into shared memory once (the encounter's pair buffers are free now): the union
+  // rounds then read them there instead of from L2 every round
+  const int ne = __ldcg(S.nedges);
+  if (ne <= EG_CAP) {
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) { s_i[e] = __ldcg(S.edges + 2 * e); s_j[e] = __ldcg(S.edges + 2 * e + 1); }
+    __syncthreads();
+    group_body(S, gbig, sm, s_i, s_j);
+  } else {
+    group_body(S, gbig, sm);
+  }
 }
 
 // ---------------------------------------------------------------------------------------------
