@@ -239,7 +239,7 @@ __device__ __forceinline__ int find_root(const int *link, int r) {
 }
 
 struct GroupShared {
-  int link[NMAX], key[NMAX], gcnt[NMAX];
+  int link[NMAX], key[NMAX], gcnt[NMAX], gst[NMAX + 1];
   unsigned char part[NMAX];
   int wtot[GROUP_THREADS / 32];
   int s_changed, s_base, s_ng;
@@ -249,7 +249,7 @@ struct GroupShared {
 // encounter kernel's other CTAs wrote it in the same launch), or from the shared-memory copy
 // (ei[e], ej[e]) when the caller made one.
 __device__ void group_body(const Sim &S, int gbig, GroupShared &sm, const int *ei = nullptr, const int *ej = nullptr) {
-  int *link = sm.link, *key = sm.key, *gcnt = sm.gcnt, *wtot = sm.wtot;
+  int *link = sm.link, *key = sm.key, *gcnt = sm.gcnt, *gst = sm.gst, *wtot = sm.wtot;
   unsigned char *part = sm.part;
   int &s_changed = sm.s_changed, &s_base = sm.s_base, &s_ng = sm.s_ng;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -279,18 +279,28 @@ __device__ void group_body(const Sim &S, int gbig, GroupShared &sm, const int *e
   }
   if (round >= GROUP_MAX_ROUNDS && tid == 0) atomicOr(S.status, ST_UNION_ROUNDS);
   // Groups by root (the smallest member: links only ever point to smaller indices), members
-  // ascending. The participants in ascending order; members counted per root; an ordered scan
-  // gives each root's first position; one warp walks the participants in order and puts each at
-  // its root's next free position (lanes with the same root take consecutive ones).
+  // ascending. The participants in ascending order; members counted per root; the roots among
+  // the participants, ascending, are the groups in order: each group's size goes to gst and an
+  // ordered scan makes it the group's first position; one warp then walks the participants in
+  // order and puts each at its root's next free position (lanes with the same root take
+  // consecutive ones). Only participants are touched after the union rounds.
   const int cnt = block_compact(np, [&](int i) { return part[i] != 0; }, [&](int i, int pos) { key[pos] = i; },
                                 wtot, &s_base);
-  for (int i = tid; i < np; i += GROUP_THREADS) gcnt[i] = 0;
+  for (int k = tid; k < cnt; k += GROUP_THREADS) gcnt[key[k]] = 0;
   __syncthreads();
   for (int k = tid; k < cnt; k += GROUP_THREADS) atomicAdd(&gcnt[link[key[k]]], 1);
   __syncthreads();
-  block_scan_excl(gcnt, np, wtot, &s_base);  // gcnt[r]: the first position of root r's group
-  s_ng = block_compact(np, [&](int r) { return part[r] != 0 && link[r] == r; },
-                       [&](int r, int g) { S.gstart[g] = gcnt[r]; }, wtot, &s_base);
+  s_ng = block_compact(cnt, [&](int k) { const int i = key[k]; return link[i] == i; },
+                       [&](int k, int g) { const int r = key[k]; gst[g] = gcnt[r]; gcnt[r] = g; }, wtot, &s_base);
+  __syncthreads();  // every thread has read the count in s_base before the scan resets it
+  block_scan_excl(gst, s_ng, wtot, &s_base);  // gst[g]: the first position of group g
+  for (int k = tid; k < cnt; k += GROUP_THREADS) {
+    const int i = key[k];
+    if (link[i] == i) gcnt[i] = gst[gcnt[i]];  // root i: its group's first position
+  }
+  for (int g = tid; g < s_ng; g += GROUP_THREADS) S.gstart[g] = gst[g];
+  if (tid == 0) gst[s_ng] = cnt;
+  __syncthreads();
   if (wid == 0) {
     for (int c0 = 0; c0 < cnt; c0 += 32) {
       const int k = c0 + lane;
@@ -316,7 +326,7 @@ __device__ void group_body(const Sim &S, int gbig, GroupShared &sm, const int *e
   }
   if (S.big) {  // the groups of gbig or more members, in group order
     __syncthreads();
-    const int nb = block_compact(s_ng, [&](int g) { return S.gstart[g + 1] - S.gstart[g] >= gbig; },
+    const int nb = block_compact(s_ng, [&](int g) { return gst[g + 1] - gst[g] >= gbig; },
                                  [&](int g, int pos) { S.big[pos] = g; }, wtot, &s_base);
     if (tid == 0) *S.nbig = nb;
   }
