@@ -167,10 +167,11 @@ def test_every_kick_shape_matches_oracle(split):
 
 
 def test_large_batch_in_parts_equals_its_halves_and_the_oracle():
-    """A batch of 2048 systems runs in two parts of 1024 systems, stepped side by side: every result
-    equals that of two separate batches made of the same halves (the same kernels and kick shape,
-    bit for bit), and the first step matches the oracle per system; the whole-batch calls (state,
-    energies, encounter pairs, counters, spins) put the parts back in the caller's order."""
+    """A batch of 2048 systems runs in four parts of 512 systems, stepped side by side: every result
+    equals that of two separate batches made of its halves (each in two parts; a system's results do
+    not depend on the systems beside it, given the kick shape), bit for bit, and the first step
+    matches the oracle per system; the whole-batch calls (state, energies, encounter pairs, counters,
+    spins) put the parts back in the caller's order."""
     b = ics.batch(11, n_sys=2048, n_lo=2, n_hi=10)  # 1 to 9 orbiting bodies per system
     off, n = b["offsets"], b["offsets"][-1]
     h = genga.genga_init_batch(off, b["m0"], b["m"], b["R"], b["x"], b["v"], b["G"], b["dt"], 2, 4)
@@ -222,7 +223,7 @@ def test_large_batch_in_parts_equals_its_halves_and_the_oracle():
 
 
 def test_batch_in_parts_reports_like_its_halves():
-    """Ejection and collision records of a batch in two parts: in each half of 1024 systems an
+    """Ejection and collision records of a batch in parts: in each half of 1024 systems an
     escaping system and a disk of enlarged bodies among small systems, RcutSun removing the
     innermost bodies. The records (the caller's body indices) are those of the two halves run as
     separate batches, offset by the half's first body."""
