@@ -166,6 +166,9 @@ struct genga_ctx {
   // a further branch: groups above BS_GMAX members (main mode; the larger batched groups too)
   cudaStream_t side2 = nullptr;
   cudaEvent_t ev_join2 = nullptr;
+  // test-particle mode: the planets' path table on a branch of its own
+  cudaStream_t side3 = nullptr;
+  cudaEvent_t ev_tab = nullptr, ev_tabj = nullptr;
   int small_grid = 0;
   int wide_grid = 8;  // CTAs of the wide BS kernel (batched groups of BS_GMAX + 1 .. BS_GWIDE members: rare)
   int grid_blocks = 1;  // CTAs of the grid-wide BS kernel (main mode: groups above BS_GMAX members)
@@ -317,7 +320,12 @@ void enqueue_step(genga_ctx *c, cudaStream_t st) {
     if (tp && j == 0) launch_tp_open_drift(S, T, P, std::fabs(dt), 0.5 * c->w[0] * dt, tau, 0.5 * tau * inv_m0, st);
     else if (tp) launch_tp_drift(S, T, P, tau, 0.5 * tau * inv_m0, hcm2, st);
     launch_drift(S, P, tau, 0.5 * tau * inv_m0, hcm2, j, st);             // clears the reuse flag
-    if (tp) launch_planet_table(S, T, P, tau, st);
+    if (tp) {  // the planets' paths for the particles, on a branch beside the planets' encounters and BS
+      cudaEventRecord(c->ev_tab, st);
+      cudaStreamWaitEvent(c->side3, c->ev_tab, 0);
+      launch_planet_table(S, T, P, tau, c->side3);
+      cudaEventRecord(c->ev_tabj, c->side3);
+    }
     // the paper's literal higher-order variant: the step-start candidates serve every substep, and
     // the closing kicks between substeps weigh every pair without prechecking
     const bool inner = c->prm.precheck_substeps == 0 && j + 1 < c->nsub;
@@ -341,6 +349,7 @@ void enqueue_step(genga_ctx *c, cudaStream_t st) {
     if (tp) {  // the particles' encounter test beside the massive closing kick
       cudaEventRecord(c->ev_fork, st);
       cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+      cudaStreamWaitEvent(c->side, c->ev_tabj, 0);  // and the planets' path table
       launch_tp_encounter(S, T, tau, c->tp_grid, c->side);
       cudaEventRecord(c->ev_join, c->side);
     }
@@ -552,6 +561,12 @@ int genga_init_tp(genga_ctx **out, int n, const double *masses, const double *ra
   launch_tp_from_helio(T, n, c->sm, c->sv, c->stx, c->stv, Rt ? sR : nullptr, 0, st);
   c->tpmode = true;
   c->tp_grid = 4 * num_sms();
+  if (cudaStreamCreateWithFlags(&c->side3, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_tab, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_tabj, cudaEventDisableTiming) != cudaSuccess) {
+    genga_free(c);
+    return GENGA_ECUDA;
+  }
   if (tp_init_constants() != 0) { genga_free(c); return GENGA_ECUDA; }
   rc = first_kick(c);
   if (rc == GENGA_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = GENGA_ECUDA;
@@ -1420,6 +1435,9 @@ void genga_free(genga_ctx *c) {
   if (c->ev_join2) cudaEventDestroy(c->ev_join2);
   if (c->side) cudaStreamDestroy(c->side);
   if (c->side2) cudaStreamDestroy(c->side2);
+  if (c->ev_tab) cudaEventDestroy(c->ev_tab);
+  if (c->ev_tabj) cudaEventDestroy(c->ev_tabj);
+  if (c->side3) cudaStreamDestroy(c->side3);
   c->mem.release();
   if (c->own) cudaStreamDestroy(c->own);
   delete c;
