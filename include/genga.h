@@ -247,7 +247,10 @@ int genga_batch_set_kick(genga_ctx *ctx, int split, int block);
  * (every phase over all systems, then the next phase) or one persistent launch in which each CTA
  * takes a system at a time and advances it through all the steps of the launch (*persistent = 1;
  * *ctas CTAs, one or two per SM). ms_graph, ms_persistent: the measured time per step of each
- * (any pointer may be NULL). The persistent launch is not used while Rcut, RcutSun or Nmin is set. */
+ * (any pointer may be NULL). The graph's trial issues its kernels one by one, which the step graph
+ * does not, so the persistent launch is chosen only when its time is below 0.85 of the graph's. A
+ * batch in parts runs the step graph in every part (the values reported are the first part's). The
+ * persistent launch is not used while Rcut, RcutSun or Nmin is set. */
 int genga_batch_schedule(genga_ctx *ctx, int *persistent, int *ctas, float *ms_graph, float *ms_persistent);
 
 /* Overrides that choice: 1 persistent launch, 0 step graph (EINVAL if the persistent launch is not
