@@ -85,7 +85,7 @@ def _check(g, os_, sens, tol, mult):
     return e, live
 
 
-@pytest.mark.parametrize("order", [2, 4])
+@pytest.mark.parametrize("order", [2, 4, 6])
 def test_tp_mode_matches_oracle(order):
     d = _inputs()
     n_tp = len(d["x_tp"])
