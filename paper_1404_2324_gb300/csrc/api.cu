@@ -886,6 +886,10 @@ int genga_init_batch(genga_ctx **out, int n_sys, const int *offsets, const doubl
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   for (genga_ctx *p : c->parts) {
+    // the parts' BS kernels run side by side: each part a share of the grids one batch would use
+    p->pair_grid = std::max(8, 2 * p->pair_grid / K);
+    p->small_grid = std::max(16, 2 * p->small_grid / K);
+    p->bs_grid = std::max(4, 2 * p->bs_grid / K);
     if (rc == GENGA_OK) rc = genga_batch_set_schedule(p, 0);
     if (rc == GENGA_OK) rc = genga_batch_set_kick(p, bsplit, bblock);
     // the counters as a batch of one part leaves them after init; then the first kick in this shape
