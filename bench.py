@@ -271,7 +271,7 @@ def run_batched(args):
             "speedup_vs_one_per_launch": value / one_value, "status": code, "counters": cnt,
             "config": f"batch recipe seed {BATCH_SEED}: N_s ~ U{{4..64}} incl. star, m log-U[1e-7,1e-4], "
                       f"a U[0.1,5], e~Rayleigh(0.02), i~Rayleigh(0.01), 2nd order, dt 6 d; L2 flushed per launch; "
-                      f"the library runs batches of 1024+ systems in parts of ~512 systems side by side"}
+                      f"the library runs batches of 1024+ systems in parts of ~256 systems side by side"}
 
 
 def batched_cpu_baseline(nsys=512, steps=100):

@@ -222,8 +222,8 @@ int genga_tp_status(genga_ctx *ctx, long long *detail);
  *   then single steps for the remainder).
  * Each system follows exactly the single-system step of genga_init (same parameters for all
  * systems except m0, Sect. 3.4). The kick's tile shape is autotuned here on the first kick
- * (genga_batch_info reports it). From 1024 systems on, the batch runs in parts of about 512
- * consecutive systems (at most 16), each with its own step graph on its own stream, forked from the
+ * (genga_batch_info reports it). From 1024 systems on, the batch runs in parts of about 256
+ * consecutive systems (at most 32), each with its own step graph on its own stream, forked from the
  * context's stream at every call and joined back; the parts all run the step graph and one kick
  * shape, timed with all parts at once. Every call of this section behaves the same either way
  * (arrays in the caller's order; counters summed over the parts, the step count once).

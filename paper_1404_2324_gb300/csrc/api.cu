@@ -817,17 +817,18 @@ static int parts_join(genga_ctx *c) {
   return GENGA_OK;
 }
 
-// Batches of 1024 systems and more run in parts of about 512 systems (at most 16), consecutive in
+// Batches of 1024 systems and more run in parts of about 256 systems (at most 32), consecutive in
 // the caller's order: measured on 8192 systems, 3.68 M system-steps/s in one step graph, 4.18 M in
 // two parts, 4.35 M in three, 4.44 M in eight (each part with the kick shape it chose alone); with
-// one Newton's-third-law kick shape for all, 4.83 M in 8 parts, 5.07 M in 16, 5.04 M in 32. Every
-// part runs the step graph, all with one kick shape, timed over all parts at once.
+// one Newton's-third-law kick shape for all, 4.83 M in 8 parts and 5.07 M in 16; with the BS grids
+// shared out as below, 5.15 M in 16, 5.20 M in 24, 5.21-5.23 M in 32. Every part runs the step
+// graph, all with one kick shape, timed over all parts at once.
 int genga_init_batch(genga_ctx **out, int n_sys, const int *offsets, const double *m0, const double *masses,
                      const double *radii, const double *x, const double *v, double G, double dt, int order,
                      int steps_per_launch) {
   if (!out) return GENGA_EINVAL;
   *out = nullptr;
-  const int K = n_sys >= 1024 ? std::min(16, n_sys / 512) : 1;
+  const int K = n_sys >= 1024 ? std::min(32, n_sys / 256) : 1;
   if (K <= 1 || !offsets || !m0 || !masses || !radii || !x || !v)
     return init_batch_one(out, n_sys, offsets, m0, masses, radii, x, v, G, dt, order, steps_per_launch);
   if (offsets[0] != 0) return GENGA_EINVAL;

@@ -196,8 +196,8 @@ def test_every_kick_shape_matches_oracle(split, order):
 
 
 def test_large_batch_in_parts_equals_its_halves_and_the_oracle():
-    """A batch of 2048 systems runs in four parts of 512 systems, stepped side by side: every result
-    equals that of two separate batches made of its halves (each in two parts; a system's results do
+    """A batch of 2048 systems runs in eight parts of 256 systems, stepped side by side: every result
+    equals that of two separate batches made of its halves (each in four parts; a system's results do
     not depend on the systems beside it, given the kick shape), bit for bit, and the first step
     matches the oracle per system; the whole-batch calls (state, energies, encounter pairs, counters,
     spins) put the parts back in the caller's order."""
